@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 mapping iteration (VIGS-SLAM Sec. 3.3, Eq. 6).
+
+One step = one full mapping iteration of the plain single-view workload:
+640x480 view (fx = fy = 525) inside a synthetic room of 200k Gaussians;
+project -> bin/sort -> composite colour+depth -> L1 colour/depth + isotropic
+loss -> backward to every parameter and the pose -> Adam.  The iteration is
+replayed from a CUDA graph; inputs (map, target image and depth) are resident
+in HBM when the timed region starts, and L2 is flushed (a 256 MiB write)
+between timed iterations, outside the per-step events.
+
+Metric: mapping iterations/s (whole job; N GPUs run independent replicas,
+weak scaling).  Also reported: Gpix-splats/s (sum over pixels of the splats a
+pixel visits, divided by the forward-raster time), per-stage times, the
+roofline of the dominant kernel, the end-to-end rate through the C ABI with
+host buffers, and the FP64 oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mapping iters/sec (fwd+bwd, 1 GB300) and Gpix-splats/s vs plain form at oracle tolerance"
+WORKLOAD = "plain single view, SLAM scale: 640x480, 200k Gaussians on a synthetic room (6 planes + 20 boxes)"
+FWD_OPS_PER_PAIR = 20    # FP32 ops per visited (pixel, splat) pair in the forward definition
+BWD_OPS_PER_PAIR = 45    # FP32 ops per blended pair in the backward definition (+ reductions)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_problem(device):
+    import torch
+    from paper_2512_02293_gb300 import gs as G, synth
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, cam = synth.cfg2_problem()
+    params = G.RenderParams(tile=16)
+    mp = MapParams()
+    P = cam.n_pixels
+    # target = render of the perturbed map (input preparation, not timed)
+    dummy_c = torch.zeros(3 * P, device=device); dummy_d = torch.zeros(P, device=device)
+    tstep = MappingStep(G.Gaussians.from_numpy(gt, device), [cam], dummy_c, dummy_d, params, mp)
+    tstep.render()
+    torch.cuda.synchronize()
+    tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
+    del tstep
+    step = MappingStep(G.Gaussians.from_numpy(g, device), [cam], tc, td, params, mp)
+    return g, gt, cam, params, mp, step, tc, td
+
+
+def launches_per_step(step) -> int:
+    from paper_2512_02293_gb300 import gs as G
+    tiles = step.total_tiles
+    tb = 0
+    while (1 << tb) < tiles:
+        tb += 1
+    passes = math.ceil((31 + tb) / 8)
+    # project 1; bin/sort: reduce + block scan + duplicate + 3 per pass + ranges;
+    # render 1; loss 2; backward raster 1 + projection backward 1; adam 1
+    return 1 + (3 + 3 * passes + 1) + 1 + 2 + 2 + 1
+
+
+def stage_times(step, K, flush):
+    """Per-call device times (ms) of an eager iteration, events on the launching stream."""
+    import torch
+    from paper_2512_02293_gb300 import gs as G
+    names = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
+             "gs_adam_step"]
+    acc = {k: [] for k in names}
+    grad2d = step.ws  # the composite backward uses the workspace the same way
+    s = torch.cuda.current_stream()
+    for _ in range(K):
+        flush()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(s)
+        G.gs_project(step.g, step.cams, step.params, step.proj); ev[1].record(s)
+        G.gs_bin_sort(step.proj, step.n, step.cams, step.params, step.bins, step.ws); ev[2].record(s)
+        G.gs_render_fwd(step.proj, step.bins, step.cams, step.params, step.img); ev[3].record(s)
+        G.gs_loss(step.img, step.target_color, step.target_depth, step.cams, step.mp.lambda_c, step.mp.lambda_d,
+                  step.dL_dcolor, step.dL_ddepth, step.loss_terms, step.ws); ev[4].record(s)
+        G.gs_render_bwd_raster(step.proj, step.bins, step.img, step.dL_dcolor, step.dL_ddepth, step.cams, step.params,
+                               step.n, grad2d); ev[5].record(s)
+        G.gs_project_bwd(step.g, step.cams, step.params, grad2d, step.mp.lambda_iso, step.grads, step.iso); ev[6].record(s)
+        step.optimizer_step(); ev[7].record(s)
+        torch.cuda.synchronize()
+        for k, nm in enumerate(names):
+            acc[nm].append(ev[k].elapsed_time(ev[k + 1]))
+    return {k: statistics.median(v) for k, v in acc.items()}
+
+
+def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: full mapping
+    iterations of the same workload until ~budget_s of CPU work."""
+    import oracle
+    prm = dict(tile=params.tile, near=params.near_plane, alpha_min=params.alpha_min, alpha_max=params.alpha_max,
+               T_cut=params.T_cut, dilation=params.dilation, radius_sigma=params.radius_sigma, bg=tuple(params.bg))
+    timg = oracle.render_fwd(oracle.project(gt, cam, prm), cam, prm)
+    targets = [(timg["color"], timg["depth"])]
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.mapping_loss_and_grads(g, [cam], targets, prm, (mp.lambda_c, mp.lambda_d, mp.lambda_iso))
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 3:
+            break
+    t = statistics.median(times)
+    return {"value": 1.0 / t, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full FP64 mapping iteration(s) of the same 640x480 / 200k-Gaussian workload "
+                      f"(forward, Eq. 6 loss and gradients; the FP64 Adam update is not included), median {t:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample of the workload (a 160x128 window of the 640x480 view, all 200k
+    Gaussians projected), rate scaled to full iterations by the pixel fraction."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2512_02293_gb300 import synth
+    g, gt, cam = synth.cfg2_problem()
+    x0, y0, w, h = 240, 176, 160, 128      # tile-aligned window
+    crop = synth.Camera(cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.R_wc, cam.t_wc)
+    prm = {}
+    timg = oracle.render_fwd(oracle.project(gt, crop, prm), crop, prm)
+    targets = [(timg["color"], timg["depth"])]
+    frac = (w * h) / float(cam.n_pixels)
+    for _ in range(args.warmup):
+        oracle.mapping_loss_and_grads(g, [crop], targets, prm, (0.9, 0.1, 10.0))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.mapping_loss_and_grads(g, [crop], targets, prm, (0.9, 0.1, 10.0))
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    per_full_iter = (total / args.steps) / frac
+    value = 1.0 / per_full_iter
+    sample = (f"each step: one FP64 oracle mapping iteration over a {w}x{h} window ({frac:.4f} of the 640x480 "
+              "pixels, all 200k Gaussians projected); rate scaled to full iterations by the pixel fraction")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    from paper_2512_02293_gb300 import build as B
+    from paper_2512_02293_gb300 import gs as G
+    B.build()
+    G.load_library()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    g, gt, cam, params, mp, step, tc, td = build_problem(device)
+    # first eager pass: size the key buffers, then check the status word
+    step.step()
+    if step.ensure_capacity():
+        step.step()
+        assert not step.ensure_capacity()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
+    flush = lambda: flush_buf.fill_(1.0)
+
+    # per-stage times (eager) and the pair count for Gpix-splats/s
+    st = stage_times(step, 10, flush)
+    pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
+
+    step.capture(warmup=1)
+    for _ in range(args.warmup):
+        step.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush()
+            starts[k].record(s)
+            step.step()
+            ends[k].record(s)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(times)
+    status = step.check()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed region")
+    if dist is not None:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: H2D of the target image and
+    # depth from pinned memory each step, D2H of the loss
+    from paper_2512_02293_gb300.mapping import MappingStep
+    e2e_step = MappingStep(step.g, step.cams, torch.empty_like(tc), torch.empty_like(td), params, mp,
+                           key_capacity=step.bins.capacity)
+    h_tc = tc.cpu().pin_memory(); h_td = td.cpu().pin_memory()
+    h_loss = torch.empty(e2e_step.loss_terms.shape, dtype=torch.float32).pin_memory()
+    h_iso = torch.empty(1, dtype=torch.float32).pin_memory()
+    for _ in range(args.warmup):
+        e2e_step.target_color.copy_(h_tc, non_blocking=True); e2e_step.target_depth.copy_(h_td, non_blocking=True)
+        e2e_step.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step.target_color.copy_(h_tc, non_blocking=True)
+        e2e_step.target_depth.copy_(h_td, non_blocking=True)
+        e2e_step.step()
+        h_loss.copy_(e2e_step.loss_terms, non_blocking=True)
+        h_iso.copy_(e2e_step.iso, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": "iters/s",
+           "h2d_bytes_per_step": int(h_tc.numel() * 4 + h_td.numel() * 4),
+           "d2h_bytes_per_step": int(h_loss.numel() * 4 + h_iso.numel() * 4),
+           "note": "eager C-ABI calls (no graph), wall clock, per-step stream sync for the loss read-back"}
+
+    peaks, peak_kind = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # FP32 lane-ops/s (FMA = 1 op), in T ops/s
+    fwd_ms = st["gs_render_fwd"]
+    bwd_ms = st["gs_render_bwd_raster"]
+    dominant = max(st, key=st.get)
+    if dominant == "gs_render_bwd_raster":
+        ach = pairs * BWD_OPS_PER_PAIR / (bwd_ms * 1e-3) / 1e12
+        kern, ops = "k_render_bwd<16>", BWD_OPS_PER_PAIR
+    else:
+        ach = pairs * FWD_OPS_PER_PAIR / (fwd_ms * 1e-3) / 1e12
+        kern, ops = "k_render_fwd<16>", FWD_OPS_PER_PAIR
+    roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
+                "frac": ach / alu_peak, "traffic": None,
+                "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
+                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480", "tile": 16,
+                       "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
+                       "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gpix_splats_per_s": pairs / (fwd_ms * 1e-3) / 1e9,
+            "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
+            "stages_ms": st, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, gt, cam, params, mp)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

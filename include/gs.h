@@ -1,0 +1,264 @@
+/*
+ * gs.h -- C ABI of libgs, the GB300 (sm_103a) differentiable Gaussian-splatting
+ * mapping step of VIGS-SLAM (arXiv 2512.02293, Sec. 3.3 "Gaussian Splatting
+ * Mapping", Eq. 6).
+ *
+ * One mapping iteration is
+ *     gs_project -> gs_bin_sort -> gs_render_fwd -> gs_loss -> gs_render_bwd -> gs_adam_step
+ * over one or more keyframe views ("views").
+ *
+ * Conventions that hold for every call
+ *  - The caller owns all memory.  libgs never allocates device or host memory;
+ *    scratch space is passed in as a workspace of gs_workspace_size() bytes.
+ *  - Pointers inside the structs below are DEVICE pointers to contiguous,
+ *    row-major arrays unless stated otherwise; `gs_camera` arrays, parameter
+ *    structs and the structs themselves live in HOST memory and are read
+ *    during the call only.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream), performs no host synchronisation and no
+ *    allocation, and may be captured into a CUDA graph.  Exceptions:
+ *    gs_read_device_status synchronises `stream`.
+ *  - Errors detectable on the host (NULL pointers, negative sizes, unsupported
+ *    tile sizes, too many views, a too-small workspace) return a non-zero
+ *    gs_status before anything is launched.  Errors found on the device
+ *    (key-capacity overflow) are recorded in the caller's device status word
+ *    (gs_bins.status) and read back with gs_read_device_status outside any
+ *    graph.  A launch failure returns GS_ERR_CUDA.
+ *  - Entries: a Gaussian i seen from view v is entry e = v * n + i, where n is
+ *    the number of Gaussians.  Per-entry arrays have n_views * n rows.
+ *  - Pixels: view v's pixels follow those of views 0..v-1; colour images are
+ *    planar per view ([3][H_v][W_v] starting at 3 * pix_base(v)), single-channel
+ *    images start at pix_base(v) = sum_{u<v} W_u H_u.  Pixel (u, v) is sampled
+ *    at (u + 0.5, v + 0.5).
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_ABI_VERSION 1
+#define GS_MAX_VIEWS 32
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter (host check) */
+    GS_ERR_CAPACITY = 2,      /* more (tile, Gaussian) keys than gs_bins.key_capacity */
+    GS_ERR_CUDA = 3,          /* a CUDA launch or runtime call failed */
+    GS_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    GS_ERR_NUMERIC = 5,       /* non-finite value where a finite one is required */
+    GS_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+} gs_status;
+
+/* Pinhole keyframe camera.  The pose is camera-to-world: x_world = R_wc x_cam
+ * + t_wc, the convention of the keyframe poses (R_k, t_k) in Sec. 3.3 "Loop
+ * Closure Gaussian Update".  Camera axes: x right, y down, z forward. */
+typedef struct gs_camera {
+    float fx, fy, cx, cy;     /* focal lengths and principal point, pixels */
+    int32_t width, height;    /* image size, pixels (each >= 1) */
+    float R_wc[9];            /* rotation, row-major */
+    float t_wc[3];            /* camera centre in world coordinates */
+} gs_camera;
+
+/* Rendering parameters.  The paper fixes none of these (Sec. 3.3 defers the
+ * renderer to 3D Gaussian splatting); the values noted are the defaults the
+ * binding uses. */
+typedef struct gs_render_params {
+    int32_t tile;             /* tile edge in pixels: 8, 16 or 32 (16) */
+    float near_plane;         /* Gaussians with camera z <= near are culled (0.2) */
+    float alpha_min;          /* splats with alpha < alpha_min are skipped (1/255) */
+    float alpha_max;          /* alpha = min(alpha_max, o exp(power)) (0.99) */
+    float T_cut;              /* a pixel stops before blending a splat that would
+                                 take its transmittance below T_cut (1e-4) */
+    float dilation;           /* added to the diagonal of the 2D covariance, px^2 (0.3) */
+    float radius_sigma;       /* splat radius = ceil(radius_sigma sqrt(lambda_max)) (3) */
+    float bg[3];              /* background colour (0, 0, 0) */
+    int32_t sh_degree;        /* 0: direct RGB colour (Sec. 3.3); 3: degree-3 SH */
+    int32_t reserved;         /* must be 0 */
+} gs_render_params;
+
+/* The Gaussian map G (Sec. 3.3 "Preliminary"), structure of arrays, device. */
+typedef struct gs_gaussians {
+    const float* mean;            /* [n][3] world position mu */
+    const float* quat;            /* [n][4] rotation (w, x, y, z), normalised inside */
+    const float* log_scale;       /* [n][3] per-axis log standard deviation */
+    const float* opacity_logit;   /* [n] opacity o = sigmoid(logit) */
+    const float* color;           /* [n][3] RGB (sh_degree 0) or [n][16][3] SH coefficients */
+    int64_t n;                    /* number of Gaussians, 0 <= n < 2^31 / n_views */
+} gs_gaussians;
+
+/* Per-entry output of gs_project (device, caller-allocated, n_views * n rows). */
+typedef struct gs_projected {
+    float* xy;                /* [E][2] projected mean, pixels */
+    float* conic_o;           /* [E][4] inverse 2D covariance (A, B, C) and opacity */
+    float* rgbd;              /* [E][4] colour (r, g, b) and camera z of the mean */
+    int32_t* rect;            /* [E][4] covered tiles x0, y0, x1, y1 (x1, y1 exclusive) */
+    int32_t* radius;          /* [E] splat radius in pixels, 0 if culled */
+    uint32_t* tiles_touched;  /* [E] (x1 - x0) * (y1 - y0), 0 if culled */
+} gs_projected;
+
+/* Binned, depth-sorted splat lists (device, caller-allocated). */
+typedef struct gs_bins {
+    uint64_t* keys;           /* [key_capacity] (global tile << 32) | bits(float z) */
+    uint32_t* vals;           /* [key_capacity] entry index e */
+    int64_t key_capacity;     /* number of slots in keys / vals */
+    uint32_t* ranges;         /* [total_tiles][2] [start, end) of each tile's list */
+    uint32_t* num_keys;       /* [1] number of keys M the projection produced */
+    int32_t* status;          /* [1] device status word (gs_status), sticky */
+} gs_bins;
+
+/* Rendered images and the per-pixel checkpoint the backward pass uses. */
+typedef struct gs_image {
+    float* color;             /* [3 * P] planar per view (see Pixels above) */
+    float* depth;             /* [P] alpha-blended camera z of the means */
+    float* T_final;           /* [P] transmittance after the last blended splat */
+    uint32_t* n_contrib;      /* [P] splats visited up to the last blended one */
+} gs_image;
+
+/* Gradients; same layouts as gs_gaussians.  `pose` is [n_views][6], the
+ * gradient w.r.t. xi = (rho, phi) of the left perturbation T_cw <- Exp(xi) T_cw
+ * of each view's world-to-camera pose at xi = 0; it may be NULL. */
+typedef struct gs_grads {
+    float* mean;
+    float* quat;
+    float* log_scale;
+    float* opacity_logit;
+    float* color;
+    float* pose;
+} gs_grads;
+
+/* One Adam parameter group (device arrays of n floats). */
+typedef struct gs_adam_group {
+    float* param;
+    const float* grad;
+    float* m;
+    float* v;
+    int64_t n;
+    float lr;
+    int32_t reserved;         /* must be 0 */
+} gs_adam_group;
+
+/* ABI version of the loaded library (GS_ABI_VERSION). */
+int32_t gs_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* gs_status_string(int32_t status);
+
+/* Tiles of all views for the given tile size (host computation). */
+int64_t gs_total_tiles(const gs_camera* cams, int32_t n_views, int32_t tile);
+
+/* Pixels of all views (host computation). */
+int64_t gs_total_pixels(const gs_camera* cams, int32_t n_views);
+
+/* Bytes of workspace that gs_bin_sort, gs_loss and gs_render_bwd need for
+ * n Gaussians, these views and a key capacity; one buffer of this size may be
+ * shared by all three calls on the same stream. Returns 0 on invalid input. */
+size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams,
+                         const gs_render_params* params, int64_t key_capacity);
+
+/* EWA projection of every Gaussian into every view (Sec. 3.3 "Preliminary":
+ * mean mu, covariance Sigma = R(q) diag(exp(log_scale))^2 R(q)^T, opacity
+ * sigmoid(logit), colour).  p_c = R_wc^T (mu - t_wc); entries with
+ * z <= near_plane, a non-positive 2D determinant or no covered tile are culled
+ * (radius = tiles_touched = 0).  conic = inverse of J W Sigma W^T J^T +
+ * dilation I with J the perspective Jacobian at p_c.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers, n < 0, n_views outside
+ * [1, GS_MAX_VIEWS], bad params; GS_ERR_CUDA on launch failure. */
+int32_t gs_project(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                   const gs_render_params* params, gs_projected* out, void* stream);
+
+/* Tile binning and depth sort: one key (global tile << 32) | bits(float z) per
+ * (entry, covered tile), keys sorted ascending by a stable LSD radix sort of
+ * the entry-ordered list (ties in z keep entry order), and [start, end) of each
+ * tile in the sorted list.  Global tile of view v = tile_base(v) + ty * tiles_x(v)
+ * + tx with tile_base(v) = tiles of views 0..v-1.  Writes M to *bins->num_keys;
+ * if M > key_capacity it sets *bins->status = GS_ERR_CAPACITY and the outputs
+ * are undefined (grow the capacity to M and call again).
+ * `ws` must hold gs_workspace_size(...) bytes.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers or a small workspace. */
+int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, int32_t n_views,
+                    const gs_render_params* params, gs_bins* bins, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* Front-to-back alpha compositing of colour and depth per pixel (Sec. 3.3:
+ * pixel colour by alpha blending the visible Gaussians; colour I_hat and depth
+ * D_hat rendered per keyframe): over the pixel's tile list, power =
+ * -1/2 (A dx^2 + C dy^2) - B dx dy with (dx, dy) = sample - xy; splats with
+ * power > 0 or alpha = min(alpha_max, o exp(power)) < alpha_min are skipped; the
+ * pixel stops before a splat with T (1 - alpha) < T_cut; C += c alpha T,
+ * D += z alpha T, T *= 1 - alpha.  colour = C + T bg.  Also writes T_final and
+ * n_contrib (the checkpoint gs_render_bwd starts from).
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers. */
+int32_t gs_render_fwd(const gs_projected* proj, const gs_bins* bins, const gs_camera* cams,
+                      int32_t n_views, const gs_render_params* params, gs_image* img, void* stream);
+
+/* Colour and depth terms of Eq. 6 per view: L_c = mean over 3 W H of
+ * |I_hat - I|, L_d = mean over pixels with D > 0 of |D_hat - D| (sign(0) = 0).
+ * Writes dL/dI_hat = lambda_c sign / (3 W H) and dL/dD_hat = lambda_d sign / n_valid
+ * (0 where D <= 0) for every view, and loss_terms[2 v] = L_c, [2 v + 1] = L_d
+ * (unweighted; device, [n_views][2]).  Target layouts equal gs_image's.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers or a small workspace. */
+int32_t gs_loss(const gs_image* img, const float* target_color, const float* target_depth,
+                const gs_camera* cams, int32_t n_views, float lambda_c, float lambda_d,
+                float* dL_dcolor, float* dL_ddepth, float* loss_terms,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* Backward of gs_render_fwd and gs_project: gradient of the loss whose image
+ * gradients are dL_dcolor / dL_ddepth, summed over views, w.r.t. every Gaussian
+ * parameter and each view's pose tangent.  The compositing is walked back to
+ * front from the per-pixel checkpoint (T_final, n_contrib); no per-splat state
+ * is read from the forward pass.  Adds lambda_iso times the gradient of the
+ * isotropic regulariser L_iso = (1/n) sum_i sum_j |s_ij - mean_j s_ij|,
+ * s = exp(log_scale) (the MonoGS form Sec. 3.3 cites); if iso_loss is not NULL
+ * it receives L_iso (device scalar).  All gradient arrays are OVERWRITTEN.
+ * Gradient at the non-smooth points: 0 for culled entries, skipped splats and
+ * splats whose alpha is clamped at alpha_max; SH colours clamped at 0 pass no
+ * gradient.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers or a small workspace. */
+int32_t gs_render_bwd(const gs_gaussians* g, const gs_projected* proj, const gs_bins* bins,
+                      const gs_image* img, const float* dL_dcolor, const float* dL_ddepth,
+                      const gs_camera* cams, int32_t n_views, const gs_render_params* params,
+                      float lambda_iso, gs_grads* grads, float* iso_loss,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* The two halves of gs_render_bwd, callable on their own (gs_render_bwd is
+ * exactly gs_render_bwd_raster into its workspace followed by gs_project_bwd).
+ *
+ * gs_render_bwd_raster: zeroes grad2d and accumulates, per entry, the gradient
+ * of the loss w.r.t. the projected quantities: grad2d[e] = {d xy (2), d conic
+ * (A, B, C), d opacity, d z, 0, d rgb (3), 0} (12 floats, 16-byte aligned).
+ * gs_project_bwd: chain rule from grad2d (summed over views) to the Gaussian
+ * parameters and each view's pose tangent, plus lambda_iso dL_iso (see
+ * gs_render_bwd); OVERWRITES grads.
+ * Errors: GS_ERR_INVALID_ARG on NULL or misaligned pointers. */
+int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, const gs_image* img,
+                             const float* dL_dcolor, const float* dL_ddepth, const gs_camera* cams,
+                             int32_t n_views, const gs_render_params* params, int64_t n, float* grad2d,
+                             void* stream);
+int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                       const gs_render_params* params, const float* grad2d, float lambda_iso,
+                       gs_grads* grads, float* iso_loss, void* stream);
+
+/* Adam with bias correction over n_groups parameter groups in one launch (the
+ * optimiser step of each mapping iteration, Sec. 3.3 "Map Management"; the
+ * paper does not name the optimiser).  d_step is a device int32[2]: d_step[0]
+ * is the number of steps taken so far (the step applied is d_step[0] + 1 and
+ * d_step[0] is incremented by the call), d_step[1] is internal and must be 0
+ * before the first call.  m and v are updated in place.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers, n < 0, n_groups outside [1, 8]. */
+int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1, float beta2,
+                     float eps, int32_t* d_step, void* stream);
+
+/* Synchronises `stream`, copies the device status word to *host_status and
+ * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
+int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -172,15 +172,15 @@ static void sh_basis_grad(const double* d, const double* w, double* gd) {
  * (mx, my) in sample coordinates: the tiles whose span [k t, (k+1) t) meets
  * [m - r, m + r], clamped to the grid.  Returns the number of tiles. */
 static int tile_rect(double mx, double my, int r, int tile, int tx, int ty, int* rect) {
-    int x0 = (int)floor((mx - r) / tile), x1 = (int)floor((mx + r) / tile) + 1;
-    int y0 = (int)floor((my - r) / tile), y1 = (int)floor((my + r) / tile) + 1;
-    if (x0 < 0) x0 = 0;
-    if (y0 < 0) y0 = 0;
-    if (x1 > tx) x1 = tx;
-    if (y1 > ty) y1 = ty;
-    if (x1 <= x0 || y1 <= y0) { rect[0] = rect[1] = rect[2] = rect[3] = 0; return 0; }
-    rect[0] = x0; rect[1] = y0; rect[2] = x1; rect[3] = y1;
-    return (x1 - x0) * (y1 - y0);
+    double fx0 = floor((mx - r) / tile), fx1 = floor((mx + r) / tile) + 1;
+    double fy0 = floor((my - r) / tile), fy1 = floor((my + r) / tile) + 1;
+    if (fx0 < 0) fx0 = 0;
+    if (fy0 < 0) fy0 = 0;
+    if (fx1 > tx) fx1 = tx;
+    if (fy1 > ty) fy1 = ty;
+    if (!(fx1 > fx0) || !(fy1 > fy0)) { rect[0] = rect[1] = rect[2] = rect[3] = 0; return 0; }
+    rect[0] = (int)fx0; rect[1] = (int)fy0; rect[2] = (int)fx1; rect[3] = (int)fy1;
+    return (rect[2] - rect[0]) * (rect[3] - rect[1]);
 }
 
 int or_tile_rect(double mx, double my, int r, int tile, int tx, int ty, int* rect) {
@@ -269,7 +269,8 @@ static void project_one(const double* mu, const double* q, const double* ls, dou
     if (disc < 0.1) disc = 0.1;
     double lmax = mid + sqrt(disc);
     double rr = p->k_sigma * sqrt(lmax);
-    o->radius = (int)ceil(rr);
+    /* a radius only selects tiles; 2^24 px already covers any image */
+    o->radius = rr < 16777216.0 ? (int)ceil(rr) : 16777216;
     double fr = rr - floor(rr);
     o->margin = fr < 1 - fr ? fr : 1 - fr;   /* distance of the radius to an integer */
     if (o->radius <= 0) return;

@@ -1,0 +1,269 @@
+// api.cu -- the extern "C" entry points of libgs (declared in include/gs.h):
+// host-side argument checks, per-view constants, workspace carving, launches.
+#include <math.h>
+#include <string.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+size_t loss_workspace(int32_t n_views);
+
+bool make_views(const gs_camera* cams, int32_t n_views, int32_t tile, Views* out) {
+    memset(out, 0, sizeof(*out));
+    if (cams == nullptr || n_views < 1 || n_views > GS_MAX_VIEWS) return false;
+    if (tile != 8 && tile != 16 && tile != 32) return false;
+    int64_t tiles = 0, pixels = 0;
+    out->n = n_views;
+    for (int v = 0; v < n_views; v++) {
+        const gs_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > (1 << 16) || c.height > (1 << 16)) return false;
+        if (!(isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy)) || c.fx == 0.f || c.fy == 0.f)
+            return false;
+        ViewParams& p = out->v[v];
+        for (int k = 0; k < 9; k++)
+            if (!isfinite(c.R_wc[k])) return false;
+        for (int k = 0; k < 3; k++)
+            if (!isfinite(c.t_wc[k])) return false;
+        // R_cw = R_wc^T, t_cw = -R_wc^T t_wc (accumulated in double, rounded once)
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) p.Rcw[3 * r + q] = c.R_wc[3 * q + r];
+        for (int r = 0; r < 3; r++) {
+            double s = 0.0;
+            for (int q = 0; q < 3; q++) s -= (double)c.R_wc[3 * q + r] * (double)c.t_wc[q];
+            p.tcw[r] = (float)s;
+            p.centre[r] = c.t_wc[r];
+        }
+        p.fx = c.fx; p.fy = c.fy; p.cx = c.cx; p.cy = c.cy;
+        p.W = c.width; p.H = c.height;
+        p.tiles_x = (c.width + tile - 1) / tile;
+        p.tiles_y = (c.height + tile - 1) / tile;
+        p.tile_base = (int32_t)tiles;
+        p.pix_base = (int32_t)pixels;
+        tiles += (int64_t)p.tiles_x * p.tiles_y;
+        pixels += (int64_t)c.width * c.height;
+        if (tiles >= (1ll << 31) || pixels >= (1ll << 31)) return false;
+    }
+    out->total_tiles = (int32_t)tiles;
+    out->total_pixels = (int32_t)pixels;
+    return true;
+}
+
+RenderConsts make_consts(const gs_render_params* p) {
+    RenderConsts c;
+    c.tile = p->tile;
+    c.near_plane = p->near_plane;
+    c.alpha_min = p->alpha_min;
+    c.alpha_max = p->alpha_max;
+    c.T_cut = p->T_cut;
+    c.dilation = p->dilation;
+    c.radius_sigma = p->radius_sigma;
+    c.bg[0] = p->bg[0]; c.bg[1] = p->bg[1]; c.bg[2] = p->bg[2];
+    c.sh_degree = p->sh_degree;
+    return c;
+}
+
+static bool params_ok(const gs_render_params* p) {
+    if (p == nullptr) return false;
+    if (p->tile != 8 && p->tile != 16 && p->tile != 32) return false;
+    if (p->sh_degree != 0 && p->sh_degree != 3) return false;
+    if (p->reserved != 0) return false;
+    if (!(p->near_plane > 0.f) || !isfinite(p->near_plane)) return false;
+    if (!(p->alpha_min >= 0.f) || !(p->alpha_max <= 1.f) || !(p->alpha_min <= p->alpha_max)) return false;
+    if (!(p->T_cut >= 0.f) || !(p->T_cut < 1.f)) return false;
+    if (!(p->dilation >= 0.f) || !isfinite(p->dilation)) return false;
+    if (!(p->radius_sigma > 0.f) || !isfinite(p->radius_sigma)) return false;
+    for (int k = 0; k < 3; k++)
+        if (!isfinite(p->bg[k])) return false;
+    return true;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static bool gaussians_ok(const gs_gaussians* g, int32_t n_views) {
+    if (g == nullptr || g->n < 0) return false;
+    if (g->n * (int64_t)n_views >= (1ll << 31)) return false;
+    if (g->n == 0) return true;
+    if (!g->mean || !g->quat || !g->log_scale || !g->opacity_logit || !g->color) return false;
+    return aligned(g->quat, 16);
+}
+
+static bool projected_ok(const gs_projected* p) {
+    if (p == nullptr) return false;
+    if (!p->xy || !p->conic_o || !p->rgbd || !p->rect || !p->radius || !p->tiles_touched) return false;
+    return aligned(p->xy, 8) && aligned(p->conic_o, 16) && aligned(p->rgbd, 16) && aligned(p->rect, 16);
+}
+
+static bool image_ok(const gs_image* im) {
+    return im != nullptr && im->color && im->depth && im->T_final && im->n_contrib;
+}
+
+static bool bins_ok(const gs_bins* b) {
+    return b != nullptr && b->keys && b->vals && b->ranges && b->num_keys && b->status && b->key_capacity >= 0 &&
+           b->key_capacity < (1ll << 32) && aligned(b->ranges, 8);
+}
+
+static size_t render_bwd_workspace(int64_t n_entries) {
+    return align_up(sizeof(float) * kGradStride * (size_t)n_entries, 256);
+}
+
+static int32_t cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int32_t gs_abi_version(void) { return GS_ABI_VERSION; }
+
+const char* gs_status_string(int32_t s) {
+    switch (s) {
+        case GS_OK: return "GS_OK";
+        case GS_ERR_INVALID_ARG: return "GS_ERR_INVALID_ARG";
+        case GS_ERR_CAPACITY: return "GS_ERR_CAPACITY";
+        case GS_ERR_CUDA: return "GS_ERR_CUDA";
+        case GS_ERR_TIMEOUT: return "GS_ERR_TIMEOUT";
+        case GS_ERR_NUMERIC: return "GS_ERR_NUMERIC";
+        case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+        default: return "GS_ERR_UNKNOWN";
+    }
+}
+
+int64_t gs_total_tiles(const gs_camera* cams, int32_t n_views, int32_t tile) {
+    Views v;
+    if (!make_views(cams, n_views, tile, &v)) return -1;
+    return v.total_tiles;
+}
+
+int64_t gs_total_pixels(const gs_camera* cams, int32_t n_views) {
+    Views v;
+    if (!make_views(cams, n_views, 16, &v)) return -1;
+    return v.total_pixels;
+}
+
+size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_params* params,
+                         int64_t key_capacity) {
+    Views v;
+    if (n < 0 || key_capacity < 0 || !params_ok(params) || !make_views(cams, n_views, params->tile, &v)) return 0;
+    const int64_t E = n * n_views;
+    size_t a = bin_sort_workspace(E, key_capacity);
+    size_t b = loss_workspace(n_views);
+    size_t c = render_bwd_workspace(E);
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+int32_t gs_project(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, const gs_render_params* params,
+                   gs_projected* out, void* stream) {
+    if (!params_ok(params) || !gaussians_ok(g, n_views)) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    if (g->n > 0 && !projected_ok(out)) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_project(*g, views, make_consts(params), *out, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, int32_t n_views,
+                    const gs_render_params* params, gs_bins* bins, void* ws, size_t ws_bytes, void* stream) {
+    if (!params_ok(params) || n < 0 || !bins_ok(bins)) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    if (n * (int64_t)n_views >= (1ll << 31)) return GS_ERR_INVALID_ARG;
+    if (n > 0 && !projected_ok(proj)) return GS_ERR_INVALID_ARG;
+    const size_t need = bin_sort_workspace(n * n_views, bins->key_capacity);
+    if (ws == nullptr || ws_bytes < need || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
+    SortPlan plan = make_sort_plan(bins->key_capacity, views.total_tiles);
+    return cuda_status(launch_bin_sort(*proj, n, views, plan, *bins, ws, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_render_fwd(const gs_projected* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
+                      const gs_render_params* params, gs_image* img, void* stream) {
+    if (!params_ok(params) || !bins_ok(bins) || !projected_ok(proj) || !image_ok(img)) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_fwd(*proj, *bins, views, make_consts(params), *img,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_loss(const gs_image* img, const float* target_color, const float* target_depth, const gs_camera* cams,
+                int32_t n_views, float lambda_c, float lambda_d, float* dL_dcolor, float* dL_ddepth, float* loss_terms,
+                void* ws, size_t ws_bytes, void* stream) {
+    if (!image_ok(img) || !target_color || !target_depth || !dL_dcolor || !dL_ddepth || !loss_terms)
+        return GS_ERR_INVALID_ARG;
+    if (!isfinite(lambda_c) || !isfinite(lambda_d)) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, 16, &views)) return GS_ERR_INVALID_ARG;
+    if (ws == nullptr || ws_bytes < loss_workspace(n_views) || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_loss(*img, target_color, target_depth, views, lambda_c, lambda_d, dL_dcolor, dL_ddepth,
+                                   loss_terms, ws, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, const gs_image* img,
+                             const float* dL_dcolor, const float* dL_ddepth, const gs_camera* cams, int32_t n_views,
+                             const gs_render_params* params, int64_t n, float* grad2d, void* stream) {
+    if (!params_ok(params) || !bins_ok(bins) || !projected_ok(proj) || !image_ok(img)) return GS_ERR_INVALID_ARG;
+    if (!dL_dcolor || !dL_ddepth || !grad2d || !aligned(grad2d, 16) || n < 0) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    const int64_t E = n * n_views;
+    if (E >= (1ll << 31)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (E == 0) return GS_OK;
+    cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float) * kGradStride * (size_t)E, s);
+    if (e == cudaSuccess)
+        e = launch_render_bwd(*proj, *bins, *img, dL_dcolor, dL_ddepth, views, make_consts(params), grad2d, s);
+    return cuda_status(e);
+}
+
+int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, const gs_render_params* params,
+                       const float* grad2d, float lambda_iso, gs_grads* grads, float* iso_loss, void* stream) {
+    if (!params_ok(params) || !gaussians_ok(g, n_views) || grads == nullptr || !isfinite(lambda_iso))
+        return GS_ERR_INVALID_ARG;
+    if (g->n > 0 && (!grad2d || !aligned(grad2d, 16) || !grads->mean || !grads->quat || !grads->log_scale ||
+                     !grads->opacity_logit || !grads->color || !aligned(grads->quat, 16)))
+        return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (grads->pose) e = cudaMemsetAsync(grads->pose, 0, sizeof(float) * 6 * (size_t)n_views, s);
+    if (e == cudaSuccess && iso_loss) e = cudaMemsetAsync(iso_loss, 0, sizeof(float), s);
+    if (e == cudaSuccess && g->n > 0)
+        e = launch_project_bwd(*g, views, make_consts(params), grad2d, lambda_iso, *grads, iso_loss, s);
+    return cuda_status(e);
+}
+
+int32_t gs_render_bwd(const gs_gaussians* g, const gs_projected* proj, const gs_bins* bins, const gs_image* img,
+                      const float* dL_dcolor, const float* dL_ddepth, const gs_camera* cams, int32_t n_views,
+                      const gs_render_params* params, float lambda_iso, gs_grads* grads, float* iso_loss, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!gaussians_ok(g, n_views)) return GS_ERR_INVALID_ARG;
+    const int64_t E = g->n * n_views;
+    if (ws == nullptr || ws_bytes < render_bwd_workspace(E) || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
+    float* g2d = static_cast<float*>(ws);
+    int32_t st = gs_render_bwd_raster(proj, bins, img, dL_dcolor, dL_ddepth, cams, n_views, params, g->n, g2d, stream);
+    if (st != GS_OK) return st;
+    return gs_project_bwd(g, cams, n_views, params, g2d, lambda_iso, grads, iso_loss, stream);
+}
+
+int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1, float beta2, float eps,
+                     int32_t* d_step, void* stream) {
+    if (groups == nullptr || n_groups < 1 || n_groups > 8 || d_step == nullptr) return GS_ERR_INVALID_ARG;
+    if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f)) return GS_ERR_INVALID_ARG;
+    for (int k = 0; k < n_groups; k++) {
+        const gs_adam_group& G = groups[k];
+        if (G.n < 0 || G.reserved != 0 || !isfinite(G.lr)) return GS_ERR_INVALID_ARG;
+        if (G.n > 0 && (!G.param || !G.grad || !G.m || !G.v)) return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_adam(groups, n_groups, beta1, beta2, eps, d_step, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status) {
+    if (d_status == nullptr || host_status == nullptr) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(host_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // extern "C"

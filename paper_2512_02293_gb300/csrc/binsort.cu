@@ -1,0 +1,333 @@
+// binsort.cu -- tile binning and depth sort of the projected splats.
+//
+//   1. k_scan_reduce   : per-block sums of tiles_touched
+//   2. k_scan_blocks   : exclusive scan of the block sums (one CTA), M, overflow flag
+//   3. k_duplicate     : block-local scan + emission of one key per (entry, tile):
+//                        key = (global tile << 32) | bits(float z), value = entry
+//   4. LSD radix sort  : per 8-bit digit pass k_radix_hist -> k_radix_scan ->
+//                        k_radix_scatter (stable: per-warp ranks from match_any,
+//                        per-digit warp prefixes in shared memory)
+//   5. k_tile_ranges   : [start, end) of every tile in the sorted list
+//
+// The key's bit 31 (the sign of z > 0) is always 0, so the sort runs over the
+// 31 depth bits and the tile bits only.  Kernels never read M on the host: grids
+// are sized for the key capacity and blocks past M return at once, which keeps
+// the whole sequence free of host synchronisation (capturable in a CUDA graph).
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x == kThreads).
+template <int kThreads>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kThreads / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kThreads / 32) s_warp[lane] = wi - w;   // exclusive warp offsets
+        if (lane == kThreads / 32 - 1) s_warp[kThreads / 32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = s_warp[warp] + inc - x;
+    *total = s_warp[kThreads / 32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt, int64_t E,
+                                                             uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+        if (base + k < E) s += tt[base + k];
+    uint32_t total;
+    block_exclusive_scan<kScanThreads>(s, &total, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of nb block sums in place; M = total.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ block_sums, int nb,
+                                                      uint32_t* __restrict__ num_keys, int64_t capacity,
+                                                      int32_t* __restrict__ status) {
+    __shared__ uint32_t s_warp[1024 / 32 + 1];
+    const int chunk = (nb + 1023) / 1024;
+    const int lo = threadIdx.x * chunk;
+    uint32_t s = 0;
+    for (int k = 0; k < chunk; k++)
+        if (lo + k < nb) s += block_sums[lo + k];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<1024>(s, &total, s_warp);
+    for (int k = 0; k < chunk; k++) {
+        if (lo + k < nb) {
+            uint32_t v = block_sums[lo + k];
+            block_sums[lo + k] = run;
+            run += v;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *num_keys = total;
+        if ((int64_t)total > capacity) *status = GS_ERR_CAPACITY;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_duplicate(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
+                                                           const float4* __restrict__ rgbd, int64_t E, int64_t n,
+                                                           const uint32_t* __restrict__ block_offsets, Views views,
+                                                           int64_t capacity, uint64_t* __restrict__ keys,
+                                                           uint32_t* __restrict__ vals) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    uint32_t cnt[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        cnt[k] = base + k < E ? tt[base + k] : 0u;
+        s += cnt[k];
+    }
+    uint32_t total;
+    uint32_t off = block_offsets[blockIdx.x] + block_exclusive_scan<kScanThreads>(s, &total, s_warp);
+#pragma unroll 1
+    for (int k = 0; k < kScanItems; k++) {
+        if (cnt[k] == 0) continue;
+        const int64_t e = base + k;
+        const int v = (int)(e / n);
+        const int4 r = rect[e];
+        const uint32_t zbits = __float_as_uint(rgbd[e].w);
+        const int tb = views.v[v].tile_base, tx = views.v[v].tiles_x;
+        for (int y = r.y; y < r.w; y++) {
+            for (int x = r.x; x < r.z; x++) {
+                if ((int64_t)off < capacity) {
+                    const uint64_t g = (uint64_t)(tb + y * tx + x);
+                    keys[off] = (g << 32) | (uint64_t)zbits;
+                    vals[off] = (uint32_t)e;
+                }
+                off++;
+            }
+        }
+    }
+}
+
+// digit of the compacted key ((tile << 31) | z bits) at [shift, shift + bits)
+__device__ __forceinline__ uint32_t key_digit(uint64_t key, int shift, uint32_t mask) {
+    const uint64_t c = ((key >> 32) << 31) | (key & 0x7fffffffull);
+    return (uint32_t)(c >> shift) & mask;
+}
+
+__device__ __forceinline__ int64_t sort_count(const uint32_t* num_keys, int64_t capacity) {
+    const int64_t m = (int64_t)*num_keys;
+    return m < capacity ? m : capacity;
+}
+
+constexpr int kSortWarps = kSortThreads / 32;
+
+// Per-block digit counts, stored digit-major: counts[d * nb + b].
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ num_keys, int64_t capacity,
+                                                            int shift, int bits, uint32_t* __restrict__ counts) {
+    const int64_t M = sort_count(num_keys, capacity);
+    const int nb = (int)ceil_div(M, kSortBlock);
+    if ((int)blockIdx.x >= nb) return;
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&h[0][0])[k] = 0u;
+    __syncthreads();
+    const uint32_t mask = (1u << bits) - 1u;
+    const int warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+#pragma unroll 4
+    for (int r = 0; r < kSortItems; r++) {
+        const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+        if (idx < M) atomicAdd(&h[warp][key_digit(keys[idx], shift, mask)], 1u);
+    }
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) s += h[w][d];
+    counts[(int64_t)d * nb + blockIdx.x] = s;
+}
+
+// One CTA: exclusive scan of the digit-major counts (256 * nb entries).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ counts,
+                                                     const uint32_t* __restrict__ num_keys, int64_t capacity) {
+    __shared__ uint32_t s_warp[1024 / 32 + 1];
+    const int64_t M = sort_count(num_keys, capacity);
+    const int nb = (int)ceil_div(M, kSortBlock);
+    const int N = kRadix * nb;
+    const int chunk = (N + 1023) / 1024;
+    const int lo = threadIdx.x * chunk;
+    uint32_t s = 0;
+    for (int k = 0; k < chunk; k++)
+        if (lo + k < N) s += counts[lo + k];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<1024>(s, &total, s_warp);
+    for (int k = 0; k < chunk; k++) {
+        if (lo + k < N) {
+            uint32_t v = counts[lo + k];
+            counts[lo + k] = run;
+            run += v;
+        }
+    }
+}
+
+// Stable scatter.  Each round places 256 consecutive keys: ranks inside a warp
+// come from match_any, the offsets of earlier warps from a per-digit prefix in
+// shared memory, and s_base carries the digit's running position across rounds.
+// Counts are double-buffered so that a round needs two barriers.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                               const uint32_t* __restrict__ offsets,
+                                                               const uint32_t* __restrict__ num_keys,
+                                                               int64_t capacity, int shift, int bits) {
+    const int64_t M = sort_count(num_keys, capacity);
+    const int nb = (int)ceil_div(M, kSortBlock);
+    if ((int)blockIdx.x >= nb) return;
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_rbase[kRadix];
+    __shared__ uint32_t s_cnt[2][kSortWarps][kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mask = (1u << bits) - 1u;
+    s_base[tid] = offsets[(int64_t)tid * nb + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) { s_cnt[0][w][tid] = 0u; s_cnt[1][w][tid] = 0u; }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll 1
+    for (int r = 0; r < kSortItems; r++) {
+        const int buf = r & 1;
+        const int64_t idx = base + (int64_t)r * kSortThreads + tid;
+        const bool valid = idx < M;
+        const uint64_t key = valid ? kin[idx] : 0ull;
+        const uint32_t val = valid ? vin[idx] : 0u;
+        const uint32_t d = valid ? key_digit(key, shift, mask) : (uint32_t)kRadix;   // sentinel
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) s_cnt[buf][warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) {
+                const uint32_t c = s_cnt[buf][w][tid];
+                s_cnt[buf][w][tid] = run;
+                run += c;
+                s_cnt[buf ^ 1][w][tid] = 0u;
+            }
+            s_rbase[tid] = s_base[tid];
+            s_base[tid] += run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_rbase[d] + s_cnt[buf][warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+    }
+}
+
+__global__ void k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
+                              int64_t capacity, uint2* __restrict__ ranges) {
+    const int64_t M = sort_count(num_keys, capacity);
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const uint32_t t = (uint32_t)(keys[s] >> 32);
+    if (s == 0 || (uint32_t)(keys[s - 1] >> 32) != t) ranges[t].x = (uint32_t)s;
+    if (s == M - 1 || (uint32_t)(keys[s + 1] >> 32) != t) ranges[t].y = (uint32_t)(s + 1);
+}
+
+}  // namespace
+
+SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
+    SortPlan p;
+    p.capacity = key_capacity;
+    int tile_bits = 0;
+    while ((1ll << tile_bits) < (int64_t)total_tiles) tile_bits++;
+    const int bits = 31 + tile_bits;
+    p.n_passes = (bits + kRadixBits - 1) / kRadixBits;
+    for (int k = 0; k < p.n_passes; k++) {
+        p.shift[k] = k * kRadixBits;
+        p.bits[k] = (bits - k * kRadixBits) < kRadixBits ? bits - k * kRadixBits : kRadixBits;
+    }
+    return p;
+}
+
+// Workspace layout of launch_bin_sort (offsets in bytes, 256-byte aligned):
+//   block sums   : ceil(E / kScanBlock) u32
+//   counts       : kRadix * ceil(capacity / kSortBlock) u32
+//   keys (alt)   : capacity u64
+//   vals (alt)   : capacity u32
+size_t bin_sort_workspace(int64_t n_entries, int64_t capacity) {
+    size_t b = 0;
+    b += align_up(sizeof(uint32_t) * (size_t)(ceil_div(n_entries, kScanBlock) + 1), 256);
+    b += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(capacity, kSortBlock) + 1), 256);
+    b += align_up(sizeof(uint64_t) * (size_t)capacity, 256);
+    b += align_up(sizeof(uint32_t) * (size_t)capacity, 256);
+    return b;
+}
+
+cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& views, const SortPlan& plan,
+                            const gs_bins& bins, void* ws, cudaStream_t s) {
+    const int64_t E = n * views.n;
+    const int64_t cap = plan.capacity;
+    char* p = static_cast<char*>(ws);
+    uint32_t* block_sums = reinterpret_cast<uint32_t*>(p);
+    p += align_up(sizeof(uint32_t) * (size_t)(ceil_div(E, kScanBlock) + 1), 256);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(p);
+    p += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(cap, kSortBlock) + 1), 256);
+    uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
+    p += align_up(sizeof(uint64_t) * (size_t)cap, 256);
+    uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
+
+    cudaError_t err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)views.total_tiles, s);
+    if (err != cudaSuccess) return err;
+    const int nb_scan = (int)ceil_div(E, kScanBlock);
+    if (E == 0) return cudaMemsetAsync(bins.num_keys, 0, sizeof(uint32_t), s);
+    k_scan_reduce<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, E, block_sums);
+    k_scan_blocks<<<1, 1024, 0, s>>>(block_sums, nb_scan, bins.num_keys, cap, bins.status);
+    // The duplicated list goes into the buffer that makes the last pass land in bins.keys.
+    uint64_t* k0 = (plan.n_passes % 2 == 0) ? bins.keys : keys_alt;
+    uint32_t* v0 = (plan.n_passes % 2 == 0) ? bins.vals : vals_alt;
+    uint64_t* k1 = (plan.n_passes % 2 == 0) ? keys_alt : bins.keys;
+    uint32_t* v1 = (plan.n_passes % 2 == 0) ? vals_alt : bins.vals;
+    k_duplicate<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, reinterpret_cast<const int4*>(pr.rect),
+                                                 reinterpret_cast<const float4*>(pr.rgbd), E, n, block_sums, views,
+                                                 cap, k0, v0);
+    const int nb_sort = (int)ceil_div(cap, kSortBlock);
+    for (int pass = 0; pass < plan.n_passes; pass++) {
+        k_radix_hist<<<nb_sort, kSortThreads, 0, s>>>(k0, bins.num_keys, cap, plan.shift[pass], plan.bits[pass],
+                                                      counts);
+        k_radix_scan<<<1, 1024, 0, s>>>(counts, bins.num_keys, cap);
+        k_radix_scatter<<<nb_sort, kSortThreads, 0, s>>>(k0, v0, k1, v1, counts, bins.num_keys, cap,
+                                                         plan.shift[pass], plan.bits[pass]);
+        uint64_t* tk = k0; k0 = k1; k1 = tk;
+        uint32_t* tv = v0; v0 = v1; v1 = tv;
+    }
+    const int nb_rng = (int)ceil_div(cap, 256);
+    k_tile_ranges<<<nb_rng, 256, 0, s>>>(bins.keys, bins.num_keys, cap, reinterpret_cast<uint2*>(bins.ranges));
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,122 @@
+// gs_internal.cuh -- shared definitions of the libgs CUDA translation units.
+// Not part of the public ABI (see include/gs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+// Per-view constants, passed to kernels by value (kernel parameter space).
+struct ViewParams {
+    float Rcw[9];      // world-to-camera rotation R_wc^T, row-major
+    float tcw[3];      // -R_wc^T t_wc
+    float centre[3];   // camera centre t_wc (SH viewing direction)
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    int32_t tile_base;  // first global tile of this view
+    int32_t pix_base;   // first pixel of this view
+};
+
+struct Views {
+    int32_t n;
+    int32_t total_tiles;
+    int32_t total_pixels;
+    int32_t pad;
+    ViewParams v[GS_MAX_VIEWS];
+};
+
+struct RenderConsts {
+    int32_t tile;
+    float near_plane, alpha_min, alpha_max, T_cut, dilation, radius_sigma;
+    float bg[3];
+    int32_t sh_degree;
+};
+
+// Host helpers (api.cu).
+bool make_views(const gs_camera* cams, int32_t n_views, int32_t tile, Views* out);
+RenderConsts make_consts(const gs_render_params* p);
+
+// Workspace layout shared by the entry points (api.cu).
+struct SortPlan {
+    int64_t capacity;
+    int32_t n_passes;
+    int32_t shift[8];
+    int32_t bits[8];
+};
+SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles);
+size_t bin_sort_workspace(int64_t n_entries, int64_t capacity);
+
+constexpr int kScanItems = 8;                    // entries per thread in scan / duplicate
+constexpr int kScanThreads = 256;
+constexpr int kScanBlock = kScanItems * kScanThreads;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortBlock = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kGradStride = 12;                  // floats per entry of the 2D-gradient scratch
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Launchers (one translation unit each).
+cudaError_t launch_project(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
+                           const gs_projected& out, cudaStream_t s);
+cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n_entries, const Views& views,
+                            const SortPlan& plan, const gs_bins& bins, void* ws, cudaStream_t s);
+cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
+                              const RenderConsts& rc, const gs_image& img, cudaStream_t s);
+cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, const Views& views,
+                        float lc, float ld, float* dc, float* dd, float* terms, void* ws, cudaStream_t s);
+cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img,
+                              const float* dc, const float* dd, const Views& views, const RenderConsts& rc,
+                              float* g2d, cudaStream_t s);
+cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
+                               const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
+                               cudaStream_t s);
+cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps,
+                        int32_t* d_step, cudaStream_t s);
+
+// ---------------------------------------------------------------- device side
+
+#ifdef __CUDACC__
+// log2(e): the splat weight is evaluated as exp2(power * log2 e).
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The splat's shared-memory form: conic pre-scaled so that the exponent comes
+// out in log2 units, p2 = log2(e) * power.  Forward and backward both call
+// splat_power2 / splat_alpha with identical operands, and every rounding step
+// is an explicit intrinsic, so the two passes take identical decisions.
+struct SplatGeom {
+    float mx, my;       // projected mean
+    float qa, qb, qc;   // -0.5 log2e A, -log2e B, -0.5 log2e C
+    float o;            // opacity
+};
+
+__device__ __forceinline__ void scale_conic(float A, float B, float C, float* qa, float* qb, float* qc) {
+    *qa = __fmul_rn(-0.5f * kLog2e, A);
+    *qb = __fmul_rn(-kLog2e, B);
+    *qc = __fmul_rn(-0.5f * kLog2e, C);
+}
+
+// p2 = qa dx^2 + qb dx dy + qc dy^2 with dx = px - mx, dy = py - my.
+__device__ __forceinline__ float splat_power2(float qa, float qb, float qc, float dx, float dy) {
+    float u = __fmaf_rn(qb, dy, __fmul_rn(qa, dx));   // qa dx + qb dy
+    float w = __fmul_rn(qc, dy);                      // qc dy
+    return __fmaf_rn(dx, u, __fmul_rn(w, dy));        // dx (qa dx + qb dy) + qc dy^2
+}
+
+__device__ __forceinline__ float splat_weight(float p2) { return ex2_approx(p2); }
+#endif
+
+}  // namespace gs

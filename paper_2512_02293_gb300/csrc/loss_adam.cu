@@ -1,0 +1,203 @@
+// loss_adam.cu -- the colour/depth L1 terms of Eq. 6 with their image
+// gradients, and the Adam step of the mapping iteration.
+//
+// Loss: grid (pixel blocks, view).  Pass 1 reduces |I_hat - I|, |D_hat - D| over
+// D > 0 and the valid-pixel count of each view (block reduction, three atomics
+// per block into a per-view accumulator in the workspace); pass 2 writes the
+// signed, normalised image gradients and the per-view loss terms.
+// Adam: one launch over all parameter groups (blockIdx.y = group), float4
+// loads/stores where the group is 16-byte aligned; the step counter lives on
+// the device so the launch can be replayed from a CUDA graph.
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kLossThreads = 256;
+constexpr int kLossItems = 4;
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_reduce(gs_image img, const float* __restrict__ tc,
+                                                             const float* __restrict__ td, Views views,
+                                                             float* __restrict__ acc) {
+    const int v = blockIdx.y;
+    const ViewParams& vp = views.v[v];
+    const int HW = vp.W * vp.H;
+    const int base = blockIdx.x * kLossThreads * kLossItems;
+    if (base >= HW) return;
+    const float* c = img.color + 3 * (size_t)vp.pix_base;
+    const float* t = tc + 3 * (size_t)vp.pix_base;
+    const float* d = img.depth + vp.pix_base;
+    const float* t1 = td + vp.pix_base;
+    float sc = 0.f, sd = 0.f, nv = 0.f;
+#pragma unroll
+    for (int k = 0; k < kLossItems; k++) {
+        const int p = base + k * kLossThreads + threadIdx.x;
+        if (p < HW) {
+            sc += fabsf(c[p] - t[p]) + fabsf(c[HW + p] - t[HW + p]) + fabsf(c[2 * HW + p] - t[2 * HW + p]);
+            const float tdv = t1[p];
+            if (tdv > 0.f) {
+                sd += fabsf(d[p] - tdv);
+                nv += 1.f;
+            }
+        }
+    }
+    __shared__ float s[3][kLossThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { s[0][warp] = sc; s[1][warp] = sd; s[2][warp] = nv; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float x = 0.f;
+#pragma unroll
+        for (int w = 0; w < kLossThreads / 32; w++) x += s[threadIdx.x][w];
+        atomicAdd(acc + 4 * v + threadIdx.x, x);
+    }
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_grad(gs_image img, const float* __restrict__ tc,
+                                                           const float* __restrict__ td, Views views,
+                                                           const float* __restrict__ acc, float lc, float ld,
+                                                           float* __restrict__ dc, float* __restrict__ dd,
+                                                           float* __restrict__ terms) {
+    const int v = blockIdx.y;
+    const ViewParams& vp = views.v[v];
+    const int HW = vp.W * vp.H;
+    const int base = blockIdx.x * kLossThreads * kLossItems;
+    if (base >= HW) return;
+    const float nvalid = acc[4 * v + 2];
+    const float kc = lc / (3.0f * (float)HW);
+    const float kd = nvalid > 0.f ? ld / nvalid : 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        terms[2 * v] = acc[4 * v] / (3.0f * (float)HW);
+        terms[2 * v + 1] = nvalid > 0.f ? acc[4 * v + 1] / nvalid : 0.f;
+    }
+    const float* c = img.color + 3 * (size_t)vp.pix_base;
+    const float* t = tc + 3 * (size_t)vp.pix_base;
+    float* g = dc + 3 * (size_t)vp.pix_base;
+#pragma unroll
+    for (int k = 0; k < kLossItems; k++) {
+        const int p = base + k * kLossThreads + threadIdx.x;
+        if (p < HW) {
+            g[p] = kc * sgnf(c[p] - t[p]);
+            g[HW + p] = kc * sgnf(c[HW + p] - t[HW + p]);
+            g[2 * HW + p] = kc * sgnf(c[2 * HW + p] - t[2 * HW + p]);
+            const float tdv = td[vp.pix_base + p];
+            dd[vp.pix_base + p] = tdv > 0.f ? kd * sgnf(img.depth[vp.pix_base + p] - tdv) : 0.f;
+        }
+    }
+}
+
+struct AdamArgs {
+    gs_adam_group g[8];
+    int n_groups;
+    float b1, b2, eps;
+    int32_t* d_step;
+    unsigned total_blocks;
+};
+
+constexpr int kAdamThreads = 256;
+constexpr int kAdamPerBlock = kAdamThreads * 4;
+
+__global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
+    __shared__ float s_bc[2];
+    __shared__ int s_t;
+    if (threadIdx.x == 0) {
+        const int t = args.d_step[0] + 1;
+        s_t = t;
+        // bias corrections in double (two pow per block)
+        s_bc[0] = (float)(1.0 - pow((double)args.b1, (double)t));
+        s_bc[1] = (float)(1.0 - pow((double)args.b2, (double)t));
+    }
+    __syncthreads();
+    const gs_adam_group& G = args.g[blockIdx.y];
+    const float bc1 = s_bc[0], bc2 = s_bc[1];
+    const float b1 = args.b1, b2 = args.b2, eps = args.eps, lr = G.lr;
+    const float ib1 = 1.0f - b1, ib2 = 1.0f - b2;
+    const int64_t start = (int64_t)blockIdx.x * kAdamPerBlock;
+    if (start < G.n) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
+                           reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
+        const int64_t i0 = start + 4 * (int64_t)threadIdx.x;
+        if (vec && i0 + 3 < G.n) {
+            float4 p = *reinterpret_cast<const float4*>(G.param + i0);
+            const float4 g = *reinterpret_cast<const float4*>(G.grad + i0);
+            float4 m = *reinterpret_cast<const float4*>(G.m + i0);
+            float4 v = *reinterpret_cast<const float4*>(G.v + i0);
+            float* pp = &p.x; const float* gg = &g.x; float* mm = &m.x; float* vv = &v.x;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                mm[k] = b1 * mm[k] + ib1 * gg[k];
+                vv[k] = b2 * vv[k] + ib2 * gg[k] * gg[k];
+                pp[k] -= lr * (mm[k] / bc1) / (sqrtf(vv[k] / bc2) + eps);
+            }
+            *reinterpret_cast<float4*>(G.param + i0) = p;
+            *reinterpret_cast<float4*>(G.m + i0) = m;
+            *reinterpret_cast<float4*>(G.v + i0) = v;
+        } else {
+            for (int k = 0; k < 4; k++) {
+                const int64_t i = i0 + k;
+                if (i >= G.n) break;
+                const float g = G.grad[i];
+                const float m = b1 * G.m[i] + ib1 * g;
+                const float v = b2 * G.v[i] + ib2 * g * g;
+                G.m[i] = m;
+                G.v[i] = v;
+                G.param[i] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+            }
+        }
+    }
+    // The last block to finish advances the step counter (every block has read it by now).
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(reinterpret_cast<unsigned*>(args.d_step + 1), 1u);
+        if (prev == args.total_blocks - 1) {
+            args.d_step[0] = s_t;
+            args.d_step[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace
+
+size_t loss_workspace(int32_t n_views) { return align_up(sizeof(float) * 4 * (size_t)n_views, 256); }
+
+cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, const Views& views, float lc, float ld,
+                        float* dc, float* dd, float* terms, void* ws, cudaStream_t s) {
+    float* acc = static_cast<float*>(ws);
+    cudaError_t err = cudaMemsetAsync(acc, 0, sizeof(float) * 4 * (size_t)views.n, s);
+    if (err != cudaSuccess) return err;
+    int max_hw = 0;
+    for (int v = 0; v < views.n; v++) max_hw = max(max_hw, views.v[v].W * views.v[v].H);
+    dim3 grid((unsigned)ceil_div(max_hw, kLossThreads * kLossItems), (unsigned)views.n);
+    k_loss_reduce<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc);
+    k_loss_grad<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc, lc, ld, dc, dd, terms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps, int32_t* d_step,
+                        cudaStream_t s) {
+    AdamArgs a;
+    int64_t max_n = 0;
+    for (int k = 0; k < 8; k++) a.g[k] = k < n_groups ? groups[k] : gs_adam_group{};
+    for (int k = 0; k < n_groups; k++) max_n = groups[k].n > max_n ? groups[k].n : max_n;
+    a.n_groups = n_groups;
+    a.b1 = b1; a.b2 = b2; a.eps = eps;
+    a.d_step = d_step;
+    const unsigned bx = (unsigned)(max_n > 0 ? ceil_div(max_n, kAdamPerBlock) : 1);
+    a.total_blocks = bx * (unsigned)n_groups;
+    k_adam<<<dim3(bx, (unsigned)n_groups), kAdamThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,390 @@
+"""Thin Python binding of libgs (include/gs.h): ctypes structs with the same
+layout as the C ones and one function per entry point, with the same names.
+
+Arguments are torch CUDA tensors (device memory) plus host-side cameras and
+parameters; every function only converts them to pointers and calls the
+library on the current torch stream.  There is no fallback: if libgs.so is
+missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs.so")
+GS_MAX_VIEWS = 32
+_lib = None
+
+STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA", 4: "GS_ERR_TIMEOUT",
+          5: "GS_ERR_NUMERIC", 6: "GS_ERR_UNSUPPORTED"}
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA = 0, 1, 2, 3
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+# ----------------------------------------------------------------- C structs
+
+c_float_p = ctypes.POINTER(ctypes.c_float)
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("R_wc", ctypes.c_float * 9),
+                ("t_wc", ctypes.c_float * 3)]
+
+
+class gs_render_params(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("near_plane", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("T_cut", ctypes.c_float), ("dilation", ctypes.c_float),
+                ("radius_sigma", ctypes.c_float), ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class gs_gaussians(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("color", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class gs_projected(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("conic_o", ctypes.c_void_p), ("rgbd", ctypes.c_void_p),
+                ("rect", ctypes.c_void_p), ("radius", ctypes.c_void_p), ("tiles_touched", ctypes.c_void_p)]
+
+
+class gs_bins(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("key_capacity", ctypes.c_int64),
+                ("ranges", ctypes.c_void_p), ("num_keys", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class gs_image(ctypes.Structure):
+    _fields_ = [("color", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("T_final", ctypes.c_void_p),
+                ("n_contrib", ctypes.c_void_p)]
+
+
+class gs_grads(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("color", ctypes.c_void_p), ("pose", ctypes.c_void_p)]
+
+
+class gs_adam_group(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pixels", "gs_workspace_size",
+           "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd", "gs_render_bwd_raster",
+           "gs_project_bwd", "gs_adam_step", "gs_read_device_status"]
+
+
+def load_library(path: str | None = None):
+    """Load libgs.so (no GPU needed to load it)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libgs.so is not built ({p}); run __graft_entry__.build() or "
+                           "python paper_2512_02293_gb300/build.py")
+    lib = ctypes.CDLL(p)
+    V = ctypes.c_void_p
+    lib.gs_abi_version.restype = ctypes.c_int32
+    lib.gs_status_string.restype = ctypes.c_char_p
+    lib.gs_status_string.argtypes = [ctypes.c_int32]
+    lib.gs_total_tiles.restype = ctypes.c_int64
+    lib.gs_total_tiles.argtypes = [V, ctypes.c_int32, ctypes.c_int32]
+    lib.gs_total_pixels.restype = ctypes.c_int64
+    lib.gs_total_pixels.argtypes = [V, ctypes.c_int32]
+    lib.gs_workspace_size.restype = ctypes.c_size_t
+    lib.gs_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, V, V, ctypes.c_int64]
+    lib.gs_project.restype = ctypes.c_int32
+    lib.gs_project.argtypes = [V, V, ctypes.c_int32, V, V, V]
+    lib.gs_bin_sort.restype = ctypes.c_int32
+    lib.gs_bin_sort.argtypes = [V, ctypes.c_int64, V, ctypes.c_int32, V, V, V, ctypes.c_size_t, V]
+    lib.gs_render_fwd.restype = ctypes.c_int32
+    lib.gs_render_fwd.argtypes = [V, V, V, ctypes.c_int32, V, V, V]
+    lib.gs_loss.restype = ctypes.c_int32
+    lib.gs_loss.argtypes = [V, V, V, V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, V, V, V, V,
+                            ctypes.c_size_t, V]
+    lib.gs_render_bwd.restype = ctypes.c_int32
+    lib.gs_render_bwd.argtypes = [V, V, V, V, V, V, V, ctypes.c_int32, V, ctypes.c_float, V, V, V, ctypes.c_size_t, V]
+    lib.gs_render_bwd_raster.restype = ctypes.c_int32
+    lib.gs_render_bwd_raster.argtypes = [V, V, V, V, V, V, ctypes.c_int32, V, ctypes.c_int64, V, V]
+    lib.gs_project_bwd.restype = ctypes.c_int32
+    lib.gs_project_bwd.argtypes = [V, V, ctypes.c_int32, V, V, ctypes.c_float, V, V, V]
+    lib.gs_adam_step.restype = ctypes.c_int32
+    lib.gs_adam_step.argtypes = [V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float, V, V]
+    lib.gs_read_device_status.restype = ctypes.c_int32
+    lib.gs_read_device_status.argtypes = [V, V, V]
+    if lib.gs_abi_version() != 1:
+        raise RuntimeError("libgs ABI version mismatch")
+    if path is None:
+        _lib = lib
+    return lib
+
+
+# --------------------------------------------------------- host-side values
+
+@dataclass
+class RenderParams:
+    tile: int = 16
+    near_plane: float = 0.2
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_cut: float = 1e-4
+    dilation: float = 0.3
+    radius_sigma: float = 3.0
+    bg: tuple = (0.0, 0.0, 0.0)
+    sh_degree: int = 0
+
+    def struct(self) -> gs_render_params:
+        return gs_render_params(int(self.tile), self.near_plane, self.alpha_min, self.alpha_max, self.T_cut,
+                                self.dilation, self.radius_sigma, (ctypes.c_float * 3)(*self.bg),
+                                int(self.sh_degree), 0)
+
+
+def camera_array(cams) -> ctypes.Array:
+    """Array of gs_camera from objects with fx, fy, cx, cy, width, height, R_wc, t_wc."""
+    arr = (gs_camera * len(cams))()
+    for k, c in enumerate(cams):
+        R = np.asarray(c.R_wc, dtype=np.float32).reshape(9)
+        t = np.asarray(c.t_wc, dtype=np.float32).reshape(3)
+        arr[k] = gs_camera(float(c.fx), float(c.fy), float(c.cx), float(c.cy), int(c.width), int(c.height),
+                           (ctypes.c_float * 9)(*R), (ctypes.c_float * 3)(*t))
+    return arr
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libgs takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libgs takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status, where):
+    if status != GS_OK:
+        raise GsError(status, where)
+
+
+# ------------------------------------------------------- device containers
+
+@dataclass
+class Gaussians:
+    mean: "torch.Tensor"
+    quat: "torch.Tensor"
+    log_scale: "torch.Tensor"
+    opacity_logit: "torch.Tensor"
+    color: "torch.Tensor"
+
+    @property
+    def n(self):
+        return int(self.mean.shape[0])
+
+    @staticmethod
+    def from_numpy(g, device="cuda"):
+        import torch
+        return Gaussians(*(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device) for a in g.arrays()))
+
+    def tensors(self):
+        return [self.mean, self.quat, self.log_scale, self.opacity_logit, self.color]
+
+    def struct(self) -> gs_gaussians:
+        for t in self.tensors():
+            if t.dtype.itemsize != 4:
+                raise ValueError("Gaussian parameters are float32")
+        return gs_gaussians(*(_ptr(t) for t in self.tensors()), self.n)
+
+
+@dataclass
+class Projected:
+    xy: "torch.Tensor"
+    conic_o: "torch.Tensor"
+    rgbd: "torch.Tensor"
+    rect: "torch.Tensor"
+    radius: "torch.Tensor"
+    tiles_touched: "torch.Tensor"
+
+    @staticmethod
+    def empty(n_entries, device="cuda"):
+        import torch
+        f = dict(device=device, dtype=torch.float32)
+        i = dict(device=device, dtype=torch.int32)
+        return Projected(torch.empty(n_entries, 2, **f), torch.empty(n_entries, 4, **f), torch.empty(n_entries, 4, **f),
+                         torch.empty(n_entries, 4, **i), torch.empty(n_entries, **i), torch.empty(n_entries, **i))
+
+    def struct(self) -> gs_projected:
+        return gs_projected(*(_ptr(getattr(self, f.name)) for f in fields(self)))
+
+
+@dataclass
+class Bins:
+    keys: "torch.Tensor"       # int64 storage of uint64 keys
+    vals: "torch.Tensor"       # int32 storage of uint32 values
+    ranges: "torch.Tensor"     # int32 [total_tiles, 2]
+    num_keys: "torch.Tensor"   # int32 [1]
+    status: "torch.Tensor"     # int32 [1]
+
+    @staticmethod
+    def empty(capacity, total_tiles, device="cuda"):
+        import torch
+        i = dict(device=device, dtype=torch.int32)
+        return Bins(torch.empty(max(capacity, 1), device=device, dtype=torch.int64), torch.empty(max(capacity, 1), **i),
+                    torch.zeros(total_tiles, 2, **i), torch.zeros(1, **i), torch.zeros(1, **i))
+
+    @property
+    def capacity(self):
+        return int(self.keys.shape[0])
+
+    def struct(self) -> gs_bins:
+        return gs_bins(_ptr(self.keys), _ptr(self.vals), self.capacity, _ptr(self.ranges), _ptr(self.num_keys),
+                       _ptr(self.status))
+
+
+@dataclass
+class Image:
+    color: "torch.Tensor"      # [3 * P]
+    depth: "torch.Tensor"      # [P]
+    T_final: "torch.Tensor"    # [P]
+    n_contrib: "torch.Tensor"  # [P] int32 storage of uint32
+
+    @staticmethod
+    def empty(total_pixels, device="cuda"):
+        import torch
+        f = dict(device=device, dtype=torch.float32)
+        return Image(torch.empty(3 * total_pixels, **f), torch.empty(total_pixels, **f), torch.empty(total_pixels, **f),
+                     torch.empty(total_pixels, device=device, dtype=torch.int32))
+
+    def struct(self) -> gs_image:
+        return gs_image(_ptr(self.color), _ptr(self.depth), _ptr(self.T_final), _ptr(self.n_contrib))
+
+
+@dataclass
+class Grads:
+    mean: "torch.Tensor"
+    quat: "torch.Tensor"
+    log_scale: "torch.Tensor"
+    opacity_logit: "torch.Tensor"
+    color: "torch.Tensor"
+    pose: "torch.Tensor | None" = None
+
+    @staticmethod
+    def empty_like(g: Gaussians, n_views: int | None = None):
+        import torch
+        pose = None if n_views is None else torch.zeros(n_views, 6, device=g.mean.device, dtype=torch.float32)
+        return Grads(*(torch.empty_like(t) for t in g.tensors()), pose)
+
+    def tensors(self):
+        return [self.mean, self.quat, self.log_scale, self.opacity_logit, self.color]
+
+    def struct(self) -> gs_grads:
+        return gs_grads(*(_ptr(t) for t in self.tensors()), _ptr(self.pose))
+
+
+# ------------------------------------------------------------- entry points
+
+def gs_total_tiles(cams, tile: int) -> int:
+    arr = camera_array(cams)
+    r = load_library().gs_total_tiles(arr, len(cams), tile)
+    if r < 0:
+        raise GsError(GS_ERR_INVALID_ARG, "gs_total_tiles")
+    return int(r)
+
+
+def gs_total_pixels(cams) -> int:
+    arr = camera_array(cams)
+    r = load_library().gs_total_pixels(arr, len(cams))
+    if r < 0:
+        raise GsError(GS_ERR_INVALID_ARG, "gs_total_pixels")
+    return int(r)
+
+
+def gs_workspace_size(n: int, cams, params: RenderParams, key_capacity: int) -> int:
+    arr = camera_array(cams)
+    p = params.struct()
+    r = load_library().gs_workspace_size(n, len(cams), arr, ctypes.byref(p), key_capacity)
+    if r == 0:
+        raise GsError(GS_ERR_INVALID_ARG, "gs_workspace_size")
+    return int(r)
+
+
+def gs_project(g: Gaussians, cams, params: RenderParams, out: Projected, stream=None):
+    arr = camera_array(cams); p = params.struct(); gg = g.struct(); o = out.struct()
+    _check(load_library().gs_project(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), ctypes.byref(o),
+                                     _stream(stream)), "gs_project")
+
+
+def gs_bin_sort(proj: Projected, n: int, cams, params: RenderParams, bins: Bins, ws, stream=None):
+    arr = camera_array(cams); p = params.struct(); pr = proj.struct(); b = bins.struct()
+    _check(load_library().gs_bin_sort(ctypes.byref(pr), n, arr, len(cams), ctypes.byref(p), ctypes.byref(b),
+                                      _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "gs_bin_sort")
+
+
+def gs_render_fwd(proj: Projected, bins: Bins, cams, params: RenderParams, img: Image, stream=None):
+    arr = camera_array(cams); p = params.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct()
+    _check(load_library().gs_render_fwd(ctypes.byref(pr), ctypes.byref(b), arr, len(cams), ctypes.byref(p),
+                                        ctypes.byref(im), _stream(stream)), "gs_render_fwd")
+
+
+def gs_loss(img: Image, target_color, target_depth, cams, lambda_c: float, lambda_d: float, dL_dcolor, dL_ddepth,
+            loss_terms, ws, stream=None):
+    arr = camera_array(cams); im = img.struct()
+    _check(load_library().gs_loss(ctypes.byref(im), _ptr(target_color), _ptr(target_depth), arr, len(cams),
+                                  float(lambda_c), float(lambda_d), _ptr(dL_dcolor), _ptr(dL_ddepth), _ptr(loss_terms),
+                                  _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "gs_loss")
+
+
+def gs_render_bwd(g: Gaussians, proj: Projected, bins: Bins, img: Image, dL_dcolor, dL_ddepth, cams,
+                  params: RenderParams, lambda_iso: float, grads: Grads, iso_loss, ws, stream=None):
+    arr = camera_array(cams); p = params.struct(); gg = g.struct(); pr = proj.struct(); b = bins.struct()
+    im = img.struct(); gr = grads.struct()
+    _check(load_library().gs_render_bwd(ctypes.byref(gg), ctypes.byref(pr), ctypes.byref(b), ctypes.byref(im),
+                                        _ptr(dL_dcolor), _ptr(dL_ddepth), arr, len(cams), ctypes.byref(p),
+                                        float(lambda_iso), ctypes.byref(gr), _ptr(iso_loss), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _stream(stream)), "gs_render_bwd")
+
+
+def gs_render_bwd_raster(proj: Projected, bins: Bins, img: Image, dL_dcolor, dL_ddepth, cams, params: RenderParams,
+                         n: int, grad2d, stream=None):
+    arr = camera_array(cams); p = params.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct()
+    _check(load_library().gs_render_bwd_raster(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(im), _ptr(dL_dcolor),
+                                               _ptr(dL_ddepth), arr, len(cams), ctypes.byref(p), n, _ptr(grad2d),
+                                               _stream(stream)), "gs_render_bwd_raster")
+
+
+def gs_project_bwd(g: Gaussians, cams, params: RenderParams, grad2d, lambda_iso: float, grads: Grads, iso_loss,
+                   stream=None):
+    arr = camera_array(cams); p = params.struct(); gg = g.struct(); gr = grads.struct()
+    _check(load_library().gs_project_bwd(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), _ptr(grad2d),
+                                         float(lambda_iso), ctypes.byref(gr), _ptr(iso_loss), _stream(stream)),
+           "gs_project_bwd")
+
+
+def gs_adam_step(groups, beta1: float, beta2: float, eps: float, d_step, stream=None):
+    """groups: list of (param, grad, m, v, lr) tensors/floats."""
+    arr = (gs_adam_group * len(groups))()
+    for k, (p, gr, m, v, lr) in enumerate(groups):
+        arr[k] = gs_adam_group(_ptr(p), _ptr(gr), _ptr(m), _ptr(v), p.numel(), float(lr), 0)
+    _check(load_library().gs_adam_step(arr, len(groups), float(beta1), float(beta2), float(eps), _ptr(d_step),
+                                       _stream(stream)), "gs_adam_step")
+
+
+def gs_read_device_status(d_status, stream=None) -> int:
+    out = ctypes.c_int32(0)
+    _check(load_library().gs_read_device_status(_ptr(d_status), _stream(stream), ctypes.byref(out)),
+           "gs_read_device_status")
+    return int(out.value)

@@ -1,0 +1,164 @@
+"""One mapping iteration of Sec. 3.3 "Map Management" on the GPU:
+
+    render colour and depth of every view -> Eq. 6 loss -> backward -> Adam
+
+driven through the C ABI (gs_project, gs_bin_sort, gs_render_fwd, gs_loss,
+gs_render_bwd, gs_adam_step).  All buffers are allocated once, up front, by
+torch; the iteration itself allocates nothing and reads nothing back, so it
+can be captured into a CUDA graph and replayed (``capture()`` / ``replay()``).
+
+The number of (tile, Gaussian) keys depends on the map and the poses.  The key
+buffers get a capacity with headroom from a first, uncaptured pass; every call
+checks the device status word only when asked (``check()``), so an overflow
+during replay is detected after the fact and ``ensure_capacity`` grows the
+buffers.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import gs as G
+
+PARAM_NAMES = ("mean", "quat", "log_scale", "opacity_logit", "color")
+
+
+@dataclass
+class MapParams:
+    lambda_c: float = 0.9
+    lambda_d: float = 0.1
+    lambda_iso: float = 10.0
+    lr: tuple = (1e-3, 1e-3, 5e-3, 5e-2, 2.5e-3)   # mean, quat, log_scale, logit, colour
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+
+class MappingStep:
+    def __init__(self, gaussians: G.Gaussians, cams, target_color: torch.Tensor, target_depth: torch.Tensor,
+                 params: G.RenderParams | None = None, mparams: MapParams | None = None,
+                 key_capacity: int | None = None, headroom: float = 1.3):
+        self.g = gaussians
+        self.cams = list(cams)
+        self.params = params or G.RenderParams()
+        self.mp = mparams or MapParams()
+        dev = gaussians.mean.device
+        self.device = dev
+        self.n = gaussians.n
+        self.V = len(self.cams)
+        self.E = self.n * self.V
+        self.total_tiles = G.gs_total_tiles(self.cams, self.params.tile)
+        self.total_pixels = G.gs_total_pixels(self.cams)
+        assert target_color.numel() == 3 * self.total_pixels and target_depth.numel() == self.total_pixels
+        self.target_color = target_color.contiguous()
+        self.target_depth = target_depth.contiguous()
+        self.proj = G.Projected.empty(self.E, dev)
+        self.img = G.Image.empty(self.total_pixels, dev)
+        self.dL_dcolor = torch.empty(3 * self.total_pixels, device=dev, dtype=torch.float32)
+        self.dL_ddepth = torch.empty(self.total_pixels, device=dev, dtype=torch.float32)
+        self.loss_terms = torch.zeros(self.V, 2, device=dev, dtype=torch.float32)
+        self.iso = torch.zeros(1, device=dev, dtype=torch.float32)
+        self.grads = G.Grads.empty_like(gaussians, self.V)
+        self.m = [torch.zeros_like(t) for t in gaussians.tensors()]
+        self.v = [torch.zeros_like(t) for t in gaussians.tensors()]
+        self.d_step = torch.zeros(2, device=dev, dtype=torch.int32)
+        self.headroom = headroom
+        self.graph = None
+        self._alloc_bins(key_capacity if key_capacity is not None else self._measure_keys())
+
+    # -------------------------------------------------------------- buffers
+    def _alloc_bins(self, capacity: int):
+        capacity = max(int(capacity), 1024)
+        self.bins = G.Bins.empty(capacity, self.total_tiles, self.device)
+        ws = G.gs_workspace_size(self.n, self.cams, self.params, capacity)
+        self.ws = torch.empty((ws + 255) // 256 * 64, device=self.device, dtype=torch.float32)
+        self.graph = None
+
+    def _measure_keys(self) -> int:
+        """Project once and count the keys (host read; outside any graph)."""
+        G.gs_project(self.g, self.cams, self.params, self.proj)
+        m = int(self.proj.tiles_touched.to(torch.int64).sum().item())
+        return int(m * self.headroom) + 1024
+
+    def num_keys(self) -> int:
+        return int(self.bins.num_keys.item()) & 0xFFFFFFFF
+
+    def check(self) -> int:
+        """Device status word (0 = fine); synchronises the stream."""
+        return G.gs_read_device_status(self.bins.status)
+
+    def ensure_capacity(self) -> bool:
+        """Grow the key buffers if the last pass overflowed.  Returns True if grown."""
+        st = self.check()
+        if st == G.GS_ERR_CAPACITY or self.num_keys() > self.bins.capacity:
+            self._alloc_bins(int(self.num_keys() * self.headroom) + 1024)
+            return True
+        if st != 0:
+            raise G.GsError(st, "device status")
+        return False
+
+    # ------------------------------------------------------------ iteration
+    def render(self):
+        G.gs_project(self.g, self.cams, self.params, self.proj)
+        G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
+        G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
+
+    def loss_and_backward(self):
+        G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c, self.mp.lambda_d,
+                  self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
+        G.gs_render_bwd(self.g, self.proj, self.bins, self.img, self.dL_dcolor, self.dL_ddepth, self.cams,
+                        self.params, self.mp.lambda_iso, self.grads, self.iso, self.ws)
+
+    def optimizer_step(self):
+        groups = [(p, gr, m, v, lr) for p, gr, m, v, lr in
+                  zip(self.g.tensors(), self.grads.tensors(), self.m, self.v, self.mp.lr)]
+        G.gs_adam_step(groups, self.mp.beta1, self.mp.beta2, self.mp.eps, self.d_step)
+
+    def step(self):
+        """One full mapping iteration (no host synchronisation)."""
+        if self.graph is not None:
+            self.graph.replay()
+            return
+        self.render()
+        self.loss_and_backward()
+        self.optimizer_step()
+
+    def capture(self, warmup: int = 1):
+        """Capture the iteration into a CUDA graph (replayed by step())."""
+        self.graph = None
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.render()
+            self.loss_and_backward()
+            self.optimizer_step()
+        self.graph = g
+        return g
+
+    def loss(self) -> torch.Tensor:
+        """Total Eq. 6 loss of the last pass (device tensor)."""
+        t = self.loss_terms
+        return (self.mp.lambda_c * t[:, 0] + self.mp.lambda_d * t[:, 1]).sum() + self.mp.lambda_iso * self.iso[0]
+
+    # ------------------------------------------------------------- views
+    def view_slices(self):
+        """(pixel offset, W, H) of every view in the packed image buffers."""
+        out, base = [], 0
+        for c in self.cams:
+            out.append((base, int(c.width), int(c.height)))
+            base += int(c.width) * int(c.height)
+        return out
+
+    def color_image(self, v: int) -> torch.Tensor:
+        base, W, H = self.view_slices()[v]
+        return self.img.color[3 * base:3 * (base + W * H)].view(3, H, W)
+
+    def depth_image(self, v: int) -> torch.Tensor:
+        base, W, H = self.view_slices()[v]
+        return self.img.depth[base:base + W * H].view(H, W)

@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every entry point include/gs.h
+declares; host-side argument checks answer without a GPU (no compute call is
+made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_02293_gb300 import build as B
+from paper_2512_02293_gb300 import gs as G
+from paper_2512_02293_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return G.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(gs_[a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12, names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(names) == sorted(G.EXPORTS)
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.gs_abi_version() == 1
+    assert lib.gs_status_string(0) == b"GS_OK"
+    assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
+    assert lib.gs_status_string(99) == b"GS_ERR_UNKNOWN"
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(G.gs_camera) == 4 * 4 + 2 * 4 + 9 * 4 + 3 * 4
+    assert ctypes.sizeof(G.gs_render_params) == 4 * 12
+    assert ctypes.sizeof(G.gs_gaussians) == 6 * 8
+    assert ctypes.sizeof(G.gs_bins) == 6 * 8
+    assert ctypes.sizeof(G.gs_adam_group) == 4 * 8 + 8 + 8
+
+
+def test_tiles_pixels_workspace_host_only(lib):
+    cams = [synth.identity_camera(64, 48), synth.identity_camera(70, 45)]
+    assert G.gs_total_tiles(cams, 16) == 4 * 3 + 5 * 3
+    assert G.gs_total_tiles(cams, 8) == 8 * 6 + 9 * 6
+    assert G.gs_total_pixels(cams) == 64 * 48 + 70 * 45
+    ws = G.gs_workspace_size(256, cams, G.RenderParams(), 4096)
+    assert ws >= 4096 * 12 and ws % 256 == 0
+    with pytest.raises(G.GsError):
+        G.gs_total_tiles(cams, 12)          # unsupported tile size
+    with pytest.raises(G.GsError):
+        G.gs_workspace_size(-1, cams, G.RenderParams(), 10)
+
+
+def test_invalid_arguments_are_rejected_before_any_launch(lib):
+    # NULL pointers and bad parameters come back as GS_ERR_INVALID_ARG without
+    # touching the device.
+    cams = G.camera_array([synth.identity_camera()])
+    p = G.RenderParams().struct()
+    g = G.gs_gaussians(None, None, None, None, None, 10)
+    out = G.gs_projected()
+    assert lib.gs_project(ctypes.byref(g), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == 1
+    bad = G.RenderParams(tile=12).struct()
+    g0 = G.gs_gaussians(None, None, None, None, None, 0)
+    assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(bad), ctypes.byref(out), None) == 1
+    assert lib.gs_project(ctypes.byref(g0), cams, 0, ctypes.byref(p), ctypes.byref(out), None) == 1
+    assert lib.gs_project(ctypes.byref(g0), cams, 33, ctypes.byref(p), ctypes.byref(out), None) == 1
+    assert lib.gs_adam_step(None, 1, 0.9, 0.999, 1e-15, None, None) == 1
+    grp = (G.gs_adam_group * 1)()
+    assert lib.gs_adam_step(grp, 9, 0.9, 0.999, 1e-15, ctypes.c_void_p(16), None) == 1
+    assert lib.gs_read_device_status(None, None, None) == 1
+    bins = G.gs_bins()
+    assert lib.gs_bin_sort(None, 0, cams, 1, ctypes.byref(p), ctypes.byref(bins), None, 0, None) == 1
+    nan_cam = G.camera_array([synth.Camera(float("nan"), 60.0, 32.0, 24.0, 64, 48)])
+    assert lib.gs_total_tiles(nan_cam, 1, 16) == -1

@@ -1,0 +1,357 @@
+"""GPU (libgs, through the C ABI) against the FP64 oracle, stage by stage and
+end to end, on the 64x48 / 256-Gaussian case, ragged images, other tile
+sizes, several views and the degenerate cases.
+
+Tolerances: tile keys, order and ranges bit-exact; rendered colour and depth
+within 1e-4 absolute; gradients within 1e-3 relative L2.  Pixels whose
+threshold decisions (alpha_min, T_cut) lie within 1e-5 relative of the
+threshold may legitimately differ between fp32 and fp64; the oracle reports
+that margin and such pixels are counted (expected: none here)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_02293_gb300 import gs as G
+from paper_2512_02293_gb300 import synth
+from gpu_common import (COLOR_TOL, GRAD_RTOL, MARGIN_EXCUSE, bins_to_numpy, ensure_lib, f32, grads_to_numpy,
+                        image_views, oracle_bins, pack_images, prm_dict, projected_to_device, rel_l2,
+                        round_projection, run_bin_sort)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def _problem(trial=0):
+    g, gt, cam = synth.cfg1_problem(trial)
+    return g, gt, cam
+
+
+def _stage_inputs(g, cams, params):
+    """Oracle projection of every view, rounded to fp32."""
+    prm = prm_dict(params)
+    return [round_projection(oracle.project(g, c, prm)) for c in cams]
+
+
+# ------------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("trial", [0, 1])
+def test_project_matches_oracle(trial):
+    g, _, cam = _problem(trial)
+    params = G.RenderParams()
+    gd = G.Gaussians.from_numpy(g)
+    out = G.Projected.empty(g.n)
+    G.gs_project(gd, [cam], params, out)
+    torch.cuda.synchronize()
+    pr = oracle.project(g, cam, prm_dict(params))
+    tt = out.tiles_touched.cpu().numpy()
+    vis = pr["tiles"] > 0
+    boundary = pr["margin"] < 1e-3
+    np.testing.assert_array_equal((tt > 0)[~boundary], vis[~boundary])
+    both = vis & (tt > 0)
+    np.testing.assert_allclose(out.xy.cpu().numpy()[both], pr["xy"][both], atol=2e-4)
+    co = out.conic_o.cpu().numpy()
+    np.testing.assert_allclose(co[both, :3], pr["conic"][both], rtol=2e-4, atol=1e-6)
+    np.testing.assert_allclose(co[both, 3], pr["opacity"][both], rtol=1e-6)
+    cd = out.rgbd.cpu().numpy()
+    np.testing.assert_allclose(cd[both, :3], pr["rgb"][both], rtol=1e-7)
+    np.testing.assert_allclose(cd[both, 3], pr["depth"][both], rtol=1e-6)
+    ok = both & ~boundary
+    np.testing.assert_array_equal(out.radius.cpu().numpy()[ok], pr["radius"][ok])
+    np.testing.assert_array_equal(out.rect.cpu().numpy()[ok], pr["rect"][ok])
+    np.testing.assert_array_equal(tt[ok], pr["tiles"][ok])
+    assert boundary[vis].sum() == 0   # no rounding-boundary case in this workload
+
+
+# ------------------------------------------------------------------ binning
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_sort_bit_exact(tile):
+    g, _, cam = _problem(0)
+    params = G.RenderParams(tile=tile)
+    prs = _stage_inputs(g, [cam], params)
+    proj = projected_to_device(prs)
+    keys_o, vals_o, ranges_o = oracle_bins(prs, [cam], tile)
+    bins, _ = run_bin_sort(proj, g.n, [cam], params, capacity=len(keys_o) + 17)
+    keys, vals, ranges = bins_to_numpy(bins)
+    assert int(bins.status.item()) == 0
+    np.testing.assert_array_equal(keys, keys_o)
+    np.testing.assert_array_equal(vals, vals_o)
+    np.testing.assert_array_equal(ranges, ranges_o)
+
+
+def test_bin_sort_bit_exact_many_keys_ties_and_views():
+    # Synthetic projected entries over three views of uneven size: ~300k keys,
+    # many equal depths (ties broken by entry index), several sort blocks.
+    rng = np.random.default_rng(7)
+    cams = [synth.identity_camera(640, 480), synth.identity_camera(752, 480), synth.identity_camera(1280, 1024)]
+    params = G.RenderParams(tile=16)
+    n = 20000
+    prs = []
+    for c in cams:
+        tx, ty = (c.width + 15) // 16, (c.height + 15) // 16
+        x0 = rng.integers(0, tx, n); y0 = rng.integers(0, ty, n)
+        rect = np.stack([x0, y0, np.minimum(x0 + rng.integers(1, 5, n), tx), np.minimum(y0 + rng.integers(1, 4, n), ty)], 1)
+        culled = rng.random(n) < 0.2
+        rect[culled] = 0
+        depth = rng.choice(np.linspace(0.3, 8.0, 500), n)     # heavy ties
+        tiles = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
+        prs.append(dict(xy=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)),
+                        depth=f32(depth), rect=rect.astype(np.int32), radius=np.ones(n, np.int32), tiles=tiles))
+    proj = projected_to_device(prs)
+    keys_o, vals_o, ranges_o = oracle_bins(prs, cams, 16)
+    bins, _ = run_bin_sort(proj, n, cams, params, capacity=len(keys_o))
+    keys, vals, ranges = bins_to_numpy(bins)
+    assert len(keys_o) > 100_000
+    np.testing.assert_array_equal(keys, keys_o)
+    np.testing.assert_array_equal(vals, vals_o)
+    np.testing.assert_array_equal(ranges, ranges_o)
+
+
+def test_capacity_overflow_is_reported_not_faulted():
+    g, _, cam = _problem(0)
+    params = G.RenderParams()
+    prs = _stage_inputs(g, [cam], params)
+    proj = projected_to_device(prs)
+    keys_o, _, _ = oracle_bins(prs, [cam], 16)
+    bins, _ = run_bin_sort(proj, g.n, [cam], params, capacity=len(keys_o) // 3)
+    assert G.gs_read_device_status(bins.status) == G.GS_ERR_CAPACITY
+    assert int(bins.num_keys.item()) == len(keys_o)
+    bins2, _ = run_bin_sort(proj, g.n, [cam], params, capacity=len(keys_o))
+    assert G.gs_read_device_status(bins2.status) == 0
+    np.testing.assert_array_equal(bins_to_numpy(bins2)[0], keys_o)
+
+
+# ------------------------------------------------------------------ forward
+
+def _gpu_forward(proj, n, cams, params, capacity):
+    bins, ws = run_bin_sort(proj, n, cams, params, capacity)
+    img = G.Image.empty(G.gs_total_pixels(cams))
+    G.gs_render_fwd(proj, bins, cams, params, img)
+    torch.cuda.synchronize()
+    return bins, ws, img
+
+
+def _compare_images(gpu, ref, what=""):
+    excused = ref["margin"] < MARGIN_EXCUSE
+    n_exc = int(excused.sum())
+    ok = ~excused
+    np.testing.assert_allclose(gpu["color"][:, ok], ref["color"][:, ok], atol=COLOR_TOL, err_msg=what)
+    np.testing.assert_allclose(gpu["depth"][ok], ref["depth"][ok], atol=COLOR_TOL, err_msg=what)
+    np.testing.assert_allclose(gpu["T_final"][ok], ref["T_final"][ok], atol=1e-5, err_msg=what)
+    np.testing.assert_array_equal(gpu["n_contrib"][ok], ref["n_contrib"][ok], err_msg=what)
+    return n_exc
+
+
+@pytest.mark.parametrize("tile,bg", [(16, (0.0, 0.0, 0.0)), (8, (0.2, 0.3, 0.4)), (32, (0.0, 0.0, 0.0))])
+def test_render_fwd_matches_oracle(tile, bg):
+    g, _, cam = _problem(1)
+    params = G.RenderParams(tile=tile, bg=bg)
+    prs = _stage_inputs(g, [cam], params)
+    proj = projected_to_device(prs)
+    m = int(sum(p["tiles"].sum() for p in prs))
+    _, _, img = _gpu_forward(proj, g.n, [cam], params, m + 1)
+    ref = oracle.render_fwd(prs[0], cam, prm_dict(params))
+    assert _compare_images(image_views(img, [cam])[0], ref) == 0
+
+
+def test_render_fwd_ragged_and_multiview():
+    # Image sizes that are not multiples of the tile, several views in one call;
+    # every view must equal its own oracle render.
+    g, _, _ = _problem(2)
+    R, e = synth.look_at([0.2, -0.1, -0.3], [0.0, 0.1, 2.0])
+    cams = [synth.Camera(55.0, 57.0, 35.3, 22.1, 70, 45),
+            synth.Camera(40.0, 40.0, 16.5, 13.0, 33, 26, R, e),
+            synth.Camera(62.0, 62.0, 31.0, 24.0, 64, 48)]
+    for tile in (8, 16):
+        params = G.RenderParams(tile=tile)
+        prs = _stage_inputs(g, cams, params)
+        proj = projected_to_device(prs)
+        m = int(sum(p["tiles"].sum() for p in prs))
+        _, _, img = _gpu_forward(proj, g.n, cams, params, m)
+        for v, (c, p) in enumerate(zip(cams, prs)):
+            ref = oracle.render_fwd(p, c, prm_dict(params))
+            assert _compare_images(image_views(img, cams)[v], ref, f"view {v} tile {tile}") == 0
+
+
+def test_degenerate_inputs():
+    params = G.RenderParams()
+    cam = synth.identity_camera()
+    # no Gaussians at all
+    g0 = synth.random_cloud(0, 1)
+    gd = G.Gaussians.from_numpy(g0)
+    proj = G.Projected.empty(0)
+    G.gs_project(gd, [cam], params, proj)
+    bins, ws = run_bin_sort(proj, 0, [cam], params, 1024)
+    img = G.Image.empty(cam.n_pixels)
+    G.gs_render_fwd(proj, bins, [cam], params, img)
+    torch.cuda.synchronize()
+    assert int(bins.num_keys.item()) == 0
+    v = image_views(img, [cam])[0]
+    assert np.all(v["color"] == 0) and np.all(v["T_final"] == 1) and np.all(v["n_contrib"] == 0)
+    # every Gaussian behind the camera: all culled
+    g = synth.random_cloud(64, 3, box=((-1, 1), (-1, 1), (-3, -1)))
+    gd = G.Gaussians.from_numpy(g)
+    proj = G.Projected.empty(g.n)
+    G.gs_project(gd, [cam], params, proj)
+    torch.cuda.synchronize()
+    assert int(proj.tiles_touched.sum().item()) == 0
+    bins, ws = run_bin_sort(proj, g.n, [cam], params, 1024)
+    G.gs_render_fwd(proj, bins, [cam], params, img)
+    torch.cuda.synchronize()
+    assert int(bins.num_keys.item()) == 0
+    assert np.all(image_views(img, [cam])[0]["T_final"] == 1)
+
+
+# ------------------------------------------------------------------ loss
+
+def test_loss_matches_oracle():
+    rng = np.random.default_rng(4)
+    cams = [synth.identity_camera(64, 48), synth.identity_camera(70, 45)]
+    colors = [rng.random((3, c.height, c.width)) for c in cams]
+    depths = [rng.random((c.height, c.width)) * 3 for c in cams]
+    tcol = [np.where(rng.random(a.shape) < 0.1, f32(a), rng.random(a.shape)) for a in colors]
+    tdep = [np.where(rng.random(a.shape) < 0.3, 0.0, rng.random(a.shape) * 3) for a in depths]
+    c_d, d_d = pack_images(colors, depths)
+    tc_d, td_d = pack_images(tcol, tdep)
+    P = sum(c.n_pixels for c in cams)
+    img = G.Image(c_d, d_d, torch.ones(P, device="cuda"), torch.zeros(P, device="cuda", dtype=torch.int32))
+    dc = torch.empty_like(c_d); dd = torch.empty_like(d_d)
+    terms = torch.empty(len(cams), 2, device="cuda")
+    ws = torch.empty(1024, device="cuda")
+    G.gs_loss(img, tc_d, td_d, cams, 0.9, 0.1, dc, dd, terms, ws)
+    torch.cuda.synchronize()
+    base = 0
+    for v, c in enumerate(cams):
+        t, gdc, gdd = oracle.l1_loss(f32(colors[v]), f32(depths[v]), f32(tcol[v]), f32(tdep[v]), 0.9, 0.1)
+        HW = c.n_pixels
+        np.testing.assert_allclose(terms[v].cpu().numpy(), t, rtol=1e-5)
+        np.testing.assert_allclose(dc[3 * base:3 * (base + HW)].cpu().numpy(), gdc.reshape(-1), rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(dd[base:base + HW].cpu().numpy(), gdd.reshape(-1), rtol=1e-6, atol=1e-12)
+        base += HW
+
+
+# ------------------------------------------------------------------ backward
+
+def _oracle_targets(gt, cams, params):
+    prm = prm_dict(params)
+    out = []
+    for c in cams:
+        img = oracle.render_fwd(oracle.project(gt, c, prm), c, prm)
+        out.append((f32(img["color"]), f32(img["depth"])))
+    return out
+
+
+@pytest.mark.parametrize("sh", [0, 3])
+def test_render_bwd_stagewise_matches_oracle(sh):
+    g, gt, cam = _problem(3)
+    if sh:
+        rng = np.random.default_rng(5)
+        g = synth.GaussianMap(g.mean, g.quat, g.log_scale, g.opacity_logit,
+                              synth.sh3_from_rgb(g.color.astype(np.float64), rng).astype(np.float32))
+    params = G.RenderParams(sh_degree=sh)
+    prm = prm_dict(params)
+    cams = [cam]
+    prs = _stage_inputs(g, cams, params)
+    proj = projected_to_device(prs)
+    m = int(sum(p["tiles"].sum() for p in prs))
+    bins, ws, img = _gpu_forward(proj, g.n, cams, params, m)
+    rng = np.random.default_rng(9)
+    # image gradients of a generic linear functional (no L1 kinks)
+    dcol = [rng.standard_normal((3, c.height, c.width)) * 1e-3 for c in cams]
+    ddep = [rng.standard_normal((c.height, c.width)) * 1e-3 for c in cams]
+    dc, dd = pack_images(dcol, ddep)
+    gd = G.Gaussians.from_numpy(g)
+    grads = G.Grads.empty_like(gd, len(cams))
+    iso = torch.zeros(1, device="cuda")
+    G.gs_render_bwd(gd, proj, bins, img, dc, dd, cams, params, 0.0, grads, iso, ws)
+    torch.cuda.synchronize()
+    g2d_gpu = ws[: g.n * len(cams) * 12].view(-1, 12).cpu().numpy().astype(np.float64)
+    ref2d = oracle.render_bwd(prs[0], cam, prm, f32(dcol[0]), f32(ddep[0]))
+    # diagnostic: per-entry 2D gradients before the projection chain rule
+    assert rel_l2(g2d_gpu[:, 0:2], ref2d["xy"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 2:5], ref2d["conic"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 5], ref2d["opacity"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 6], ref2d["depth"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 7:10], ref2d["rgb"]) < GRAD_RTOL
+    ref = oracle.project_bwd(g, cam, prm, ref2d)
+    got = grads_to_numpy(grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(got[k], ref[k]) < GRAD_RTOL, k
+    assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
+
+
+@pytest.mark.parametrize("lambdas", [(1.0, 1.0, 0.0), (0.9, 0.1, 10.0)])
+def test_full_iteration_end_to_end_matches_oracle(lambdas):
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, cam = _problem(0)
+    params = G.RenderParams()
+    cams = [cam]
+    targets = _oracle_targets(gt, cams, params)
+    tc, td = pack_images([t[0] for t in targets], [t[1] for t in targets])
+    mp = MapParams(lambda_c=lambdas[0], lambda_d=lambdas[1], lambda_iso=lambdas[2])
+    step = MappingStep(G.Gaussians.from_numpy(g), cams, tc, td, params, mp)
+    step.render()
+    step.loss_and_backward()
+    torch.cuda.synchronize()
+    ref = oracle.mapping_loss_and_grads(g, cams, targets, prm_dict(params), lambdas)
+    assert _compare_images(image_views(step.img, cams)[0], ref.images[0]) == 0
+    np.testing.assert_allclose(step.loss_terms.cpu().numpy()[0], ref.loss_terms[0], rtol=1e-5)
+    if lambdas[2]:
+        assert step.iso.item() == pytest.approx(ref.iso, rel=1e-5)
+    got = grads_to_numpy(step.grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(got[k], ref.grads[k]) < GRAD_RTOL, k
+    assert rel_l2(got["pose"][0], ref.pose_grads[0]) < GRAD_RTOL
+
+
+def test_multiview_gradients_are_the_sum_of_single_views():
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, _ = _problem(4)
+    R, e = synth.look_at([0.3, 0.2, -0.2], [0.0, 0.0, 2.0])
+    cams = [synth.Camera(60.0, 60.0, 32.0, 24.0, 64, 48), synth.Camera(45.0, 45.0, 20.0, 15.0, 40, 30, R, e)]
+    params = G.RenderParams()
+    targets = _oracle_targets(gt, cams, params)
+    tc, td = pack_images([t[0] for t in targets], [t[1] for t in targets])
+    mp = MapParams(1.0, 1.0, 0.0)
+    step = MappingStep(G.Gaussians.from_numpy(g), cams, tc, td, params, mp)
+    step.render(); step.loss_and_backward()
+    torch.cuda.synchronize()
+    ref = oracle.mapping_loss_and_grads(g, cams, targets, prm_dict(params), (1.0, 1.0, 0.0))
+    got = grads_to_numpy(step.grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(got[k], ref.grads[k]) < GRAD_RTOL, k
+    for v in range(2):
+        assert rel_l2(got["pose"][v], ref.pose_grads[v]) < GRAD_RTOL
+        assert _compare_images(image_views(step.img, cams)[v], ref.images[v]) == 0
+
+
+# ------------------------------------------------------------------ Adam
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(1)
+    sizes = [1000, 37, 4003]            # includes non-multiple-of-4 tails
+    lrs = [1e-3, 5e-2, 2e-3]
+    b1, b2, eps = np.float32(0.9), np.float32(0.999), np.float32(1e-15)
+    ps = [rng.standard_normal(s).astype(np.float32) for s in sizes]
+    dev = [[torch.from_numpy(p.copy()).cuda(), None, torch.zeros(s, device="cuda"), torch.zeros(s, device="cuda"), lr]
+           for p, s, lr in zip(ps, sizes, lrs)]
+    ref = [[p.astype(np.float64), np.zeros(s), np.zeros(s)] for p, s in zip(ps, sizes)]
+    d_step = torch.zeros(2, device="cuda", dtype=torch.int32)
+    for step in range(1, 6):
+        grads = [rng.standard_normal(s).astype(np.float32) * 10 ** rng.uniform(-6, 0) for s in sizes]
+        for d, gr in zip(dev, grads):
+            d[1] = torch.from_numpy(gr).cuda()
+        G.gs_adam_step([tuple(d) for d in dev], b1, b2, eps, d_step)
+        for r, gr, lr in zip(ref, grads, lrs):
+            oracle.adam(r[0], gr, r[1], r[2], lr, float(b1), float(b2), float(eps), step)
+        torch.cuda.synchronize()
+        assert int(d_step[0].item()) == step and int(d_step[1].item()) == 0
+        for d, r in zip(dev, ref):
+            np.testing.assert_allclose(d[0].cpu().numpy(), r[0], rtol=1e-6, atol=1e-7)
+            np.testing.assert_allclose(d[2].cpu().numpy(), r[1], rtol=1e-5, atol=1e-12)
+            np.testing.assert_allclose(d[3].cpu().numpy(), r[2], rtol=1e-5, atol=1e-20)
