@@ -1,6 +1,6 @@
 // raster.cu -- front-to-back alpha compositing of colour and depth (Sec. 3.3:
-// "the colour of each pixel is calculated by alpha-blending the visible
-// Gaussians"; colour and depth are both rendered) and its backward pass.
+// a pixel's colour is the alpha blend of the Gaussians covering it, and the
+// mapper renders both colour and depth per keyframe) and its backward pass.
 //
 // One CTA per tile, one thread per pixel.  The tile's depth-sorted splats are
 // staged through shared memory in batches (one splat per thread, coalesced
