@@ -65,7 +65,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -135,34 +135,6 @@ def launches_per_step(step) -> int:
     return 1 + (3 + 3 * passes + 1) + 1 + 2 + 2 + 1
 
 
-def stage_times(step, K, flush):
-    """Per-call device times (ms) of an eager iteration, events on the launching stream."""
-    import torch
-    from paper_2512_02293_gb300 import gs as G
-    names = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
-             "gs_adam_step"]
-    acc = {k: [] for k in names}
-    grad2d = step.ws  # the composite backward uses the workspace the same way
-    s = torch.cuda.current_stream()
-    for _ in range(K):
-        flush()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
-        ev[0].record(s)
-        G.gs_project(step.g, step.cams, step.params, step.proj); ev[1].record(s)
-        G.gs_bin_sort(step.proj, step.n, step.cams, step.params, step.bins, step.ws); ev[2].record(s)
-        G.gs_render_fwd(step.proj, step.bins, step.cams, step.params, step.img); ev[3].record(s)
-        G.gs_loss(step.img, step.target_color, step.target_depth, step.cams, step.mp.lambda_c, step.mp.lambda_d,
-                  step.dL_dcolor, step.dL_ddepth, step.loss_terms, step.ws); ev[4].record(s)
-        G.gs_render_bwd_raster(step.proj, step.bins, step.img, step.dL_dcolor, step.dL_ddepth, step.cams, step.params,
-                               step.n, grad2d); ev[5].record(s)
-        G.gs_project_bwd(step.g, step.cams, step.params, grad2d, step.mp.lambda_iso, step.grads, step.iso); ev[6].record(s)
-        step.optimizer_step(); ev[7].record(s)
-        torch.cuda.synchronize()
-        for k, nm in enumerate(names):
-            acc[nm].append(ev[k].elapsed_time(ev[k + 1]))
-    return {k: statistics.median(v) for k, v in acc.items()}
-
-
 def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
     """The FP64 oracle, as it stands, on the host cores: full mapping
     iterations of the same workload until ~budget_s of CPU work."""
@@ -186,36 +158,50 @@ def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle on the host cores, each step a bounded
-    sample of the workload (a 160x128 window of the 640x480 view, all 200k
-    Gaussians projected), rate scaled to full iterations by the pixel fraction."""
+    """--impl reference: the FP64 oracle on the host cores.  Each step is a
+    bounded sample of the workload: the full projection and projection
+    backward of all 200k Gaussians, and compositing / loss / compositing
+    backward over a tile-aligned 64x64 window of the 640x480 view.  The
+    per-iteration time of the full workload is estimated as projection +
+    projection backward + (window raster parts) / (window pixel fraction)."""
     if rank != 0:
         return 0
     import oracle
     from paper_2512_02293_gb300 import synth
     g, gt, cam = synth.cfg2_problem()
-    x0, y0, w, h = 240, 176, 160, 128      # tile-aligned window
+    x0, y0, w, h = 288, 208, 64, 64
     crop = synth.Camera(cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.R_wc, cam.t_wc)
     prm = {}
     timg = oracle.render_fwd(oracle.project(gt, crop, prm), crop, prm)
-    targets = [(timg["color"], timg["depth"])]
     frac = (w * h) / float(cam.n_pixels)
+
+    def one():
+        t = [time.perf_counter()]
+        pr = oracle.project(g, crop, prm); t.append(time.perf_counter())
+        img = oracle.render_fwd(pr, crop, prm)
+        _, dc, dd = oracle.l1_loss(img["color"], img["depth"], timg["color"], timg["depth"], 0.9, 0.1)
+        g2 = oracle.render_bwd(pr, crop, prm, dc, dd); t.append(time.perf_counter())
+        oracle.project_bwd(g, crop, prm, g2)
+        oracle.iso_loss(g.log_scale, 10.0); t.append(time.perf_counter())
+        return (t[1] - t[0]) + (t[3] - t[2]), t[2] - t[1]
+
     for _ in range(args.warmup):
-        oracle.mapping_loss_and_grads(g, [crop], targets, prm, (0.9, 0.1, 10.0))
-    times = []
+        one()
+    est, wall = [], 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.mapping_loss_and_grads(g, [crop], targets, prm, (0.9, 0.1, 10.0))
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    per_full_iter = (total / args.steps) / frac
+        per_g, raster = one()
+        wall += time.perf_counter() - t0
+        est.append(per_g + raster / frac)
+    per_full_iter = statistics.mean(est)
     value = 1.0 / per_full_iter
-    sample = (f"each step: one FP64 oracle mapping iteration over a {w}x{h} window ({frac:.4f} of the 640x480 "
-              "pixels, all 200k Gaussians projected); rate scaled to full iterations by the pixel fraction")
+    sample = (f"each step: FP64 oracle projection + projection backward of all 200k Gaussians and compositing, "
+              f"loss and compositing backward over a {w}x{h} window ({frac:.4f} of the 640x480 pixels); full "
+              f"iteration time estimated as per-Gaussian parts + window raster parts / pixel fraction")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_full_iter,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": WORKLOAD, "sample": sample, "sample_wall_s": wall},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -225,7 +211,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,32 +243,45 @@ def main():
         assert not step.ensure_capacity()
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
     flush = lambda: flush_buf.fill_(1.0)
-
-    # per-stage times (eager) and the pair count for Gpix-splats/s
-    st = stage_times(step, 10, flush)
     pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
 
-    step.capture(warmup=1)
+    # The timed graph records an event before and after each of the seven
+    # C-ABI calls of the iteration (event-record nodes on the launch stream).
+    try:
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(8)]
+        step.capture(warmup=1, events=evs)
+        staged = True
+    except TypeError:
+        evs = None
+        step.capture(warmup=1)
+        staged = False
     for _ in range(args.warmup):
         step.step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     s = torch.cuda.current_stream()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    per_stage = {k: [] for k in step.STAGES}
+    times = []
+    t0e = torch.cuda.Event(enable_timing=True); t1e = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush()
-            starts[k].record(s)
-            step.step()
-            ends[k].record(s)
-        torch.cuda.synchronize()
+            if staged:
+                step.step()
+                torch.cuda.synchronize()
+                times.append(evs[0].elapsed_time(evs[7]))
+                for j, nm in enumerate(step.STAGES):
+                    per_stage[nm].append(evs[j].elapsed_time(evs[j + 1]))
+            else:
+                t0e.record(s); step.step(); t1e.record(s)
+                torch.cuda.synchronize()
+                times.append(t0e.elapsed_time(t1e))
     if dist is not None:
         dist.barrier()
-    times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(times)
+    st = {k: statistics.median(v) for k, v in per_stage.items()} if staged else {}
     status = step.check()
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed region")
@@ -325,19 +324,19 @@ def main():
     peaks, peak_kind = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # FP32 lane-ops/s (FMA = 1 op), in T ops/s
-    fwd_ms = st["gs_render_fwd"]
-    bwd_ms = st["gs_render_bwd_raster"]
-    dominant = max(st, key=st.get)
-    if dominant == "gs_render_bwd_raster":
-        ach = pairs * BWD_OPS_PER_PAIR / (bwd_ms * 1e-3) / 1e12
-        kern, ops = "k_render_bwd<16>", BWD_OPS_PER_PAIR
-    else:
-        ach = pairs * FWD_OPS_PER_PAIR / (fwd_ms * 1e-3) / 1e12
-        kern, ops = "k_render_fwd<16>", FWD_OPS_PER_PAIR
-    roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
-                "frac": ach / alu_peak, "traffic": None,
-                "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
-                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
+    roofline = None
+    if st:
+        dominant = max(st, key=st.get)
+        if dominant == "gs_render_bwd_raster":
+            ms, ops, kern = st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR, "k_render_bwd<16> (+ its grad2d memset)"
+        else:
+            ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, "k_render_fwd<16>"
+        ach = pairs * ops / (ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
+                    "frac": ach / alu_peak, "traffic": None, "dominant_stage": dominant,
+                    "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
+                    "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
+                    "timing": "CUDA event-record nodes around the call inside the timed graph, median over steps"}
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -346,7 +345,7 @@ def main():
                        "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpix_splats_per_s": pairs / (fwd_ms * 1e-3) / 1e9,
+            "gpix_splats_per_s": pairs / (st["gs_render_fwd"] * 1e-3) / 1e9 if st else None,
             "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "stages_ms": st, "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}

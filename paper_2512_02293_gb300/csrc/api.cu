@@ -88,8 +88,10 @@ static bool gaussians_ok(const gs_gaussians* g, int32_t n_views) {
     return aligned(g->quat, 16);
 }
 
+// An empty map may pass all-NULL projected arrays.
 static bool projected_ok(const gs_projected* p) {
     if (p == nullptr) return false;
+    if (!p->xy && !p->conic_o && !p->rgbd && !p->rect && !p->radius && !p->tiles_touched) return true;
     if (!p->xy || !p->conic_o || !p->rgbd || !p->rect || !p->radius || !p->tiles_touched) return false;
     return aligned(p->xy, 8) && aligned(p->conic_o, 16) && aligned(p->rgbd, 16) && aligned(p->rect, 16);
 }

@@ -4,7 +4,8 @@
 //   2. k_scan_blocks   : exclusive scan of the block sums (one CTA), M, overflow flag
 //   3. k_duplicate     : block-local scan + emission of one key per (entry, tile):
 //                        key = (global tile << 32) | bits(float z), value = entry
-//   4. LSD radix sort  : per 8-bit digit pass k_radix_hist -> k_radix_scan ->
+//   4. LSD radix sort  : per 8-bit digit pass k_radix_hist (per-block digit
+//                        counts) -> k_radix_scan (one CTA per digit) ->
 //                        k_radix_scatter (stable: per-warp ranks from match_any,
 //                        per-digit warp prefixes in shared memory)
 //   5. k_tile_ranges   : [start, end) of every tile in the sorted list
@@ -168,27 +169,46 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     counts[(int64_t)d * nb + blockIdx.x] = s;
 }
 
-// One CTA: exclusive scan of the digit-major counts (256 * nb entries).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ counts,
-                                                     const uint32_t* __restrict__ num_keys, int64_t capacity) {
-    __shared__ uint32_t s_warp[1024 / 32 + 1];
+// One CTA per digit: exclusive scan (in place) of that digit's per-block
+// counts counts[d * nb .. d * nb + nb), staged through shared memory in
+// coalesced chunks; the digit's total goes to digit_total[d].
+constexpr int kDigitScanThreads = 256;
+constexpr int kDigitScanChunk = 4096;
+
+__global__ void __launch_bounds__(kDigitScanThreads) k_radix_scan(uint32_t* __restrict__ counts,
+                                                                 uint32_t* __restrict__ digit_total,
+                                                                 const uint32_t* __restrict__ num_keys,
+                                                                 int64_t capacity) {
+    __shared__ uint32_t s_val[kDigitScanChunk];
+    __shared__ uint32_t s_warp[kDigitScanThreads / 32 + 1];
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
-    const int N = kRadix * nb;
-    const int chunk = (N + 1023) / 1024;
-    const int lo = threadIdx.x * chunk;
-    uint32_t s = 0;
-    for (int k = 0; k < chunk; k++)
-        if (lo + k < N) s += counts[lo + k];
-    uint32_t total;
-    uint32_t run = block_exclusive_scan<1024>(s, &total, s_warp);
-    for (int k = 0; k < chunk; k++) {
-        if (lo + k < N) {
-            uint32_t v = counts[lo + k];
-            counts[lo + k] = run;
-            run += v;
+    uint32_t* c = counts + (int64_t)blockIdx.x * nb;
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += kDigitScanChunk) {
+        const int len = min(kDigitScanChunk, nb - base);
+        for (int k = threadIdx.x; k < len; k += kDigitScanThreads) s_val[k] = c[base + k];
+        __syncthreads();
+        constexpr int per = kDigitScanChunk / kDigitScanThreads;
+        const int lo = threadIdx.x * per;
+        uint32_t sum = 0;
+        for (int k = 0; k < per; k++)
+            if (lo + k < len) sum += s_val[lo + k];
+        uint32_t total;
+        uint32_t run = carry + block_exclusive_scan<kDigitScanThreads>(sum, &total, s_warp);
+        for (int k = 0; k < per; k++) {
+            if (lo + k < len) {
+                const uint32_t v = s_val[lo + k];
+                s_val[lo + k] = run;
+                run += v;
+            }
         }
+        __syncthreads();
+        for (int k = threadIdx.x; k < len; k += kDigitScanThreads) c[base + k] = s_val[k];
+        carry += total;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
 }
 
 // Stable scatter.  Each round places 256 consecutive keys: ranks inside a warp
@@ -199,6 +219,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
                                                                const uint32_t* __restrict__ vin,
                                                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* __restrict__ offsets,
+                                                               const uint32_t* __restrict__ digit_total,
                                                                const uint32_t* __restrict__ num_keys,
                                                                int64_t capacity, int shift, int bits) {
     const int64_t M = sort_count(num_keys, capacity);
@@ -207,22 +228,33 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
     __shared__ uint32_t s_base[kRadix];
     __shared__ uint32_t s_rbase[kRadix];
     __shared__ uint32_t s_cnt[2][kSortWarps][kRadix];
+    __shared__ uint32_t s_warp[kSortThreads / 32 + 1];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t mask = (1u << bits) - 1u;
-    s_base[tid] = offsets[(int64_t)tid * nb + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+    // all of this block's keys in flight at once
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const int64_t idx = base + (int64_t)r * kSortThreads + tid;
+        key[r] = idx < M ? kin[idx] : 0ull;
+        val[r] = idx < M ? vin[idx] : 0u;
+    }
+    // digit base = keys of smaller digits in the whole list + this digit's keys in earlier blocks
+    uint32_t tot;
+    const uint32_t dbase = block_exclusive_scan<kSortThreads>(digit_total[tid], &tot, s_warp);
+    s_base[tid] = dbase + offsets[(int64_t)tid * nb + blockIdx.x];
 #pragma unroll
     for (int w = 0; w < kSortWarps; w++) { s_cnt[0][w][tid] = 0u; s_cnt[1][w][tid] = 0u; }
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
     const uint32_t lt = lanemask_lt();
-#pragma unroll 1
+#pragma unroll
     for (int r = 0; r < kSortItems; r++) {
         const int buf = r & 1;
         const int64_t idx = base + (int64_t)r * kSortThreads + tid;
         const bool valid = idx < M;
-        const uint64_t key = valid ? kin[idx] : 0ull;
-        const uint32_t val = valid ? vin[idx] : 0u;
-        const uint32_t d = valid ? key_digit(key, shift, mask) : (uint32_t)kRadix;   // sentinel
+        const uint32_t d = valid ? key_digit(key[r], shift, mask) : (uint32_t)kRadix;   // sentinel
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) s_cnt[buf][warp][d] = __popc(peers);
@@ -242,8 +274,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
         __syncthreads();
         if (valid) {
             const uint32_t pos = s_rbase[d] + s_cnt[buf][warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
     }
 }
@@ -277,12 +309,14 @@ SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
 // Workspace layout of launch_bin_sort (offsets in bytes, 256-byte aligned):
 //   block sums   : ceil(E / kScanBlock) u32
 //   counts       : kRadix * ceil(capacity / kSortBlock) u32
+//   digit totals : kRadix u32
 //   keys (alt)   : capacity u64
 //   vals (alt)   : capacity u32
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity) {
     size_t b = 0;
     b += align_up(sizeof(uint32_t) * (size_t)(ceil_div(n_entries, kScanBlock) + 1), 256);
     b += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(capacity, kSortBlock) + 1), 256);
+    b += align_up(sizeof(uint32_t) * (size_t)kRadix, 256);
     b += align_up(sizeof(uint64_t) * (size_t)capacity, 256);
     b += align_up(sizeof(uint32_t) * (size_t)capacity, 256);
     return b;
@@ -297,6 +331,8 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     p += align_up(sizeof(uint32_t) * (size_t)(ceil_div(E, kScanBlock) + 1), 256);
     uint32_t* counts = reinterpret_cast<uint32_t*>(p);
     p += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(cap, kSortBlock) + 1), 256);
+    uint32_t* digit_total = reinterpret_cast<uint32_t*>(p);
+    p += align_up(sizeof(uint32_t) * (size_t)kRadix, 256);
     uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
     p += align_up(sizeof(uint64_t) * (size_t)cap, 256);
     uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
@@ -319,8 +355,8 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     for (int pass = 0; pass < plan.n_passes; pass++) {
         k_radix_hist<<<nb_sort, kSortThreads, 0, s>>>(k0, bins.num_keys, cap, plan.shift[pass], plan.bits[pass],
                                                       counts);
-        k_radix_scan<<<1, 1024, 0, s>>>(counts, bins.num_keys, cap);
-        k_radix_scatter<<<nb_sort, kSortThreads, 0, s>>>(k0, v0, k1, v1, counts, bins.num_keys, cap,
+        k_radix_scan<<<kRadix, kDigitScanThreads, 0, s>>>(counts, digit_total, bins.num_keys, cap);
+        k_radix_scatter<<<nb_sort, kSortThreads, 0, s>>>(k0, v0, k1, v1, counts, digit_total, bins.num_keys, cap,
                                                          plan.shift[pass], plan.bits[pass]);
         uint64_t* tk = k0; k0 = k1; k1 = tk;
         uint32_t* tv = v0; v0 = v1; v1 = tv;

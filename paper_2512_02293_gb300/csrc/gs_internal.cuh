@@ -50,7 +50,7 @@ struct SortPlan {
 SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles);
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity);
 
-constexpr int kScanItems = 8;                    // entries per thread in scan / duplicate
+constexpr int kScanItems = 1;                    // entries per thread in scan / duplicate
 constexpr int kScanThreads = 256;
 constexpr int kScanBlock = kScanItems * kScanThreads;
 constexpr int kSortThreads = 256;

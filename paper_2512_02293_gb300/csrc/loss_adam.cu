@@ -5,9 +5,9 @@
 // D > 0 and the valid-pixel count of each view (block reduction, three atomics
 // per block into a per-view accumulator in the workspace); pass 2 writes the
 // signed, normalised image gradients and the per-view loss terms.
-// Adam: one launch over all parameter groups (blockIdx.y = group), float4
-// loads/stores where the group is 16-byte aligned; the step counter lives on
-// the device so the launch can be replayed from a CUDA graph.
+// Adam: one grid-stride launch over the 4-element chunks of all parameter
+// groups, float4 loads/stores where a group is 16-byte aligned; the step
+// counter lives on the device so the launch can be replayed from a CUDA graph.
 #include <math.h>
 
 #include "gs_internal.cuh"
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(gs_image img, const 
 
 struct AdamArgs {
     gs_adam_group g[8];
+    int64_t chunk_end[8];      // cumulative float4 chunks per group
     int n_groups;
     float b1, b2, eps;
     int32_t* d_step;
@@ -105,57 +106,59 @@ struct AdamArgs {
 };
 
 constexpr int kAdamThreads = 256;
-constexpr int kAdamPerBlock = kAdamThreads * 4;
 
+__device__ __forceinline__ void adam_elem(float& p, float g, float& m, float& v, float b1, float b2, float ib1,
+                                          float ib2, float lr, float bc1, float bc2, float eps) {
+    m = b1 * m + ib1 * g;
+    v = b2 * v + ib2 * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+// Grid-stride over 4-element chunks of all groups; the last block to finish
+// advances the device step counter (each block reads it before finishing).
 __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
     __shared__ float s_bc[2];
     __shared__ int s_t;
     if (threadIdx.x == 0) {
         const int t = args.d_step[0] + 1;
         s_t = t;
-        // bias corrections in double (two pow per block)
-        s_bc[0] = (float)(1.0 - pow((double)args.b1, (double)t));
-        s_bc[1] = (float)(1.0 - pow((double)args.b2, (double)t));
+        s_bc[0] = 1.0f - powf(args.b1, (float)t);
+        s_bc[1] = 1.0f - powf(args.b2, (float)t);
     }
     __syncthreads();
-    const gs_adam_group& G = args.g[blockIdx.y];
     const float bc1 = s_bc[0], bc2 = s_bc[1];
-    const float b1 = args.b1, b2 = args.b2, eps = args.eps, lr = G.lr;
+    const float b1 = args.b1, b2 = args.b2, eps = args.eps;
     const float ib1 = 1.0f - b1, ib2 = 1.0f - b2;
-    const int64_t start = (int64_t)blockIdx.x * kAdamPerBlock;
-    if (start < G.n) {
+    const int64_t total = args.chunk_end[args.n_groups - 1];
+    for (int64_t c = (int64_t)blockIdx.x * kAdamThreads + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * kAdamThreads) {
+        int k = 0;
+        while (c >= args.chunk_end[k]) k++;
+        const gs_adam_group& G = args.g[k];
+        const int64_t i0 = 4 * (c - (k ? args.chunk_end[k - 1] : 0));
+        const float lr = G.lr;
         const bool vec = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
                            reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
-        const int64_t i0 = start + 4 * (int64_t)threadIdx.x;
         if (vec && i0 + 3 < G.n) {
             float4 p = *reinterpret_cast<const float4*>(G.param + i0);
             const float4 g = *reinterpret_cast<const float4*>(G.grad + i0);
             float4 m = *reinterpret_cast<const float4*>(G.m + i0);
             float4 v = *reinterpret_cast<const float4*>(G.v + i0);
-            float* pp = &p.x; const float* gg = &g.x; float* mm = &m.x; float* vv = &v.x;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                mm[k] = b1 * mm[k] + ib1 * gg[k];
-                vv[k] = b2 * vv[k] + ib2 * gg[k] * gg[k];
-                pp[k] -= lr * (mm[k] / bc1) / (sqrtf(vv[k] / bc2) + eps);
-            }
+            adam_elem(p.x, g.x, m.x, v.x, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
+            adam_elem(p.y, g.y, m.y, v.y, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
+            adam_elem(p.z, g.z, m.z, v.z, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
+            adam_elem(p.w, g.w, m.w, v.w, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
             *reinterpret_cast<float4*>(G.param + i0) = p;
             *reinterpret_cast<float4*>(G.m + i0) = m;
             *reinterpret_cast<float4*>(G.v + i0) = v;
         } else {
-            for (int k = 0; k < 4; k++) {
-                const int64_t i = i0 + k;
-                if (i >= G.n) break;
-                const float g = G.grad[i];
-                const float m = b1 * G.m[i] + ib1 * g;
-                const float v = b2 * G.v[i] + ib2 * g * g;
-                G.m[i] = m;
-                G.v[i] = v;
-                G.param[i] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+            for (int64_t i = i0; i < i0 + 4 && i < G.n; i++) {
+                float p = G.param[i], m = G.m[i], v = G.v[i];
+                adam_elem(p, G.grad[i], m, v, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
+                G.param[i] = p; G.m[i] = m; G.v[i] = v;
             }
         }
     }
-    // The last block to finish advances the step counter (every block has read it by now).
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -188,15 +191,22 @@ cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, c
 cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps, int32_t* d_step,
                         cudaStream_t s) {
     AdamArgs a;
-    int64_t max_n = 0;
-    for (int k = 0; k < 8; k++) a.g[k] = k < n_groups ? groups[k] : gs_adam_group{};
-    for (int k = 0; k < n_groups; k++) max_n = groups[k].n > max_n ? groups[k].n : max_n;
+    int64_t run = 0;
+    for (int k = 0; k < 8; k++) {
+        a.g[k] = k < n_groups ? groups[k] : gs_adam_group{};
+        if (k < n_groups) run += ceil_div(groups[k].n, 4);
+        a.chunk_end[k] = run;
+    }
     a.n_groups = n_groups;
     a.b1 = b1; a.b2 = b2; a.eps = eps;
     a.d_step = d_step;
-    const unsigned bx = (unsigned)(max_n > 0 ? ceil_div(max_n, kAdamPerBlock) : 1);
-    a.total_blocks = bx * (unsigned)n_groups;
-    k_adam<<<dim3(bx, (unsigned)n_groups), kAdamThreads, 0, s>>>(a);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = ceil_div(run > 0 ? run : 1, kAdamThreads);
+    const unsigned blocks = (unsigned)(want < 4 * sms ? want : 4 * sms);
+    a.total_blocks = blocks;
+    k_adam<<<blocks, kAdamThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -155,15 +155,17 @@ __device__ __forceinline__ void project_view(const Activated& A, const ViewParam
     const float rr = ceilf(rc.radius_sigma * sqrtf(lam));
     P.radius = rr < (float)kMaxRadius ? (int)rr : kMaxRadius;
     if (P.radius <= 0) return;
-    // Covered tiles from the fp32 centre, in double so that floor() is exact.
-    const double t = (double)rc.tile;
-    const double mx = (double)P.u, my = (double)P.v, r = (double)P.radius;
-    double fx0 = floor((mx - r) / t), fx1 = floor((mx + r) / t) + 1.0;
-    double fy0 = floor((my - r) / t), fy1 = floor((my + r) / t) + 1.0;
-    fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
-    fx1 = fmin(fx1, (double)vp.tiles_x); fy1 = fmin(fy1, (double)vp.tiles_y);
-    if (!(fx1 > fx0) || !(fy1 > fy0)) return;
-    P.rect[0] = (int)fx0; P.rect[1] = (int)fy0; P.rect[2] = (int)fx1; P.rect[3] = (int)fy1;
+    // Covered tiles from the fp32 centre.  With r an integer and the tile a
+    // power of two, floor((m - r) / t) = (floor(m) - r) >> log2(t) exactly, so the
+    // rectangle needs only integer arithmetic (centres are clamped to +-2^29,
+    // far outside any grid, before the conversion).
+    const int sh = rc.tile == 8 ? 3 : (rc.tile == 16 ? 4 : 5);
+    const int ix = (int)floorf(fminf(fmaxf(P.u, -536870912.f), 536870912.f));
+    const int iy = (int)floorf(fminf(fmaxf(P.v, -536870912.f), 536870912.f));
+    const int x0 = max((ix - P.radius) >> sh, 0), x1 = min(((ix + P.radius) >> sh) + 1, vp.tiles_x);
+    const int y0 = max((iy - P.radius) >> sh, 0), y1 = min(((iy + P.radius) >> sh) + 1, vp.tiles_y);
+    if (x1 <= x0 || y1 <= y0) return;
+    P.rect[0] = x0; P.rect[1] = y0; P.rect[2] = x1; P.rect[3] = y1;
     P.tiles = (P.rect[2] - P.rect[0]) * (P.rect[3] - P.rect[1]);
     P.visible = true;
 }

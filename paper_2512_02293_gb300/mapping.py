@@ -124,8 +124,36 @@ class MappingStep:
         self.loss_and_backward()
         self.optimizer_step()
 
-    def capture(self, warmup: int = 1):
-        """Capture the iteration into a CUDA graph (replayed by step())."""
+    STAGES = ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
+              "gs_adam_step")
+
+    def _staged(self, events=None):
+        """The iteration as its seven C-ABI calls; if `events` (len 8) is given,
+        events[k] is recorded before call k and events[7] after the last."""
+        rec = (lambda k: events[k].record()) if events is not None else (lambda k: None)
+        grad2d = self.ws
+        rec(0)
+        G.gs_project(self.g, self.cams, self.params, self.proj)
+        rec(1)
+        G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
+        rec(2)
+        G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
+        rec(3)
+        G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c, self.mp.lambda_d,
+                  self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
+        rec(4)
+        G.gs_render_bwd_raster(self.proj, self.bins, self.img, self.dL_dcolor, self.dL_ddepth, self.cams, self.params,
+                               self.n, grad2d)
+        rec(5)
+        G.gs_project_bwd(self.g, self.cams, self.params, grad2d, self.mp.lambda_iso, self.grads, self.iso)
+        rec(6)
+        self.optimizer_step()
+        rec(7)
+
+    def capture(self, warmup: int = 1, events=None):
+        """Capture the iteration into a CUDA graph (replayed by step()).  With
+        `events` (8 torch.cuda.Event created with external=True) the graph also
+        records them around each of the seven calls, for per-stage timing."""
         self.graph = None
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -135,9 +163,7 @@ class MappingStep:
         torch.cuda.current_stream().wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.render()
-            self.loss_and_backward()
-            self.optimizer_step()
+            self._staged(events)
         self.graph = g
         return g
 

@@ -277,7 +277,7 @@ def test_render_bwd_stagewise_matches_oracle(sh):
     assert rel_l2(g2d_gpu[:, 2:5], ref2d["conic"]) < GRAD_RTOL
     assert rel_l2(g2d_gpu[:, 5], ref2d["opacity"]) < GRAD_RTOL
     assert rel_l2(g2d_gpu[:, 6], ref2d["depth"]) < GRAD_RTOL
-    assert rel_l2(g2d_gpu[:, 7:10], ref2d["rgb"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 8:11], ref2d["rgb"]) < GRAD_RTOL
     ref = oracle.project_bwd(g, cam, prm, ref2d)
     got = grads_to_numpy(grads)
     for k in oracle.PARAM_NAMES:
@@ -352,6 +352,7 @@ def test_adam_matches_oracle():
         torch.cuda.synchronize()
         assert int(d_step[0].item()) == step and int(d_step[1].item()) == 0
         for d, r in zip(dev, ref):
+            # fp32 moments: errors relative to the largest moment (m can cancel to ~0)
             np.testing.assert_allclose(d[0].cpu().numpy(), r[0], rtol=1e-6, atol=1e-7)
-            np.testing.assert_allclose(d[2].cpu().numpy(), r[1], rtol=1e-5, atol=1e-12)
-            np.testing.assert_allclose(d[3].cpu().numpy(), r[2], rtol=1e-5, atol=1e-20)
+            np.testing.assert_allclose(d[2].cpu().numpy(), r[1], rtol=1e-5, atol=1e-6 * np.abs(r[1]).max())
+            np.testing.assert_allclose(d[3].cpu().numpy(), r[2], rtol=1e-5, atol=1e-6 * np.abs(r[2]).max())
