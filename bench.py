@@ -208,6 +208,18 @@ def run_reference(args, rank, world):
     return 0
 
 
+def whole_job_rate(local_ms: float, steps: int, world: int, dist=None, device=None):
+    """Replicas: every rank ran `steps` iterations; the job's time is the
+    slowest rank's (max over ranks), its rate = all ranks' iterations / time."""
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1000.0), total_ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,11 +297,7 @@ def main():
     status = step.check()
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed region")
-    if dist is not None:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    value, total_ms = whole_job_rate(total_ms, args.steps, world, dist, device)
 
     # end to end through the C ABI with host buffers: H2D of the target image and
     # depth from pinned memory each step, D2H of the loss
@@ -312,11 +320,8 @@ def main():
         h_iso.copy_(e2e_step.iso, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.steps / e2e_s, "unit": "iters/s",
+    e2e_rate, _ = whole_job_rate(e2e_s * 1000.0, args.steps, world, dist, device)
+    e2e = {"value": e2e_rate, "unit": "iters/s",
            "h2d_bytes_per_step": int(h_tc.numel() * 4 + h_td.numel() * 4),
            "d2h_bytes_per_step": int(h_loss.numel() * 4 + h_iso.numel() * 4),
            "note": "eager C-ABI calls (no graph), wall clock, per-step stream sync for the loss read-back"}

