@@ -207,6 +207,28 @@ int32_t gs_loss(const gs_image* img, const float* target_color, const float* tar
                 float* dL_dcolor, float* dL_ddepth, float* loss_terms,
                 void* ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of gs_loss, for callers that cannot allocate device
+ * memory for a workspace (no counterpart in the paper; it exists for such
+ * callers only).  Examples: code that runs while a CUDA graph is being
+ * captured in global mode, where allocation calls are illegal; processes that
+ * must keep a fixed, pre-planned device-memory budget (an embedded or
+ * real-time tracker); a plugin inside a host application that owns the
+ * allocator and forbids other allocations.
+ * Same arguments, outputs and errors as gs_loss, without the workspace: the
+ * per-view accumulators live in a static device array of
+ * GS_NOALLOC_LOSS_MAX_VIEWS x 4 floats that every device loading the library
+ * keeps until exit.  n_views > GS_NOALLOC_LOSS_MAX_VIEWS returns
+ * GS_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc / cudaFree /
+ * allocating library routine).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  Each call zeroes the
+ * accumulators before use, but all calls on a device share them: calls whose
+ * executions overlap on the GPU (different streams, no ordering) race. */
+#define GS_NOALLOC_LOSS_MAX_VIEWS 32
+int32_t gs_loss_noalloc(const gs_image* img, const float* target_color, const float* target_depth,
+                        const gs_camera* cams, int32_t n_views, float lambda_c, float lambda_d,
+                        float* dL_dcolor, float* dL_ddepth, float* loss_terms, void* stream);
+
 /* Backward of gs_render_fwd and gs_project: gradient of the loss whose image
  * gradients are dL_dcolor / dL_ddepth, summed over views, w.r.t. every Gaussian
  * parameter and each view's pose tangent.  The compositing is walked back to

@@ -200,6 +200,22 @@ int32_t gs_loss(const gs_image* img, const float* target_color, const float* tar
                                    loss_terms, ws, static_cast<cudaStream_t>(stream)));
 }
 
+int32_t gs_loss_noalloc(const gs_image* img, const float* target_color, const float* target_depth,
+                        const gs_camera* cams, int32_t n_views, float lambda_c, float lambda_d, float* dL_dcolor,
+                        float* dL_ddepth, float* loss_terms, void* stream) {
+    if (!image_ok(img) || !target_color || !target_depth || !dL_dcolor || !dL_ddepth || !loss_terms)
+        return GS_ERR_INVALID_ARG;
+    if (!isfinite(lambda_c) || !isfinite(lambda_d)) return GS_ERR_INVALID_ARG;
+    if (n_views < 1 || n_views > GS_NOALLOC_LOSS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, 16, &views)) return GS_ERR_INVALID_ARG;
+    float* scratch = nullptr;
+    if (noalloc_loss_scratch(&scratch) != cudaSuccess) return GS_ERR_CUDA;
+    // launch_loss zeroes the accumulators it uses before accumulating
+    return cuda_status(launch_loss(*img, target_color, target_depth, views, lambda_c, lambda_d, dL_dcolor, dL_ddepth,
+                                   loss_terms, scratch, static_cast<cudaStream_t>(stream)));
+}
+
 int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, const gs_image* img,
                              const float* dL_dcolor, const float* dL_ddepth, const gs_camera* cams, int32_t n_views,
                              const gs_render_params* params, int64_t n, float* grad2d, void* stream) {

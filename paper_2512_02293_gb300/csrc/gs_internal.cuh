@@ -78,6 +78,7 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
 cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s);
+cudaError_t noalloc_loss_scratch(float** out);
 cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps,
                         int32_t* d_step, cudaStream_t s);
 

@@ -10,6 +10,8 @@
 // counter lives on the device so the launch can be replayed from a CUDA graph.
 #include <math.h>
 
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -186,6 +188,36 @@ cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, c
     k_loss_reduce<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc);
     k_loss_grad<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc, lc, ld, dc, dd, terms);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ allocation-free loss variant
+//
+// gs_loss_noalloc keeps the per-view accumulators that gs_loss places in the
+// caller's workspace in this file-scope device array instead.  Every device
+// that loads the library holds it (4 floats per view, GS_NOALLOC_LOSS_MAX_VIEWS
+// views, 512 bytes) until the process exits.  Host code cannot use the array's
+// name as a device address, so its address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached.
+static __device__ __align__(256) float g_noalloc_loss_scratch[4 * GS_NOALLOC_LOSS_MAX_VIEWS];
+
+constexpr int kMaxDevices = 64;
+static float* g_noalloc_loss_ptr[kMaxDevices] = {};
+static std::mutex g_noalloc_loss_mutex;
+
+cudaError_t noalloc_loss_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_loss_mutex);
+    if (g_noalloc_loss_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_loss_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_loss_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_loss_ptr[dev];
+    return cudaSuccess;
 }
 
 cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps, int32_t* d_step,

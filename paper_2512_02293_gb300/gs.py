@@ -79,7 +79,8 @@ class gs_adam_group(ctypes.Structure):
 
 
 EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pixels", "gs_workspace_size",
-           "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd", "gs_render_bwd_raster",
+           "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_loss_noalloc", "gs_render_bwd",
+           "gs_render_bwd_raster",
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status"]
 
 
@@ -112,6 +113,8 @@ def load_library(path: str | None = None):
     lib.gs_loss.restype = ctypes.c_int32
     lib.gs_loss.argtypes = [V, V, V, V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, V, V, V, V,
                             ctypes.c_size_t, V]
+    lib.gs_loss_noalloc.restype = ctypes.c_int32
+    lib.gs_loss_noalloc.argtypes = [V, V, V, V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, V, V, V, V]
     lib.gs_render_bwd.restype = ctypes.c_int32
     lib.gs_render_bwd.argtypes = [V, V, V, V, V, V, V, ctypes.c_int32, V, ctypes.c_float, V, V, V, ctypes.c_size_t, V]
     lib.gs_render_bwd_raster.restype = ctypes.c_int32
@@ -346,6 +349,15 @@ def gs_loss(img: Image, target_color, target_depth, cams, lambda_c: float, lambd
     _check(load_library().gs_loss(ctypes.byref(im), _ptr(target_color), _ptr(target_depth), arr, len(cams),
                                   float(lambda_c), float(lambda_d), _ptr(dL_dcolor), _ptr(dL_ddepth), _ptr(loss_terms),
                                   _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "gs_loss")
+
+
+def gs_loss_noalloc(img: Image, target_color, target_depth, cams, lambda_c: float, lambda_d: float, dL_dcolor,
+                    dL_ddepth, loss_terms, stream=None):
+    """gs_loss without a workspace (for callers that cannot allocate one); see gs.h."""
+    arr = camera_array(cams); im = img.struct()
+    _check(load_library().gs_loss_noalloc(ctypes.byref(im), _ptr(target_color), _ptr(target_depth), arr, len(cams),
+                                          float(lambda_c), float(lambda_d), _ptr(dL_dcolor), _ptr(dL_ddepth),
+                                          _ptr(loss_terms), _stream(stream)), "gs_loss_noalloc")
 
 
 def gs_render_bwd(g: Gaussians, proj: Projected, bins: Bins, img: Image, dL_dcolor, dL_ddepth, cams,
