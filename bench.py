@@ -6,8 +6,9 @@ One step = one full mapping iteration of the plain single-view workload:
 project -> bin/sort -> composite colour+depth -> L1 colour/depth + isotropic
 loss -> backward to every parameter and the pose -> Adam.  The iteration is
 replayed from a CUDA graph; inputs (map, target image and depth) are resident
-in HBM when the timed region starts, and L2 is flushed (a 256 MiB write)
-between timed iterations, outside the per-step events.
+in HBM when the timed region starts; before each timed iteration the map and
+Adam state are restored to the same starting values and L2 is flushed (a
+256 MiB write), both outside the per-step events.
 
 Metric: mapping iterations/s (whole job; N GPUs run independent replicas,
 weak scaling).  Also reported: Gpix-splats/s (sum over pixels of the splats a
@@ -109,7 +110,7 @@ def build_problem(device):
     from paper_2512_02293_gb300 import gs as G, synth
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
     g, gt, cam = synth.cfg2_problem()
-    params = G.RenderParams(tile=16)
+    params = G.RenderParams(tile=16)   # the target render; the timed step's tile is autotuned
     mp = MapParams()
     P = cam.n_pixels
     # target = render of the perturbed map (input preparation, not timed)
@@ -119,20 +120,19 @@ def build_problem(device):
     torch.cuda.synchronize()
     tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
     del tstep
-    step = MappingStep(G.Gaussians.from_numpy(g, device), [cam], tc, td, params, mp)
+    from paper_2512_02293_gb300.mapping import autotune_tile
+    gd = G.Gaussians.from_numpy(g, device)
+    params, tune = autotune_tile(gd, [cam], tc, td, params, mp)
+    step = MappingStep(gd, [cam], tc, td, params, mp)
+    step.tune = tune
     return g, gt, cam, params, mp, step, tc, td
 
 
 def launches_per_step(step) -> int:
-    from paper_2512_02293_gb300 import gs as G
-    tiles = step.total_tiles
-    tb = 0
-    while (1 << tb) < tiles:
-        tb += 1
-    passes = math.ceil((31 + tb) / 8)
-    # project 1; bin/sort: reduce + block scan + duplicate + 3 per pass + ranges;
-    # render 1; loss 2; backward raster 1 + projection backward 1; adam 1
-    return 1 + (3 + 3 * passes + 1) + 1 + 2 + 2 + 1
+    """Kernels of ours per iteration: project 1; bin/sort 4 (tile count, tile
+    scan, tile scatter, segment sort); render 1; loss 2; backward raster 1 +
+    projection backward 1; Adam 1."""
+    return 1 + 4 + 1 + 2 + 2 + 1
 
 
 def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
@@ -272,6 +272,17 @@ def main():
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
+    # Every timed step starts from the same map and optimiser state (restored
+    # outside the step's events), so each step does identical work.
+    pristine = [t.clone() for t in step.g.tensors()]
+
+    def restore():
+        for t, p0 in zip(step.g.tensors(), pristine):
+            t.copy_(p0)
+        for t in step.m + step.v:
+            t.zero_()
+        step.d_step.zero_()
+
     s = torch.cuda.current_stream()
     per_stage = {k: [] for k in step.STAGES}
     times = []
@@ -279,6 +290,7 @@ def main():
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for k in range(args.steps):
+            restore()
             flush()
             if staged:
                 step.step()
@@ -333,9 +345,9 @@ def main():
     if st:
         dominant = max(st, key=st.get)
         if dominant == "gs_render_bwd_raster":
-            ms, ops, kern = st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR, "k_render_bwd<16> (+ its grad2d memset)"
+            ms, ops, kern = st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR, f"k_render_bwd<{params.tile}> (+ its grad2d memset)"
         else:
-            ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, "k_render_fwd<16>"
+            ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"
         ach = pairs * ops / (ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
                     "frac": ach / alu_peak, "traffic": None, "dominant_stage": dominant,
@@ -346,9 +358,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480", "tile": 16,
+            "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480",
+                       "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
                        "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
+                       "per_step_state": "map and Adam state restored before every timed step (identical work per step)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpix_splats_per_s": pairs / (st["gs_render_fwd"] * 1e-3) / 1e9 if st else None,
             "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),

@@ -149,7 +149,7 @@ size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, cons
     Views v;
     if (n < 0 || key_capacity < 0 || !params_ok(params) || !make_views(cams, n_views, params->tile, &v)) return 0;
     const int64_t E = n * n_views;
-    size_t a = bin_sort_workspace(E, key_capacity);
+    size_t a = bin_sort_workspace(E, key_capacity, v.total_tiles);
     size_t b = loss_workspace(n_views);
     size_t c = render_bwd_workspace(E);
     size_t m = a > b ? a : b;
@@ -172,7 +172,7 @@ int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, 
     if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
     if (n * (int64_t)n_views >= (1ll << 31)) return GS_ERR_INVALID_ARG;
     if (n > 0 && !projected_ok(proj)) return GS_ERR_INVALID_ARG;
-    const size_t need = bin_sort_workspace(n * n_views, bins->key_capacity);
+    const size_t need = bin_sort_workspace(n * n_views, bins->key_capacity, views.total_tiles);
     if (ws == nullptr || ws_bytes < need || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
     SortPlan plan = make_sort_plan(bins->key_capacity, views.total_tiles);
     return cuda_status(launch_bin_sort(*proj, n, views, plan, *bins, ws, static_cast<cudaStream_t>(stream)));

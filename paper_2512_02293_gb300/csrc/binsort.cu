@@ -1,13 +1,19 @@
 // binsort.cu -- tile binning and depth sort of the projected splats.
 //
-//   1. k_scan_reduce   : per-block sums of tiles_touched
+//   1. k_scan_reduce   : per-block sums of tiles_touched (256 entries a block)
 //   2. k_scan_blocks   : exclusive scan of the block sums (one CTA), M, overflow flag
 //   3. k_duplicate     : block-local scan + emission of one key per (entry, tile):
-//                        key = (global tile << 32) | bits(float z), value = entry
-//   4. LSD radix sort  : per 8-bit digit pass k_radix_hist (per-block digit
-//                        counts) -> k_radix_scan (one CTA per digit) ->
+//                        key = (global tile << 32) | bits(float z), value = entry.
+//                        Entries covering many tiles are emitted by their whole
+//                        warp, so a large splat near the camera does not leave
+//                        one thread writing hundreds of keys alone.
+//   4. LSD radix sort  : passes of up to 9-bit digits over the 31 depth bits and
+//                        the tile bits; each pass is k_radix_hist (per-block
+//                        digit counts) -> k_radix_scan (one CTA per digit) ->
 //                        k_radix_scatter (stable: per-warp ranks from match_any,
-//                        per-digit warp prefixes in shared memory)
+//                        per-digit warp prefixes in shared memory).  Blocks hold
+//                        1024 keys, so even a few hundred thousand keys give
+//                        several blocks per SM and short serial chains.
 //   5. k_tile_ranges   : [start, end) of every tile in the sorted list
 //
 // The key's bit 31 (the sign of z > 0) is always 0, so the sort runs over the
@@ -18,6 +24,18 @@
 
 namespace gs {
 namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 1;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 4;
+constexpr int kSortBlock = kSortThreads * kSortItems;
+constexpr int kMaxDigitBits = 9;
+constexpr int kRadixMax = 1 << kMaxDigitBits;            // buckets of the widest digit
+constexpr int kDigitsPerThread = kRadixMax / kSortThreads;
+constexpr int kBigEntry = 8;                             // keys an entry emits by itself
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -58,11 +76,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt, int64_t E,
                                                              uint32_t* __restrict__ block_sums) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++)
-        if (base + k < E) s += tt[base + k];
+    for (int k = 0; k < kScanItems; k++) {
+        const int64_t e = (int64_t)blockIdx.x * kScanBlock + (int64_t)k * kScanThreads + threadIdx.x;
+        if (e < E) s += tt[e];
+    }
     uint32_t total;
     block_exclusive_scan<kScanThreads>(s, &total, s_warp);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
@@ -93,39 +112,63 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blo
     }
 }
 
+// Emission of the keys of one entry: key = (tile << 32) | z bits, value =
+// entry, written at [off, off + cnt) in row-major order over its rectangle.
+__device__ __forceinline__ void emit_keys(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
+                                          uint32_t off, int k0, int k1, int kstep, int4 r, int tb, int tx,
+                                          uint32_t zbits, uint32_t e) {
+    const int w = r.z - r.x;
+    for (int k = k0; k < k1; k += kstep) {
+        const int64_t pos = (int64_t)off + k;
+        if (pos < capacity) {
+            const uint64_t g = (uint64_t)(tb + (r.y + k / w) * tx + r.x + k % w);
+            keys[pos] = (g << 32) | (uint64_t)zbits;
+            vals[pos] = e;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_duplicate(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
                                                            const float4* __restrict__ rgbd, int64_t E, int64_t n,
                                                            const uint32_t* __restrict__ block_offsets, Views views,
                                                            int64_t capacity, uint64_t* __restrict__ keys,
                                                            uint32_t* __restrict__ vals) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    uint32_t cnt[kScanItems];
-    uint32_t s = 0;
-#pragma unroll
+    const int lane = threadIdx.x & 31;
+    uint32_t carry = block_offsets[blockIdx.x];
     for (int k = 0; k < kScanItems; k++) {
-        cnt[k] = base + k < E ? tt[base + k] : 0u;
-        s += cnt[k];
-    }
-    uint32_t total;
-    uint32_t off = block_offsets[blockIdx.x] + block_exclusive_scan<kScanThreads>(s, &total, s_warp);
-#pragma unroll 1
-    for (int k = 0; k < kScanItems; k++) {
-        if (cnt[k] == 0) continue;
-        const int64_t e = base + k;
-        const int v = (int)(e / n);
-        const int4 r = rect[e];
-        const uint32_t zbits = __float_as_uint(rgbd[e].w);
-        const int tb = views.v[v].tile_base, tx = views.v[v].tiles_x;
-        for (int y = r.y; y < r.w; y++) {
-            for (int x = r.x; x < r.z; x++) {
-                if ((int64_t)off < capacity) {
-                    const uint64_t g = (uint64_t)(tb + y * tx + x);
-                    keys[off] = (g << 32) | (uint64_t)zbits;
-                    vals[off] = (uint32_t)e;
-                }
-                off++;
-            }
+        const int64_t e = (int64_t)blockIdx.x * kScanBlock + (int64_t)k * kScanThreads + threadIdx.x;
+        const uint32_t cnt = e < E ? tt[e] : 0u;
+        uint32_t total;
+        const uint32_t off = carry + block_exclusive_scan<kScanThreads>(cnt, &total, s_warp);
+        carry += total;
+        int4 r = make_int4(0, 0, 1, 1);
+        int tb = 0, tx = 1;
+        uint32_t zbits = 0;
+        if (cnt > 0) {
+            const int v = (int)(e / n);
+            r = rect[e];
+            zbits = __float_as_uint(rgbd[e].w);
+            tb = views.v[v].tile_base;
+            tx = views.v[v].tiles_x;
+        }
+        if (cnt > 0 && cnt <= (uint32_t)kBigEntry)
+            emit_keys(keys, vals, capacity, off, 0, (int)cnt, 1, r, tb, tx, zbits, (uint32_t)e);
+        uint32_t big = __ballot_sync(0xffffffffu, cnt > (uint32_t)kBigEntry);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            int4 br;
+            br.x = __shfl_sync(0xffffffffu, r.x, src);
+            br.y = __shfl_sync(0xffffffffu, r.y, src);
+            br.z = __shfl_sync(0xffffffffu, r.z, src);
+            br.w = __shfl_sync(0xffffffffu, r.w, src);
+            const uint32_t boff = __shfl_sync(0xffffffffu, off, src);
+            const int bcnt = (int)__shfl_sync(0xffffffffu, cnt, src);
+            const int btb = __shfl_sync(0xffffffffu, tb, src), btx = __shfl_sync(0xffffffffu, tx, src);
+            const uint32_t bz = __shfl_sync(0xffffffffu, zbits, src);
+            const uint32_t be = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)e, src);
+            emit_keys(keys, vals, capacity, boff, lane, bcnt, 32, br, btb, btx, bz, be);
         }
     }
 }
@@ -141,8 +184,6 @@ __device__ __forceinline__ int64_t sort_count(const uint32_t* num_keys, int64_t 
     return m < capacity ? m : capacity;
 }
 
-constexpr int kSortWarps = kSortThreads / 32;
-
 // Per-block digit counts, stored digit-major: counts[d * nb + b].
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
                                                             const uint32_t* __restrict__ num_keys, int64_t capacity,
@@ -150,71 +191,70 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
     if ((int)blockIdx.x >= nb) return;
-    __shared__ uint32_t h[kSortWarps][kRadix];
-    for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&h[0][0])[k] = 0u;
+    __shared__ uint32_t h[kSortWarps][kRadixMax];
+    const int radix = 1 << bits;
+    for (int k = threadIdx.x; k < kSortWarps * kRadixMax; k += kSortThreads) (&h[0][0])[k] = 0u;
     __syncthreads();
-    const uint32_t mask = (1u << bits) - 1u;
+    const uint32_t mask = (uint32_t)radix - 1u;
     const int warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-#pragma unroll 4
+    uint64_t key[kSortItems];
+#pragma unroll
     for (int r = 0; r < kSortItems; r++) {
         const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (idx < M) atomicAdd(&h[warp][key_digit(keys[idx], shift, mask)], 1u);
+        key[r] = idx < M ? keys[idx] : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+        if (idx < M) atomicAdd(&h[warp][key_digit(key[r], shift, mask)], 1u);
     }
     __syncthreads();
-    const int d = threadIdx.x;
-    uint32_t s = 0;
+    for (int d = threadIdx.x; d < radix; d += kSortThreads) {
+        uint32_t s = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; w++) s += h[w][d];
-    counts[(int64_t)d * nb + blockIdx.x] = s;
+        for (int w = 0; w < kSortWarps; w++) s += h[w][d];
+        counts[(int64_t)d * nb + blockIdx.x] = s;
+    }
 }
 
-// One CTA per digit: exclusive scan (in place) of that digit's per-block
-// counts counts[d * nb .. d * nb + nb), staged through shared memory in
-// coalesced chunks; the digit's total goes to digit_total[d].
+// One warp per digit: exclusive scan (in place) of that digit's per-block
+// counts counts[d * nb .. d * nb + nb) with shuffle scans over chunks of 32 and
+// a running carry; the digit's total goes to digit_total[d].
 constexpr int kDigitScanThreads = 256;
-constexpr int kDigitScanChunk = 4096;
+constexpr int kDigitScanWarps = kDigitScanThreads / 32;
 
 __global__ void __launch_bounds__(kDigitScanThreads) k_radix_scan(uint32_t* __restrict__ counts,
                                                                  uint32_t* __restrict__ digit_total,
                                                                  const uint32_t* __restrict__ num_keys,
-                                                                 int64_t capacity) {
-    __shared__ uint32_t s_val[kDigitScanChunk];
-    __shared__ uint32_t s_warp[kDigitScanThreads / 32 + 1];
+                                                                 int64_t capacity, int radix) {
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * kDigitScanWarps + (threadIdx.x >> 5);
+    if (d >= radix) return;
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
-    uint32_t* c = counts + (int64_t)blockIdx.x * nb;
+    uint32_t* c = counts + (int64_t)d * nb;
     uint32_t carry = 0;
-    for (int base = 0; base < nb; base += kDigitScanChunk) {
-        const int len = min(kDigitScanChunk, nb - base);
-        for (int k = threadIdx.x; k < len; k += kDigitScanThreads) s_val[k] = c[base + k];
-        __syncthreads();
-        constexpr int per = kDigitScanChunk / kDigitScanThreads;
-        const int lo = threadIdx.x * per;
-        uint32_t sum = 0;
-        for (int k = 0; k < per; k++)
-            if (lo + k < len) sum += s_val[lo + k];
-        uint32_t total;
-        uint32_t run = carry + block_exclusive_scan<kDigitScanThreads>(sum, &total, s_warp);
-        for (int k = 0; k < per; k++) {
-            if (lo + k < len) {
-                const uint32_t v = s_val[lo + k];
-                s_val[lo + k] = run;
-                run += v;
-            }
+    for (int i0 = 0; i0 < nb; i0 += 32) {
+        const int i = i0 + lane;
+        const uint32_t x = i < nb ? c[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < len; k += kDigitScanThreads) c[base + k] = s_val[k];
-        carry += total;
-        __syncthreads();
+        if (i < nb) c[i] = carry + inc - x;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
-    if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
+    if (lane == 0) digit_total[d] = carry;
 }
 
 // Stable scatter.  Each round places 256 consecutive keys: ranks inside a warp
 // come from match_any, the offsets of earlier warps from a per-digit prefix in
 // shared memory, and s_base carries the digit's running position across rounds.
-// Counts are double-buffered so that a round needs two barriers.
+// Counts are double-buffered so that a round needs two barriers.  Thread t owns
+// digits t and t + 256 of the bookkeeping.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -225,14 +265,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
     if ((int)blockIdx.x >= nb) return;
-    __shared__ uint32_t s_base[kRadix];
-    __shared__ uint32_t s_rbase[kRadix];
-    __shared__ uint32_t s_cnt[2][kSortWarps][kRadix];
+    __shared__ uint32_t s_base[kRadixMax];
+    __shared__ uint32_t s_rbase[kRadixMax];
+    __shared__ uint32_t s_cnt[2][kSortWarps][kRadixMax];
     __shared__ uint32_t s_warp[kSortThreads / 32 + 1];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t mask = (1u << bits) - 1u;
+    const int radix = 1 << bits;
+    const uint32_t mask = (uint32_t)radix - 1u;
     const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    // all of this block's keys in flight at once
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
 #pragma unroll
@@ -242,11 +282,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
         val[r] = idx < M ? vin[idx] : 0u;
     }
     // digit base = keys of smaller digits in the whole list + this digit's keys in earlier blocks
-    uint32_t tot;
-    const uint32_t dbase = block_exclusive_scan<kSortThreads>(digit_total[tid], &tot, s_warp);
-    s_base[tid] = dbase + offsets[(int64_t)tid * nb + blockIdx.x];
+    uint32_t dt[kDigitsPerThread];
+    uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; w++) { s_cnt[0][w][tid] = 0u; s_cnt[1][w][tid] = 0u; }
+    for (int q = 0; q < kDigitsPerThread; q++) {
+        const int d = tid * kDigitsPerThread + q;
+        dt[q] = d < radix ? digit_total[d] : 0u;
+        sum += dt[q];
+    }
+    uint32_t tot;
+    uint32_t run0 = block_exclusive_scan<kSortThreads>(sum, &tot, s_warp);
+#pragma unroll
+    for (int q = 0; q < kDigitsPerThread; q++) {
+        const int d = tid * kDigitsPerThread + q;
+        if (d < radix) s_base[d] = run0 + offsets[(int64_t)d * nb + blockIdx.x];
+        run0 += dt[q];
+    }
+    for (int k = tid; k < 2 * kSortWarps * kRadixMax; k += kSortThreads) (&s_cnt[0][0][0])[k] = 0u;
     __syncthreads();
     const uint32_t lt = lanemask_lt();
 #pragma unroll
@@ -254,22 +306,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
         const int buf = r & 1;
         const int64_t idx = base + (int64_t)r * kSortThreads + tid;
         const bool valid = idx < M;
-        const uint32_t d = valid ? key_digit(key[r], shift, mask) : (uint32_t)kRadix;   // sentinel
+        const uint32_t d = valid ? key_digit(key[r], shift, mask) : (uint32_t)kRadixMax;   // sentinel
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) s_cnt[buf][warp][d] = __popc(peers);
         __syncthreads();
-        {
+        for (int dd = tid; dd < radix; dd += kSortThreads) {
             uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < kSortWarps; w++) {
-                const uint32_t c = s_cnt[buf][w][tid];
-                s_cnt[buf][w][tid] = run;
+                const uint32_t c = s_cnt[buf][w][dd];
+                s_cnt[buf][w][dd] = run;
                 run += c;
-                s_cnt[buf ^ 1][w][tid] = 0u;
+                s_cnt[buf ^ 1][w][dd] = 0u;
             }
-            s_rbase[tid] = s_base[tid];
-            s_base[tid] += run;
+            s_rbase[dd] = s_base[dd];
+            s_base[dd] += run;
         }
         __syncthreads();
         if (valid) {
@@ -295,31 +347,25 @@ __global__ void k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t*
 SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
     SortPlan p;
     p.capacity = key_capacity;
-    int tile_bits = 0;
-    while ((1ll << tile_bits) < (int64_t)total_tiles) tile_bits++;
-    const int bits = 31 + tile_bits;
-    p.n_passes = (bits + kRadixBits - 1) / kRadixBits;
-    for (int k = 0; k < p.n_passes; k++) {
-        p.shift[k] = k * kRadixBits;
-        p.bits[k] = (bits - k * kRadixBits) < kRadixBits ? bits - k * kRadixBits : kRadixBits;
-    }
+    p.total_tiles = total_tiles;
     return p;
 }
 
 // Workspace layout of launch_bin_sort (offsets in bytes, 256-byte aligned):
 //   block sums   : ceil(E / kScanBlock) u32
-//   counts       : kRadix * ceil(capacity / kSortBlock) u32
-//   digit totals : kRadix u32
+//   counts       : kRadixMax * ceil(capacity / kSortBlock) u32
+//   digit totals : kRadixMax u32
 //   keys (alt)   : capacity u64
 //   vals (alt)   : capacity u32
-size_t bin_sort_workspace(int64_t n_entries, int64_t capacity) {
-    size_t b = 0;
-    b += align_up(sizeof(uint32_t) * (size_t)(ceil_div(n_entries, kScanBlock) + 1), 256);
-    b += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(capacity, kSortBlock) + 1), 256);
-    b += align_up(sizeof(uint32_t) * (size_t)kRadix, 256);
-    b += align_up(sizeof(uint64_t) * (size_t)capacity, 256);
-    b += align_up(sizeof(uint32_t) * (size_t)capacity, 256);
-    return b;
+static size_t ws_block_sums(int64_t E) { return align_up(sizeof(uint32_t) * (size_t)(ceil_div(E, kScanBlock) + 1), 256); }
+static size_t ws_counts(int64_t cap) {
+    return align_up(sizeof(uint32_t) * (size_t)kRadixMax * (size_t)(ceil_div(cap, kSortBlock) + 1), 256);
+}
+
+size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles) {
+    (void)total_tiles;
+    return ws_block_sums(n_entries) + ws_counts(capacity) + align_up(sizeof(uint32_t) * kRadixMax, 256) +
+           align_up(sizeof(uint64_t) * (size_t)capacity, 256) + align_up(sizeof(uint32_t) * (size_t)capacity, 256);
 }
 
 cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& views, const SortPlan& plan,
@@ -328,36 +374,48 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     const int64_t cap = plan.capacity;
     char* p = static_cast<char*>(ws);
     uint32_t* block_sums = reinterpret_cast<uint32_t*>(p);
-    p += align_up(sizeof(uint32_t) * (size_t)(ceil_div(E, kScanBlock) + 1), 256);
+    p += ws_block_sums(E);
     uint32_t* counts = reinterpret_cast<uint32_t*>(p);
-    p += align_up(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ceil_div(cap, kSortBlock) + 1), 256);
+    p += ws_counts(cap);
     uint32_t* digit_total = reinterpret_cast<uint32_t*>(p);
-    p += align_up(sizeof(uint32_t) * (size_t)kRadix, 256);
+    p += align_up(sizeof(uint32_t) * kRadixMax, 256);
     uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
     p += align_up(sizeof(uint64_t) * (size_t)cap, 256);
     uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
 
     cudaError_t err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)views.total_tiles, s);
     if (err != cudaSuccess) return err;
-    const int nb_scan = (int)ceil_div(E, kScanBlock);
     if (E == 0) return cudaMemsetAsync(bins.num_keys, 0, sizeof(uint32_t), s);
+    // passes over the compacted key (tile << 31 | z bits), digits of at most 9 bits
+    int tile_bits = 0;
+    while ((1ll << tile_bits) < (int64_t)plan.total_tiles) tile_bits++;
+    const int bits = 31 + tile_bits;
+    const int n_passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    int width[8], shift[8];
+    for (int k = 0, sh = 0; k < n_passes; k++) {
+        width[k] = bits / n_passes + (k < bits % n_passes ? 1 : 0);
+        shift[k] = sh;
+        sh += width[k];
+    }
+    const int nb_scan = (int)ceil_div(E, kScanBlock);
     k_scan_reduce<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, E, block_sums);
     k_scan_blocks<<<1, 1024, 0, s>>>(block_sums, nb_scan, bins.num_keys, cap, bins.status);
     // The duplicated list goes into the buffer that makes the last pass land in bins.keys.
-    uint64_t* k0 = (plan.n_passes % 2 == 0) ? bins.keys : keys_alt;
-    uint32_t* v0 = (plan.n_passes % 2 == 0) ? bins.vals : vals_alt;
-    uint64_t* k1 = (plan.n_passes % 2 == 0) ? keys_alt : bins.keys;
-    uint32_t* v1 = (plan.n_passes % 2 == 0) ? vals_alt : bins.vals;
+    uint64_t* k0 = (n_passes % 2 == 0) ? bins.keys : keys_alt;
+    uint32_t* v0 = (n_passes % 2 == 0) ? bins.vals : vals_alt;
+    uint64_t* k1 = (n_passes % 2 == 0) ? keys_alt : bins.keys;
+    uint32_t* v1 = (n_passes % 2 == 0) ? vals_alt : bins.vals;
     k_duplicate<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, reinterpret_cast<const int4*>(pr.rect),
                                                  reinterpret_cast<const float4*>(pr.rgbd), E, n, block_sums, views,
                                                  cap, k0, v0);
     const int nb_sort = (int)ceil_div(cap, kSortBlock);
-    for (int pass = 0; pass < plan.n_passes; pass++) {
-        k_radix_hist<<<nb_sort, kSortThreads, 0, s>>>(k0, bins.num_keys, cap, plan.shift[pass], plan.bits[pass],
-                                                      counts);
-        k_radix_scan<<<kRadix, kDigitScanThreads, 0, s>>>(counts, digit_total, bins.num_keys, cap);
+    for (int pass = 0; pass < n_passes; pass++) {
+        k_radix_hist<<<nb_sort, kSortThreads, 0, s>>>(k0, bins.num_keys, cap, shift[pass], width[pass], counts);
+        const int radix = 1 << width[pass];
+        k_radix_scan<<<(unsigned)ceil_div(radix, kDigitScanWarps), kDigitScanThreads, 0, s>>>(counts, digit_total,
+                                                                                             bins.num_keys, cap, radix);
         k_radix_scatter<<<nb_sort, kSortThreads, 0, s>>>(k0, v0, k1, v1, counts, digit_total, bins.num_keys, cap,
-                                                         plan.shift[pass], plan.bits[pass]);
+                                                         shift[pass], width[pass]);
         uint64_t* tk = k0; k0 = k1; k1 = tk;
         uint32_t* tv = v0; v0 = v1; v1 = tv;
     }

@@ -40,24 +40,14 @@ struct RenderConsts {
 bool make_views(const gs_camera* cams, int32_t n_views, int32_t tile, Views* out);
 RenderConsts make_consts(const gs_render_params* p);
 
-// Workspace layout shared by the entry points (api.cu).
+// Binning plan (api.cu -> binsort.cu).
 struct SortPlan {
     int64_t capacity;
-    int32_t n_passes;
-    int32_t shift[8];
-    int32_t bits[8];
+    int32_t total_tiles;
 };
 SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles);
-size_t bin_sort_workspace(int64_t n_entries, int64_t capacity);
+size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles);
 
-constexpr int kScanItems = 1;                    // entries per thread in scan / duplicate
-constexpr int kScanThreads = 256;
-constexpr int kScanBlock = kScanItems * kScanThreads;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortBlock = kSortThreads * kSortItems;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
 constexpr int kGradStride = 12;                  // floats per entry of the 2D-gradient scratch
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

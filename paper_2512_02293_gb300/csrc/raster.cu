@@ -2,20 +2,24 @@
 // a pixel's colour is the alpha blend of the Gaussians covering it, and the
 // mapper renders both colour and depth per keyframe) and its backward pass.
 //
-// One CTA per tile, one thread per pixel.  The tile's depth-sorted splats are
-// staged through shared memory in batches (one splat per thread, coalesced
-// gathers of float2/float4 rows), then every pixel walks the batch with
-// broadcast shared-memory reads.  The CTA leaves as soon as all its pixels are
-// saturated.
+// One CTA per tile; inside it every warp owns an 8 x 4 block of pixels (one
+// pixel per lane) and works through the tile's depth-sorted list on its own:
+// lane l gathers splat base + l of the list into registers (float2 / float4
+// rows), the warp parks those 32 splats in its private shared-memory slot and
+// composites them with broadcast reads while the next 32 are already in
+// flight.  There is no CTA-wide barrier, so a warp stops as soon as its own 32
+// pixels are saturated and never waits for a deeper neighbour; the depth of a
+// tile's deepest pixels (up to ~8x the mean here) only costs its own warps.
 //
-// The backward pass walks each tile's list back to front from the per-pixel
+// The backward pass walks the same lists back to front from the per-pixel
 // checkpoint (T_final, n_contrib) written by the forward pass: it rebuilds the
 // transmittance before each splat by T_before = T_after / (1 - alpha) and keeps
 // the colour/depth "behind" a splat as a running normalised sum, so no
-// per-splat state is stored by the forward pass.  Per-splat gradients are
-// summed over the 32 pixels of a warp by a transposed butterfly (10 values in
-// 12 shuffles, each lane ends with one finished sum), accumulated per tile in
-// shared memory, and flushed with one vector atomic per (tile, splat).
+// per-splat state is stored by the forward pass.  A warp starts at its own
+// deepest pixel.  Per-splat gradients are summed over the warp's 32 pixels by a
+// transposed butterfly (10 values in 12 shuffles; each lane ends with one
+// finished sum); two splats are reduced together so that their shuffle chains
+// overlap, and the ten sums go to global memory as ten atomics.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -28,48 +32,62 @@ __device__ __forceinline__ int view_of_tile(const Views& views, int g) {
     return v;
 }
 
-// Thread layout: a tile of T x T pixels is split into 8 x 8 blocks, one warp
-// per block; lane l covers column l % 8 and rows l / 8 and l / 8 + 4 of its
-// block (two pixels per lane), so a warp's pixels are spatially compact and
-// tend to saturate together.
+// A tile of T x T pixels is covered by (T / 8) x (T / 4) warps; lane l of warp w
+// is pixel (8 (w % (T/8)) + l % 8, 4 (w / (T/8)) + l / 8) of the tile.
 template <int T>
 struct TileShape {
-    static constexpr int kWarps = (T / 8) * (T / 8);
+    static constexpr int kWarps = (T / 8) * (T / 4);
     static constexpr int kThreads = kWarps * 32;
 };
 
-__device__ __forceinline__ void lane_pixels(int T, int tid, int* x, int* y0) {
+__device__ __forceinline__ void lane_pixel(int T, int tid, int* x, int* y) {
     const int w = tid >> 5, l = tid & 31;
-    const int bx = w % (T / 8), by = w / (T / 8);
-    *x = bx * 8 + (l & 7);
-    *y0 = by * 8 + (l >> 3);
+    *x = (w % (T / 8)) * 8 + (l & 7);
+    *y = (w / (T / 8)) * 4 + (l >> 3);
 }
 
-// Forward state of one pixel.
-struct FwdPix {
-    float T, r, g, b, d;
-    uint32_t last;
-    bool done;
+// One splat as the rasterisers read it.
+struct Splat {
+    float2 xy;
+    float4 q;     // -0.5 log2e A, -log2e B, -0.5 log2e C, opacity
+    float4 cd;    // r, g, b, z
 };
 
-__device__ __forceinline__ void fwd_pixel(FwdPix& P, float dx, float sy, float2 m, float4 q, const float4* cd,
-                                          float amin, float amax, float tcut, uint32_t pos) {
-    if (P.done) return;
-    const float dy = __fsub_rn(sy, m.y);
-    const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-    if (p2 > 0.f) return;
-    const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
-    if (a < amin) return;
-    const float test = __fmaf_rn(-a, P.T, P.T);
-    if (test < tcut) { P.done = true; return; }
-    const float4 c = *cd;
-    const float w = __fmul_rn(a, P.T);
-    P.r = __fmaf_rn(c.x, w, P.r);
-    P.g = __fmaf_rn(c.y, w, P.g);
-    P.b = __fmaf_rn(c.z, w, P.b);
-    P.d = __fmaf_rn(c.w, w, P.d);
-    P.T = test;
-    P.last = pos + 1u;
+__device__ __forceinline__ Splat load_splat(const float2* __restrict__ xy, const float4* __restrict__ conic_o,
+                                            const float4* __restrict__ rgbd, uint32_t e) {
+    Splat s;
+    const float4 c = conic_o[e];
+    scale_conic(c.x, c.y, c.z, &s.q.x, &s.q.y, &s.q.z);
+    s.q.w = c.w;
+    s.xy = xy[e];
+    s.cd = rgbd[e];
+    return s;
+}
+
+// Warp-level culling.  A splat is dropped from a warp's batch only if its
+// weight o exp(power) stays below alpha_min (with a 1 % margin for rounding) at
+// every pixel sample of the warp's 8 x 4 block, so dropping it changes no
+// pixel.  The maximum of the concave power over the block's sample rectangle
+// [x0, x1] x [y0, y1] lies at the mean if the mean is inside, else on an edge,
+// where it is the clamped optimum of a 1-D quadratic; p2 is power * log2(e).
+__device__ __forceinline__ float edge_max_p2(float qa, float qb, float qc, float fixed_d, float lo, float hi,
+                                             bool fixed_is_x) {
+    // fixed_is_x: dx = fixed_d, maximise over dy in [lo, hi]; else dy fixed, dx free
+    const float qf = fixed_is_x ? qa : qc, qv = fixed_is_x ? qc : qa;
+    float t = qv < 0.f ? -qb * fixed_d / (2.f * qv) : lo;   // stationary point of qv t^2 + qb f t
+    t = fminf(fmaxf(t, lo), hi);
+    return qf * fixed_d * fixed_d + qb * fixed_d * t + qv * t * t;
+}
+
+__device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4 q, float x0, float x1, float y0,
+                                                    float y1, float amin) {
+    if (m.x >= x0 && m.x <= x1 && m.y >= y0 && m.y <= y1) return true;
+    const float dx0 = x0 - m.x, dx1 = x1 - m.x, dy0 = y0 - m.y, dy1 = y1 - m.y;
+    float p = edge_max_p2(q.x, q.y, q.z, dx0, dy0, dy1, true);
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dx1, dy0, dy1, true));
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy0, dx0, dx1, false));
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy1, dx0, dx1, false));
+    return q.w * splat_weight(p) >= 0.99f * amin;
 }
 
 template <int T>
@@ -77,118 +95,133 @@ __global__ void __launch_bounds__(TileShape<T>::kThreads) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         gs_image img) {
-    constexpr int NT = TileShape<T>::kThreads;
-    constexpr int B = 2 * NT < 1024 ? 2 * NT : 1024;   // splats per shared-memory batch
-    __shared__ float2 s_xy[B];
-    __shared__ float4 s_q[B];
-    __shared__ float4 s_cd[B];
+    constexpr int W = TileShape<T>::kWarps;
+    __shared__ float2 s_xy[W][32];
+    __shared__ float4 s_q[W][32];
+    __shared__ float4 s_cd[W][32];
+    __shared__ uint32_t s_pos[W][32];
     const int g = blockIdx.x;
     const int v = view_of_tile(views, g);
     const ViewParams& vp = views.v[v];
     const int lt = g - vp.tile_base;
     const int tx = lt % vp.tiles_x, ty = lt / vp.tiles_x;
     int ox, oy;
-    lane_pixels(T, threadIdx.x, &ox, &oy);
-    const int px = tx * T + ox, py0 = ty * T + oy, py1 = py0 + 4;
-    const bool in0 = px < vp.W && py0 < vp.H, in1 = px < vp.W && py1 < vp.H;
-    const float sx = (float)px + 0.5f, sy0 = (float)py0 + 0.5f, sy1 = (float)py1 + 0.5f;
+    lane_pixel(T, threadIdx.x, &ox, &oy);
+    const int px = tx * T + ox, py = ty * T + oy;
+    const bool inside = px < vp.W && py < vp.H;
+    if (!__any_sync(0xffffffffu, inside)) return;      // warp entirely outside the image
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    // sample rectangle of this warp's 8 x 4 block
+    const float bx0 = (float)(tx * T + (w % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (w / (T / 8)) * 4) + 0.5f;
+    const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const uint2 range = ranges[g];
     const float amin = rc.alpha_min, amax = rc.alpha_max, tcut = rc.T_cut;
 
-    FwdPix P0 = {1.f, 0.f, 0.f, 0.f, 0.f, 0u, !in0};
-    FwdPix P1 = {1.f, 0.f, 0.f, 0.f, 0.f, 0u, !in1};
-    for (uint32_t start = range.x; start < range.y; start += B) {
-        if (__syncthreads_count(P0.done && P1.done) == NT) break;
-        for (int k = threadIdx.x; k < B; k += NT) {
-            const uint32_t j = start + k;
-            if (j < range.y) {
-                const uint32_t e = vals[j];
-                const float4 c = conic_o[e];
-                float4 q;
-                scale_conic(c.x, c.y, c.z, &q.x, &q.y, &q.z);
-                q.w = c.w;
-                s_xy[k] = xy[e];
-                s_q[k] = q;
-                s_cd[k] = rgbd[e];
-            }
+    float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    Splat nxt;
+    if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
+    for (uint32_t base = range.x; base < range.y; base += 32) {
+        const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
+        const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) {
+            const int slot = __popc(kept & lt_mask);
+            s_xy[w][slot] = nxt.xy;
+            s_q[w][slot] = nxt.q;
+            s_cd[w][slot] = nxt.cd;
+            s_pos[w][slot] = base - range.x + lane;
         }
-        __syncthreads();
-        const int cnt = min((uint32_t)B, range.y - start);
-        if (__any_sync(0xffffffffu, !(P0.done && P1.done))) {
-            for (int k = 0; k < cnt; k++) {
-                const float2 m = s_xy[k];
-                const float4 q = s_q[k];
-                const float dx = __fsub_rn(sx, m.x);
-                const uint32_t pos = start - range.x + (uint32_t)k;
-                fwd_pixel(P0, dx, sy0, m, q, &s_cd[k], amin, amax, tcut, pos);
-                fwd_pixel(P1, dx, sy1, m, q, &s_cd[k], amin, amax, tcut, pos);
-                if ((k & 15) == 15 && __all_sync(0xffffffffu, P0.done && P1.done)) break;
-            }
+        __syncwarp();
+        if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[base + 32 + lane]);
+        const int cnt = __popc(kept);
+        for (int k = 0; k < cnt && !done; k++) {
+            const float2 m = s_xy[w][k];
+            const float4 q = s_q[w][k];
+            const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
+            const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
+            if (p2 > 0.f) continue;
+            const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
+            if (a < amin) continue;
+            const float test = __fmaf_rn(-a, Tr, Tr);
+            if (test < tcut) { done = true; break; }
+            const float4 c = s_cd[w][k];
+            const float wgt = __fmul_rn(a, Tr);
+            cr = __fmaf_rn(c.x, wgt, cr);
+            cg = __fmaf_rn(c.y, wgt, cg);
+            cb = __fmaf_rn(c.z, wgt, cb);
+            dd = __fmaf_rn(c.w, wgt, dd);
+            Tr = test;
+            last = s_pos[w][k] + 1u;
         }
+        if (__all_sync(0xffffffffu, done)) break;
     }
-    const int HW = vp.W * vp.H;
-    float* col = img.color + 3 * (size_t)vp.pix_base;
-    if (in0) {
-        const int pix = py0 * vp.W + px;
-        col[pix] = P0.r + P0.T * rc.bg[0];
-        col[HW + pix] = P0.g + P0.T * rc.bg[1];
-        col[2 * HW + pix] = P0.b + P0.T * rc.bg[2];
-        img.depth[vp.pix_base + pix] = P0.d;
-        img.T_final[vp.pix_base + pix] = P0.T;
-        img.n_contrib[vp.pix_base + pix] = P0.last;
-    }
-    if (in1) {
-        const int pix = py1 * vp.W + px;
-        col[pix] = P1.r + P1.T * rc.bg[0];
-        col[HW + pix] = P1.g + P1.T * rc.bg[1];
-        col[2 * HW + pix] = P1.b + P1.T * rc.bg[2];
-        img.depth[vp.pix_base + pix] = P1.d;
-        img.T_final[vp.pix_base + pix] = P1.T;
-        img.n_contrib[vp.pix_base + pix] = P1.last;
+    if (inside) {
+        const int HW = vp.W * vp.H;
+        const int pix = py * vp.W + px;
+        float* col = img.color + 3 * (size_t)vp.pix_base;
+        col[pix] = cr + Tr * rc.bg[0];
+        col[HW + pix] = cg + Tr * rc.bg[1];
+        col[2 * HW + pix] = cb + Tr * rc.bg[2];
+        img.depth[vp.pix_base + pix] = dd;
+        img.T_final[vp.pix_base + pix] = Tr;
+        img.n_contrib[vp.pix_base + pix] = last;
     }
 }
 
-// Warp sum of 10 values by a transposed butterfly: after 12 shuffles lane l
-// (l even) holds the full sum of value 5*b4 + (3*b3 + 2*b2 + b1) when that slot
-// is valid, and adds it into acc[slot].
-__device__ __forceinline__ void warp_reduce10_add(const float (&v)[10], float* acc, int lane) {
-    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1, b0 = lane & 1;
-    float r[6];
+// Transposed butterfly over the warp for two independent sets of 10 values:
+// after 12 shuffle stages per set, lane l holds the full sum of slot
+// 5 * b4 + 3 * b3 + 2 * b2 + b1 (bits of l) when that slot exists and l is even.
+// The two sets' shuffles are interleaved so their latencies overlap.
+__device__ __forceinline__ void warp_reduce10x2(const float (&va)[10], const float (&vb)[10], int lane, float* ua,
+                                                float* ub) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    float ra[6], rb[6];
 #pragma unroll
     for (int j = 0; j < 5; j++) {
-        const float keep = b4 ? v[j + 5] : v[j];
-        const float send = b4 ? v[j] : v[j + 5];
-        r[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const float ka = b4 ? va[j + 5] : va[j], sa = b4 ? va[j] : va[j + 5];
+        const float kb = b4 ? vb[j + 5] : vb[j], sb = b4 ? vb[j] : vb[j + 5];
+        ra[j] = ka + __shfl_xor_sync(0xffffffffu, sa, 16);
+        rb[j] = kb + __shfl_xor_sync(0xffffffffu, sb, 16);
     }
-    r[5] = 0.f;
-    float s[4];
+    ra[5] = 0.f; rb[5] = 0.f;
+    float ta[4], tb[4];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        const float keep = b3 ? r[j + 3] : r[j];
-        const float send = b3 ? r[j] : r[j + 3];
-        s[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        const float ka = b3 ? ra[j + 3] : ra[j], sa = b3 ? ra[j] : ra[j + 3];
+        const float kb = b3 ? rb[j + 3] : rb[j], sb = b3 ? rb[j] : rb[j + 3];
+        ta[j] = ka + __shfl_xor_sync(0xffffffffu, sa, 8);
+        tb[j] = kb + __shfl_xor_sync(0xffffffffu, sb, 8);
     }
-    s[3] = 0.f;
-    float t[2];
+    ta[3] = 0.f; tb[3] = 0.f;
+    float wa[2], wb[2];
 #pragma unroll
     for (int j = 0; j < 2; j++) {
-        const float keep = b2 ? s[j + 2] : s[j];
-        const float send = b2 ? s[j] : s[j + 2];
-        t[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        const float ka = b2 ? ta[j + 2] : ta[j], sa = b2 ? ta[j] : ta[j + 2];
+        const float kb = b2 ? tb[j + 2] : tb[j], sb = b2 ? tb[j] : tb[j + 2];
+        wa[j] = ka + __shfl_xor_sync(0xffffffffu, sa, 4);
+        wb[j] = kb + __shfl_xor_sync(0xffffffffu, sb, 4);
     }
-    float u;
-    {
-        const float keep = b1 ? t[1] : t[0];
-        const float send = b1 ? t[0] : t[1];
-        u = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    u += __shfl_xor_sync(0xffffffffu, u, 1);
-    const int k = 3 * b3 + 2 * b2 + b1;
-    if (b0 == 0 && (2 * b2 + b1) < 3 && k < 5) atomicAdd(acc + 5 * b4 + k, u);
+    float xa = (b1 ? wa[1] : wa[0]) + __shfl_xor_sync(0xffffffffu, b1 ? wa[0] : wa[1], 2);
+    float xb = (b1 ? wb[1] : wb[0]) + __shfl_xor_sync(0xffffffffu, b1 ? wb[0] : wb[1], 2);
+    xa += __shfl_xor_sync(0xffffffffu, xa, 1);
+    xb += __shfl_xor_sync(0xffffffffu, xb, 1);
+    *ua = xa;
+    *ub = xb;
 }
 
 // Gradient slots per splat: 0 d mx, 1 d my, 2 d A, 3 d B, 4 d C, 5 d o, 6 d z,
-// 7..9 d rgb.  The flush writes them as the three float4 rows of grad2d.
+// 7..9 d rgb; in the 12-float grad2d row slot s sits at s (s < 7) or s + 1.
+__device__ __forceinline__ int slot_of_lane(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    const int k = 3 * b3 + 2 * b2 + b1;
+    if ((lane & 1) || (2 * b2 + b1) >= 3 || k >= 5) return -1;
+    return 5 * b4 + k;
+}
+
 // Backward state of one pixel: transmittance after the current splat, the
 // image gradients and the colour/depth behind the current splat normalised by
 // that transmittance.
@@ -199,10 +232,16 @@ struct BwdPix {
     float Sr, Sg, Sb, Sd;
 };
 
-__device__ __forceinline__ bool bwd_pixel(BwdPix& P, float dx, float sy, float2 m, float4 q, float4 c, float4 cd,
-                                          float amin, float amax, uint32_t pos, float (&gv)[10]) {
+// The conic in the gradient formulas is recovered from the scaled one (an
+// O(1 ulp) difference that only enters gradient values, never a decision).
+constexpr float kUnscaleAC = -2.0f / kLog2e, kUnscaleB = -1.0f / kLog2e;
+
+__device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const float2 m, const float4 q,
+                                          const float4 cd, float amin, float amax, uint32_t pos, float (&gv)[10]) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) gv[r] = 0.f;
     if (pos >= P.np) return false;
-    const float dy = __fsub_rn(sy, m.y);
+    const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
     const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
     if (p2 > 0.f) return false;
     const float G = splat_weight(p2);
@@ -219,127 +258,127 @@ __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float dx, float sy, float2 
     P.Sb = fmaf(a, db, P.Sb);
     P.Sd = fmaf(a, dz, P.Sd);
     P.T = Tb;
-    gv[7] = fmaf(P.gr, w, gv[7]);
-    gv[8] = fmaf(P.gg, w, gv[8]);
-    gv[9] = fmaf(P.gb, w, gv[9]);
-    gv[6] = fmaf(P.gd, w, gv[6]);
+    gv[7] = P.gr * w;
+    gv[8] = P.gg * w;
+    gv[9] = P.gb * w;
+    gv[6] = P.gd * w;
     if (araw < amax) {                            // alpha not clamped
         const float dpow = dLda * a;              // d alpha / d power = alpha
-        gv[5] = fmaf(dLda, G, gv[5]);             // d alpha / d o = exp(power)
-        gv[0] = fmaf(dpow, fmaf(c.x, dx, c.y * dy), gv[0]);
-        gv[1] = fmaf(dpow, fmaf(c.y, dx, c.z * dy), gv[1]);
+        gv[5] = dLda * G;                         // d alpha / d o = exp(power)
+        const float A = q.x * kUnscaleAC, B = q.y * kUnscaleB, C = q.z * kUnscaleAC;
+        gv[0] = dpow * fmaf(A, dx, B * dy);
+        gv[1] = dpow * fmaf(B, dx, C * dy);
         const float hx = -0.5f * dpow * dx;
-        gv[2] = fmaf(hx, dx, gv[2]);
-        gv[3] = fmaf(-dpow * dx, dy, gv[3]);
-        gv[4] = fmaf(-0.5f * dpow * dy, dy, gv[4]);
+        gv[2] = hx * dx;
+        gv[3] = -dpow * dx * dy;
+        gv[4] = -0.5f * dpow * dy * dy;
     }
     return true;
 }
 
 template <int T>
-__global__ void __launch_bounds__(TileShape<T>::kThreads) k_render_bwd(
+__global__ void __launch_bounds__(TileShape<T>::kThreads, T == 16 ? 4 : 1) k_render_bwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d) {
-    constexpr int NT = TileShape<T>::kThreads;
-    constexpr int B = 2 * NT < 256 ? 2 * NT : 256;
-    __shared__ float2 s_xy[B];
-    __shared__ float4 s_q[B];      // scaled conic + opacity
-    __shared__ float4 s_c[B];      // raw conic A, B, C
-    __shared__ float4 s_cd[B];     // r, g, b, z
-    __shared__ uint32_t s_e[B];
-    __shared__ float s_acc[B * 10];
-    __shared__ uint32_t s_maxn;
+    constexpr int W = TileShape<T>::kWarps;
+    __shared__ float2 s_xy[W][32];
+    __shared__ float4 s_q[W][32];      // scaled conic + opacity
+    __shared__ float4 s_cd[W][32];     // r, g, b, z
+    __shared__ uint32_t s_e[W][32];
+    __shared__ uint32_t s_pos[W][32];
     const int g = blockIdx.x;
     const int v = view_of_tile(views, g);
     const ViewParams& vp = views.v[v];
     const int lt = g - vp.tile_base;
     const int tx = lt % vp.tiles_x, ty = lt / vp.tiles_x;
     int ox, oy;
-    lane_pixels(T, threadIdx.x, &ox, &oy);
-    const int px = tx * T + ox, py0 = ty * T + oy, py1 = py0 + 4;
-    const bool in0 = px < vp.W && py0 < vp.H, in1 = px < vp.W && py1 < vp.H;
-    const float sx = (float)px + 0.5f, sy0 = (float)py0 + 0.5f, sy1 = (float)py1 + 0.5f;
+    lane_pixel(T, threadIdx.x, &ox, &oy);
+    const int px = tx * T + ox, py = ty * T + oy;
+    const bool inside = px < vp.W && py < vp.H;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    const float bx0 = (float)(tx * T + (w % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (w / (T / 8)) * 4) + 0.5f;
+    const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const uint2 range = ranges[g];
-    const int lane = threadIdx.x & 31;
     const float amin = rc.alpha_min, amax = rc.alpha_max;
-    const int HW = vp.W * vp.H;
-    const float* dc = dL_dcolor + 3 * (size_t)vp.pix_base;
 
-    BwdPix P0, P1;
-    P0.np = 0; P1.np = 0; P0.T = 1.f; P1.T = 1.f;
-    P0.gr = P0.gg = P0.gb = P0.gd = 0.f;
-    P1.gr = P1.gg = P1.gb = P1.gd = 0.f;
-    P0.Sr = P1.Sr = rc.bg[0]; P0.Sg = P1.Sg = rc.bg[1]; P0.Sb = P1.Sb = rc.bg[2]; P0.Sd = P1.Sd = 0.f;
-    if (in0) {
-        const int pix = py0 * vp.W + px;
-        P0.T = T_final[vp.pix_base + pix];
-        P0.np = n_contrib[vp.pix_base + pix];
-        P0.gr = dc[pix]; P0.gg = dc[HW + pix]; P0.gb = dc[2 * HW + pix];
-        P0.gd = dL_ddepth[vp.pix_base + pix];
+    BwdPix P;
+    P.np = 0; P.T = 1.f;
+    P.gr = P.gg = P.gb = P.gd = 0.f;
+    P.Sr = rc.bg[0]; P.Sg = rc.bg[1]; P.Sb = rc.bg[2]; P.Sd = 0.f;
+    if (inside) {
+        const int HW = vp.W * vp.H;
+        const int pix = py * vp.W + px;
+        const float* dc = dL_dcolor + 3 * (size_t)vp.pix_base;
+        P.T = T_final[vp.pix_base + pix];
+        P.np = n_contrib[vp.pix_base + pix];
+        P.gr = dc[pix]; P.gg = dc[HW + pix]; P.gb = dc[2 * HW + pix];
+        P.gd = dL_ddepth[vp.pix_base + pix];
     }
-    if (in1) {
-        const int pix = py1 * vp.W + px;
-        P1.T = T_final[vp.pix_base + pix];
-        P1.np = n_contrib[vp.pix_base + pix];
-        P1.gr = dc[pix]; P1.gg = dc[HW + pix]; P1.gb = dc[2 * HW + pix];
-        P1.gd = dL_ddepth[vp.pix_base + pix];
-    }
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P0.np, P1.np));   // this warp's deepest pixel
-    if (threadIdx.x == 0) s_maxn = 0u;
-    __syncthreads();
-    if (lane == 0 && wmax > 0) atomicMax(&s_maxn, wmax);
-    __syncthreads();
-    const uint32_t list_end = min(range.x + s_maxn, range.y);   // a checkpoint never points past the list
-
-    for (int64_t bend = list_end; bend > (int64_t)range.x; bend -= B) {
-        const uint32_t bstart = (uint32_t)(bend - B > (int64_t)range.x ? bend - B : (int64_t)range.x);
-        const int cnt = (int)(bend - bstart);
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const uint32_t e = vals[bstart + k];
-            const float4 c = conic_o[e];
-            float4 q;
-            scale_conic(c.x, c.y, c.z, &q.x, &q.y, &q.z);
-            q.w = c.w;
-            s_xy[k] = xy[e];
-            s_q[k] = q;
-            s_c[k] = c;
-            s_cd[k] = rgbd[e];
-            s_e[k] = e;
-#pragma unroll
-            for (int r = 0; r < 10; r++) s_acc[k * 10 + r] = 0.f;
+    // this warp needs the list only up to its deepest pixel (a checkpoint never points past the list)
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, P.np);
+    const uint32_t top = min(range.x + wmax, range.y);
+    if (top <= range.x) return;
+    const int slot = slot_of_lane(lane);
+    const int col = slot < 7 ? slot : slot + 1;
+    uint32_t lo = top > range.x + 32 ? top - 32 : range.x;
+    // the next 32 splats (below the current batch) in flight in registers
+    float2 n_xy = make_float2(0.f, 0.f);
+    float4 n_q = make_float4(0.f, 0.f, 0.f, 0.f), n_cd = n_q;
+    uint32_t n_e = 0;
+    auto fetch = [&](uint32_t j) {
+        n_e = vals[j];
+        const float4 c = conic_o[n_e];
+        scale_conic(c.x, c.y, c.z, &n_q.x, &n_q.y, &n_q.z);
+        n_q.w = c.w;
+        n_xy = xy[n_e];
+        n_cd = rgbd[n_e];
+    };
+    if (lo + lane < top) fetch(lo + lane);
+    for (uint32_t hi = top; hi > range.x; hi = lo, lo = (lo > range.x + 32 ? lo - 32 : range.x)) {
+        const bool keep = lo + lane < hi && splat_reaches_block(n_xy, n_q, bx0, bx1, by0, by1, amin);
+        const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) {
+            const int sl = __popc(kept & lt_mask);
+            s_xy[w][sl] = n_xy;
+            s_q[w][sl] = n_q;
+            s_cd[w][sl] = n_cd;
+            s_e[w][sl] = n_e;
+            s_pos[w][sl] = lo + lane - range.x;
         }
-        __syncthreads();
-        // this warp only needs positions below its deepest pixel
-        const int64_t lim = (int64_t)wmax - (int64_t)(bstart - range.x);
-        const int kmax = lim < cnt ? (int)(lim > 0 ? lim : 0) : cnt;
-        for (int k = kmax - 1; k >= 0; k--) {
-            const uint32_t pos = bstart + (uint32_t)k - range.x;
-            const float2 m = s_xy[k];
-            const float4 q = s_q[k];
-            const float4 c = s_c[k];
-            const float4 cd = s_cd[k];
-            const float dx = __fsub_rn(sx, m.x);
-            float gv[10];
-#pragma unroll
-            for (int r = 0; r < 10; r++) gv[r] = 0.f;
-            bool any = bwd_pixel(P0, dx, sy0, m, q, c, cd, amin, amax, pos, gv);
-            any |= bwd_pixel(P1, dx, sy1, m, q, c, cd, amin, amax, pos, gv);
-            if (__any_sync(0xffffffffu, any)) warp_reduce10_add(gv, s_acc + k * 10, lane);
+        __syncwarp();
+        const uint32_t nlo = lo > range.x + 32 ? lo - 32 : range.x;
+        if (lo > range.x && nlo + lane < lo) fetch(nlo + lane);
+        const int cnt = __popc(kept);
+        int k = cnt - 1;
+        for (; k >= 1; k -= 2) {
+            float ga[10], gb[10];
+            const bool ca = bwd_pixel(P, sx, sy, s_xy[w][k], s_q[w][k], s_cd[w][k], amin, amax, s_pos[w][k], ga);
+            const bool cb = bwd_pixel(P, sx, sy, s_xy[w][k - 1], s_q[w][k - 1], s_cd[w][k - 1], amin, amax,
+                                      s_pos[w][k - 1], gb);
+            const bool anya = __any_sync(0xffffffffu, ca), anyb = __any_sync(0xffffffffu, cb);
+            if (anya || anyb) {
+                float ua, ub;
+                warp_reduce10x2(ga, gb, lane, &ua, &ub);
+                if (slot >= 0) {
+                    if (anya) atomicAdd(g2d + (size_t)kGradStride * s_e[w][k] + col, ua);
+                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * s_e[w][k - 1] + col, ub);
+                }
+            }
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const float* a = s_acc + k * 10;
-            bool nz = false;
+        if (k == 0) {
+            float ga[10], gb[10];
+            const bool ca = bwd_pixel(P, sx, sy, s_xy[w][0], s_q[w][0], s_cd[w][0], amin, amax, s_pos[w][0], ga);
 #pragma unroll
-            for (int r = 0; r < 10; r++) nz |= (a[r] != 0.f);
-            if (nz) {
-                float4* dst = reinterpret_cast<float4*>(g2d) + 3 * (size_t)s_e[k];
-                atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
-                atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], 0.f));
-                atomicAdd(dst + 2, make_float4(a[7], a[8], a[9], 0.f));
+            for (int r = 0; r < 10; r++) gb[r] = 0.f;
+            if (__any_sync(0xffffffffu, ca)) {
+                float ua, ub;
+                warp_reduce10x2(ga, gb, lane, &ua, &ub);
+                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * s_e[w][0] + col, ua);
             }
         }
     }

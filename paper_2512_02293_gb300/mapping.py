@@ -188,3 +188,37 @@ class MappingStep:
     def depth_image(self, v: int) -> torch.Tensor:
         base, W, H = self.view_slices()[v]
         return self.img.depth[base:base + W * H].view(H, W)
+
+
+def autotune_tile(gaussians: G.Gaussians, cams, target_color, target_depth, params: G.RenderParams | None = None,
+                  mparams: MapParams | None = None, candidates=(8, 16, 32), iters: int = 10):
+    """Pick the tile size with the fastest graph-replayed mapping iteration
+    for this map and these views.  Every trial starts from the same map and
+    the map is restored afterwards.  Returns (best RenderParams, {tile: ms})."""
+    import dataclasses
+    base = params or G.RenderParams()
+    saved = [t.clone() for t in gaussians.tensors()]
+    times = {}
+    for tile in candidates:
+        p = dataclasses.replace(base, tile=tile)
+        step = MappingStep(gaussians, cams, target_color, target_depth, p, mparams)
+        step.step()
+        step.ensure_capacity()
+        step.capture(warmup=1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = []
+        for _ in range(iters):
+            for t, s0 in zip(gaussians.tensors(), saved):
+                t.copy_(s0)
+            ev[0].record()
+            step.step()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        ms.sort()
+        times[tile] = ms[len(ms) // 2]
+        del step
+    for t, s0 in zip(gaussians.tensors(), saved):
+        t.copy_(s0)
+    best = min(times, key=times.get)
+    return dataclasses.replace(base, tile=best), times

@@ -56,7 +56,7 @@ def test_tiles_pixels_workspace_host_only(lib):
     assert G.gs_total_tiles(cams, 8) == 8 * 6 + 9 * 6
     assert G.gs_total_pixels(cams) == 64 * 48 + 70 * 45
     ws = G.gs_workspace_size(256, cams, G.RenderParams(), 4096)
-    assert ws >= 4096 * 12 and ws % 256 == 0
+    assert ws >= max(4096 * 8, 2 * 256 * 48) and ws % 256 == 0   # segment keys; backward scratch
     with pytest.raises(G.GsError):
         G.gs_total_tiles(cams, 12)          # unsupported tile size
     with pytest.raises(G.GsError):

@@ -158,17 +158,27 @@ def test_graph_replay_equals_eager(setup):
     a = MappingStep(G.Gaussians.from_numpy(g), [cam], tgt_c, tgt_d, params, MapParams())
     b = MappingStep(G.Gaussians.from_numpy(g), [cam], tgt_c, tgt_d, params, MapParams(),
                     key_capacity=a.bins.capacity)
-    for _ in range(3):
-        a.step()
+    a.step()
     b.capture(warmup=0)
-    for _ in range(3):
+    b.step()
+    torch.cuda.synchronize()
+    # one iteration: same arithmetic, same order except float atomics in the backward
+    for ga, gb in zip(a.grads.tensors(), b.grads.tensors()):
+        assert rel_l2(gb.cpu().numpy(), ga.cpu().numpy()) < 1e-5
+    for _ in range(2):
+        a.step()
         b.step()
     torch.cuda.synchronize()
     assert a.check() == 0 and b.check() == 0
     assert int(a.d_step[0].item()) == 3 and int(b.d_step[0].item()) == 3
-    # same arithmetic, same order except float atomics in the backward
-    for ta, tb in zip(a.g.tensors(), b.g.tensors()):
-        np.testing.assert_allclose(tb.cpu().numpy(), ta.cpu().numpy(), rtol=1e-4, atol=1e-6)
+    # Adam divides by sqrt(v): a near-zero gradient whose atomic summation order
+    # differs may change the sign of its step; allow a handful such elements,
+    # each off by at most the three steps' lr
+    lrs = MapParams().lr
+    for ta, tb, lr in zip(a.g.tensors(), b.g.tensors(), lrs):
+        d = np.abs(tb.cpu().numpy() - ta.cpu().numpy())
+        off = d > 1e-6 + 1e-4 * np.abs(ta.cpu().numpy())
+        assert off.mean() < 1e-4 and (d[off].max() if off.any() else 0.0) <= 6 * lr + 1e-6
 
 
 def test_mapping_iterations_reduce_the_loss(setup):
