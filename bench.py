@@ -105,34 +105,105 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_problem(device):
+def build_step(device, g, gt, cams):
+    """Target images of the perturbed map (input preparation, not timed), then a
+    mapping step on the map with the autotuned tile size."""
     import torch
-    from paper_2512_02293_gb300 import gs as G, synth
-    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
-    g, gt, cam = synth.cfg2_problem()
-    params = G.RenderParams(tile=16)   # the target render; the timed step's tile is autotuned
+    from paper_2512_02293_gb300 import gs as G
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep, autotune_tile
+    params = G.RenderParams(tile=16)
     mp = MapParams()
-    P = cam.n_pixels
-    # target = render of the perturbed map (input preparation, not timed)
+    P = G.gs_total_pixels(cams)
     dummy_c = torch.zeros(3 * P, device=device); dummy_d = torch.zeros(P, device=device)
-    tstep = MappingStep(G.Gaussians.from_numpy(gt, device), [cam], dummy_c, dummy_d, params, mp)
+    tstep = MappingStep(G.Gaussians.from_numpy(gt, device), cams, dummy_c, dummy_d, params, mp)
     tstep.render()
     torch.cuda.synchronize()
     tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
     del tstep
-    from paper_2512_02293_gb300.mapping import autotune_tile
     gd = G.Gaussians.from_numpy(g, device)
-    params, tune = autotune_tile(gd, [cam], tc, td, params, mp)
-    step = MappingStep(gd, [cam], tc, td, params, mp)
+    params, tune = autotune_tile(gd, cams, tc, td, params, mp)
+    step = MappingStep(gd, cams, tc, td, params, mp)
     step.tune = tune
-    return g, gt, cam, params, mp, step, tc, td
+    return params, mp, step, tc, td
+
+
+def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
+    """Graph-replayed iterations, each from the same map and Adam state (restored
+    outside the step's events) after an L2 flush.  The graph records an event
+    before and after each of the seven C-ABI calls (event-record nodes on the
+    launch stream).  Returns per-step ms, per-stage median ms, visited pairs and
+    the clock summary."""
+    import torch
+    step.step()
+    if step.ensure_capacity():
+        step.step()
+        assert not step.ensure_capacity()
+    pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
+    try:
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(8)]
+        step.capture(warmup=1, events=evs)
+        staged = True
+    except TypeError:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        step.capture(warmup=1)
+        staged = False
+    for _ in range(warmup):
+        step.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    pristine = [t.clone() for t in step.g.tensors()]
+
+    def restore():
+        for t, p0 in zip(step.g.tensors(), pristine):
+            t.copy_(p0)
+        for t in step.m + step.v:
+            t.zero_()
+        step.d_step.zero_()
+
+    s = torch.cuda.current_stream()
+    per_stage = {k: [] for k in step.STAGES}
+    times = []
+    clk = ClockSampler(clock_index) if clock_index is not None else None
+    if clk:
+        clk.__enter__()
+    try:
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            restore()
+            flush()
+            if staged:
+                step.step()
+                torch.cuda.synchronize()
+                times.append(evs[0].elapsed_time(evs[7]))
+                for j, nm in enumerate(step.STAGES):
+                    per_stage[nm].append(evs[j].elapsed_time(evs[j + 1]))
+            else:
+                evs[0].record(s); step.step(); evs[1].record(s)
+                torch.cuda.synchronize()
+                times.append(evs[0].elapsed_time(evs[1]))
+    finally:
+        if clk:
+            clk.__exit__()
+    if dist is not None:
+        dist.barrier()
+    status = step.check()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed region")
+    st = {k: statistics.median(v) for k, v in per_stage.items()} if staged else {}
+    return times, st, pairs, (clk.summary() if clk else None)
 
 
 def launches_per_step(step) -> int:
-    """Kernels of ours per iteration: project 1; bin/sort 4 (tile count, tile
-    scan, tile scatter, segment sort); render 1; loss 2; backward raster 1 +
+    """Kernels of ours per iteration: project 1; bin/sort: entry scan 2,
+    duplicate 1, 3 per radix pass (digits of at most 9 bits over 31 depth bits
+    and the tile bits), tile ranges 1; render 1; loss 2; backward raster 1 +
     projection backward 1; Adam 1."""
-    return 1 + 4 + 1 + 2 + 2 + 1
+    tb = 0
+    while (1 << tb) < step.total_tiles:
+        tb += 1
+    passes = math.ceil((31 + tb) / 9)
+    return 1 + (2 + 1 + 3 * passes + 1) + 1 + 2 + 2 + 1
 
 
 def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
@@ -220,6 +291,27 @@ def whole_job_rate(local_ms: float, steps: int, world: int, dist=None, device=No
     return world * steps / (total_ms / 1000.0), total_ms
 
 
+def window_run(device, args, flush, plain_rate, dist=None, world=1):
+    """The batched mapping window: 8 keyframes of uneven size (4x 640x480,
+    2x 752x480, 2x 1280x1024) on a 5 m trajectory through a 500k-Gaussian room,
+    every stage one launch over all views (persistent rasterisers), the whole
+    iteration one CUDA graph, tile size autotuned."""
+    from paper_2512_02293_gb300 import synth
+    g, gt, cams = synth.cfg3_problem()
+    params, mp, step, tc, td = build_step(device, g, gt, cams)
+    steps = max(10, args.steps // 4)
+    times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
+    rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
+    views = len(cams)
+    return {"workload": "batched window: 8 keyframes (4x 640x480, 2x 752x480, 2x 1280x1024), 500k Gaussians",
+            "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
+            "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
+            "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
+            "pixels_per_iter": step.total_pixels, "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
+            "gpix_splats_per_s": pairs / (st["gs_render_fwd"] * 1e-3) / 1e9 if st else None,
+            "stages_ms": st, "graph": True, "persistent_raster": True}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,6 +319,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-window", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -247,69 +340,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
 
-    g, gt, cam, params, mp, step, tc, td = build_problem(device)
-    # first eager pass: size the key buffers, then check the status word
-    step.step()
-    if step.ensure_capacity():
-        step.step()
-        assert not step.ensure_capacity()
+    from paper_2512_02293_gb300 import synth
+    g, gt, cam = synth.cfg2_problem()
+    params, mp, step, tc, td = build_step(device, g, gt, [cam])
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
     flush = lambda: flush_buf.fill_(1.0)
-    pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
-
-    # The timed graph records an event before and after each of the seven
-    # C-ABI calls of the iteration (event-record nodes on the launch stream).
-    try:
-        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(8)]
-        step.capture(warmup=1, events=evs)
-        staged = True
-    except TypeError:
-        evs = None
-        step.capture(warmup=1)
-        staged = False
-    for _ in range(args.warmup):
-        step.step()
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    # Every timed step starts from the same map and optimiser state (restored
-    # outside the step's events), so each step does identical work.
-    pristine = [t.clone() for t in step.g.tensors()]
-
-    def restore():
-        for t, p0 in zip(step.g.tensors(), pristine):
-            t.copy_(p0)
-        for t in step.m + step.v:
-            t.zero_()
-        step.d_step.zero_()
-
-    s = torch.cuda.current_stream()
-    per_stage = {k: [] for k in step.STAGES}
-    times = []
-    t0e = torch.cuda.Event(enable_timing=True); t1e = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            restore()
-            flush()
-            if staged:
-                step.step()
-                torch.cuda.synchronize()
-                times.append(evs[0].elapsed_time(evs[7]))
-                for j, nm in enumerate(step.STAGES):
-                    per_stage[nm].append(evs[j].elapsed_time(evs[j + 1]))
-            else:
-                t0e.record(s); step.step(); t1e.record(s)
-                torch.cuda.synchronize()
-                times.append(t0e.elapsed_time(t1e))
-    if dist is not None:
-        dist.barrier()
-    total_ms = sum(times)
-    st = {k: statistics.median(v) for k, v in per_stage.items()} if staged else {}
-    status = step.check()
-    if status != 0:
-        raise RuntimeError(f"device status {status} after the timed region")
-    value, total_ms = whole_job_rate(total_ms, args.steps, world, dist, device)
+    times, st, pairs, clocks = timed_run(step, args.steps, args.warmup, flush, dist, local)
+    value, total_ms = whole_job_rate(sum(times), args.steps, world, dist, device)
 
     # end to end through the C ABI with host buffers: H2D of the target image and
     # depth from pinned memory each step, D2H of the loss
@@ -354,7 +391,6 @@ def main():
                     "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
                     "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
                     "timing": "CUDA event-record nodes around the call inside the timed graph, median over steps"}
-    clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -368,6 +404,8 @@ def main():
             "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "stages_ms": st, "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}
+    if not args.no_window:
+        line["window"] = window_run(device, args, flush, value, dist, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, gt, cam, params, mp)
     if rank == 0:

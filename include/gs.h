@@ -108,7 +108,8 @@ typedef struct gs_bins {
     int64_t key_capacity;     /* number of slots in keys / vals */
     uint32_t* ranges;         /* [total_tiles][2] [start, end) of each tile's list */
     uint32_t* num_keys;       /* [1] number of keys M the projection produced */
-    int32_t* status;          /* [1] device status word (gs_status), sticky */
+    int32_t* status;          /* [4] [0] device status word (gs_status), sticky; [1..3]
+                                 work counters of the persistent rasterisers */
 } gs_bins;
 
 /* Rendered images and the per-pixel checkpoint the backward pass uses. */

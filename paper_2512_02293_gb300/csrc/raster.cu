@@ -2,14 +2,17 @@
 // a pixel's colour is the alpha blend of the Gaussians covering it, and the
 // mapper renders both colour and depth per keyframe) and its backward pass.
 //
-// One CTA per tile; inside it every warp owns an 8 x 4 block of pixels (one
-// pixel per lane) and works through the tile's depth-sorted list on its own:
+// Work item = one 8 x 4 block of pixels of one tile (one pixel per lane); a
+// persistent grid's warps take items from a device counter (views of uneven
+// size balance across SMs) and each works through its tile's depth-sorted
+// list on its own:
 // lane l gathers splat base + l of the list into registers (float2 / float4
 // rows), the warp parks those 32 splats in its private shared-memory slot and
 // composites them with broadcast reads while the next 32 are already in
-// flight.  There is no CTA-wide barrier, so a warp stops as soon as its own 32
-// pixels are saturated and never waits for a deeper neighbour; the depth of a
-// tile's deepest pixels (up to ~8x the mean here) only costs its own warps.
+// flight.  Before compositing, the warp drops the splats that cannot reach
+// alpha_min anywhere in its block.  There is no CTA-wide barrier, so a warp
+// stops as soon as its own 32 pixels are saturated and takes the next item; the
+// depth of a tile's deepest pixels (up to ~8x the mean) only costs its own warp.
 //
 // The backward pass walks the same lists back to front from the per-pixel
 // checkpoint (T_final, n_contrib) written by the forward pass: it rebuilds the
@@ -36,8 +39,7 @@ __device__ __forceinline__ int view_of_tile(const Views& views, int g) {
 // is pixel (8 (w % (T/8)) + l % 8, 4 (w / (T/8)) + l / 8) of the tile.
 template <int T>
 struct TileShape {
-    static constexpr int kWarps = (T / 8) * (T / 4);
-    static constexpr int kThreads = kWarps * 32;
+    static constexpr int kWarps = (T / 8) * (T / 4);    // 8 x 4 pixel blocks per tile
 };
 
 __device__ __forceinline__ void lane_pixel(int T, int tid, int* x, int* y) {
@@ -90,85 +92,101 @@ __device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4
     return q.w * splat_weight(p) >= 0.99f * amin;
 }
 
+// Persistent launch: kRasterThreads-thread CTAs, as many as fit on the GPU;
+// every warp repeatedly takes the next work item -- one 8 x 4 pixel block of
+// one tile of one view -- from a device counter and processes it alone.
+constexpr int kRasterThreads = 256;
+constexpr int kRasterWarps = kRasterThreads / 32;
+
+__device__ __forceinline__ int next_item(int* queue, int lane) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1);
+    return __shfl_sync(0xffffffffu, item, 0);
+}
+
 template <int T>
-__global__ void __launch_bounds__(TileShape<T>::kThreads) k_render_fwd(
+__global__ void __launch_bounds__(kRasterThreads) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
-        gs_image img) {
-    constexpr int W = TileShape<T>::kWarps;
-    __shared__ float2 s_xy[W][32];
-    __shared__ float4 s_q[W][32];
-    __shared__ float4 s_cd[W][32];
-    __shared__ uint32_t s_pos[W][32];
-    const int g = blockIdx.x;
-    const int v = view_of_tile(views, g);
-    const ViewParams& vp = views.v[v];
-    const int lt = g - vp.tile_base;
-    const int tx = lt % vp.tiles_x, ty = lt / vp.tiles_x;
-    int ox, oy;
-    lane_pixel(T, threadIdx.x, &ox, &oy);
-    const int px = tx * T + ox, py = ty * T + oy;
-    const bool inside = px < vp.W && py < vp.H;
-    if (!__any_sync(0xffffffffu, inside)) return;      // warp entirely outside the image
+        gs_image img, int* __restrict__ queue, int n_items) {
+    constexpr int W = TileShape<T>::kWarps;     // pixel blocks per tile
+    __shared__ float2 s_xy[kRasterWarps][32];
+    __shared__ float4 s_q[kRasterWarps][32];
+    __shared__ float4 s_cd[kRasterWarps][32];
+    __shared__ uint32_t s_pos[kRasterWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
-    // sample rectangle of this warp's 8 x 4 block
-    const float bx0 = (float)(tx * T + (w % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (w / (T / 8)) * 4) + 0.5f;
-    const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint2 range = ranges[g];
     const float amin = rc.alpha_min, amax = rc.alpha_max, tcut = rc.T_cut;
+    for (int item = next_item(queue, lane); item < n_items; item = next_item(queue, lane)) {
+        const int g = item / W, blk = item % W;
+        const int v = view_of_tile(views, g);
+        const ViewParams& vp = views.v[v];
+        const int lt = g - vp.tile_base;
+        const int tx = lt % vp.tiles_x, ty = lt / vp.tiles_x;
+        int ox, oy;
+        lane_pixel(T, blk * 32 + lane, &ox, &oy);
+        const int px = tx * T + ox, py = ty * T + oy;
+        const bool inside = px < vp.W && py < vp.H;
+        if (!__any_sync(0xffffffffu, inside)) continue;      // block entirely outside the image
+        const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+        // sample rectangle of this 8 x 4 block
+        const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f;
+        const float by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
+        const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
+        const uint2 range = ranges[g];
 
-    float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    Splat nxt;
-    if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
-    for (uint32_t base = range.x; base < range.y; base += 32) {
-        const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
-        const uint32_t kept = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) {
-            const int slot = __popc(kept & lt_mask);
-            s_xy[w][slot] = nxt.xy;
-            s_q[w][slot] = nxt.q;
-            s_cd[w][slot] = nxt.cd;
-            s_pos[w][slot] = base - range.x + lane;
+        float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
+        uint32_t last = 0;
+        bool done = !inside;
+        Splat nxt;
+        if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
+        for (uint32_t base = range.x; base < range.y; base += 32) {
+            const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
+            const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) {
+                const int slot = __popc(kept & lt_mask);
+                s_xy[w][slot] = nxt.xy;
+                s_q[w][slot] = nxt.q;
+                s_cd[w][slot] = nxt.cd;
+                s_pos[w][slot] = base - range.x + lane;
+            }
+            __syncwarp();
+            if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[base + 32 + lane]);
+            const int cnt = __popc(kept);
+            for (int k = 0; k < cnt && !done; k++) {
+                const float2 m = s_xy[w][k];
+                const float4 q = s_q[w][k];
+                const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
+                const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
+                if (p2 > 0.f) continue;
+                const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
+                if (a < amin) continue;
+                const float test = __fmaf_rn(-a, Tr, Tr);
+                if (test < tcut) { done = true; break; }
+                const float4 c = s_cd[w][k];
+                const float wgt = __fmul_rn(a, Tr);
+                cr = __fmaf_rn(c.x, wgt, cr);
+                cg = __fmaf_rn(c.y, wgt, cg);
+                cb = __fmaf_rn(c.z, wgt, cb);
+                dd = __fmaf_rn(c.w, wgt, dd);
+                Tr = test;
+                last = s_pos[w][k] + 1u;
+            }
+            if (__all_sync(0xffffffffu, done)) break;
+        }
+        if (inside) {
+            const int HW = vp.W * vp.H;
+            const int pix = py * vp.W + px;
+            float* col = img.color + 3 * (size_t)vp.pix_base;
+            col[pix] = cr + Tr * rc.bg[0];
+            col[HW + pix] = cg + Tr * rc.bg[1];
+            col[2 * HW + pix] = cb + Tr * rc.bg[2];
+            img.depth[vp.pix_base + pix] = dd;
+            img.T_final[vp.pix_base + pix] = Tr;
+            img.n_contrib[vp.pix_base + pix] = last;
         }
         __syncwarp();
-        if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[base + 32 + lane]);
-        const int cnt = __popc(kept);
-        for (int k = 0; k < cnt && !done; k++) {
-            const float2 m = s_xy[w][k];
-            const float4 q = s_q[w][k];
-            const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
-            const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-            if (p2 > 0.f) continue;
-            const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
-            if (a < amin) continue;
-            const float test = __fmaf_rn(-a, Tr, Tr);
-            if (test < tcut) { done = true; break; }
-            const float4 c = s_cd[w][k];
-            const float wgt = __fmul_rn(a, Tr);
-            cr = __fmaf_rn(c.x, wgt, cr);
-            cg = __fmaf_rn(c.y, wgt, cg);
-            cb = __fmaf_rn(c.z, wgt, cb);
-            dd = __fmaf_rn(c.w, wgt, dd);
-            Tr = test;
-            last = s_pos[w][k] + 1u;
-        }
-        if (__all_sync(0xffffffffu, done)) break;
-    }
-    if (inside) {
-        const int HW = vp.W * vp.H;
-        const int pix = py * vp.W + px;
-        float* col = img.color + 3 * (size_t)vp.pix_base;
-        col[pix] = cr + Tr * rc.bg[0];
-        col[HW + pix] = cg + Tr * rc.bg[1];
-        col[2 * HW + pix] = cb + Tr * rc.bg[2];
-        img.depth[vp.pix_base + pix] = dd;
-        img.T_final[vp.pix_base + pix] = Tr;
-        img.n_contrib[vp.pix_base + pix] = last;
     }
 }
 
@@ -276,30 +294,26 @@ __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const f
     return true;
 }
 
+// Backward of one work item (pixel block blk of tile g) by one warp, using the
+// warp's shared-memory slot (s_xy .. s_pos: 32 entries each).
 template <int T>
-__global__ void __launch_bounds__(TileShape<T>::kThreads, T == 16 ? 4 : 1) k_render_bwd(
+__device__ __forceinline__ void bwd_item(
+        int g, int blk, float2* s_xy, float4* s_q, float4* s_cd, uint32_t* s_e, uint32_t* s_pos,
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
-        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
-        const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, const Views& views,
+        const RenderConsts& rc, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d) {
-    constexpr int W = TileShape<T>::kWarps;
-    __shared__ float2 s_xy[W][32];
-    __shared__ float4 s_q[W][32];      // scaled conic + opacity
-    __shared__ float4 s_cd[W][32];     // r, g, b, z
-    __shared__ uint32_t s_e[W][32];
-    __shared__ uint32_t s_pos[W][32];
-    const int g = blockIdx.x;
+    const int lane = threadIdx.x & 31;
     const int v = view_of_tile(views, g);
     const ViewParams& vp = views.v[v];
     const int lt = g - vp.tile_base;
     const int tx = lt % vp.tiles_x, ty = lt / vp.tiles_x;
     int ox, oy;
-    lane_pixel(T, threadIdx.x, &ox, &oy);
+    lane_pixel(T, blk * 32 + lane, &ox, &oy);
     const int px = tx * T + ox, py = ty * T + oy;
     const bool inside = px < vp.W && py < vp.H;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
-    const float bx0 = (float)(tx * T + (w % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (w / (T / 8)) * 4) + 0.5f;
+    const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
     const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint2 range = ranges[g];
@@ -344,11 +358,11 @@ __global__ void __launch_bounds__(TileShape<T>::kThreads, T == 16 ? 4 : 1) k_ren
         __syncwarp();
         if (keep) {
             const int sl = __popc(kept & lt_mask);
-            s_xy[w][sl] = n_xy;
-            s_q[w][sl] = n_q;
-            s_cd[w][sl] = n_cd;
-            s_e[w][sl] = n_e;
-            s_pos[w][sl] = lo + lane - range.x;
+            s_xy[sl] = n_xy;
+            s_q[sl] = n_q;
+            s_cd[sl] = n_cd;
+            s_e[sl] = n_e;
+            s_pos[sl] = lo + lane - range.x;
         }
         __syncwarp();
         const uint32_t nlo = lo > range.x + 32 ? lo - 32 : range.x;
@@ -357,47 +371,92 @@ __global__ void __launch_bounds__(TileShape<T>::kThreads, T == 16 ? 4 : 1) k_ren
         int k = cnt - 1;
         for (; k >= 1; k -= 2) {
             float ga[10], gb[10];
-            const bool ca = bwd_pixel(P, sx, sy, s_xy[w][k], s_q[w][k], s_cd[w][k], amin, amax, s_pos[w][k], ga);
-            const bool cb = bwd_pixel(P, sx, sy, s_xy[w][k - 1], s_q[w][k - 1], s_cd[w][k - 1], amin, amax,
-                                      s_pos[w][k - 1], gb);
+            const bool ca = bwd_pixel(P, sx, sy, s_xy[k], s_q[k], s_cd[k], amin, amax, s_pos[k], ga);
+            const bool cb = bwd_pixel(P, sx, sy, s_xy[k - 1], s_q[k - 1], s_cd[k - 1], amin, amax,
+                                      s_pos[k - 1], gb);
             const bool anya = __any_sync(0xffffffffu, ca), anyb = __any_sync(0xffffffffu, cb);
             if (anya || anyb) {
                 float ua, ub;
                 warp_reduce10x2(ga, gb, lane, &ua, &ub);
                 if (slot >= 0) {
-                    if (anya) atomicAdd(g2d + (size_t)kGradStride * s_e[w][k] + col, ua);
-                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * s_e[w][k - 1] + col, ub);
+                    if (anya) atomicAdd(g2d + (size_t)kGradStride * s_e[k] + col, ua);
+                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * s_e[k - 1] + col, ub);
                 }
             }
         }
         if (k == 0) {
             float ga[10], gb[10];
-            const bool ca = bwd_pixel(P, sx, sy, s_xy[w][0], s_q[w][0], s_cd[w][0], amin, amax, s_pos[w][0], ga);
+            const bool ca = bwd_pixel(P, sx, sy, s_xy[0], s_q[0], s_cd[0], amin, amax, s_pos[0], ga);
 #pragma unroll
             for (int r = 0; r < 10; r++) gb[r] = 0.f;
             if (__any_sync(0xffffffffu, ca)) {
                 float ua, ub;
                 warp_reduce10x2(ga, gb, lane, &ua, &ub);
-                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * s_e[w][0] + col, ua);
+                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * s_e[0] + col, ua);
             }
         }
     }
 }
 
+template <int T>
+__global__ void __launch_bounds__(kRasterThreads, 4) k_render_bwd(
+        const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
+        const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+        const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
+        int* __restrict__ queue, int n_items) {
+    constexpr int W = TileShape<T>::kWarps;
+    __shared__ float2 s_xy[kRasterWarps][32];
+    __shared__ float4 s_q[kRasterWarps][32];      // scaled conic + opacity
+    __shared__ float4 s_cd[kRasterWarps][32];     // r, g, b, z
+    __shared__ uint32_t s_e[kRasterWarps][32];
+    __shared__ uint32_t s_pos[kRasterWarps][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = next_item(queue, lane); item < n_items; item = next_item(queue, lane)) {
+        bwd_item<T>(item / W, item % W, s_xy[w], s_q[w], s_cd[w], s_e[w], s_pos[w], xy, conic_o, rgbd, vals, ranges,
+                    views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d);
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+// CTAs of a persistent raster launch: every SM filled to the kernel's occupancy
+// (host-side occupancy query; no stream operation, so it may run during capture).
+template <typename K>
+static int persistent_grid(K kernel, int n_items) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRasterThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int want = (n_items + kRasterWarps - 1) / kRasterWarps;
+    const int g = sms * per_sm;
+    return want < g ? want : g;
+}
 
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
                               const RenderConsts& rc, const gs_image& img, cudaStream_t s) {
-    const int grid = views.total_tiles;
-    if (grid == 0) return cudaSuccess;
+    if (views.total_tiles == 0) return cudaSuccess;
     const float2* xy = reinterpret_cast<const float2*>(pr.xy);
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
+    int* queue = bins.status + 1;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
     switch (rc.tile) {
-        case 8: k_render_fwd<8><<<grid, TileShape<8>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img); break;
-        case 16: k_render_fwd<16><<<grid, TileShape<16>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img); break;
-        case 32: k_render_fwd<32><<<grid, TileShape<32>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img); break;
+#define GS_FWD(TT)                                                                                     \
+    case TT: {                                                                                         \
+        const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
+        k_render_fwd<TT><<<persistent_grid(k_render_fwd<TT>, n_items), kRasterThreads, 0, s>>>(       \
+            xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items);                               \
+        break;                                                                                         \
+    }
+        GS_FWD(8)
+        GS_FWD(16)
+        GS_FWD(32)
+#undef GS_FWD
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -405,22 +464,26 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 
 cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img, const float* dc,
                               const float* dd, const Views& views, const RenderConsts& rc, float* g2d, cudaStream_t s) {
-    const int grid = views.total_tiles;
-    if (grid == 0) return cudaSuccess;
+    if (views.total_tiles == 0) return cudaSuccess;
     const float2* xy = reinterpret_cast<const float2*>(pr.xy);
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
+    int* queue = bins.status + 2;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
     switch (rc.tile) {
-        case 8:
-            k_render_bwd<8><<<grid, TileShape<8>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d);
-            break;
-        case 16:
-            k_render_bwd<16><<<grid, TileShape<16>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d);
-            break;
-        case 32:
-            k_render_bwd<32><<<grid, TileShape<32>::kThreads, 0, s>>>(xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d);
-            break;
+#define GS_BWD(TT)                                                                                     \
+    case TT: {                                                                                         \
+        const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
+        k_render_bwd<TT><<<persistent_grid(k_render_bwd<TT>, n_items), kRasterThreads, 0, s>>>(       \
+            xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
+        break;                                                                                         \
+    }
+        GS_BWD(8)
+        GS_BWD(16)
+        GS_BWD(32)
+#undef GS_BWD
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -240,14 +240,14 @@ class Bins:
     vals: "torch.Tensor"       # int32 storage of uint32 values
     ranges: "torch.Tensor"     # int32 [total_tiles, 2]
     num_keys: "torch.Tensor"   # int32 [1]
-    status: "torch.Tensor"     # int32 [1]
+    status: "torch.Tensor"     # int32 [4]: status word + raster work counters
 
     @staticmethod
     def empty(capacity, total_tiles, device="cuda"):
         import torch
         i = dict(device=device, dtype=torch.int32)
         return Bins(torch.empty(max(capacity, 1), device=device, dtype=torch.int64), torch.empty(max(capacity, 1), **i),
-                    torch.zeros(total_tiles, 2, **i), torch.zeros(1, **i), torch.zeros(1, **i))
+                    torch.zeros(total_tiles, 2, **i), torch.zeros(1, **i), torch.zeros(4, **i))
 
     @property
     def capacity(self):

@@ -15,6 +15,15 @@ GRAD_RTOL = 1e-3       # relative L2, gradients
 MARGIN_EXCUSE = 1e-5   # relative distance of a threshold decision that may flip between fp32 and fp64
 
 
+def margin_excuse(cam) -> float:
+    """Relative threshold margin within which fp32 may decide differently from
+    fp64, for a view of this size: the projected mean carries ~1 ulp of its
+    pixel coordinate (1.2e-7 x coordinate), and a splat's log-weight moves by up
+    to ~2 per pixel of mean shift at its alpha_min contour, so the relative
+    weight error reaches ~2.4e-7 x the largest coordinate (1e-5 floor)."""
+    return max(MARGIN_EXCUSE, 2.4e-7 * max(int(cam.width), int(cam.height)))
+
+
 def ensure_lib():
     B.build()
     return G.load_library()
@@ -112,3 +121,25 @@ def grads_to_numpy(gr: G.Grads):
     d = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(oracle.PARAM_NAMES, gr.tensors())}
     d["pose"] = gr.pose.cpu().numpy().astype(np.float64) if gr.pose is not None else None
     return d
+
+
+def excused_pixels(crop_xywh, gpu_rect, oracle_rect, oracle_margin, tile, excuse=MARGIN_EXCUSE):
+    """Pixels of a tile-aligned window that fp32 / fp64 rounding may
+    legitimately change: threshold decisions within MARGIN_EXCUSE of their
+    threshold, and every pixel of a tile where an entry's GPU and oracle tile
+    rectangles differ (rounding-boundary radius or centre).  gpu_rect is the
+    full view's [n, 4]; oracle_rect is relative to the window.  Returns the
+    boolean mask [h, w] and the number of differing rectangles."""
+    x0, y0, w, h = crop_xywh
+    ex = oracle_margin < excuse
+    tx0, ty0 = x0 // tile, y0 // tile
+    tw, th = (w + tile - 1) // tile, (h + tile - 1) // tile
+    g_rect = np.array(gpu_rect, copy=True)
+    g_rect[:, [0, 2]] = np.clip(g_rect[:, [0, 2]] - tx0, 0, tw)
+    g_rect[:, [1, 3]] = np.clip(g_rect[:, [1, 3]] - ty0, 0, th)
+    g_rect[(g_rect[:, 2] <= g_rect[:, 0]) | (g_rect[:, 3] <= g_rect[:, 1])] = 0
+    diff = np.nonzero(np.any(g_rect != oracle_rect, axis=1))[0]
+    for i in diff:
+        for rr in (g_rect[i], oracle_rect[i]):
+            ex[rr[1] * tile:rr[3] * tile, rr[0] * tile:rr[2] * tile] = True
+    return ex, len(diff)

@@ -18,8 +18,9 @@ import oracle
 from paper_2512_02293_gb300 import gs as G
 from paper_2512_02293_gb300 import synth
 from paper_2512_02293_gb300.mapping import MapParams, MappingStep
-from gpu_common import (COLOR_TOL, GRAD_RTOL, MARGIN_EXCUSE, bins_to_numpy, ensure_lib, f32, grads_to_numpy,
-                        oracle_bins, prm_dict, projected_to_device, rel_l2, round_projection, run_bin_sort)
+from gpu_common import (COLOR_TOL, GRAD_RTOL, bins_to_numpy, ensure_lib, excused_pixels, f32, grads_to_numpy,
+                        margin_excuse, oracle_bins, prm_dict, projected_to_device, rel_l2, round_projection,
+                        run_bin_sort)
 
 pytestmark = pytest.mark.gpu
 
@@ -97,21 +98,7 @@ def test_gpu_keys_properties(setup):
 
 
 def _excused(cam, crop_xywh, pr_gpu_rect, pr_or, img_or):
-    """Pixels of the window that fp32/fp64 rounding may legitimately change:
-    threshold margins below 1e-5 and tiles where a rectangle differs."""
-    x0, y0, w, h = crop_xywh
-    ex = img_or["margin"] < MARGIN_EXCUSE
-    tx0, ty0 = x0 // 16, y0 // 16
-    tw, th = (w + 15) // 16, (h + 15) // 16
-    g_rect = pr_gpu_rect.copy()
-    g_rect[:, [0, 2]] = np.clip(g_rect[:, [0, 2]] - tx0, 0, tw)
-    g_rect[:, [1, 3]] = np.clip(g_rect[:, [1, 3]] - ty0, 0, th)
-    g_rect[(g_rect[:, 2] <= g_rect[:, 0]) | (g_rect[:, 3] <= g_rect[:, 1])] = 0
-    diff = np.nonzero(np.any(g_rect != pr_or["rect"], axis=1))[0]
-    for i in diff:
-        for rr in (g_rect[i], pr_or["rect"][i]):
-            ex[rr[1] * 16:rr[3] * 16, rr[0] * 16:rr[2] * 16] = True
-    return ex, len(diff)
+    return excused_pixels(crop_xywh, pr_gpu_rect, pr_or["rect"], img_or["margin"], 16, margin_excuse(cam))
 
 
 @pytest.mark.parametrize("win", WINDOWS)

@@ -78,7 +78,7 @@ def test_bin_sort_bit_exact(tile):
     keys_o, vals_o, ranges_o = oracle_bins(prs, [cam], tile)
     bins, _ = run_bin_sort(proj, g.n, [cam], params, capacity=len(keys_o) + 17)
     keys, vals, ranges = bins_to_numpy(bins)
-    assert int(bins.status.item()) == 0
+    assert int(bins.status[0].item()) == 0
     np.testing.assert_array_equal(keys, keys_o)
     np.testing.assert_array_equal(vals, vals_o)
     np.testing.assert_array_equal(ranges, ranges_o)
