@@ -105,9 +105,9 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_step(device, g, gt, cams):
+def build_step(device, g, gt, cams, candidates=(8, 16, 32)):
     """Target images of the perturbed map (input preparation, not timed), then a
-    mapping step on the map with the autotuned tile size."""
+    mapping step on the map with the tile size autotuned over `candidates`."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep, autotune_tile
@@ -121,7 +121,7 @@ def build_step(device, g, gt, cams):
     tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
     del tstep
     gd = G.Gaussians.from_numpy(g, device)
-    params, tune = autotune_tile(gd, cams, tc, td, params, mp)
+    params, tune = autotune_tile(gd, cams, tc, td, params, mp, candidates=candidates)
     step = MappingStep(gd, cams, tc, td, params, mp)
     step.tune = tune
     return params, mp, step, tc, td
@@ -298,7 +298,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     iteration one CUDA graph, tile size autotuned."""
     from paper_2512_02293_gb300 import synth
     g, gt, cams = synth.cfg3_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, cams)
+    params, mp, step, tc, td = build_step(device, g, gt, cams, args.tiles)
     steps = max(10, args.steps // 4)
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
@@ -320,7 +320,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-window", action="store_true")
+    ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
+                    help="fix the tile size instead of autotuning over {8, 16, 32}")
     args = ap.parse_args()
+    args.tiles = (args.tile,) if args.tile else (8, 16, 32)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -342,7 +345,7 @@ def main():
 
     from paper_2512_02293_gb300 import synth
     g, gt, cam = synth.cfg2_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, [cam])
+    params, mp, step, tc, td = build_step(device, g, gt, [cam], args.tiles)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
     flush = lambda: flush_buf.fill_(1.0)
     times, st, pairs, clocks = timed_run(step, args.steps, args.warmup, flush, dist, local)

@@ -105,7 +105,7 @@ __device__ __forceinline__ int next_item(int* queue, int lane) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(kRasterThreads) k_render_fwd(
+__global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         gs_image img, int* __restrict__ queue, int n_items) {
@@ -138,8 +138,12 @@ __global__ void __launch_bounds__(kRasterThreads) k_render_fwd(
         float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
         uint32_t last = 0;
         bool done = !inside;
+        // the next batch's splats and the one after's list entries are in flight
+        // while a batch is composited, so a splat load never waits on its index
         Splat nxt;
+        uint32_t nidx = 0;
         if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
+        if (range.x + 32 + lane < range.y) nidx = vals[range.x + 32 + lane];
         for (uint32_t base = range.x; base < range.y; base += 32) {
             const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
             const uint32_t kept = __ballot_sync(0xffffffffu, keep);
@@ -152,7 +156,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_render_fwd(
                 s_pos[w][slot] = base - range.x + lane;
             }
             __syncwarp();
-            if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[base + 32 + lane]);
+            if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
+            if (base + 64 + lane < range.y) nidx = vals[base + 64 + lane];
             const int cnt = __popc(kept);
             for (int k = 0; k < cnt && !done; k++) {
                 const float2 m = s_xy[w][k];
@@ -254,44 +259,43 @@ struct BwdPix {
 // O(1 ulp) difference that only enters gradient values, never a decision).
 constexpr float kUnscaleAC = -2.0f / kLog2e, kUnscaleB = -1.0f / kLog2e;
 
+// Branch-free: every lane evaluates the splat, and the ones that did not blend it
+// in the forward pass (past their checkpoint, power > 0, alpha < alpha_min -- the
+// forward's tests, written the same way) keep their state and contribute zeros
+// through selects, so the warp never diverges here.
 __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const float2 m, const float4 q,
                                           const float4 cd, float amin, float amax, uint32_t pos, float (&gv)[10]) {
-#pragma unroll
-    for (int r = 0; r < 10; r++) gv[r] = 0.f;
-    if (pos >= P.np) return false;
     const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
     const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-    if (p2 > 0.f) return false;
     const float G = splat_weight(p2);
     const float araw = __fmul_rn(q.w, G);
     const float a = fminf(amax, araw);
-    if (a < amin) return false;
+    const bool c = pos < P.np && !(p2 > 0.f) && !(a < amin);
     const float one_m = 1.0f - a;
     const float Tb = __fdividef(P.T, one_m);      // transmittance before this splat
-    const float w = a * Tb;
+    const float w = c ? a * Tb : 0.f;
     const float dr = cd.x - P.Sr, dg = cd.y - P.Sg, db = cd.z - P.Sb, dz = cd.w - P.Sd;
     const float dLda = Tb * (dr * P.gr + dg * P.gg + db * P.gb + dz * P.gd);
-    P.Sr = fmaf(a, dr, P.Sr);
-    P.Sg = fmaf(a, dg, P.Sg);
-    P.Sb = fmaf(a, db, P.Sb);
-    P.Sd = fmaf(a, dz, P.Sd);
-    P.T = Tb;
+    P.Sr = c ? fmaf(a, dr, P.Sr) : P.Sr;
+    P.Sg = c ? fmaf(a, dg, P.Sg) : P.Sg;
+    P.Sb = c ? fmaf(a, db, P.Sb) : P.Sb;
+    P.Sd = c ? fmaf(a, dz, P.Sd) : P.Sd;
+    P.T = c ? Tb : P.T;
     gv[7] = P.gr * w;
     gv[8] = P.gg * w;
     gv[9] = P.gb * w;
     gv[6] = P.gd * w;
-    if (araw < amax) {                            // alpha not clamped
-        const float dpow = dLda * a;              // d alpha / d power = alpha
-        gv[5] = dLda * G;                         // d alpha / d o = exp(power)
-        const float A = q.x * kUnscaleAC, B = q.y * kUnscaleB, C = q.z * kUnscaleAC;
-        gv[0] = dpow * fmaf(A, dx, B * dy);
-        gv[1] = dpow * fmaf(B, dx, C * dy);
-        const float hx = -0.5f * dpow * dx;
-        gv[2] = hx * dx;
-        gv[3] = -dpow * dx * dy;
-        gv[4] = -0.5f * dpow * dy * dy;
-    }
-    return true;
+    const bool cu = c && araw < amax;             // alpha not clamped
+    const float dpow = cu ? dLda * a : 0.f;       // d alpha / d power = alpha
+    gv[5] = cu ? dLda * G : 0.f;                  // d alpha / d o = exp(power)
+    const float A = q.x * kUnscaleAC, B = q.y * kUnscaleB, C = q.z * kUnscaleAC;
+    gv[0] = dpow * fmaf(A, dx, B * dy);
+    gv[1] = dpow * fmaf(B, dx, C * dy);
+    const float hx = -0.5f * dpow * dx;
+    gv[2] = hx * dx;
+    gv[3] = -dpow * dx * dy;
+    gv[4] = -0.5f * dpow * dy * dy;
+    return c;
 }
 
 // Backward of one work item (pixel block blk of tile g) by one warp, using the
@@ -338,21 +342,24 @@ __device__ __forceinline__ void bwd_item(
     if (top <= range.x) return;
     const int slot = slot_of_lane(lane);
     const int col = slot < 7 ? slot : slot + 1;
-    uint32_t lo = top > range.x + 32 ? top - 32 : range.x;
-    // the next 32 splats (below the current batch) in flight in registers
+    // batches of 32 list positions [lo, hi) walk down from top; the next batch's
+    // splats and the list entries of the one below it are in flight in registers
+    auto below = [&](uint32_t b) { return b > range.x + 32 ? b - 32 : range.x; };
+    uint32_t lo = below(top);
     float2 n_xy = make_float2(0.f, 0.f);
     float4 n_q = make_float4(0.f, 0.f, 0.f, 0.f), n_cd = n_q;
-    uint32_t n_e = 0;
-    auto fetch = [&](uint32_t j) {
-        n_e = vals[j];
-        const float4 c = conic_o[n_e];
+    uint32_t n_e = 0, nn_e = 0;
+    auto fetch = [&](uint32_t e) {
+        n_e = e;
+        const float4 c = conic_o[e];
         scale_conic(c.x, c.y, c.z, &n_q.x, &n_q.y, &n_q.z);
         n_q.w = c.w;
-        n_xy = xy[n_e];
-        n_cd = rgbd[n_e];
+        n_xy = xy[e];
+        n_cd = rgbd[e];
     };
-    if (lo + lane < top) fetch(lo + lane);
-    for (uint32_t hi = top; hi > range.x; hi = lo, lo = (lo > range.x + 32 ? lo - 32 : range.x)) {
+    if (lo + lane < top) fetch(vals[lo + lane]);
+    if (lo > range.x && below(lo) + lane < lo) nn_e = vals[below(lo) + lane];
+    for (uint32_t hi = top; hi > range.x; hi = lo, lo = below(lo)) {
         const bool keep = lo + lane < hi && splat_reaches_block(n_xy, n_q, bx0, bx1, by0, by1, amin);
         const uint32_t kept = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
@@ -365,8 +372,9 @@ __device__ __forceinline__ void bwd_item(
             s_pos[sl] = lo + lane - range.x;
         }
         __syncwarp();
-        const uint32_t nlo = lo > range.x + 32 ? lo - 32 : range.x;
-        if (lo > range.x && nlo + lane < lo) fetch(nlo + lane);
+        const uint32_t nlo = below(lo);
+        if (lo > range.x && nlo + lane < lo) fetch(nn_e);
+        if (nlo > range.x && below(nlo) + lane < nlo) nn_e = vals[below(nlo) + lane];
         const int cnt = __popc(kept);
         int k = cnt - 1;
         for (; k >= 1; k -= 2) {
