@@ -8,8 +8,9 @@
 // list on its own:
 // lane l gathers splat base + l of the list into registers (float2 / float4
 // rows), the warp parks those 32 splats in its private shared-memory slot and
-// composites them with broadcast reads while the next 32 are already in
-// flight.  Before compositing, the warp drops the splats that cannot reach
+// composites them with broadcast reads while the next 32 (and the list entries
+// of the 32 after those) are already in flight.  A lane's per-splat tests are
+// predicates, not branches, so a warp never diverges inside a batch.  Before compositing, the warp drops the splats that cannot reach
 // alpha_min anywhere in its block.  There is no CTA-wide barrier, so a warp
 // stops as soon as its own 32 pixels are saturated and takes the next item; the
 // depth of a tile's deepest pixels (up to ~8x the mean) only costs its own warp.
@@ -158,25 +159,29 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
             __syncwarp();
             if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
             if (base + 64 + lane < range.y) nidx = vals[base + 64 + lane];
+            // warp-uniform loop; a lane's tests (power > 0, alpha < alpha_min, the
+            // transmittance cutoff) become predicates, so the warp never diverges
             const int cnt = __popc(kept);
-            for (int k = 0; k < cnt && !done; k++) {
+            for (int k = 0; k < cnt; k++) {
                 const float2 m = s_xy[w][k];
                 const float4 q = s_q[w][k];
                 const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
                 const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-                if (p2 > 0.f) continue;
                 const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
-                if (a < amin) continue;
                 const float test = __fmaf_rn(-a, Tr, Tr);
-                if (test < tcut) { done = true; break; }
+                const bool blend = !done && !(p2 > 0.f) && !(a < amin);
+                const bool stop = blend && test < tcut;
+                const bool b = blend && !stop;
+                done = done || stop;
                 const float4 c = s_cd[w][k];
-                const float wgt = __fmul_rn(a, Tr);
+                const float wgt = b ? __fmul_rn(a, Tr) : 0.f;
                 cr = __fmaf_rn(c.x, wgt, cr);
                 cg = __fmaf_rn(c.y, wgt, cg);
                 cb = __fmaf_rn(c.z, wgt, cb);
                 dd = __fmaf_rn(c.w, wgt, dd);
-                Tr = test;
-                last = s_pos[w][k] + 1u;
+                Tr = b ? test : Tr;
+                last = b ? s_pos[w][k] + 1u : last;
+                if (__all_sync(0xffffffffu, done)) break;
             }
             if (__all_sync(0xffffffffu, done)) break;
         }
