@@ -40,6 +40,10 @@ WORKLOAD = "plain single view, SLAM scale: 640x480, 200k Gaussians on a syntheti
 FWD_OPS_PER_PAIR = 20    # FP32 ops per visited (pixel, splat) pair in the forward definition
 BWD_OPS_PER_PAIR = 45    # FP32 ops per blended pair in the backward definition (+ reductions)
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the rasterisers
+# on this workload, from an ncu capture of the current kernels
+# (profiles/k_render_{bwd,fwd}_640x480_200k.md); keyed by (stage, tile).
+PROFILED_TRAFFIC = {("gs_render_bwd_raster", 16): 22.27e6, ("gs_render_fwd", 16): 9.27e6}
 
 
 def _peaks():
@@ -390,7 +394,8 @@ def main():
             ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"
         ach = pairs * ops / (ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
-                    "frac": ach / alu_peak, "traffic": None, "dominant_stage": dominant,
+                    "frac": ach / alu_peak, "traffic": PROFILED_TRAFFIC.get((dominant, params.tile)),
+                    "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "dominant_stage": dominant,
                     "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
                     "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
                     "timing": "CUDA event-record nodes around the call inside the timed graph, median over steps"}
