@@ -344,3 +344,20 @@ def cfg4_problem(trial: int = 0, n=1_000_000, views=16, width=1280, height=1024,
     cams, ctrl = trajectory_cameras(seed, sizes)
     g = room_scene(n, seed, keep_out=[c.t_wc for c in cams], sh_degree=3)
     return g, perturb_map(g, seed + 1), cams
+
+
+def mlp_params(seed: int, n_in: int = 196, n_hid: int = 128, n_out: int = 8, bias_sd: float = 0.1) -> dict:
+    """Seeded float32 weights of the 196 -> 128 -> 128 -> 8 initialiser network:
+    W ~ N(0, 1 / fan_in), biases ~ N(0, bias_sd^2)."""
+    rng = np.random.default_rng(seed)
+    f = lambda *shape, sd: (rng.standard_normal(shape) * sd).astype(np.float32)
+    return {"W1": f(n_hid, n_in, sd=1.0 / np.sqrt(n_in)), "b1": f(n_hid, sd=bias_sd),
+            "W2": f(n_hid, n_hid, sd=1.0 / np.sqrt(n_hid)), "b2": f(n_hid, sd=bias_sd),
+            "W3": f(n_out, n_hid, sd=1.0 / np.sqrt(n_hid)), "b3": f(n_out, sd=bias_sd)}
+
+
+def mlp_batch(seed: int, n: int, n_in: int = 196, n_out: int = 8):
+    """Seeded float32 inputs X [n, n_in] ~ U(-1, 1) and targets T [n, n_out] ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1.0, 1.0, (n, n_in)).astype(np.float32),
+            rng.standard_normal((n, n_out)).astype(np.float32))
