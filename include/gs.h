@@ -276,6 +276,69 @@ int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_v
 int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1, float beta2,
                      float eps, int32_t* d_step, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned initialiser of inserted Gaussians (keyframe insertion, Sec. 3.3
+ * "Map Management": the paper initialises a new Gaussian's opacity to 0.5 and
+ * leaves its shape to the mapper; this network predicts the shape).
+ * A perceptron GS_MLP_IN -> GS_MLP_HIDDEN -> GS_MLP_HIDDEN -> GS_MLP_OUT with
+ * GELU (x Phi(x), exact form) after both hidden layers:
+ *     Z1 = bf16(W1 x + b1), H1 = bf16(gelu(Z1)), Z2 = bf16(W2 H1 + b2),
+ *     H2 = bf16(gelu(Z2)), y = W3 H2 + b3,
+ * with BF16 weights and inputs and FP32 accumulation (tensor cores).
+ * x is a 7 x 7 RGB-D patch (see gs_extract_patches), y = (3 log-scale offsets,
+ * 4 quaternion components in the camera frame, 1 opacity logit).
+ *
+ * BF16 values are passed as uint16_t bit patterns.  Input rows are
+ * GS_MLP_IN_STRIDE values long (16-byte aligned rows); only the first
+ * GS_MLP_IN are read. */
+#define GS_MLP_IN 196
+#define GS_MLP_IN_STRIDE 208
+#define GS_MLP_HIDDEN 128
+#define GS_MLP_OUT 8
+
+/* FP32 master parameters (device): W1 [128][196], b1 [128], W2 [128][128],
+ * b2 [128], W3 [8][128], b3 [8], row-major (row = output unit). */
+typedef struct gs_mlp_params {
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+} gs_mlp_params;
+
+/* BF16 GEMM operands made by gs_mlp_pack (device, caller-owned, 16-byte
+ * aligned): W1a [128][208] (W1 | b1 | 0), W2a [128][144] (W2 | b2 | 0),
+ * W3a [16][144] (rows 0..7: W3 | b3 | 0; rows 8..15: 0), W2t [128][128] = W2^T. */
+typedef struct gs_mlp_packed {
+    uint16_t *W1a, *W2a, *W3a, *W2t;
+} gs_mlp_packed;
+
+/* FP32 gradients (device), same shapes as gs_mlp_params. */
+typedef struct gs_mlp_grads {
+    float *W1, *b1, *W2, *b2, *W3, *b3;
+} gs_mlp_grads;
+
+/* Round the master parameters to the BF16 operands.
+ * Errors: GS_ERR_INVALID_ARG on NULL or misaligned pointers. */
+int32_t gs_mlp_pack(const gs_mlp_params* params, const gs_mlp_packed* packed, void* stream);
+
+/* Forward pass over n samples X [n][GS_MLP_IN_STRIDE] (BF16).  Writes Y [n][8]
+ * (FP32) if Y is not NULL.  Training: Z1, Z2 [n][128] (BF16 pre-activations,
+ * needed by gs_mlp_bwd) if not NULL; with targets T [n][8] (FP32) also
+ * dY = 2 loss_scale (Y - T) [n][8] and *loss += loss_scale sum (Y - T)^2 (the
+ * caller zeroes *loss; loss_scale = 1 / (8 n) gives the mean squared error).
+ * d_status: device int32 status word (GS_ERR_TIMEOUT if a bounded wait gave up).
+ * One CTA per SM walks tiles of 128 samples (tcgen05 MMAs, accumulators in
+ * tensor memory).  Errors: GS_ERR_INVALID_ARG on NULL / misaligned pointers,
+ * n < 0, T without dY and loss. */
+int32_t gs_mlp_fwd(const gs_mlp_packed* packed, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
+                   uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int32_t* d_status,
+                   void* stream);
+
+/* Backward pass: gradients of sum(dY * Y) with respect to all parameters, from
+ * the inputs X, the forward's Z1, Z2 and dY (all [n][...] as above).
+ * OVERWRITES `grads` (zeroed, then accumulated over the batch).  Rounding:
+ * dZ2 = bf16((W3^T dY) * gelu'(Z2)), dZ1 = bf16((W2^T dZ2) * gelu'(Z1)).
+ * Errors: as gs_mlp_fwd. */
+int32_t gs_mlp_bwd(const gs_mlp_packed* packed, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
+                   const float* dY, int64_t n, const gs_mlp_grads* grads, int32_t* d_status, void* stream);
+
 /* Synchronises `stream`, copies the device status word to *host_status and
  * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);

@@ -284,4 +284,38 @@ int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* ho
     return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+int32_t gs_mlp_pack(const gs_mlp_params* p, const gs_mlp_packed* q, void* stream) {
+    if (p == nullptr || q == nullptr) return GS_ERR_INVALID_ARG;
+    if (!p->W1 || !p->b1 || !p->W2 || !p->b2 || !p->W3 || !p->b3) return GS_ERR_INVALID_ARG;
+    if (!q->W1a || !q->W2a || !q->W3a || !q->W2t) return GS_ERR_INVALID_ARG;
+    if (!aligned(q->W1a, 16) || !aligned(q->W2a, 16) || !aligned(q->W3a, 16) || !aligned(q->W2t, 16))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_mlp_pack(*p, *q, static_cast<cudaStream_t>(stream)));
+}
+
+static bool mlp_packed_ok(const gs_mlp_packed* q) {
+    return q != nullptr && q->W1a && q->W2a && q->W3a && q->W2t && aligned(q->W1a, 16) && aligned(q->W2a, 16) &&
+           aligned(q->W3a, 16) && aligned(q->W2t, 16);
+}
+
+int32_t gs_mlp_fwd(const gs_mlp_packed* q, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1, uint16_t* Z2,
+                   const float* T, float* dY, float* loss, float loss_scale, int32_t* d_status, void* stream) {
+    if (!mlp_packed_ok(q) || n < 0 || (n > 0 && (!X || !aligned(X, 16)))) return GS_ERR_INVALID_ARG;
+    if ((Y && !aligned(Y, 16)) || (Z1 && !aligned(Z1, 16)) || (Z2 && !aligned(Z2, 16))) return GS_ERR_INVALID_ARG;
+    if ((Z1 == nullptr) != (Z2 == nullptr)) return GS_ERR_INVALID_ARG;
+    if (T && (!aligned(T, 16) || !dY || !aligned(dY, 16) || !loss || !isfinite(loss_scale))) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_mlp_fwd(*q, X, n, Y, Z1, Z2, T, dY, loss, loss_scale, d_status,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_mlp_bwd(const gs_mlp_packed* q, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
+                   const float* dY, int64_t n, const gs_mlp_grads* g, int32_t* d_status, void* stream) {
+    if (!mlp_packed_ok(q) || n < 0 || g == nullptr) return GS_ERR_INVALID_ARG;
+    if (!g->W1 || !g->b1 || !g->W2 || !g->b2 || !g->W3 || !g->b3) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!X || !Z1 || !Z2 || !dY || !aligned(X, 16) || !aligned(Z1, 16) || !aligned(Z2, 16) ||
+                  !aligned(dY, 16)))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_mlp_bwd(*q, X, Z1, Z2, dY, n, *g, d_status, static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

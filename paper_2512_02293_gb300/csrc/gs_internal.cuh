@@ -69,6 +69,12 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const 
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s);
 cudaError_t noalloc_loss_scratch(float** out);
+cudaError_t launch_mlp_pack(const gs_mlp_params& p, const gs_mlp_packed& q, cudaStream_t s);
+cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
+                           uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int* status,
+                           cudaStream_t s);
+cudaError_t launch_mlp_bwd(const gs_mlp_packed& w, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
+                           const float* dY, int64_t n, const gs_mlp_grads& g, int* status, cudaStream_t s);
 cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps,
                         int32_t* d_step, cudaStream_t s);
 

@@ -78,10 +78,22 @@ class gs_adam_group(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
+class gs_mlp_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+class gs_mlp_packed(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1a", "W2a", "W3a", "W2t")]
+
+
+class gs_mlp_grads(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
 EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pixels", "gs_workspace_size",
            "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_loss_noalloc", "gs_render_bwd",
            "gs_render_bwd_raster",
-           "gs_project_bwd", "gs_adam_step", "gs_read_device_status"]
+           "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd"]
 
 
 def load_library(path: str | None = None):
@@ -125,6 +137,12 @@ def load_library(path: str | None = None):
     lib.gs_adam_step.argtypes = [V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float, V, V]
     lib.gs_read_device_status.restype = ctypes.c_int32
     lib.gs_read_device_status.argtypes = [V, V, V]
+    lib.gs_mlp_pack.restype = ctypes.c_int32
+    lib.gs_mlp_pack.argtypes = [V, V, V]
+    lib.gs_mlp_fwd.restype = ctypes.c_int32
+    lib.gs_mlp_fwd.argtypes = [V, V, ctypes.c_int64, V, V, V, V, V, V, ctypes.c_float, V, V]
+    lib.gs_mlp_bwd.restype = ctypes.c_int32
+    lib.gs_mlp_bwd.argtypes = [V, V, V, V, V, ctypes.c_int64, V, V, V]
     if lib.gs_abi_version() != 1:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
@@ -400,3 +418,49 @@ def gs_read_device_status(d_status, stream=None) -> int:
     _check(load_library().gs_read_device_status(_ptr(d_status), _stream(stream), ctypes.byref(out)),
            "gs_read_device_status")
     return int(out.value)
+
+
+# ------------------------------------------------------ learned initialiser
+
+MLP_IN, MLP_IN_STRIDE, MLP_HIDDEN, MLP_OUT = 196, 208, 128, 8
+MLP_PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+MLP_PARAM_SHAPES = {"W1": (128, 196), "b1": (128,), "W2": (128, 128), "b2": (128,), "W3": (8, 128), "b3": (8,)}
+
+
+class MlpPacked:
+    """BF16 GEMM operands (W1a [128,208], W2a [128,144], W3a [16,144], W2t [128,128])."""
+
+    def __init__(self, device="cuda"):
+        import torch
+        bf = torch.bfloat16
+        self.W1a = torch.zeros(128, 208, device=device, dtype=bf)
+        self.W2a = torch.zeros(128, 144, device=device, dtype=bf)
+        self.W3a = torch.zeros(16, 144, device=device, dtype=bf)
+        self.W2t = torch.zeros(128, 128, device=device, dtype=bf)
+
+    def struct(self):
+        return gs_mlp_packed(_ptr(self.W1a), _ptr(self.W2a), _ptr(self.W3a), _ptr(self.W2t))
+
+
+def gs_mlp_pack(params: dict, packed: MlpPacked, stream=None):
+    """params: dict of FP32 device tensors W1, b1, W2, b2, W3, b3."""
+    p = gs_mlp_params(*[_ptr(params[k]) for k in MLP_PARAM_NAMES])
+    q = packed.struct()
+    _check(load_library().gs_mlp_pack(ctypes.byref(p), ctypes.byref(q), _stream(stream)), "gs_mlp_pack")
+
+
+def gs_mlp_fwd(packed: MlpPacked, X, Y=None, Z1=None, Z2=None, T=None, dY=None, loss=None, loss_scale: float = 0.0,
+               status=None, stream=None):
+    """X: bfloat16 [n, 208]; Y, dY, T float32 [n, 8]; Z1, Z2 bfloat16 [n, 128]."""
+    q = packed.struct()
+    _check(load_library().gs_mlp_fwd(ctypes.byref(q), _ptr(X), X.shape[0], _ptr(Y), _ptr(Z1), _ptr(Z2), _ptr(T),
+                                     _ptr(dY), _ptr(loss), float(loss_scale), _ptr(status), _stream(stream)),
+           "gs_mlp_fwd")
+
+
+def gs_mlp_bwd(packed: MlpPacked, X, Z1, Z2, dY, grads: dict, status=None, stream=None):
+    """grads: dict of FP32 device tensors shaped like the parameters (overwritten)."""
+    q = packed.struct()
+    g = gs_mlp_grads(*[_ptr(grads[k]) for k in MLP_PARAM_NAMES])
+    _check(load_library().gs_mlp_bwd(ctypes.byref(q), _ptr(X), _ptr(Z1), _ptr(Z2), _ptr(dY), X.shape[0],
+                                     ctypes.byref(g), _ptr(status), _stream(stream)), "gs_mlp_bwd")

@@ -84,3 +84,21 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib):
     assert lib.gs_bin_sort(None, 0, cams, 1, ctypes.byref(p), ctypes.byref(bins), None, 0, None) == 1
     nan_cam = G.camera_array([synth.Camera(float("nan"), 60.0, 32.0, 24.0, 64, 48)])
     assert lib.gs_total_tiles(nan_cam, 1, 16) == -1
+
+
+def test_mlp_entry_points_reject_bad_arguments(lib):
+    # host checks of the learned-initialiser calls; nothing reaches the device
+    V = ctypes.c_void_p
+    q = G.gs_mlp_packed(V(256), V(512), V(768), V(1024))
+    qbad = G.gs_mlp_packed(V(256), V(512), V(770), V(1024))                 # misaligned W3a
+    assert lib.gs_mlp_pack(None, ctypes.byref(q), None) == 1
+    assert lib.gs_mlp_fwd(None, V(256), 4, None, None, None, None, None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(qbad), V(256), 4, None, None, None, None, None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(q), V(256), -1, None, None, None, None, None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(q), None, 4, None, None, None, None, None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(q), V(256), 4, None, V(256), None, None, None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(q), V(256), 4, None, None, None, V(256), None, None, 0.0, None, None) == 1
+    assert lib.gs_mlp_fwd(ctypes.byref(q), V(258), 4, None, None, None, None, None, None, 0.0, None, None) == 1
+    g = G.gs_mlp_grads(V(256), V(256), V(256), V(256), V(256), None)
+    assert lib.gs_mlp_bwd(ctypes.byref(q), V(256), V(256), V(256), V(256), 4, ctypes.byref(g), None, None) == 1
+    assert lib.gs_mlp_bwd(ctypes.byref(q), V(256), V(256), V(256), V(256), 4, None, None, None) == 1
