@@ -339,6 +339,48 @@ int32_t gs_mlp_fwd(const gs_mlp_packed* packed, const uint16_t* X, int64_t n, fl
 int32_t gs_mlp_bwd(const gs_mlp_packed* packed, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
                    const float* dY, int64_t n, const gs_mlp_grads* grads, int32_t* d_status, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Keyframe insertion (Sec. 3.3 "Map Management").  A keyframe is one view:
+ * colour [3][H][W] and depth [H][W] (device, FP32, planar), its gs_camera, and
+ * n sample pixels uv [n][2] (device int32, (u, v) = (column, row)).  Samples
+ * outside the image record GS_ERR_INVALID_ARG in *d_status (if not NULL). */
+
+/* Writable destination rows of a map (device): row offset + k receives the
+ * Gaussian of sample k.  Same layouts as gs_gaussians; capacity = rows. */
+typedef struct gs_map_slots {
+    float* mean;
+    float* quat;
+    float* log_scale;
+    float* opacity_logit;
+    float* color;
+    int64_t capacity;
+} gs_map_slots;
+
+/* Network input of each sample: X [n][GS_MLP_IN_STRIDE] BF16.  Window pixel
+ * p = 7 (dy + 3) + (dx + 3), dx, dy in [-3, 3], is pixel (u + dx, v + dy)
+ * clamped to the image; X[4p .. 4p+2] = its RGB, X[4p+3] = its relative depth
+ * (d_p - d_c) f / (7 d_c) with f = (fx + fy) / 2, d_c the sample's depth, 0 where
+ * either depth is <= 0; the centre's depth slot (p = 24) holds log d_c (0 if
+ * d_c <= 0).  X[196] = 1, X[197..207] = 0.  Values rounded to nearest BF16.
+ * Errors: GS_ERR_INVALID_ARG on NULL / misaligned pointers, n < 0, bad camera. */
+int32_t gs_extract_patches(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv,
+                           int64_t n, uint16_t* X, int32_t* d_status, void* stream);
+
+/* New Gaussians at the samples, written to rows offset .. offset + n - 1 of dst.
+ * Heuristic (Y == NULL): mean = back-projection of the pixel centre at its
+ * depth d, isotropic log_scale = log(d stride / f) (f = (fx + fy) / 2),
+ * identity rotation, opacity logit 0 (opacity 0.5, Sec. 3.3), colour = pixel
+ * RGB (sh_degree 3: the DC coefficient (rgb - 0.5) / Y00, others 0).
+ * Learned (Y [n][8] from gs_mlp_fwd): log_scale = heuristic + Y[0..2],
+ * rotation = R_wc composed with the normalised camera-frame quaternion Y[3..6],
+ * opacity logit = Y[7].  A sample with depth <= 0 becomes an inert Gaussian
+ * (logit -30, log_scale -10) at the camera centre.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers, n < 0, stride <= 0,
+ * offset + n > capacity, sh_degree not 0 or 3, bad camera. */
+int32_t gs_insert_gaussians(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv,
+                            int64_t n, float stride, const float* Y, const gs_map_slots* dst, int64_t offset,
+                            int32_t sh_degree, int32_t* d_status, void* stream);
+
 /* Synchronises `stream`, copies the device status word to *host_status and
  * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);

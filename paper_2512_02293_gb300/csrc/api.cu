@@ -318,4 +318,31 @@ int32_t gs_mlp_bwd(const gs_mlp_packed* q, const uint16_t* X, const uint16_t* Z1
     return cuda_status(launch_mlp_bwd(*q, X, Z1, Z2, dY, n, *g, d_status, static_cast<cudaStream_t>(stream)));
 }
 
+static bool keyframe_ok(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv, int64_t n) {
+    if (cam == nullptr || n < 0) return false;
+    Views views;
+    if (!make_views(cam, 1, 16, &views)) return false;
+    return n == 0 || (color && depth && uv && aligned(uv, 8));
+}
+
+int32_t gs_extract_patches(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv,
+                           int64_t n, uint16_t* X, int32_t* d_status, void* stream) {
+    if (!keyframe_ok(color, depth, cam, uv, n) || (n > 0 && (!X || !aligned(X, 16)))) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_extract_patches(color, depth, *cam, uv, n, X, d_status,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+int32_t gs_insert_gaussians(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv,
+                            int64_t n, float stride, const float* Y, const gs_map_slots* dst, int64_t offset,
+                            int32_t sh_degree, int32_t* d_status, void* stream) {
+    if (!keyframe_ok(color, depth, cam, uv, n) || dst == nullptr || !(stride > 0.f) || !isfinite(stride))
+        return GS_ERR_INVALID_ARG;
+    if (sh_degree != 0 && sh_degree != 3) return GS_ERR_INVALID_ARG;
+    if (offset < 0 || offset + n > dst->capacity) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!dst->mean || !dst->quat || !dst->log_scale || !dst->opacity_logit || !dst->color))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_insert(color, depth, *cam, uv, n, stride, Y, *dst, offset, sh_degree, d_status,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

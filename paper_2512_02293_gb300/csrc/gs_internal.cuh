@@ -69,6 +69,11 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const 
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s);
 cudaError_t noalloc_loss_scratch(float** out);
+cudaError_t launch_extract_patches(const float* color, const float* depth, const gs_camera& cam,
+                                   const int32_t* uv, int64_t n, uint16_t* X, int* status, cudaStream_t s);
+cudaError_t launch_insert(const float* color, const float* depth, const gs_camera& cam, const int32_t* uv,
+                          int64_t n, float stride, const float* Y, const gs_map_slots& dst, int64_t offset,
+                          int sh_degree, int* status, cudaStream_t s);
 cudaError_t launch_mlp_pack(const gs_mlp_params& p, const gs_mlp_packed& q, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
                            uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int* status,

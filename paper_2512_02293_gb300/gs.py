@@ -78,6 +78,11 @@ class gs_adam_group(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
+class gs_map_slots(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("color", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
+
+
 class gs_mlp_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
 
@@ -93,7 +98,8 @@ class gs_mlp_grads(ctypes.Structure):
 EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pixels", "gs_workspace_size",
            "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_loss_noalloc", "gs_render_bwd",
            "gs_render_bwd_raster",
-           "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd"]
+           "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
+           "gs_extract_patches", "gs_insert_gaussians"]
 
 
 def load_library(path: str | None = None):
@@ -143,6 +149,11 @@ def load_library(path: str | None = None):
     lib.gs_mlp_fwd.argtypes = [V, V, ctypes.c_int64, V, V, V, V, V, V, ctypes.c_float, V, V]
     lib.gs_mlp_bwd.restype = ctypes.c_int32
     lib.gs_mlp_bwd.argtypes = [V, V, V, V, V, ctypes.c_int64, V, V, V]
+    lib.gs_extract_patches.restype = ctypes.c_int32
+    lib.gs_extract_patches.argtypes = [V, V, V, V, ctypes.c_int64, V, V, V]
+    lib.gs_insert_gaussians.restype = ctypes.c_int32
+    lib.gs_insert_gaussians.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_float, V, V, ctypes.c_int64,
+                                        ctypes.c_int32, V, V]
     if lib.gs_abi_version() != 1:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
@@ -464,3 +475,23 @@ def gs_mlp_bwd(packed: MlpPacked, X, Z1, Z2, dY, grads: dict, status=None, strea
     g = gs_mlp_grads(*[_ptr(grads[k]) for k in MLP_PARAM_NAMES])
     _check(load_library().gs_mlp_bwd(ctypes.byref(q), _ptr(X), _ptr(Z1), _ptr(Z2), _ptr(dY), X.shape[0],
                                      ctypes.byref(g), _ptr(status), _stream(stream)), "gs_mlp_bwd")
+
+
+# ------------------------------------------------------- keyframe insertion
+
+def gs_extract_patches(color, depth, cam, uv, X, status=None, stream=None):
+    """color [3*H*W] / [3,H,W], depth [H*W] float32; uv int32 [n, 2]; X bfloat16 [n, 208] (written)."""
+    cams = camera_array([cam])
+    _check(load_library().gs_extract_patches(_ptr(color), _ptr(depth), cams, _ptr(uv), uv.shape[0], _ptr(X),
+                                             _ptr(status), _stream(stream)), "gs_extract_patches")
+
+
+def gs_insert_gaussians(color, depth, cam, uv, stride: float, dst: "Gaussians", offset: int, Y=None,
+                        sh_degree: int = 0, status=None, stream=None):
+    """Write the Gaussians of the samples uv into rows offset.. of the map dst."""
+    cams = camera_array([cam])
+    slots = gs_map_slots(_ptr(dst.mean), _ptr(dst.quat), _ptr(dst.log_scale), _ptr(dst.opacity_logit),
+                         _ptr(dst.color), dst.n)
+    _check(load_library().gs_insert_gaussians(_ptr(color), _ptr(depth), cams, _ptr(uv), uv.shape[0], float(stride),
+                                              _ptr(Y), ctypes.byref(slots), int(offset), int(sh_degree),
+                                              _ptr(status), _stream(stream)), "gs_insert_gaussians")
