@@ -316,6 +316,88 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
             "stages_ms": st, "graph": True, "persistent_raster": True}
 
 
+MLP_FWD_FLOP = 2 * (196 * 128 + 128 * 128 + 128 * 8)            # per sample, the network's own MACs x 2
+MLP_BWD_FLOP = 2 * (128 * 128 + 128 * 128 + 196 * 128 + 2 * 8 * 128)  # dH1, dW2, dW1, dW3, dH2
+MLP_FWD_BYTES = 208 * 2 + 8 * 4                                   # BF16 input row + FP32 output
+
+
+def learned_init_run(device, args):
+    """The learned initialiser: training pairs from 50 seeded rooms (the plain
+    mapper, 100 iterations from the heuristic insertion of ~49k Gaussians per
+    640x480 keyframe), tensor-core training, inference / backward throughput,
+    and iterations to the heuristic's PSNR at 100 mapper iterations on 5
+    held-out rooms."""
+    import torch
+    from paper_2512_02293_gb300 import gs as G
+    from paper_2512_02293_gb300 import learned_init as L
+    cfg = L.InitConfig()
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    for r in range(args.li_rooms):
+        X, T = L.training_pairs(100 + r, cfg, device)
+        Xs.append(X); Ts.append(T)
+    X = torch.cat(Xs); T = torch.cat(Ts)
+    del Xs, Ts
+    perm = torch.from_numpy(np.random.default_rng(0).permutation(X.shape[0])).to(device)
+    X = X.index_select(0, perm).contiguous(); T = T.index_select(0, perm).contiguous()
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n = X.shape[0]
+    net = L.LearnedInit(0, device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    losses = net.train(X, T, epochs=args.li_epochs, batch=8192, lr=1e-3)
+    ev[1].record(); torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    # kernel throughput over the whole dataset (inputs larger than L2)
+    Y = torch.empty(n, 8, device=device)
+    Z1 = torch.empty(n, 128, device=device, dtype=torch.bfloat16); Z2 = torch.empty_like(Z1)
+    dY = torch.empty(n, 8, device=device); loss = torch.zeros(1, device=device)
+    for _ in range(2):
+        G.gs_mlp_fwd(net.packed, X, Y=Y)
+    ms_f = []
+    for _ in range(5):
+        ev[0].record(); G.gs_mlp_fwd(net.packed, X, Y=Y); ev[1].record(); torch.cuda.synchronize()
+        ms_f.append(ev[0].elapsed_time(ev[1]))
+    G.gs_mlp_fwd(net.packed, X, Z1=Z1, Z2=Z2, T=T, dY=dY, loss=loss, loss_scale=1.0 / (8 * n))
+    ms_b = []
+    for _ in range(5):
+        ev[0].record(); G.gs_mlp_bwd(net.packed, X, Z1, Z2, dY, net.grads); ev[1].record(); torch.cuda.synchronize()
+        ms_b.append(ev[0].elapsed_time(ev[1]))
+    fwd_ms, bwd_ms = statistics.median(ms_f), statistics.median(ms_b)
+    peaks, kind = _peaks()
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fwd_tf = n * MLP_FWD_FLOP / (fwd_ms * 1e-3) / 1e12
+    fwd_gbs = n * MLP_FWD_BYTES / (fwd_ms * 1e-3) / 1e9
+    bwd_tf = n * MLP_BWD_FLOP / (bwd_ms * 1e-3) / 1e12
+    rooms = []
+    for seed in range(900, 900 + args.li_eval_rooms):
+        kf = L.Keyframe(seed, cfg, device)
+        heur, dh = L.mapping_curve(kf, None, 150)
+        lrn, dl = L.mapping_curve(kf, net.predict(kf.X), 150)
+        rooms.append({"seed": seed, "iters_to_heuristic_psnr100": L.iterations_to_reach(lrn, float(heur[99])),
+                      "psnr_heuristic": [round(float(heur[i]), 2) for i in (0, 9, 49, 99, 149)],
+                      "psnr_learned": [round(float(lrn[i]), 2) for i in (0, 9, 49, 99, 149)],
+                      "depth_l1_m_at150": [round(dh, 4), round(dl, 4)]})
+    its = [r["iters_to_heuristic_psnr100"] for r in rooms]
+    return {"workload": f"{args.li_rooms} rooms x ~49k inserted Gaussians per 640x480 keyframe (3-view window), "
+                        f"{n} pairs; MLP 196-128-128-8 GELU, BF16 weights/activations, FP32 accumulate",
+            "pairs": n, "pair_generation_s": round(gen_s, 2), "epochs": args.li_epochs,
+            "train_ms": round(train_ms, 1), "train_pairs_per_s": args.li_epochs * n / (train_ms * 1e-3),
+            "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)],
+            "mlp_fwd": {"ms": round(fwd_ms, 4), "samples_per_s": n / (fwd_ms * 1e-3),
+                        "roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": fwd_gbs / hbm_peak,
+                                     "tensor_tflops": fwd_tf, "tensor_frac": fwd_tf / bf16_peak,
+                                     "work": f"{MLP_FWD_BYTES} B and {MLP_FWD_FLOP} FLOP per sample",
+                                     "peak_basis": f"{kind} hbm_gbs / bf16_tflops"}},
+            "mlp_bwd": {"ms": round(bwd_ms, 4), "samples_per_s": n / (bwd_ms * 1e-3), "tensor_tflops": bwd_tf,
+                        "tensor_frac": bwd_tf / bf16_peak},
+            "eval_rooms": rooms,
+            "iters_to_heuristic_psnr100_mean": float(np.mean([i if i is not None else 151 for i in its]))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,6 +406,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-window", action="store_true")
+    ap.add_argument("--no-learned-init", action="store_true")
+    ap.add_argument("--li-rooms", type=int, default=50)
+    ap.add_argument("--li-epochs", type=int, default=40)
+    ap.add_argument("--li-eval-rooms", type=int, default=5)
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
                     help="fix the tile size instead of autotuning over {8, 16, 32}")
     args = ap.parse_args()
@@ -414,6 +500,8 @@ def main():
             "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}
     if not args.no_window:
         line["window"] = window_run(device, args, flush, value, dist, world)
+    if not args.no_learned_init:
+        line["learned_init"] = learned_init_run(device, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, gt, cam, params, mp)
     if rank == 0:

@@ -12,10 +12,11 @@ Everything numeric runs in libgs: patches (gs_extract_patches), insertion
 (gs_insert_gaussians), the network's forward / backward on the tensor cores
 (gs_mlp_fwd / gs_mlp_bwd), Adam (gs_adam_step) and the mapper that produces the
 training targets (MappingStep); the evaluation metrics (PSNR, depth L1) are
-plain torch reductions.  The host only canonicalises targets (numpy):
-the three axes are ordered by increasing scale, the rotation's columns follow,
-a reflection is undone by negating the last axis, and the quaternion's sign is
-fixed by w >= 0, so that every Gaussian has one target.
+plain torch reductions.  The host only canonicalises targets (numpy): the
+three axes are ordered by increasing scale, the rotation's columns follow, the
+axes' signs are fixed (smallest axis towards the camera, middle axis with
+non-negative camera-x, right-handed), and the quaternion's sign by w >= 0, so
+that every Gaussian has one target.
 """
 from __future__ import annotations
 
@@ -62,14 +63,19 @@ def _quat_to_rot(q):
 
 def canonical_targets(log_scale, quat, logit, R_wc, s0):
     """Targets [n, 8] = (log-scale offsets from s0, ascending; camera-frame
-    quaternion (w, x, y, z), w >= 0; opacity logit)."""
+    quaternion (w, x, y, z), w >= 0, of the axes in that order with fixed signs;
+    opacity logit)."""
     from scipy.spatial.transform import Rotation
     R_cam = np.asarray(R_wc, np.float64).T[None] @ _quat_to_rot(np.asarray(quat, np.float64))
     order = np.argsort(log_scale, axis=1)
     ls = np.take_along_axis(np.asarray(log_scale, np.float64), order, 1)
     Rp = np.take_along_axis(R_cam, order[:, None, :].repeat(3, 1), 2)
-    flip = np.linalg.det(Rp) < 0
-    Rp[flip, :, 2] *= -1.0
+    # an axis and its negation describe the same Gaussian: the smallest axis (a
+    # surface's normal) points towards the camera, the middle one has a
+    # non-negative camera-x component, the largest completes a right-handed frame
+    a0 = Rp[:, :, 0] * np.where(Rp[:, 2, 0] > 0, -1.0, 1.0)[:, None]
+    a1 = Rp[:, :, 1] * np.where(Rp[:, 0, 1] < 0, -1.0, 1.0)[:, None]
+    Rp = np.stack([a0, a1, np.cross(a0, a1)], 2)
     xyzw = Rotation.from_matrix(Rp).as_quat()
     q = np.stack([xyzw[:, 3], xyzw[:, 0], xyzw[:, 1], xyzw[:, 2]], 1)
     q[q[:, 0] < 0] *= -1.0
