@@ -398,6 +398,46 @@ def learned_init_run(device, args):
             "iters_to_heuristic_psnr100_mean": float(np.mean([i if i is not None else 151 for i in its]))}
 
 
+LOOP_CLOSURE_BYTES = 12 + 16 + 12 + 4 + 12 + 16 + 12   # read mean, quat, log-scale, anchor; write the first three
+
+
+def loop_closure_run(device, n=4_000_000, K=1000):
+    """The loop-closure Gaussian update (Eq. 7, Eq. 8) over a 4M-Gaussian map
+    anchored to 1000 keyframes, 4000 consecutive Gaussians per keyframe as
+    insertion lays them out (336 MB moved, more than L2), timed with CUDA
+    events; the roofline is HBM."""
+    import torch
+    from paper_2512_02293_gb300 import gs as G
+    rng = np.random.default_rng(11)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+    g = G.Gaussians(t(rng.uniform(-3, 3, (n, 3))), t(rng.standard_normal((n, 4))), t(rng.normal(-4, 0.3, (n, 3))),
+                    t(rng.standard_normal(n)), t(rng.uniform(0, 1, (n, 3))))
+    # insertion appends each keyframe's Gaussians as one run, so anchors are sorted
+    anchor = torch.from_numpy((np.arange(n, dtype=np.int64) * K // n).astype(np.int32)).to(device)
+    from scipy.spatial.transform import Rotation
+    pose = lambda seed: t(np.concatenate([Rotation.random(K, random_state=seed).as_matrix().reshape(K, 9),
+                                          rng.uniform(-3, 3, (K, 3))], 1))
+    pb, pa = pose(1), pose(2)
+    ds = t(rng.uniform(0.9, 1.1, K))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        G.gs_loop_closure_update(g, anchor, pb, pa, ds)
+    ms = []
+    for _ in range(10):
+        ev[0].record(); G.gs_loop_closure_update(g, anchor, pb, pa, ds); ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    m = statistics.median(ms)
+    peaks, kind = _peaks()
+    gbs = n * LOOP_CLOSURE_BYTES / (m * 1e-3) / 1e9
+    return {"workload": f"{n} Gaussians anchored to {K} keyframes ({n // K} consecutive per keyframe)",
+            "ms": round(m, 4),
+            "gaussians_per_s": n / (m * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                         "frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                         "work": f"{LOOP_CLOSURE_BYTES} B per Gaussian", "peak_basis": f"{kind} hbm_gbs"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,6 +542,7 @@ def main():
         line["window"] = window_run(device, args, flush, value, dist, world)
     if not args.no_learned_init:
         line["learned_init"] = learned_init_run(device, args)
+    line["loop_closure_update"] = loop_closure_run(device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, gt, cam, params, mp)
     if rank == 0:

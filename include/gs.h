@@ -381,6 +381,25 @@ int32_t gs_insert_gaussians(const float* color, const float* depth, const gs_cam
                             int64_t n, float stride, const float* Y, const gs_map_slots* dst, int64_t offset,
                             int32_t sh_degree, int32_t* d_status, void* stream);
 
+/* Loop-closure Gaussian update (Sec. 3.3 "Loop Closure Gaussian Update",
+ * Eq. 7 and Eq. 8), in place on map rows 0 .. map->capacity - 1.  Gaussian i is
+ * anchored to keyframe anchor[i] (device int32 [n], in [0, n_keyframes));
+ * pose_before / pose_after (device float [n_keyframes][12]) hold each
+ * keyframe's camera-to-world rotation (row-major, 9) and position (3) before
+ * and after the pose-graph optimisation; scale_change (device float
+ * [n_keyframes]) its scale factor ds_k > 0.  Then
+ *     mean <- R+ (ds (R-)^T (mean - t-)) + t+,
+ *     Sigma <- R+ ds^2 (R-)^T Sigma R- (R+)^T, i.e. quat <- q(R+ (R-)^T) * quat
+ *     (Hamilton product, norm kept) and log_scale <- log_scale + log ds;
+ * opacity and colour are unchanged.  A Gaussian with an out-of-range anchor or a
+ * non-positive ds is left unchanged and GS_ERR_INVALID_ARG is recorded in
+ * *d_status (if not NULL).  quat rows must be 16-byte aligned.
+ * Errors: GS_ERR_INVALID_ARG on NULL / misaligned pointers, capacity < 0,
+ * n_keyframes < 1. */
+int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, const float* pose_before,
+                               const float* pose_after, const float* scale_change, int32_t n_keyframes,
+                               int32_t* d_status, void* stream);
+
 /* Synchronises `stream`, copies the device status word to *host_status and
  * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);

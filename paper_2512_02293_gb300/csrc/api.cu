@@ -345,4 +345,15 @@ int32_t gs_insert_gaussians(const float* color, const float* depth, const gs_cam
                                      static_cast<cudaStream_t>(stream)));
 }
 
+int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, const float* pose_before,
+                               const float* pose_after, const float* scale_change, int32_t n_keyframes,
+                               int32_t* d_status, void* stream) {
+    if (map == nullptr || map->capacity < 0 || n_keyframes < 1) return GS_ERR_INVALID_ARG;
+    if (map->capacity > 0 && (!map->mean || !map->quat || !map->log_scale || !aligned(map->quat, 16) || !anchor ||
+                              !pose_before || !pose_after || !scale_change))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_loop_closure(*map, anchor, pose_before, pose_after, scale_change, n_keyframes,
+                                           d_status, static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

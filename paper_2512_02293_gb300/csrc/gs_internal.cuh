@@ -74,6 +74,8 @@ cudaError_t launch_extract_patches(const float* color, const float* depth, const
 cudaError_t launch_insert(const float* color, const float* depth, const gs_camera& cam, const int32_t* uv,
                           int64_t n, float stride, const float* Y, const gs_map_slots& dst, int64_t offset,
                           int sh_degree, int* status, cudaStream_t s);
+cudaError_t launch_loop_closure(const gs_map_slots& map, const int32_t* anchor, const float* before,
+                                const float* after, const float* ds, int K, int* status, cudaStream_t s);
 cudaError_t launch_mlp_pack(const gs_mlp_params& p, const gs_mlp_packed& q, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
                            uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int* status,
@@ -120,5 +122,36 @@ __device__ __forceinline__ float splat_power2(float qa, float qb, float qc, floa
 
 __device__ __forceinline__ float splat_weight(float p2) { return ex2_approx(p2); }
 #endif
+
+// Quaternion (w, x, y, z) of a rotation matrix (row-major), by the larger-of-
+// four-candidates method (Shepperd, 1978).
+__device__ __forceinline__ void rot_to_quat(const float* R, float* q) {
+    const float tr = R[0] + R[4] + R[8];
+    if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+        const float s = sqrtf(fmaxf(1.f + tr, 0.f)) * 2.f;
+        q[0] = 0.25f * s;
+        q[1] = (R[7] - R[5]) / s; q[2] = (R[2] - R[6]) / s; q[3] = (R[3] - R[1]) / s;
+    } else if (R[0] >= R[4] && R[0] >= R[8]) {
+        const float s = sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 0.f)) * 2.f;
+        q[0] = (R[7] - R[5]) / s; q[1] = 0.25f * s;
+        q[2] = (R[1] + R[3]) / s; q[3] = (R[2] + R[6]) / s;
+    } else if (R[4] >= R[8]) {
+        const float s = sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 0.f)) * 2.f;
+        q[0] = (R[2] - R[6]) / s; q[1] = (R[1] + R[3]) / s;
+        q[2] = 0.25f * s; q[3] = (R[5] + R[7]) / s;
+    } else {
+        const float s = sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 0.f)) * 2.f;
+        q[0] = (R[3] - R[1]) / s; q[1] = (R[2] + R[6]) / s;
+        q[2] = (R[5] + R[7]) / s; q[3] = 0.25f * s;
+    }
+}
+
+// Hamilton product a * b
+__device__ __forceinline__ void quat_mul(const float* a, const float* b, float* c) {
+    c[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    c[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    c[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    c[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
 
 }  // namespace gs

@@ -18,37 +18,6 @@ namespace {
 
 constexpr float kSH0 = 0.28209479177387814f;     // Y_0^0 = 1 / (2 sqrt(pi))
 
-// Quaternion (w, x, y, z) of a rotation matrix (row-major), by the larger-of-
-// four-candidates method (Shepperd, 1978).
-__device__ void rot_to_quat(const float* R, float* q) {
-    const float tr = R[0] + R[4] + R[8];
-    if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
-        const float s = sqrtf(fmaxf(1.f + tr, 0.f)) * 2.f;
-        q[0] = 0.25f * s;
-        q[1] = (R[7] - R[5]) / s; q[2] = (R[2] - R[6]) / s; q[3] = (R[3] - R[1]) / s;
-    } else if (R[0] >= R[4] && R[0] >= R[8]) {
-        const float s = sqrtf(fmaxf(1.f + R[0] - R[4] - R[8], 0.f)) * 2.f;
-        q[0] = (R[7] - R[5]) / s; q[1] = 0.25f * s;
-        q[2] = (R[1] + R[3]) / s; q[3] = (R[2] + R[6]) / s;
-    } else if (R[4] >= R[8]) {
-        const float s = sqrtf(fmaxf(1.f + R[4] - R[0] - R[8], 0.f)) * 2.f;
-        q[0] = (R[2] - R[6]) / s; q[1] = (R[1] + R[3]) / s;
-        q[2] = 0.25f * s; q[3] = (R[5] + R[7]) / s;
-    } else {
-        const float s = sqrtf(fmaxf(1.f + R[8] - R[0] - R[4], 0.f)) * 2.f;
-        q[0] = (R[3] - R[1]) / s; q[1] = (R[2] + R[6]) / s;
-        q[2] = (R[5] + R[7]) / s; q[3] = 0.25f * s;
-    }
-}
-
-// Hamilton product a * b
-__device__ __forceinline__ void quat_mul(const float* a, const float* b, float* c) {
-    c[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
-    c[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
-    c[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
-    c[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
-}
-
 __device__ __forceinline__ uint16_t f2bf16(float x) {
     // round to nearest even (finite inputs)
     const uint32_t u = __float_as_uint(x);

@@ -99,7 +99,7 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_loss_noalloc", "gs_render_bwd",
            "gs_render_bwd_raster",
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
-           "gs_extract_patches", "gs_insert_gaussians"]
+           "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update"]
 
 
 def load_library(path: str | None = None):
@@ -151,6 +151,8 @@ def load_library(path: str | None = None):
     lib.gs_mlp_bwd.argtypes = [V, V, V, V, V, ctypes.c_int64, V, V, V]
     lib.gs_extract_patches.restype = ctypes.c_int32
     lib.gs_extract_patches.argtypes = [V, V, V, V, ctypes.c_int64, V, V, V]
+    lib.gs_loop_closure_update.restype = ctypes.c_int32
+    lib.gs_loop_closure_update.argtypes = [V, V, V, V, V, ctypes.c_int32, V, V]
     lib.gs_insert_gaussians.restype = ctypes.c_int32
     lib.gs_insert_gaussians.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_float, V, V, ctypes.c_int64,
                                         ctypes.c_int32, V, V]
@@ -495,3 +497,15 @@ def gs_insert_gaussians(color, depth, cam, uv, stride: float, dst: "Gaussians", 
     _check(load_library().gs_insert_gaussians(_ptr(color), _ptr(depth), cams, _ptr(uv), uv.shape[0], float(stride),
                                               _ptr(Y), ctypes.byref(slots), int(offset), int(sh_degree),
                                               _ptr(status), _stream(stream)), "gs_insert_gaussians")
+
+
+# ------------------------------------------------------ loop-closure update
+
+def gs_loop_closure_update(g: "Gaussians", anchor, pose_before, pose_after, scale_change, status=None,
+                           stream=None):
+    """In-place Eq. 7 / Eq. 8 update of g.  anchor int32 [n]; poses float32
+    [K, 12] (R_wc row-major, t_wc); scale_change float32 [K]."""
+    slots = gs_map_slots(_ptr(g.mean), _ptr(g.quat), _ptr(g.log_scale), _ptr(g.opacity_logit), _ptr(g.color), g.n)
+    _check(load_library().gs_loop_closure_update(ctypes.byref(slots), _ptr(anchor), _ptr(pose_before),
+                                                 _ptr(pose_after), _ptr(scale_change), int(pose_before.shape[0]),
+                                                 _ptr(status), _stream(stream)), "gs_loop_closure_update")
