@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
             // warp-uniform loop; a lane's tests (power > 0, alpha < alpha_min, the
             // transmittance cutoff) become predicates, so the warp never diverges
             const int cnt = __popc(kept);
+            int last_k = -1;                         // batch slot of this lane's last blended splat
             for (int k = 0; k < cnt; k++) {
                 const float2 m = s_xy[w][k];
                 const float4 q = s_q[w][k];
@@ -180,9 +181,10 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
                 cb = __fmaf_rn(c.z, wgt, cb);
                 dd = __fmaf_rn(c.w, wgt, dd);
                 Tr = b ? test : Tr;
-                last = b ? s_pos[w][k] + 1u : last;
+                last_k = b ? k : last_k;
                 if (__all_sync(0xffffffffu, done)) break;
             }
+            if (last_k >= 0) last = s_pos[w][last_k] + 1u;
             if (__all_sync(0xffffffffu, done)) break;
         }
         if (inside) {
@@ -260,54 +262,52 @@ struct BwdPix {
     float Sr, Sg, Sb, Sd;
 };
 
-// The conic in the gradient formulas is recovered from the scaled one (an
-// O(1 ulp) difference that only enters gradient values, never a decision).
-constexpr float kUnscaleAC = -2.0f / kLog2e, kUnscaleB = -1.0f / kLog2e;
-
 // Branch-free: every lane evaluates the splat, and the ones that did not blend it
 // in the forward pass (past their checkpoint, power > 0, alpha < alpha_min -- the
-// forward's tests, written the same way) keep their state and contribute zeros
-// through selects, so the warp never diverges here.
-__device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const float2 m, const float4 q,
-                                          const float4 cd, float amin, float amax, uint32_t pos, float (&gv)[10]) {
+// forward's tests, written the same way) keep their state and contribute zeros:
+// their alpha enters the updates as 0 (ac), so no select per update is needed.
+// m = (mean x, mean y, list position, entry) with the last two as bit patterns;
+// q = scaled conic + opacity (the decisions); c = the raw conic A, B, C (the
+// gradient formulas).
+__device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const float4 m, const float4 q,
+                                          const float4 cd, const float4 c, float amin, float amax, float (&gv)[10]) {
     const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
     const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
     const float G = splat_weight(p2);
     const float araw = __fmul_rn(q.w, G);
     const float a = fminf(amax, araw);
-    const bool c = pos < P.np && !(p2 > 0.f) && !(a < amin);
-    const float one_m = 1.0f - a;
-    const float Tb = __fdividef(P.T, one_m);      // transmittance before this splat
-    const float w = c ? a * Tb : 0.f;
+    const bool blend = __float_as_uint(m.z) < P.np && !(p2 > 0.f) && !(a < amin);
+    const float ac = blend ? a : 0.f;                     // alpha of a blended splat, else 0
+    const float Tb = __fdividef(P.T, 1.0f - a);           // transmittance before this splat
+    const float w = ac * Tb;
     const float dr = cd.x - P.Sr, dg = cd.y - P.Sg, db = cd.z - P.Sb, dz = cd.w - P.Sd;
     const float dLda = Tb * (dr * P.gr + dg * P.gg + db * P.gb + dz * P.gd);
-    P.Sr = c ? fmaf(a, dr, P.Sr) : P.Sr;
-    P.Sg = c ? fmaf(a, dg, P.Sg) : P.Sg;
-    P.Sb = c ? fmaf(a, db, P.Sb) : P.Sb;
-    P.Sd = c ? fmaf(a, dz, P.Sd) : P.Sd;
-    P.T = c ? Tb : P.T;
+    P.Sr = fmaf(ac, dr, P.Sr);
+    P.Sg = fmaf(ac, dg, P.Sg);
+    P.Sb = fmaf(ac, db, P.Sb);
+    P.Sd = fmaf(ac, dz, P.Sd);
+    P.T = blend ? Tb : P.T;
+    const bool free_alpha = blend && araw < amax;        // alpha not clamped
+    const float dpow = free_alpha ? dLda * a : 0.f;       // d alpha / d power = alpha
+    const float e = dpow * dx, f = dpow * dy;             // power = -(A dx^2 + 2 B dx dy + C dy^2) / 2
+    gv[0] = fmaf(c.x, e, c.y * f);                        // d mean x
+    gv[1] = fmaf(c.y, e, c.z * f);                        // d mean y
+    gv[2] = -0.5f * e * dx;                               // d A
+    gv[3] = -e * dy;                                      // d B
+    gv[4] = -0.5f * f * dy;                               // d C
+    gv[5] = free_alpha ? dLda * G : 0.f;                  // d opacity: d alpha / d o = exp(power)
+    gv[6] = P.gd * w;
     gv[7] = P.gr * w;
     gv[8] = P.gg * w;
     gv[9] = P.gb * w;
-    gv[6] = P.gd * w;
-    const bool cu = c && araw < amax;             // alpha not clamped
-    const float dpow = cu ? dLda * a : 0.f;       // d alpha / d power = alpha
-    gv[5] = cu ? dLda * G : 0.f;                  // d alpha / d o = exp(power)
-    const float A = q.x * kUnscaleAC, B = q.y * kUnscaleB, C = q.z * kUnscaleAC;
-    gv[0] = dpow * fmaf(A, dx, B * dy);
-    gv[1] = dpow * fmaf(B, dx, C * dy);
-    const float hx = -0.5f * dpow * dx;
-    gv[2] = hx * dx;
-    gv[3] = -dpow * dx * dy;
-    gv[4] = -0.5f * dpow * dy * dy;
-    return c;
+    return blend;
 }
 
 // Backward of one work item (pixel block blk of tile g) by one warp, using the
-// warp's shared-memory slot (s_xy .. s_pos: 32 entries each).
+// warp's shared-memory slot (s_m .. s_c: 32 entries each).
 template <int T>
 __device__ __forceinline__ void bwd_item(
-        int g, int blk, float2* s_xy, float4* s_q, float4* s_cd, uint32_t* s_e, uint32_t* s_pos,
+        int g, int blk, float4* s_m, float4* s_q, float4* s_cd, float4* s_c,
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, const Views& views,
         const RenderConsts& rc, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
@@ -352,13 +352,13 @@ __device__ __forceinline__ void bwd_item(
     auto below = [&](uint32_t b) { return b > range.x + 32 ? b - 32 : range.x; };
     uint32_t lo = below(top);
     float2 n_xy = make_float2(0.f, 0.f);
-    float4 n_q = make_float4(0.f, 0.f, 0.f, 0.f), n_cd = n_q;
+    float4 n_q = make_float4(0.f, 0.f, 0.f, 0.f), n_cd = n_q, n_c = n_q;
     uint32_t n_e = 0, nn_e = 0;
     auto fetch = [&](uint32_t e) {
         n_e = e;
-        const float4 c = conic_o[e];
-        scale_conic(c.x, c.y, c.z, &n_q.x, &n_q.y, &n_q.z);
-        n_q.w = c.w;
+        n_c = conic_o[e];
+        scale_conic(n_c.x, n_c.y, n_c.z, &n_q.x, &n_q.y, &n_q.z);
+        n_q.w = n_c.w;
         n_xy = xy[e];
         n_cd = rgbd[e];
     };
@@ -370,11 +370,10 @@ __device__ __forceinline__ void bwd_item(
         __syncwarp();
         if (keep) {
             const int sl = __popc(kept & lt_mask);
-            s_xy[sl] = n_xy;
+            s_m[sl] = make_float4(n_xy.x, n_xy.y, __uint_as_float(lo + lane - range.x), __uint_as_float(n_e));
             s_q[sl] = n_q;
             s_cd[sl] = n_cd;
-            s_e[sl] = n_e;
-            s_pos[sl] = lo + lane - range.x;
+            s_c[sl] = n_c;
         }
         __syncwarp();
         const uint32_t nlo = below(lo);
@@ -384,28 +383,29 @@ __device__ __forceinline__ void bwd_item(
         int k = cnt - 1;
         for (; k >= 1; k -= 2) {
             float ga[10], gb[10];
-            const bool ca = bwd_pixel(P, sx, sy, s_xy[k], s_q[k], s_cd[k], amin, amax, s_pos[k], ga);
-            const bool cb = bwd_pixel(P, sx, sy, s_xy[k - 1], s_q[k - 1], s_cd[k - 1], amin, amax,
-                                      s_pos[k - 1], gb);
+            const float4 ma = s_m[k], mb = s_m[k - 1];
+            const bool ca = bwd_pixel(P, sx, sy, ma, s_q[k], s_cd[k], s_c[k], amin, amax, ga);
+            const bool cb = bwd_pixel(P, sx, sy, mb, s_q[k - 1], s_cd[k - 1], s_c[k - 1], amin, amax, gb);
             const bool anya = __any_sync(0xffffffffu, ca), anyb = __any_sync(0xffffffffu, cb);
             if (anya || anyb) {
                 float ua, ub;
                 warp_reduce10x2(ga, gb, lane, &ua, &ub);
                 if (slot >= 0) {
-                    if (anya) atomicAdd(g2d + (size_t)kGradStride * s_e[k] + col, ua);
-                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * s_e[k - 1] + col, ub);
+                    if (anya) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(ma.w) + col, ua);
+                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(mb.w) + col, ub);
                 }
             }
         }
         if (k == 0) {
             float ga[10], gb[10];
-            const bool ca = bwd_pixel(P, sx, sy, s_xy[0], s_q[0], s_cd[0], amin, amax, s_pos[0], ga);
+            const float4 ma = s_m[0];
+            const bool ca = bwd_pixel(P, sx, sy, ma, s_q[0], s_cd[0], s_c[0], amin, amax, ga);
 #pragma unroll
             for (int r = 0; r < 10; r++) gb[r] = 0.f;
             if (__any_sync(0xffffffffu, ca)) {
                 float ua, ub;
                 warp_reduce10x2(ga, gb, lane, &ua, &ub);
-                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * s_e[0] + col, ua);
+                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(ma.w) + col, ua);
             }
         }
     }
@@ -419,14 +419,13 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_bwd(
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
         int* __restrict__ queue, int n_items) {
     constexpr int W = TileShape<T>::kWarps;
-    __shared__ float2 s_xy[kRasterWarps][32];
+    __shared__ float4 s_m[kRasterWarps][32];      // mean x, y, list position, entry (bit patterns)
     __shared__ float4 s_q[kRasterWarps][32];      // scaled conic + opacity
     __shared__ float4 s_cd[kRasterWarps][32];     // r, g, b, z
-    __shared__ uint32_t s_e[kRasterWarps][32];
-    __shared__ uint32_t s_pos[kRasterWarps][32];
+    __shared__ float4 s_c[kRasterWarps][32];      // raw conic A, B, C
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int item = next_item(queue, lane); item < n_items; item = next_item(queue, lane)) {
-        bwd_item<T>(item / W, item % W, s_xy[w], s_q[w], s_cd[w], s_e[w], s_pos[w], xy, conic_o, rgbd, vals, ranges,
+        bwd_item<T>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
                     views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d);
         __syncwarp();
     }
