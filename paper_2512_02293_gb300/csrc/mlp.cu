@@ -17,8 +17,8 @@
 //   backward: dH1 = dZ2 W2 (B = W2^T), dW2a += dZ2^T H1_aug, dW1a += dZ1^T X_aug,
 //             dW3 / db3 and dH2 = dY W3 on the CUDA cores (8 outputs).
 //
-// One CTA of 128 threads per SM walks tiles of 128 samples; thread t owns sample
-// row t of a tile, which is tensor-memory lane t of every accumulator.
+// One CTA of 512 threads per SM walks tiles of 128 samples; the four threads of
+// sample row r (tensor-memory lane r of every accumulator) split its columns.
 #include <cuda_bf16.h>
 
 #include "gs_internal.cuh"
@@ -28,7 +28,10 @@ namespace gs {
 namespace {
 
 constexpr int kIn = 196, kK1 = 208, kHid = 128, kK2 = 144, kOut = 8, kN3 = 16;
-constexpr int kTile = 128, kThreads = 128;
+constexpr int kTile = 128;
+// Both kernels run 16 warps: warp w reaches tensor-memory lanes 32 (w % 4) ..
+// 32 (w % 4) + 31 (sample rows) and takes column group w / 4 of every epilogue.
+constexpr int kFwdThreads = 512, kColGroups = kFwdThreads / 128;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kWaitPolls = 1u << 26;     // bounded mbarrier polls before GS_ERR_TIMEOUT
 
@@ -121,12 +124,13 @@ struct MlpFwdArgs {
     int* status;
 };
 
-// Hidden-layer epilogue for this thread's sample row: accumulator -> Z = bf16,
-// H = bf16(gelu(Z)) into the next layer's K-major operand, Z to global memory.
+// Hidden-layer epilogue for this thread's sample row and columns [c_lo, c_hi):
+// accumulator -> Z = bf16, H = bf16(gelu(Z)) into the next layer's K-major
+// operand, Z to global memory.
 __device__ __forceinline__ void hidden_epilogue(uint32_t tacc, uint8_t* sH, int r, int64_t row, int64_t n,
-                                                uint16_t* __restrict__ Zout) {
+                                                uint16_t* __restrict__ Zout, int c_lo, int c_hi) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tacc + (uint32_t)c0, v);
         uint32_t zp[8], hp[8];
@@ -172,9 +176,11 @@ __device__ __forceinline__ void operands_ready() {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, cg = warp >> 2;            // tensor-memory lane quarter, column group
+    const int r = quarter * 32 + lane;                       // this thread's sample row in the tile
     uint8_t* sX = sm + kFwdX;
     uint8_t* sH = sm + kFwdH;
     const uint32_t bar = tc::smem_addr(sm + kFwdBar);
@@ -183,65 +189,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
     fill_kmajor(sm + kFwdW1, a.w.W1a, kHid, kK1);
     fill_kmajor(sm + kFwdW2, a.w.W2a, kHid, kK2);
     fill_kmajor(sm + kFwdW3, a.w.W3a, kN3, kK2);
-    // constant augmentation of H: column 128 = 1, columns 129..143 = 0
-    *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(tid, kHid, kK2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(tid, kHid + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
+    if (cg == 0) {   // constant augmentation of H: column 128 = 1, columns 129..143 = 0
+        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, kHid, kK2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, kHid + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) tc::mbar_init(bar, 1);
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
     operands_ready();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const uint32_t tD1 = tbase, tD2 = tbase + 128, tD3 = tbase + 256;
     const uint32_t sa_x = tc::smem_addr(sX), sa_h = tc::smem_addr(sH);
     const uint32_t sa_w1 = tc::smem_addr(sm + kFwdW1), sa_w2 = tc::smem_addr(sm + kFwdW2);
     const uint32_t sa_w3 = tc::smem_addr(sm + kFwdW3);
+    const int c_lo = cg * (kHid / kColGroups), c_hi = c_lo + kHid / kColGroups;
     uint32_t phase = 0;
     bool ok = true;
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int64_t row0 = t * kTile, row = row0 + tid;
-        // X tile: thread t fills sample row t (26 chunks of 8 values)
+        const int64_t row0 = t * kTile, row = row0 + r;
+        // X tile: the four threads of a sample row take every fourth 8-value chunk
 #pragma unroll 2
-        for (int c = 0; c < kK1 / 8; c++)
-            *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(tid, 8 * c, kK1)) = x_chunk(a.X, row, a.n, c);
+        for (int c = cg; c < kK1 / 8; c += kColGroups)
+            *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(r, 8 * c, kK1)) = x_chunk(a.X, row, a.n, c);
         operands_ready();
         if (tid == 0) issue_gemm(tD1, sa_x, sa_w1, kK1, tc::idesc_bf16(128, kHid), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
-        hidden_epilogue(tD1 + lane_off, sH, tid, row, a.n, a.Z1);
+        hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi);
         operands_ready();
         if (tid == 0) issue_gemm(tD2, sa_h, sa_w2, kK2, tc::idesc_bf16(128, kHid), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
-        hidden_epilogue(tD2 + lane_off, sH, tid, row, a.n, a.Z2);
+        hidden_epilogue(tD2 + lane_off, sH, r, row, a.n, a.Z2, c_lo, c_hi);
         operands_ready();
         if (tid == 0) issue_gemm(tD3, sa_h, sa_w3, kK2, tc::idesc_bf16(128, kN3), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
-        float y[16];
-        tc::tmem_ld16(tD3 + lane_off, y);
-        float part = 0.f;
-        if (row < a.n) {
-            if (a.Y != nullptr) {
-                float4* yr = reinterpret_cast<float4*>(a.Y + row * kOut);
-                yr[0] = make_float4(y[0], y[1], y[2], y[3]);
-                yr[1] = make_float4(y[4], y[5], y[6], y[7]);
+        if (cg == 0) {                       // the 8 outputs: one column group (warp-uniform)
+            float y[16];
+            tc::tmem_ld16(tD3 + lane_off, y);
+            float part = 0.f;
+            if (row < a.n) {
+                if (a.Y != nullptr) {
+                    float4* yr = reinterpret_cast<float4*>(a.Y + row * kOut);
+                    yr[0] = make_float4(y[0], y[1], y[2], y[3]);
+                    yr[1] = make_float4(y[4], y[5], y[6], y[7]);
+                }
+                if (a.T != nullptr) {
+                    const float4* tr = reinterpret_cast<const float4*>(a.T + row * kOut);
+                    const float4 t0 = tr[0], t1 = tr[1];
+                    const float d[8] = {y[0] - t0.x, y[1] - t0.y, y[2] - t0.z, y[3] - t0.w,
+                                        y[4] - t1.x, y[5] - t1.y, y[6] - t1.z, y[7] - t1.w};
+                    float gr[8];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) { part += d[i] * d[i]; gr[i] = 2.f * a.loss_scale * d[i]; }
+                    float4* dr = reinterpret_cast<float4*>(a.dY + row * kOut);
+                    dr[0] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+                    dr[1] = make_float4(gr[4], gr[5], gr[6], gr[7]);
+                }
             }
             if (a.T != nullptr) {
-                const float4* tr = reinterpret_cast<const float4*>(a.T + row * kOut);
-                const float4 t0 = tr[0], t1 = tr[1];
-                const float d[8] = {y[0] - t0.x, y[1] - t0.y, y[2] - t0.z, y[3] - t0.w,
-                                    y[4] - t1.x, y[5] - t1.y, y[6] - t1.z, y[7] - t1.w};
-                float g[8];
 #pragma unroll
-                for (int i = 0; i < 8; i++) { part += d[i] * d[i]; g[i] = 2.f * a.loss_scale * d[i]; }
-                float4* dr = reinterpret_cast<float4*>(a.dY + row * kOut);
-                dr[0] = make_float4(g[0], g[1], g[2], g[3]);
-                dr[1] = make_float4(g[4], g[5], g[6], g[7]);
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == 0) atomicAdd(a.loss, a.loss_scale * part);
             }
-        }
-        if (a.T != nullptr) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) atomicAdd(a.loss, a.loss_scale * part);
         }
         tc::fence_before_sync();
         __syncthreads();      // tensor memory and shared operands are reused by the next tile
@@ -286,9 +296,11 @@ __device__ __forceinline__ void st_bf16(uint8_t* base, int r, int b, uint16_t v)
     *reinterpret_cast<uint16_t*>(base + tc::kmajor_offset(r, b, kTile)) = v;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, cg = warp >> 2;            // tensor-memory lane quarter, column group
+    const int r = quarter * 32 + lane;                       // this thread's sample (or weight) row
     float* sW3f = reinterpret_cast<float*>(sm + kBwdW3f);
     uint8_t* sA2 = sm + kBwdA2;
     uint8_t* sA2t = sm + kBwdA2t;
@@ -299,37 +311,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBwdBar + 8);
 
     fill_kmajor(sm + kBwdW2t, a.w.W2t, kHid, kHid);
-    for (int i = tid; i < kOut * kHid; i += kThreads)
+    for (int i = tid; i < kOut * kHid; i += kFwdThreads)
         sW3f[i] = bf2f(a.w.W3a[(i / kHid) * kK2 + (i % kHid)]);
     // constant rows of H1_aug^T: row 128 = 1 (the ones column of H1), rows 129..143 = 0
-    for (int r = kHid; r < kK2; r++) st_bf16(sB2, r, tid, r == kHid ? 0x3F80u : 0u);
+    for (int k = tid; k < (kK2 - kHid) * kTile; k += kFwdThreads) {
+        const int rr = kHid + k / kTile, b = k % kTile;
+        st_bf16(sB2, rr, b, rr == kHid ? 0x3F80u : 0u);
+    }
     if (tid == 0) tc::mbar_init(bar, 1);
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
     operands_ready();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const uint32_t sa_a2 = tc::smem_addr(sA2), sa_a2t = tc::smem_addr(sA2t), sa_b2 = tc::smem_addr(sB2);
     const uint32_t sa_b1 = tc::smem_addr(sB1), sa_w2t = tc::smem_addr(sm + kBwdW2t);
-    float acc3[kOut];                   // dW3[o][tid] over this CTA's tiles
+    const int jw = tid & (kHid - 1), part = tid >> 7;        // dW3: hidden unit, quarter of the samples
+    float acc3[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; o++) acc3[o] = 0.f;
-    float accb3 = 0.f;                  // db3[tid] (tid < 8)
+    float accb3 = 0.f;
     uint32_t phase = 0;
     bool ok = true, first = true;
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int64_t row = t * kTile + tid;
+        const int64_t row = t * kTile + r;
         const bool valid = row < a.n;
         // (1) X_aug^T, dY and H2 (row-major, for the CUDA-core dW3) of this sample
 #pragma unroll 1
-        for (int c = 0; c < kK1 / 8; c++) {
+        for (int c = cg; c < kK1 / 8; c += kColGroups) {
             const uint4 v = x_chunk(a.X, row, a.n, c);
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                st_bf16(sB1, 8 * c + 2 * i, tid, (uint16_t)(w[i] & 0xFFFFu));
-                st_bf16(sB1, 8 * c + 2 * i + 1, tid, (uint16_t)(w[i] >> 16));
+                st_bf16(sB1, 8 * c + 2 * i, r, (uint16_t)(w[i] & 0xFFFFu));
+                st_bf16(sB1, 8 * c + 2 * i + 1, r, (uint16_t)(w[i] >> 16));
             }
         }
         float dy[kOut];
@@ -341,12 +357,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             }
             dy[0] = d0.x; dy[1] = d0.y; dy[2] = d0.z; dy[3] = d0.w;
             dy[4] = d1.x; dy[5] = d1.y; dy[6] = d1.z; dy[7] = d1.w;
-            reinterpret_cast<float4*>(sDY + tid * kOut)[0] = d0;
-            reinterpret_cast<float4*>(sDY + tid * kOut)[1] = d1;
+            if (cg == 0) {
+                reinterpret_cast<float4*>(sDY + r * kOut)[0] = d0;
+                reinterpret_cast<float4*>(sDY + r * kOut)[1] = d1;
+            }
         }
         uint16_t* sH2 = reinterpret_cast<uint16_t*>(sA2t);   // [b][j], aliases dZ2^T until step (3)
 #pragma unroll 1
-        for (int c = 0; c < kHid / 8; c++) {
+        for (int c = cg; c < kHid / 8; c += kColGroups) {
             uint4 z = make_uint4(0u, 0u, 0u, 0u);
             if (valid) z = __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c);
             const uint32_t w[4] = {z.x, z.y, z.z, z.w};
@@ -354,13 +372,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
 #pragma unroll
             for (int i = 0; i < 4; i++)
                 h[i] = pack2(f2bf(gelu(bf2f(w[i] & 0xFFFFu))), f2bf(gelu(bf2f(w[i] >> 16))));
-            *reinterpret_cast<uint4*>(sH2 + tid * kHid + 8 * c) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(sH2 + r * kHid + 8 * c) = make_uint4(h[0], h[1], h[2], h[3]);
         }
         __syncthreads();
-        // (2) dW3[o][j] += sum_b dY[b][o] H2[b][j] (thread j), db3[o] += sum_b dY[b][o] (thread o)
+        // (2) dW3[o][j] += sum_b dY[b][o] H2[b][j] (thread j, a quarter of the samples); db3
 #pragma unroll 4
-        for (int b = 0; b < kTile; b++) {
-            const float h = bf2f(sH2[b * kHid + tid]);
+        for (int b = part * 32; b < part * 32 + 32; b++) {
+            const float h = bf2f(sH2[b * kHid + jw]);
             const float4 d0 = reinterpret_cast<const float4*>(sDY + b * kOut)[0];
             const float4 d1 = reinterpret_cast<const float4*>(sDY + b * kOut)[1];
             acc3[0] += d0.x * h; acc3[1] += d0.y * h; acc3[2] += d0.z * h; acc3[3] += d0.w * h;
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
         __syncthreads();
         // (3) dZ2 = bf16((dY W3) * gelu'(Z2)) as dZ2 rows and dZ2^T; H1 = bf16(gelu(Z1)) as H1_aug^T
 #pragma unroll 1
-        for (int c = 0; c < kHid / 8; c++) {
+        for (int c = cg; c < kHid / 8; c += kColGroups) {
             uint4 z = make_uint4(0u, 0u, 0u, 0u);
             if (valid) z = __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c);
             const uint32_t w[4] = {z.x, z.y, z.z, z.w};
@@ -384,36 +402,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                 for (int o = 0; o < kOut; o++) dh += dy[o] * sW3f[o * kHid + j];
                 const float zv = bf2f((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu));
                 g[i] = f2bf(dh * gelu_grad(zv));
-                st_bf16(sA2t, j, tid, g[i]);
+                st_bf16(sA2t, j, r, g[i]);
             }
-            *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(tid, 8 * c, kHid)) =
+            *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(r, 8 * c, kHid)) =
                 make_uint4(pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
             uint4 z1 = make_uint4(0u, 0u, 0u, 0u);
             if (valid) z1 = __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid) + c);
             const uint32_t w1[4] = {z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                st_bf16(sB2, 8 * c + 2 * i, tid, f2bf(gelu(bf2f(w1[i] & 0xFFFFu))));
-                st_bf16(sB2, 8 * c + 2 * i + 1, tid, f2bf(gelu(bf2f(w1[i] >> 16))));
+                st_bf16(sB2, 8 * c + 2 * i, r, f2bf(gelu(bf2f(w1[i] & 0xFFFFu))));
+                st_bf16(sB2, 8 * c + 2 * i + 1, r, f2bf(gelu(bf2f(w1[i] >> 16))));
             }
         }
         operands_ready();
         // (4) dH1 = dZ2 W2 and dW2_aug += dZ2^T H1_aug
         if (tid == 0) {
             tc::fence_after_sync();
-            for (int s = 0; s < kHid / 16; s++)
-                tc::mma_bf16(tbase + kTdH1, tc::kstep_desc(sa_a2, kHid, s), tc::kstep_desc(sa_w2t, kHid, s),
-                             tc::idesc_bf16(128, kHid), s > 0);
-            for (int s = 0; s < kTile / 16; s++)
-                tc::mma_bf16(tbase + kTdW2, tc::kstep_desc(sa_a2t, kTile, s), tc::kstep_desc(sa_b2, kTile, s),
-                             tc::idesc_bf16(128, kK2), !first || s > 0);
+            for (int st = 0; st < kHid / 16; st++)
+                tc::mma_bf16(tbase + kTdH1, tc::kstep_desc(sa_a2, kHid, st), tc::kstep_desc(sa_w2t, kHid, st),
+                             tc::idesc_bf16(128, kHid), st > 0);
+            for (int st = 0; st < kTile / 16; st++)
+                tc::mma_bf16(tbase + kTdW2, tc::kstep_desc(sa_a2t, kTile, st), tc::kstep_desc(sa_b2, kTile, st),
+                             tc::idesc_bf16(128, kK2), !first || st > 0);
             tc::mma_commit(bar);
         }
         if (!(ok = wait_all(bar, phase))) break;
         // (5) dZ1 = bf16(dH1 * gelu'(Z1)) as dZ1^T (over the dZ2 buffer, whose GEMM is done)
         uint8_t* sA1t = sA2;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kHid; c0 += 16) {
+        for (int c0 = cg * (kHid / kColGroups); c0 < (cg + 1) * (kHid / kColGroups); c0 += 16) {
             float v[16];
             tc::tmem_ld16(tbase + kTdH1 + lane_off + (uint32_t)c0, v);
             uint4 z[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
@@ -425,16 +443,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const float zv = bf2f((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu));
-                st_bf16(sA1t, c0 + i, tid, f2bf(v[i] * gelu_grad(zv)));
+                st_bf16(sA1t, c0 + i, r, f2bf(v[i] * gelu_grad(zv)));
             }
         }
         operands_ready();
         // (6) dW1_aug += dZ1^T X_aug
         if (tid == 0) {
             tc::fence_after_sync();
-            for (int s = 0; s < kTile / 16; s++)
-                tc::mma_bf16(tbase + kTdW1, tc::kstep_desc(sa_a2, kTile, s), tc::kstep_desc(sa_b1, kTile, s),
-                             tc::idesc_bf16(128, kK1), !first || s > 0);
+            for (int st = 0; st < kTile / 16; st++)
+                tc::mma_bf16(tbase + kTdW1, tc::kstep_desc(sa_a2, kTile, st), tc::kstep_desc(sa_b1, kTile, st),
+                             tc::idesc_bf16(128, kK1), !first || st > 0);
             tc::mma_commit(bar);
         }
         if (!(ok = wait_all(bar, phase))) break;
@@ -442,31 +460,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     }
     if (!ok && tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
     if (ok && !first) {
-        // accumulated weight gradients of this CTA -> global (row tid of dW1_aug, dW2_aug)
+        // accumulated weight gradients of this CTA -> global (row r of dW1_aug, dW2_aug; every fourth chunk)
 #pragma unroll 1
-        for (int c0 = 0; c0 < kK1; c0 += 16) {
+        for (int c0 = 16 * cg; c0 < kK1; c0 += 16 * kColGroups) {
             float v[16];
             tc::tmem_ld16(tbase + kTdW1 + lane_off + (uint32_t)c0, v);
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const int k = c0 + i;
-                if (k < kIn) atomicAdd(a.g.W1 + tid * kIn + k, v[i]);
-                else if (k == kIn) atomicAdd(a.g.b1 + tid, v[i]);
+                if (k < kIn) atomicAdd(a.g.W1 + r * kIn + k, v[i]);
+                else if (k == kIn) atomicAdd(a.g.b1 + r, v[i]);
             }
         }
 #pragma unroll 1
-        for (int c0 = 0; c0 < kK2; c0 += 16) {
+        for (int c0 = 16 * cg; c0 < kK2; c0 += 16 * kColGroups) {
             float v[16];
             tc::tmem_ld16(tbase + kTdW2 + lane_off + (uint32_t)c0, v);
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const int k = c0 + i;
-                if (k < kHid) atomicAdd(a.g.W2 + tid * kHid + k, v[i]);
-                else if (k == kHid) atomicAdd(a.g.b2 + tid, v[i]);
+                if (k < kHid) atomicAdd(a.g.W2 + r * kHid + k, v[i]);
+                else if (k == kHid) atomicAdd(a.g.b2 + r, v[i]);
             }
         }
 #pragma unroll
-        for (int o = 0; o < kOut; o++) atomicAdd(a.g.W3 + o * kHid + tid, acc3[o]);
+        for (int o = 0; o < kOut; o++) atomicAdd(a.g.W3 + o * kHid + jw, acc3[o]);
         if (tid < kOut) atomicAdd(a.g.b3 + tid, accb3);
     }
     tc::fence_before_sync();
@@ -500,7 +518,7 @@ cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n,
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
     MlpFwdArgs a{w, X, n, Y, Z1, Z2, T, dY, loss, loss_scale, status};
-    k_mlp_fwd<<<grid, kThreads, kFwdSmem, s>>>(a);
+    k_mlp_fwd<<<grid, kFwdThreads, kFwdSmem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -519,7 +537,7 @@ cudaError_t launch_mlp_bwd(const gs_mlp_packed& w, const uint16_t* X, const uint
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
     MlpBwdArgs a{w, X, Z1, Z2, dY, n, g, status};
-    k_mlp_bwd<<<grid, kThreads, kBwdSmem, s>>>(a);
+    k_mlp_bwd<<<grid, kFwdThreads, kBwdSmem, s>>>(a);
     return cudaGetLastError();
 }
 
