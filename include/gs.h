@@ -304,9 +304,15 @@ typedef struct gs_mlp_params {
 
 /* BF16 GEMM operands made by gs_mlp_pack (device, caller-owned, 16-byte
  * aligned): W1a [128][208] (W1 | b1 | 0), W2a [128][144] (W2 | b2 | 0),
- * W3a [16][144] (rows 0..7: W3 | b3 | 0; rows 8..15: 0), W2t [128][128] = W2^T. */
+ * W3a [16][144] (rows 0..7: W3 | b3 | 0; rows 8..15: 0), W2t [128][128] = W2^T;
+ * and, because every pre-activation is a BF16 value, the activation tabulated
+ * over all 65536 BF16 inputs z (indexed by the bit pattern): gelu_tab [65536]
+ * = bf16(gelu(z)) (BF16) and dgelu_tab [65536] = gelu'(z) (FP32), evaluated in
+ * FP32 with the exact erf form. */
 typedef struct gs_mlp_packed {
     uint16_t *W1a, *W2a, *W3a, *W2t;
+    uint16_t* gelu_tab;
+    float* dgelu_tab;
 } gs_mlp_packed;
 
 /* FP32 gradients (device), same shapes as gs_mlp_params. */

@@ -287,15 +287,15 @@ int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* ho
 int32_t gs_mlp_pack(const gs_mlp_params* p, const gs_mlp_packed* q, void* stream) {
     if (p == nullptr || q == nullptr) return GS_ERR_INVALID_ARG;
     if (!p->W1 || !p->b1 || !p->W2 || !p->b2 || !p->W3 || !p->b3) return GS_ERR_INVALID_ARG;
-    if (!q->W1a || !q->W2a || !q->W3a || !q->W2t) return GS_ERR_INVALID_ARG;
+    if (!q->W1a || !q->W2a || !q->W3a || !q->W2t || !q->gelu_tab || !q->dgelu_tab) return GS_ERR_INVALID_ARG;
     if (!aligned(q->W1a, 16) || !aligned(q->W2a, 16) || !aligned(q->W3a, 16) || !aligned(q->W2t, 16))
         return GS_ERR_INVALID_ARG;
     return cuda_status(launch_mlp_pack(*p, *q, static_cast<cudaStream_t>(stream)));
 }
 
 static bool mlp_packed_ok(const gs_mlp_packed* q) {
-    return q != nullptr && q->W1a && q->W2a && q->W3a && q->W2t && aligned(q->W1a, 16) && aligned(q->W2a, 16) &&
-           aligned(q->W3a, 16) && aligned(q->W2t, 16);
+    return q != nullptr && q->W1a && q->W2a && q->W3a && q->W2t && q->gelu_tab && q->dgelu_tab &&
+           aligned(q->W1a, 16) && aligned(q->W2a, 16) && aligned(q->W3a, 16) && aligned(q->W2t, 16);
 }
 
 int32_t gs_mlp_fwd(const gs_mlp_packed* q, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1, uint16_t* Z2,

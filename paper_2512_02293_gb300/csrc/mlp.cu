@@ -71,6 +71,12 @@ __global__ void k_mlp_pack(gs_mlp_params p, gs_mlp_packed q) {
             q.W2t[j] = f2bf(p.W2[c * kHid + r]);
         }
     }
+    // the activation and its derivative at every BF16 input
+    for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < 65536; z += gridDim.x * blockDim.x) {
+        const float x = bf2f((uint32_t)z);
+        q.gelu_tab[z] = f2bf(gelu(x));
+        q.dgelu_tab[z] = gelu_grad(x);
+    }
 }
 
 // Copy a row-major BF16 matrix [R][K] from global memory into the K-major
@@ -128,7 +134,8 @@ struct MlpFwdArgs {
 // accumulator -> Z = bf16, H = bf16(gelu(Z)) into the next layer's K-major
 // operand, Z to global memory.
 __device__ __forceinline__ void hidden_epilogue(uint32_t tacc, uint8_t* sH, int r, int64_t row, int64_t n,
-                                                uint16_t* __restrict__ Zout, int c_lo, int c_hi) {
+                                                uint16_t* __restrict__ Zout, int c_lo, int c_hi,
+                                                const uint16_t* __restrict__ gtab) {
 #pragma unroll 1
     for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
         float v[16];
@@ -138,7 +145,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tacc, uint8_t* sH, int 
         for (int i = 0; i < 8; i++) {
             const uint16_t z0 = f2bf(v[2 * i]), z1 = f2bf(v[2 * i + 1]);
             zp[i] = pack2(z0, z1);
-            hp[i] = pack2(f2bf(gelu(bf2f(z0))), f2bf(gelu(bf2f(z1))));
+            hp[i] = pack2(__ldg(gtab + z0), __ldg(gtab + z1));
         }
         *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, c0, kK2)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
         *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, c0 + 8, kK2)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
@@ -216,11 +223,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
         operands_ready();
         if (tid == 0) issue_gemm(tD1, sa_x, sa_w1, kK1, tc::idesc_bf16(128, kHid), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
-        hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi);
+        hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi, a.w.gelu_tab);
         operands_ready();
         if (tid == 0) issue_gemm(tD2, sa_h, sa_w2, kK2, tc::idesc_bf16(128, kHid), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
-        hidden_epilogue(tD2 + lane_off, sH, r, row, a.n, a.Z2, c_lo, c_hi);
+        hidden_epilogue(tD2 + lane_off, sH, r, row, a.n, a.Z2, c_lo, c_hi, a.w.gelu_tab);
         operands_ready();
         if (tid == 0) issue_gemm(tD3, sa_h, sa_w3, kK2, tc::idesc_bf16(128, kN3), false, bar);
         if (!(ok = wait_all(bar, phase))) break;
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             uint32_t h[4];
 #pragma unroll
             for (int i = 0; i < 4; i++)
-                h[i] = pack2(f2bf(gelu(bf2f(w[i] & 0xFFFFu))), f2bf(gelu(bf2f(w[i] >> 16))));
+                h[i] = pack2(__ldg(a.w.gelu_tab + (w[i] & 0xFFFFu)), __ldg(a.w.gelu_tab + (w[i] >> 16)));
             *reinterpret_cast<uint4*>(sH2 + r * kHid + 8 * c) = make_uint4(h[0], h[1], h[2], h[3]);
         }
         __syncthreads();
@@ -400,8 +407,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                 float dh = 0.f;
 #pragma unroll
                 for (int o = 0; o < kOut; o++) dh += dy[o] * sW3f[o * kHid + j];
-                const float zv = bf2f((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu));
-                g[i] = f2bf(dh * gelu_grad(zv));
+                const uint32_t zb = (i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu);
+                g[i] = f2bf(dh * __ldg(a.w.dgelu_tab + zb));
                 st_bf16(sA2t, j, r, g[i]);
             }
             *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(r, 8 * c, kHid)) =
@@ -411,8 +418,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             const uint32_t w1[4] = {z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                st_bf16(sB2, 8 * c + 2 * i, r, f2bf(gelu(bf2f(w1[i] & 0xFFFFu))));
-                st_bf16(sB2, 8 * c + 2 * i + 1, r, f2bf(gelu(bf2f(w1[i] >> 16))));
+                st_bf16(sB2, 8 * c + 2 * i, r, __ldg(a.w.gelu_tab + (w1[i] & 0xFFFFu)));
+                st_bf16(sB2, 8 * c + 2 * i + 1, r, __ldg(a.w.gelu_tab + (w1[i] >> 16)));
             }
         }
         operands_ready();
@@ -442,8 +449,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             const uint32_t w[8] = {z[0].x, z[0].y, z[0].z, z[0].w, z[1].x, z[1].y, z[1].z, z[1].w};
 #pragma unroll
             for (int i = 0; i < 16; i++) {
-                const float zv = bf2f((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu));
-                st_bf16(sA1t, c0 + i, r, f2bf(v[i] * gelu_grad(zv)));
+                const uint32_t zb = (i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu);
+                st_bf16(sA1t, c0 + i, r, f2bf(v[i] * __ldg(a.w.dgelu_tab + zb)));
             }
         }
         operands_ready();

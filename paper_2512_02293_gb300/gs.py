@@ -88,7 +88,7 @@ class gs_mlp_params(ctypes.Structure):
 
 
 class gs_mlp_packed(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("W1a", "W2a", "W3a", "W2t")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1a", "W2a", "W3a", "W2t", "gelu_tab", "dgelu_tab")]
 
 
 class gs_mlp_grads(ctypes.Structure):
@@ -441,7 +441,8 @@ MLP_PARAM_SHAPES = {"W1": (128, 196), "b1": (128,), "W2": (128, 128), "b2": (128
 
 
 class MlpPacked:
-    """BF16 GEMM operands (W1a [128,208], W2a [128,144], W3a [16,144], W2t [128,128])."""
+    """BF16 GEMM operands (W1a [128,208], W2a [128,144], W3a [16,144], W2t [128,128]) and the
+    activation tables over all BF16 inputs (gelu_tab BF16, dgelu_tab FP32, 65536 each)."""
 
     def __init__(self, device="cuda"):
         import torch
@@ -450,9 +451,12 @@ class MlpPacked:
         self.W2a = torch.zeros(128, 144, device=device, dtype=bf)
         self.W3a = torch.zeros(16, 144, device=device, dtype=bf)
         self.W2t = torch.zeros(128, 128, device=device, dtype=bf)
+        self.gelu_tab = torch.zeros(65536, device=device, dtype=bf)
+        self.dgelu_tab = torch.zeros(65536, device=device, dtype=torch.float32)
 
     def struct(self):
-        return gs_mlp_packed(_ptr(self.W1a), _ptr(self.W2a), _ptr(self.W3a), _ptr(self.W2t))
+        return gs_mlp_packed(_ptr(self.W1a), _ptr(self.W2a), _ptr(self.W3a), _ptr(self.W2t), _ptr(self.gelu_tab),
+                             _ptr(self.dgelu_tab))
 
 
 def gs_mlp_pack(params: dict, packed: MlpPacked, stream=None):

@@ -89,8 +89,8 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib):
 def test_mlp_entry_points_reject_bad_arguments(lib):
     # host checks of the learned-initialiser calls; nothing reaches the device
     V = ctypes.c_void_p
-    q = G.gs_mlp_packed(V(256), V(512), V(768), V(1024))
-    qbad = G.gs_mlp_packed(V(256), V(512), V(770), V(1024))                 # misaligned W3a
+    q = G.gs_mlp_packed(V(256), V(512), V(768), V(1024), V(2048), V(4096))
+    qbad = G.gs_mlp_packed(V(256), V(512), V(770), V(1024), V(2048), V(4096))   # misaligned W3a
     assert lib.gs_mlp_pack(None, ctypes.byref(q), None) == 1
     assert lib.gs_mlp_fwd(None, V(256), 4, None, None, None, None, None, None, 0.0, None, None) == 1
     assert lib.gs_mlp_fwd(ctypes.byref(qbad), V(256), 4, None, None, None, None, None, None, 0.0, None, None) == 1
