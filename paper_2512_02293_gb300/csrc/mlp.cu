@@ -214,14 +214,28 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
     uint32_t phase = 0;
     bool ok = true;
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
+    // the four threads of a sample row take every fourth 8-value chunk of its X row;
+    // the next tile's chunks are loaded into registers while this tile computes
+    constexpr int kXc = (kK1 / 8 + kColGroups - 1) / kColGroups;
+    uint4 xn[kXc];
+    auto load_x = [&](int64_t tile) {
+#pragma unroll
+        for (int q = 0; q < kXc; q++) {
+            const int c = cg + q * kColGroups;
+            xn[q] = c < kK1 / 8 ? x_chunk(a.X, tile * kTile + r, a.n, c) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    if ((int64_t)blockIdx.x < n_tiles) load_x(blockIdx.x);
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int64_t row0 = t * kTile, row = row0 + r;
-        // X tile: the four threads of a sample row take every fourth 8-value chunk
-#pragma unroll 2
-        for (int c = cg; c < kK1 / 8; c += kColGroups)
-            *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(r, 8 * c, kK1)) = x_chunk(a.X, row, a.n, c);
+#pragma unroll
+        for (int q = 0; q < kXc; q++) {
+            const int c = cg + q * kColGroups;
+            if (c < kK1 / 8) *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(r, 8 * c, kK1)) = xn[q];
+        }
         operands_ready();
         if (tid == 0) issue_gemm(tD1, sa_x, sa_w1, kK1, tc::idesc_bf16(128, kHid), false, bar);
+        if (t + gridDim.x < n_tiles) load_x(t + gridDim.x);     // in flight during the epilogues
         if (!(ok = wait_all(bar, phase))) break;
         hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi, a.w.gelu_tab);
         operands_ready();
