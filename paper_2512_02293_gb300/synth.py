@@ -361,3 +361,31 @@ def mlp_batch(seed: int, n: int, n_in: int = 196, n_out: int = 8):
     rng = np.random.default_rng(seed)
     return (rng.uniform(-1.0, 1.0, (n, n_in)).astype(np.float32),
             rng.standard_normal((n, n_out)).astype(np.float32))
+
+
+def ba_scene(seed: int, K: int = 4, h: int = 12, w: int = 16, f: float = 20.0, window: int = 2):
+    """A bundle-adjustment window: K keyframes (world-to-camera R [K,3,3], t
+    [K,3]) on a short sideways path looking at a smooth surface 2-4 m away,
+    each with its inverse-depth map [K, h, w] of that surface seen along the
+    pixel rays; edges (i, j) for 0 < |i - j| <= window; positive confidence
+    weights [E, h, w, 2]; pinhole intrinsics (fx, fy, cx, cy) of the h x w grid."""
+    rng = np.random.default_rng(seed)
+    intr = (f, f * (1.0 + 0.05 * rng.uniform(-1, 1)), w / 2.0 + rng.uniform(-0.5, 0.5), h / 2.0 + rng.uniform(-0.5, 0.5))
+    R = np.zeros((K, 3, 3)); t = np.zeros((K, 3))
+    for k in range(K):
+        ang = rng.normal(0.0, 0.02, 3) + np.array([0.0, 0.03 * k, 0.0])
+        th = np.linalg.norm(ang)
+        Kx = np.array([[0, -ang[2], ang[1]], [ang[2], 0, -ang[0]], [-ang[1], ang[0], 0]])
+        Rk = np.eye(3) + np.sin(th) / th * Kx + (1 - np.cos(th)) / th ** 2 * Kx @ Kx if th > 0 else np.eye(3)
+        c = np.array([0.15 * k, rng.normal(0, 0.02), rng.normal(0, 0.02)])        # camera centre
+        R[k] = Rk; t[k] = -Rk @ c
+    ys, xs = np.mgrid[0:h, 0:w]
+    a = rng.uniform(-0.5, 0.5, 3)
+    disp = np.zeros((K, h, w))
+    for k in range(K):
+        u = (xs + 0.5 - intr[2]) / intr[0]; v = (ys + 0.5 - intr[3]) / intr[1]
+        depth = 3.0 + a[0] * u + a[1] * v + 0.3 * np.sin(2.0 * u + a[2]) * np.cos(1.5 * v)
+        disp[k] = 1.0 / depth
+    edges = [(i, j) for i in range(K) for j in range(K) if i != j and abs(i - j) <= window]
+    weights = rng.uniform(0.5, 2.0, (len(edges), h, w, 2))
+    return R, t, disp, intr, edges, weights
