@@ -477,6 +477,34 @@ def tracking_run(device, seeds=(0, 1, 2)):
             "iterations": tr.iters, "ms_per_iteration": round(total_ms / total_it, 4), "runs": out}
 
 
+def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
+    """One Levenberg-Marquardt step of the dense visual bundle adjustment
+    (Eq. 2 / Eq. 4) on a 16-keyframe window at the tracker's 1/8 resolution of
+    640x480 (60 x 80 inverse depths per keyframe), every pair of keyframes at
+    most 3 apart as an edge; CUDA-event time of gs_ba_step."""
+    import torch
+    from paper_2512_02293_gb300 import gs as G
+    from paper_2512_02293_gb300 import synth
+    R, t, disp, intr, edges, wts = synth.ba_scene(21, K=K, h=h, w=w, f=70.0, window=window)
+    rng = np.random.default_rng(22)
+    targets = rng.normal(0.0, 0.5, (len(edges), h, w, 2)) + np.stack(np.meshgrid(np.arange(w) + 0.5,
+                                                                             np.arange(h) + 0.5), -1)
+    win = G.BAWindow(R, t, disp, intr, edges, targets, wts, 2, device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        G.gs_ba_step(win, 1e-3, 1e-3)
+    ms = []
+    for _ in range(steps):
+        ev[0].record(); G.gs_ba_step(win, 1e-3, 1e-3); ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    m = statistics.median(ms)
+    n_res = len(edges) * h * w
+    return {"workload": f"{K} keyframes, {h}x{w} inverse depths each, {len(edges)} edges (|i - j| <= {window}), "
+                        f"{n_res} residual pixels, 2 poses fixed", "ms_per_step": round(m, 4),
+            "residual_pixels_per_s": n_res / (m * 1e-3), "status": int(win.status[0].item())}
+
+
 LOOP_CLOSURE_BYTES = 12 + 16 + 12 + 4 + 12 + 16 + 12   # read mean, quat, log-scale, anchor; write the first three
 
 
@@ -623,6 +651,7 @@ def main():
         line["learned_init"] = learned_init_run(device, args)
     line["loop_closure_update"] = loop_closure_run(device)
     line["pose_refinement"] = tracking_run(device)
+    line["bundle_adjustment"] = ba_run(device)
     if not args.no_window:
         line["differentiation"] = differentiation_run(device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

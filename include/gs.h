@@ -406,6 +406,44 @@ int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, c
                                const float* pose_after, const float* scale_change, int32_t n_keyframes,
                                int32_t* d_status, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Dense visual bundle adjustment of the tracker (Sec. 3.2, "Vision Residual"
+ * Eq. 2, "Frontend Tracking: Local Bundle Adjustment" Eq. 4): one
+ * Levenberg-Marquardt step over a window of keyframes.
+ *   r = u*_ij - Pi(T_j T_i^-1 Pi^-1(u, d_i(u))) for every edge (i, j) and every
+ *   pixel u of keyframe i's h x w grid (sampled at pixel centres); cost
+ *   sum w r^2.  Variables: the left perturbations xi_k = (rho, phi) of the poses
+ *   k >= n_fixed (T_k <- Exp(xi_k) T_k; rotation exact, translation to first
+ *   order) and every inverse depth of every keyframe that is an edge source.
+ *   (H + lambda diag(H) + eps I) delta = -g with H = J^T W J, g = J^T W r,
+ *   solved through the Schur complement of the diagonal inverse-depth block.
+ * The inertial factor of Eq. 3 is not part of this call. */
+typedef struct gs_ba_problem {
+    float* poses;            /* [K][12] world-to-camera R (row-major) and t; updated */
+    float* disp;             /* [K][h][w] inverse depths; updated */
+    const float* targets;    /* [E][h][w][2] target pixel coordinates u*_ij */
+    const float* weights;    /* [E][h][w][2] confidences w_ij (>= 0) */
+    const int32_t* ii;       /* [E] edge sources (device) */
+    const int32_t* jj;       /* [E] edge targets (device) */
+    int32_t n_keyframes, n_edges, height, width;
+    int32_t n_fixed;         /* the first n_fixed poses are held (gauge) */
+    float fx, fy, cx, cy;    /* intrinsics of the h x w grid */
+    int32_t* status;         /* device status word: bad edge indices record
+                                GS_ERR_INVALID_ARG, a reduced system that is not
+                                positive definite GS_ERR_NUMERIC */
+} gs_ba_problem;
+
+/* Workspace bytes of gs_ba_step. */
+size_t gs_ba_workspace_size(int32_t n_keyframes, int32_t n_edges, int32_t height, int32_t width, int32_t n_fixed);
+
+/* One step; *cost (device float) receives sum w r^2 at the poses and inverse
+ * depths before the step.  At most 31 free poses (n_keyframes - n_fixed <= 31).
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers, bad sizes, a too-small or
+ * misaligned workspace, lambda < 0, eps < 0; GS_ERR_UNSUPPORTED above 31 free
+ * poses. */
+int32_t gs_ba_step(const gs_ba_problem* problem, float lambda, float eps, float* cost, void* ws, size_t ws_bytes,
+                   void* stream);
+
 /* Synchronises `stream`, copies the device status word to *host_status and
  * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgs.so")
-SOURCES = ["api.cu", "project.cu", "binsort.cu", "raster.cu", "loss_adam.cu", "mlp.cu", "insert.cu", "loop_closure.cu"]
+SOURCES = ["api.cu", "project.cu", "binsort.cu", "raster.cu", "loss_adam.cu", "mlp.cu", "insert.cu", "loop_closure.cu", "ba.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -356,4 +356,27 @@ int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, c
                                            d_status, static_cast<cudaStream_t>(stream)));
 }
 
+size_t gs_ba_workspace_size(int32_t K, int32_t E, int32_t h, int32_t w, int32_t n_fixed) {
+    if (K < 1 || E < 0 || h < 1 || w < 1 || n_fixed < 0 || n_fixed > K) return 0;
+    return ba_workspace(K, E, h * w, 6 * (K - n_fixed));
+}
+
+int32_t gs_ba_step(const gs_ba_problem* pr, float lambda, float eps, float* cost, void* ws, size_t ws_bytes,
+                   void* stream) {
+    if (pr == nullptr || cost == nullptr) return GS_ERR_INVALID_ARG;
+    const int K = pr->n_keyframes, E = pr->n_edges, h = pr->height, w = pr->width;
+    if (K < 1 || E < 0 || h < 1 || w < 1 || pr->n_fixed < 0 || pr->n_fixed > K) return GS_ERR_INVALID_ARG;
+    if ((int64_t)h * w >= (1 << 26) || (int64_t)E * h * w * 12 >= (1ll << 40)) return GS_ERR_INVALID_ARG;
+    if (!(lambda >= 0.f) || !(eps >= 0.f) || !isfinite(lambda) || !isfinite(eps)) return GS_ERR_INVALID_ARG;
+    if (!isfinite(pr->fx) || !isfinite(pr->fy) || !isfinite(pr->cx) || !isfinite(pr->cy) || pr->fx == 0.f ||
+        pr->fy == 0.f)
+        return GS_ERR_INVALID_ARG;
+    if (!pr->poses || !pr->disp || !pr->status || (E > 0 && (!pr->targets || !pr->weights || !pr->ii || !pr->jj)))
+        return GS_ERR_INVALID_ARG;
+    if (K - pr->n_fixed > 31) return GS_ERR_UNSUPPORTED;
+    if (ws == nullptr || !aligned(ws, 256) || ws_bytes < ba_workspace(K, E, h * w, 6 * (K - pr->n_fixed)))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_ba_step(*pr, lambda, eps, cost, ws, static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

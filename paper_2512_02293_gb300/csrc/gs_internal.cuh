@@ -76,6 +76,8 @@ cudaError_t launch_insert(const float* color, const float* depth, const gs_camer
                           int sh_degree, int* status, cudaStream_t s);
 cudaError_t launch_loop_closure(const gs_map_slots& map, const int32_t* anchor, const float* before,
                                 const float* after, const float* ds, int K, int* status, cudaStream_t s);
+size_t ba_workspace(int K, int E, int P, int n);
+cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, float* cost, void* ws, cudaStream_t s);
 cudaError_t launch_mlp_pack(const gs_mlp_params& p, const gs_mlp_packed& q, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
                            uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int* status,

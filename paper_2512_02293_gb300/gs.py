@@ -83,6 +83,14 @@ class gs_map_slots(ctypes.Structure):
                 ("opacity_logit", ctypes.c_void_p), ("color", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
 
 
+class gs_ba_problem(ctypes.Structure):
+    _fields_ = [("poses", ctypes.c_void_p), ("disp", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("ii", ctypes.c_void_p), ("jj", ctypes.c_void_p),
+                ("n_keyframes", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("n_fixed", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("status", ctypes.c_void_p)]
+
+
 class gs_mlp_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
 
@@ -99,7 +107,8 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_loss_noalloc", "gs_render_bwd",
            "gs_render_bwd_raster",
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
-           "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update"]
+           "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
+           "gs_ba_step"]
 
 
 def load_library(path: str | None = None):
@@ -151,6 +160,10 @@ def load_library(path: str | None = None):
     lib.gs_mlp_bwd.argtypes = [V, V, V, V, V, ctypes.c_int64, V, V, V]
     lib.gs_extract_patches.restype = ctypes.c_int32
     lib.gs_extract_patches.argtypes = [V, V, V, V, ctypes.c_int64, V, V, V]
+    lib.gs_ba_workspace_size.restype = ctypes.c_size_t
+    lib.gs_ba_workspace_size.argtypes = [ctypes.c_int32] * 5
+    lib.gs_ba_step.restype = ctypes.c_int32
+    lib.gs_ba_step.argtypes = [V, ctypes.c_float, ctypes.c_float, V, V, ctypes.c_size_t, V]
     lib.gs_loop_closure_update.restype = ctypes.c_int32
     lib.gs_loop_closure_update.argtypes = [V, V, V, V, V, ctypes.c_int32, V, V]
     lib.gs_insert_gaussians.restype = ctypes.c_int32
@@ -513,3 +526,47 @@ def gs_loop_closure_update(g: "Gaussians", anchor, pose_before, pose_after, scal
     _check(load_library().gs_loop_closure_update(ctypes.byref(slots), _ptr(anchor), _ptr(pose_before),
                                                  _ptr(pose_after), _ptr(scale_change), int(pose_before.shape[0]),
                                                  _ptr(status), _stream(stream)), "gs_loop_closure_update")
+
+
+# ------------------------------------------------------- bundle adjustment
+
+class BAWindow:
+    """Device state of a bundle-adjustment window (see gs_ba_step): poses
+    [K, 12] (world-to-camera R row-major, t), inverse depths [K, h, w], targets
+    and weights [E, h, w, 2], edges ii / jj [E], intrinsics of the grid."""
+
+    def __init__(self, R, t, disp, intr, edges, targets, weights, n_fixed, device="cuda"):
+        import torch
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        K, h, w = np.asarray(disp).shape
+        self.K, self.h, self.w, self.E = K, h, w, len(edges)
+        self.poses = f(np.concatenate([np.asarray(R).reshape(K, 9), np.asarray(t).reshape(K, 3)], 1))
+        self.disp = f(disp)
+        self.targets = f(targets)
+        self.weights = f(weights)
+        e = np.asarray(edges, np.int32).reshape(-1, 2)
+        self.ii = torch.from_numpy(np.ascontiguousarray(e[:, 0])).to(device)
+        self.jj = torch.from_numpy(np.ascontiguousarray(e[:, 1])).to(device)
+        self.intr = tuple(float(x) for x in intr)
+        self.n_fixed = int(n_fixed)
+        self.status = torch.zeros(4, device=device, dtype=torch.int32)
+        self.cost = torch.zeros(1, device=device)
+        nbytes = gs_ba_workspace_size(K, self.E, h, w, n_fixed)
+        self.ws = torch.empty((nbytes + 255) // 256 * 64 + 64, device=device, dtype=torch.float32)
+
+    def struct(self):
+        fx, fy, cx, cy = self.intr
+        return gs_ba_problem(_ptr(self.poses), _ptr(self.disp), _ptr(self.targets), _ptr(self.weights), _ptr(self.ii),
+                             _ptr(self.jj), self.K, self.E, self.h, self.w, self.n_fixed, fx, fy, cx, cy,
+                             _ptr(self.status))
+
+
+def gs_ba_workspace_size(K: int, E: int, h: int, w: int, n_fixed: int) -> int:
+    return int(load_library().gs_ba_workspace_size(K, E, h, w, n_fixed))
+
+
+def gs_ba_step(win: BAWindow, lam: float = 1e-4, eps: float = 1e-4, stream=None):
+    """One Levenberg-Marquardt step in place; win.cost gets the cost before the step."""
+    pr = win.struct()
+    _check(load_library().gs_ba_step(ctypes.byref(pr), float(lam), float(eps), _ptr(win.cost), _ptr(win.ws),
+                                     win.ws.numel() * 4, _stream(stream)), "gs_ba_step")

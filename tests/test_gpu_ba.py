@@ -1,0 +1,89 @@
+"""Dense visual bundle adjustment on the GPU (gs_ba_step: Eq. 2 residuals, Eq. 4
+Schur complement of the inverse-depth block) against the FP64 oracle's full
+dense solve."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ba
+from paper_2512_02293_gb300 import gs as G
+from paper_2512_02293_gb300 import synth
+from gpu_common import ensure_lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def _f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def _exact_targets(R, t, disp, intr, edges):
+    h, w = disp.shape[1:]
+    return -ba.residuals(R, t, disp, intr, edges, np.zeros((len(edges), h, w, 2)))
+
+
+def _gpu_state(win):
+    P = win.poses.cpu().numpy().astype(np.float64)
+    return P[:, :9].reshape(-1, 3, 3), P[:, 9:], win.disp.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n_fixed", [1, 2])
+def test_one_step_matches_dense_solve(n_fixed):
+    R, t, disp, intr, edges, wts = synth.ba_scene(7, K=5, h=12, w=16)
+    rng = np.random.default_rng(8)
+    targets = _exact_targets(R, t, disp, intr, edges) + rng.normal(0, 0.3, (len(edges), 12, 16, 2))
+    win = G.BAWindow(R, t, disp, intr, edges, targets, wts, n_fixed)
+    lam, eps = 1e-3, 1e-3
+    G.gs_ba_step(win, lam, eps)
+    torch.cuda.synchronize()
+    assert int(win.status[0].item()) == 0
+    # the oracle on the same float32 inputs
+    R32, t32, d32, T32, W32 = _f32(R), _f32(t), _f32(disp), _f32(targets), _f32(wts)
+    intr32 = tuple(float(np.float32(x)) for x in intr)
+    dx, dd, H, g, cost = ba.lm_step(R32, t32, d32, intr32, edges, T32, W32, n_fixed, lam=lam, eps=eps)
+    Rr, tr, dr = ba.apply_step(R32, t32, d32, dx, dd, n_fixed)
+    assert win.cost.item() == pytest.approx(cost, rel=1e-4)
+    Rg, tg, dg = _gpu_state(win)
+    step_d = np.abs(dd).max()
+    np.testing.assert_allclose(dg, dr, atol=2e-3 * step_d + 1e-6)
+    step_x = np.abs(dx).max()
+    np.testing.assert_allclose(tg, tr, atol=2e-3 * step_x + 1e-6)
+    np.testing.assert_allclose(Rg, Rr, atol=2e-3 * step_x + 1e-6)
+    # the fixed poses did not move
+    np.testing.assert_array_equal(win.poses.cpu().numpy()[:n_fixed], np.concatenate(
+        [np.asarray(R, np.float32).reshape(-1, 9), np.asarray(t, np.float32)], 1)[:n_fixed])
+
+
+def test_gauss_newton_recovers_the_window():
+    R, t, disp, intr, edges, wts = synth.ba_scene(9, K=6, h=24, w=32)
+    targets = _exact_targets(R, t, disp, intr, edges)
+    rng = np.random.default_rng(10)
+    n_fixed = 2
+    R1, t1, d1 = ba.apply_step(R, t, disp, rng.normal(0, 0.01, (4, 6)), rng.normal(0, 0.01, disp.shape), n_fixed)
+    win = G.BAWindow(R1, t1, d1, intr, edges, targets, wts, n_fixed)
+    costs = []
+    for _ in range(10):
+        G.gs_ba_step(win, 1e-5, 1e-6)
+        costs.append(win.cost.item())
+    torch.cuda.synchronize()
+    assert int(win.status[0].item()) == 0
+    assert costs[-1] < 1e-6 * costs[0]
+    Rg, tg, dg = _gpu_state(win)
+    np.testing.assert_allclose(dg, disp, atol=2e-5)
+    np.testing.assert_allclose(tg, t, atol=2e-5)
+    np.testing.assert_allclose(Rg, R, atol=2e-5)
+
+
+def test_bad_edge_is_reported():
+    R, t, disp, intr, edges, wts = synth.ba_scene(11, K=3, h=4, w=4)
+    targets = _exact_targets(R, t, disp, intr, edges)
+    bad = list(edges) + [(1, 7)]
+    win = G.BAWindow(R, t, disp, intr, bad, np.concatenate([targets, targets[:1]]),
+                     np.concatenate([wts, wts[:1]]), 1)
+    G.gs_ba_step(win)
+    assert G.gs_read_device_status(win.status) == G.GS_ERR_INVALID_ARG
