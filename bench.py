@@ -307,7 +307,19 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
     views = len(cams)
+    peaks, peak_kind = _peaks()
+    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roof = None
+    if st:
+        roof = {}
+        for stage, ops, kern in (("gs_render_fwd", FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"),
+                                 ("gs_render_bwd_raster", BWD_OPS_PER_PAIR, f"k_render_bwd<{params.tile}>")):
+            ach = pairs * ops / (st[stage] * 1e-3) / 1e12
+            roof[stage] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
+                           "frac": ach / alu_peak, "work": f"{pairs} visited pairs x {ops} FP32 ops per launch",
+                           "peak_basis": f"152 SMs x 128 FP32 lanes x sm_max_mhz ({peak_kind})"}
     return {"workload": "batched window: 8 keyframes (4x 640x480, 2x 752x480, 2x 1280x1024), 500k Gaussians",
+            "roofline": roof,
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
             "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
             "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},

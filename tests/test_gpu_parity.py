@@ -178,6 +178,58 @@ def test_render_fwd_ragged_and_multiview():
             assert _compare_images(image_views(img, cams)[v], ref, f"view {v} tile {tile}") == 0
 
 
+def test_thirty_two_views_the_maximum():
+    # GS_MAX_VIEWS views of different sizes and poses in one call: keys bit-exact,
+    # every view equal to its own oracle render, the 33rd view refused on the host
+    g, _, _ = _problem(3)
+    rng = np.random.default_rng(32)
+    cams = []
+    for v in range(G.GS_MAX_VIEWS):
+        R, e = synth.look_at(rng.normal(0, 0.15, 3) + [0.0, 0.0, -0.2], [0.0, 0.0, 2.0])
+        W, H = int(rng.integers(20, 70)), int(rng.integers(16, 50))
+        cams.append(synth.Camera(50.0, 50.0, W / 2, H / 2, W, H, R, e))
+    params = G.RenderParams(tile=8)
+    prs = _stage_inputs(g, cams, params)
+    proj = projected_to_device(prs)
+    m = int(sum(p["tiles"].sum() for p in prs))
+    bins, _, img = _gpu_forward(proj, g.n, cams, params, m)
+    keys, vals, ranges = bins_to_numpy(bins)
+    ok_, ov, orr = oracle_bins(prs, cams, 8)
+    np.testing.assert_array_equal(keys, ok_)
+    np.testing.assert_array_equal(vals, ov)
+    np.testing.assert_array_equal(ranges, orr)
+    views = image_views(img, cams)
+    excused = 0
+    for v, (c, p) in enumerate(zip(cams, prs)):
+        excused += _compare_images(views[v], oracle.render_fwd(p, c, prm_dict(params)), f"view {v}")
+    assert excused <= 5          # near-threshold pixels over 32 views (each compared elsewhere exactly)
+    with pytest.raises(G.GsError):
+        G.gs_project(G.Gaussians.from_numpy(g), cams + cams[:1], params, G.Projected.empty(g.n * 33))
+
+
+def test_splats_covering_every_tile():
+    # Gaussians a few centimetres in front of the camera: their radius spans the
+    # whole grid (and, for the nearest, exceeds any image), so every one of them
+    # is keyed to every tile; bins and images still equal the oracle's.
+    g, _, cam = _problem(4)
+    big = synth.random_cloud(12, 5, box=((-0.05, 0.05), (-0.05, 0.05), (0.25, 0.4)), log_scale_mu=-1.0,
+                             log_scale_sd=0.2)
+    both = synth.GaussianMap(*(np.concatenate([a, b]) for a, b in zip(g.arrays(), big.arrays())))
+    params = G.RenderParams(tile=16)
+    prs = _stage_inputs(both, [cam], params)
+    tiles = prs[0]["tiles"]
+    total = G.gs_total_tiles([cam], 16)
+    assert np.sum(tiles[g.n:] == total) >= 6
+    proj = projected_to_device(prs)
+    bins, _, img = _gpu_forward(proj, both.n, [cam], params, int(tiles.sum()))
+    keys, vals, ranges = bins_to_numpy(bins)
+    ok_, ov, orr = oracle_bins(prs, [cam], 16)
+    np.testing.assert_array_equal(keys, ok_)
+    np.testing.assert_array_equal(vals, ov)
+    np.testing.assert_array_equal(ranges, orr)
+    assert _compare_images(image_views(img, [cam])[0], oracle.render_fwd(prs[0], cam, prm_dict(params))) < 20
+
+
 def test_degenerate_inputs():
     params = G.RenderParams()
     cam = synth.identity_camera()
