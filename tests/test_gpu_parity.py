@@ -337,6 +337,50 @@ def test_render_bwd_stagewise_matches_oracle(sh):
     assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_render_bwd_deep_lists(tile):
+    # Thousands of faint, wide splats over the 64x48 case: front-to-back lists
+    # of more than 2048 blending splats per pixel (the transmittance reaches its
+    # cutoff only after thousands of splats; many batches of the backward's walk
+    # per pixel block, each with every lane blending); colour, depth and the
+    # gradients still equal the oracle's.
+    g, _, cam = _problem(2)
+    faint = synth.random_cloud(3000, 21, box=((-0.8, 0.8), (-0.6, 0.6), (1.5, 3.0)), log_scale_mu=-0.8,
+                               log_scale_sd=0.2)
+    faint = synth.GaussianMap(faint.mean, faint.quat, faint.log_scale,
+                              np.full(faint.n, -6.0, np.float32), faint.color)
+    both = synth.GaussianMap(*(np.concatenate([b, a]) for a, b in zip(g.arrays(), faint.arrays())))
+    params = G.RenderParams(tile=tile)
+    prm = prm_dict(params)
+    prs = _stage_inputs(both, [cam], params)
+    proj = projected_to_device(prs)
+    bins, ws, img = _gpu_forward(proj, both.n, [cam], params, int(prs[0]["tiles"].sum()))
+    ref_img = oracle.render_fwd(prs[0], cam, prm)
+    assert _compare_images(image_views(img, [cam])[0], ref_img) < 20
+    assert int(img.n_contrib.max()) > 2048
+    rng = np.random.default_rng(17)
+    dcol = rng.standard_normal((3, cam.height, cam.width)) * 1e-3
+    ddep = rng.standard_normal((cam.height, cam.width)) * 1e-3
+    dc, dd = pack_images([dcol], [ddep])
+    gd = G.Gaussians.from_numpy(both)
+    grads = G.Grads.empty_like(gd, 1)
+    iso = torch.zeros(1, device="cuda")
+    G.gs_render_bwd(gd, proj, bins, img, dc, dd, [cam], params, 0.0, grads, iso, ws)
+    torch.cuda.synchronize()
+    g2d_gpu = ws[: both.n * 12].view(-1, 12).cpu().numpy().astype(np.float64)
+    ref2d = oracle.render_bwd(prs[0], cam, prm, f32(dcol), f32(ddep))
+    assert rel_l2(g2d_gpu[:, 0:2], ref2d["xy"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 2:5], ref2d["conic"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 5], ref2d["opacity"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 6], ref2d["depth"]) < GRAD_RTOL
+    assert rel_l2(g2d_gpu[:, 8:11], ref2d["rgb"]) < GRAD_RTOL
+    ref = oracle.project_bwd(both, cam, prm, ref2d)
+    got = grads_to_numpy(grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(got[k], ref[k]) < GRAD_RTOL, k
+    assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
+
+
 @pytest.mark.parametrize("lambdas", [(1.0, 1.0, 0.0), (0.9, 0.1, 10.0)])
 def test_full_iteration_end_to_end_matches_oracle(lambdas):
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
