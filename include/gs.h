@@ -429,15 +429,17 @@ typedef struct gs_ba_problem {
     int32_t n_fixed;         /* the first n_fixed poses are held (gauge) */
     float fx, fy, cx, cy;    /* intrinsics of the h x w grid */
     int32_t* status;         /* device status word: bad edge indices record
-                                GS_ERR_INVALID_ARG, a reduced system that is not
-                                positive definite GS_ERR_NUMERIC */
+                                GS_ERR_INVALID_ARG, more than 15 edges out of one
+                                keyframe GS_ERR_UNSUPPORTED, a reduced system
+                                that is not positive definite GS_ERR_NUMERIC */
 } gs_ba_problem;
 
 /* Workspace bytes of gs_ba_step. */
 size_t gs_ba_workspace_size(int32_t n_keyframes, int32_t n_edges, int32_t height, int32_t width, int32_t n_fixed);
 
 /* One step; *cost (device float) receives sum w r^2 at the poses and inverse
- * depths before the step.  At most 31 free poses (n_keyframes - n_fixed <= 31).
+ * depths before the step.  At most 31 free poses (n_keyframes - n_fixed <= 31)
+ * and at most 15 edges with the same source keyframe.
  * Errors: GS_ERR_INVALID_ARG on NULL pointers, bad sizes, a too-small or
  * misaligned workspace, lambda < 0, eps < 0; GS_ERR_UNSUPPORTED above 31 free
  * poses. */

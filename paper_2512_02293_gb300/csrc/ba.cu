@@ -13,21 +13,33 @@
 //   (B + damping - E C'^-1 E^T) dxi = -g_xi + E C'^-1 g_d,
 //   dd = C'^-1 (-g_d - E^T dxi),  C' = (1 + lambda) C + eps.
 //
-// Kernels: k_ba_terms (one thread per (edge, pixel): residual, Jacobians, B and
-// g_xi reduced per CTA into dense buffers, C and g_d by atomics, the 12-vector
-// E(e, p) = [J_i^T W J_d, J_j^T W J_d] stored), k_ba_damp (diagonal damping of
-// B), k_ba_schur (one CTA per ordered pair of edges with the same source
-// keyframe: sum_p E(e1, p) E(e2, p)^T / C'_p into the four 6x6 blocks it touches,
-// and E C'^-1 g_d into the right-hand side), k_ba_solve (one CTA: Cholesky of
-// the n x n reduced system in shared memory), k_ba_update (inverse depths by
-// back-substitution, poses by Exp).
+// Kernels:
+//   k_ba_terms  : each thread takes 4 pixels of one edge (i, j): residual and
+//                 Jacobians; the 91 values of B_ii, B_ij, B_jj, g_i, g_j and the
+//                 cost are reduced per CTA into dense buffers; a 16-float record
+//                 per (edge, pixel) keeps E(e, p) = [J_i^T W J_d, J_j^T W J_d] and
+//                 the pixel's share of C and g_d.
+//   k_ba_schur  : one CTA per (source keyframe i, chunk of pixels): per pixel the
+//                 column v_p of E over the slots [pose i, target of each edge out
+//                 of i] (summed over the edges for pose i), C'_p and g_d,p from the
+//                 records; sum_p v_p v_p^T / C'_p in 2 x 2 register tiles and
+//                 sum_p v_p g_d,p / C'_p, added once per CTA into the reduced system.
+//   k_ba_solve  : one CTA: damping of B, then Gaussian elimination of the
+//                 symmetric positive definite reduced system in shared memory
+//                 (no pivoting; one barrier per column) and back substitution by
+//                 one warp.
+//   k_ba_update : inverse depths by back-substitution, poses by Exp.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
 constexpr int kTermThreads = 128;
+constexpr int kTermPix = 4;                            // pixels per thread
 constexpr int kTermVals = 21 + 36 + 21 + 6 + 6 + 1;   // H_ii (upper), H_ij, H_jj (upper), g_i, g_j, cost
+constexpr int kRec = 16;                               // record: E_i (6), E_j (6), C share, g_d share, 2 unused
+constexpr int kMaxOut = 15;                            // edges with one source keyframe
+constexpr int kMaxSlots = 6 * (1 + kMaxOut);
 
 struct BaDev {
     float* poses;          // [K][12]
@@ -38,10 +50,9 @@ struct BaDev {
     const int32_t* jj;
     int K, E, h, w, P, n_fixed, n;   // n = 6 (K - n_fixed)
     float fx, fy, cx, cy;
-    float* Eb;             // [E][P][12]
-    float* C;              // [K][P]
-    float* gd;             // [K][P]
-    float* S;              // [n][n]
+    float* rec;            // [E][P][kRec]
+    float* SB;             // [n][n] B (undamped)
+    float* SS;             // [n][n] -E C'^-1 E^T
     float* rhs;            // [n]
     float* dxi;            // [n]
     float* cost;           // [1]
@@ -82,7 +93,6 @@ __device__ __forceinline__ float block_sum_vals(float (&v)[kTermVals], float* s_
 __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
     __shared__ float s_part[(kTermThreads / 32) * kTermVals];
     const int e = blockIdx.y;
-    const int q = blockIdx.x * kTermThreads + threadIdx.x;
     const int i = b.ii[e], j = b.jj[e];
     float v[kTermVals];
 #pragma unroll
@@ -91,9 +101,12 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(b.status, 0, GS_ERR_INVALID_ARG);
         return;   // the whole CTA returns: no barrier is reached
     }
-    if (q < b.P) {
-        float Rij[9], tij[3];
-        rel_pose(b, i, j, Rij, tij);
+    float Rij[9], tij[3];
+    rel_pose(b, i, j, Rij, tij);
+    const bool fi = i >= b.n_fixed, fj = j >= b.n_fixed;
+    for (int pk = 0; pk < kTermPix; pk++) {
+        const int q = ((int)blockIdx.x * kTermPix + pk) * kTermThreads + (int)threadIdx.x;
+        if (q >= b.P) break;
         const int y = q / b.w, x = q % b.w;
         const float xb[3] = {((float)x + 0.5f - b.cx) / b.fx, ((float)y + 0.5f - b.cy) / b.fy, 1.0f};
         const float d = b.disp[(size_t)i * b.P + q];
@@ -109,41 +122,45 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
         const float a11 = -b.fy * iz, a12 = b.fy * p[1] * iz * iz;
         // dp/d(xi_j) = [d I, -[p]x], dp/d(xi_i) = [-d R_ij, R_ij [xb]x]
         float Dj[3][6], Di[3][6];
-        const float pk[3][3] = {{0.f, p[2], -p[1]}, {-p[2], 0.f, p[0]}, {p[1], -p[0], 0.f}};      // -[p]x
+        const float pk3[3][3] = {{0.f, p[2], -p[1]}, {-p[2], 0.f, p[0]}, {p[1], -p[0], 0.f}};      // -[p]x
         const float xk[3][3] = {{0.f, -xb[2], xb[1]}, {xb[2], 0.f, -xb[0]}, {-xb[1], xb[0], 0.f}}; // [xb]x
         for (int r = 0; r < 3; r++)
             for (int c = 0; c < 3; c++) {
                 Dj[r][c] = r == c ? d : 0.f;
-                Dj[r][3 + c] = pk[r][c];
+                Dj[r][3 + c] = pk3[r][c];
                 Di[r][c] = -d * Rij[3 * r + c];
                 Di[r][3 + c] = Rij[3 * r] * xk[0][c] + Rij[3 * r + 1] * xk[1][c] + Rij[3 * r + 2] * xk[2][c];
             }
         float Ji[2][6], Jj[2][6];
         for (int c = 0; c < 6; c++) {
-            Ji[0][c] = a00 * Di[0][c] + a02 * Di[2][c];
-            Ji[1][c] = a11 * Di[1][c] + a12 * Di[2][c];
-            Jj[0][c] = a00 * Dj[0][c] + a02 * Dj[2][c];
-            Jj[1][c] = a11 * Dj[1][c] + a12 * Dj[2][c];
+            Ji[0][c] = fi ? a00 * Di[0][c] + a02 * Di[2][c] : 0.f;
+            Ji[1][c] = fi ? a11 * Di[1][c] + a12 * Di[2][c] : 0.f;
+            Jj[0][c] = fj ? a00 * Dj[0][c] + a02 * Dj[2][c] : 0.f;
+            Jj[1][c] = fj ? a11 * Dj[1][c] + a12 * Dj[2][c] : 0.f;
         }
         const float Jd0 = a00 * tij[0] + a02 * tij[2], Jd1 = a11 * tij[1] + a12 * tij[2];
-        const bool fi = i >= b.n_fixed, fj = j >= b.n_fixed;
         int k = 0;
         for (int a = 0; a < 6; a++)
-            for (int c = a; c < 6; c++) v[k++] = fi ? w0 * Ji[0][a] * Ji[0][c] + w1 * Ji[1][a] * Ji[1][c] : 0.f;
+            for (int c = a; c < 6; c++) v[k++] += w0 * Ji[0][a] * Ji[0][c] + w1 * Ji[1][a] * Ji[1][c];
         for (int a = 0; a < 6; a++)
-            for (int c = 0; c < 6; c++) v[k++] = (fi && fj) ? w0 * Ji[0][a] * Jj[0][c] + w1 * Ji[1][a] * Jj[1][c] : 0.f;
+            for (int c = 0; c < 6; c++) v[k++] += w0 * Ji[0][a] * Jj[0][c] + w1 * Ji[1][a] * Jj[1][c];
         for (int a = 0; a < 6; a++)
-            for (int c = a; c < 6; c++) v[k++] = fj ? w0 * Jj[0][a] * Jj[0][c] + w1 * Jj[1][a] * Jj[1][c] : 0.f;
-        for (int a = 0; a < 6; a++) v[k++] = fi ? w0 * Ji[0][a] * r0 + w1 * Ji[1][a] * r1 : 0.f;
-        for (int a = 0; a < 6; a++) v[k++] = fj ? w0 * Jj[0][a] * r0 + w1 * Jj[1][a] * r1 : 0.f;
-        v[k] = w0 * r0 * r0 + w1 * r1 * r1;
-        float* Eo = b.Eb + ((size_t)e * b.P + q) * 12;
+            for (int c = a; c < 6; c++) v[k++] += w0 * Jj[0][a] * Jj[0][c] + w1 * Jj[1][a] * Jj[1][c];
+        for (int a = 0; a < 6; a++) v[k++] += w0 * Ji[0][a] * r0 + w1 * Ji[1][a] * r1;
+        for (int a = 0; a < 6; a++) v[k++] += w0 * Jj[0][a] * r0 + w1 * Jj[1][a] * r1;
+        v[k] += w0 * r0 * r0 + w1 * r1 * r1;
+        float rc[kRec];
         for (int a = 0; a < 6; a++) {
-            Eo[a] = fi ? w0 * Ji[0][a] * Jd0 + w1 * Ji[1][a] * Jd1 : 0.f;
-            Eo[6 + a] = fj ? w0 * Jj[0][a] * Jd0 + w1 * Jj[1][a] * Jd1 : 0.f;
+            rc[a] = w0 * Ji[0][a] * Jd0 + w1 * Ji[1][a] * Jd1;
+            rc[6 + a] = w0 * Jj[0][a] * Jd0 + w1 * Jj[1][a] * Jd1;
         }
-        atomicAdd(b.C + (size_t)i * b.P + q, w0 * Jd0 * Jd0 + w1 * Jd1 * Jd1);
-        atomicAdd(b.gd + (size_t)i * b.P + q, w0 * Jd0 * r0 + w1 * Jd1 * r1);
+        rc[12] = w0 * Jd0 * Jd0 + w1 * Jd1 * Jd1;
+        rc[13] = w0 * Jd0 * r0 + w1 * Jd1 * r1;
+        rc[14] = 0.f;
+        rc[15] = 0.f;
+        float4* ro = reinterpret_cast<float4*>(b.rec + ((size_t)e * b.P + q) * kRec);
+#pragma unroll
+        for (int m = 0; m < kRec / 4; m++) ro[m] = make_float4(rc[4 * m], rc[4 * m + 1], rc[4 * m + 2], rc[4 * m + 3]);
     }
     const float tot = block_sum_vals(v, s_part);
     const int t = threadIdx.x;
@@ -154,22 +171,22 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
                 int a = 0, c = t, rem = t;          // t -> (a, c), c >= a
                 while (rem >= 6 - a) { rem -= 6 - a; a++; }
                 c = a + rem;
-                atomicAdd(b.S + (size_t)(bi + a) * b.n + bi + c, tot);
-                if (c != a) atomicAdd(b.S + (size_t)(bi + c) * b.n + bi + a, tot);
+                atomicAdd(b.SB + (size_t)(bi + a) * b.n + bi + c, tot);
+                if (c != a) atomicAdd(b.SB + (size_t)(bi + c) * b.n + bi + a, tot);
             }
         } else if (t < 57) {
             if (i >= b.n_fixed && j >= b.n_fixed) {
                 const int a = (t - 21) / 6, c = (t - 21) % 6;
-                atomicAdd(b.S + (size_t)(bi + a) * b.n + bj + c, tot);
-                atomicAdd(b.S + (size_t)(bj + c) * b.n + bi + a, tot);
+                atomicAdd(b.SB + (size_t)(bi + a) * b.n + bj + c, tot);
+                atomicAdd(b.SB + (size_t)(bj + c) * b.n + bi + a, tot);
             }
         } else if (t < 78) {
             if (j >= b.n_fixed) {
                 int a = 0, rem = t - 57;
                 while (rem >= 6 - a) { rem -= 6 - a; a++; }
                 const int c = a + rem;
-                atomicAdd(b.S + (size_t)(bj + a) * b.n + bj + c, tot);
-                if (c != a) atomicAdd(b.S + (size_t)(bj + c) * b.n + bj + a, tot);
+                atomicAdd(b.SB + (size_t)(bj + a) * b.n + bj + c, tot);
+                if (c != a) atomicAdd(b.SB + (size_t)(bj + c) * b.n + bj + a, tot);
             }
         } else if (t < 84) {
             if (i >= b.n_fixed) atomicAdd(b.rhs + bi + (t - 78), -tot);
@@ -181,102 +198,348 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
     }
 }
 
-// Levenberg-Marquardt damping of the pose block (before the elimination, so that
-// it scales with diag(B) as in the full system).
-__global__ void k_ba_damp(BaDev b, float lambda, float eps) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < b.n) b.S[(size_t)k * b.n + k] = (1.0f + lambda) * b.S[(size_t)k * b.n + k] + eps;
+// The edges out of keyframe i (valid ones, in edge order) into s_out[0 .. kMaxOut);
+// *s_deg = their count (which may exceed kMaxOut).  Called by every thread of
+// the CTA; ends with a barrier.
+__device__ __forceinline__ void out_edges(const BaDev& b, int i, int* s_out, int* s_deg) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int deg = 0;
+        for (int e0 = 0; e0 < b.E; e0 += 32) {
+            const int e = e0 + lane;
+            const bool is = e < b.E && b.ii[e] == i && edge_ok(b, i, b.jj[e]);
+            const uint32_t m = __ballot_sync(0xffffffffu, is);
+            if (is) {
+                const int pos = deg + __popc(m & ((1u << lane) - 1u));
+                if (pos < kMaxOut) s_out[pos] = e;
+            }
+            deg += __popc(m);
+        }
+        if (lane == 0) *s_deg = deg;
+    }
+    __syncthreads();
 }
 
-// One CTA per ordered edge pair (e1, e2) with the same source keyframe.
-constexpr int kSchurThreads = 160;      // 144 products + spare lanes for the right-hand side
-constexpr int kSchurTile = 64;
+// Schur complement of the inverse-depth block.  CTA (chunk, i): the pixels
+// [chunk * kSchurChunk, ...) of source keyframe i.  Slot 0 is pose i, slot 1 + k
+// the target of the k-th edge out of i; v_p (6 per slot, m = 6 (1 + deg) rows) is
+// the column of E of pixel p's inverse depth.  Row m of the staged block holds
+// g_d,p and row m + 1 zeros, so the 2 x 2 register tiles of the upper triangle of
+// sum_p u_p [v_p; g_d,p; 0]^T (u_p = v_p / C'_p) give both E C'^-1 E^T and, in
+// their last column, E C'^-1 g_d.
+constexpr int kSchurThreads = 256;
+constexpr int kSchurPix = 32;            // pixels staged per round
+constexpr int kSchurChunk = 256;         // pixels per CTA
+constexpr int kSchurRows = kMaxSlots + 2;
+constexpr int kMaxTileRows = kSchurRows / 2;
+constexpr int kTilesPerThread = (kMaxTileRows * (kMaxTileRows + 1) / 2 + kSchurThreads - 1) / kSchurThreads;
+static_assert(kSchurPix * 8 == kSchurThreads, "one (pixel, record float pair) per thread");
 
 __global__ void __launch_bounds__(kSchurThreads) k_ba_schur(BaDev b, float lambda, float eps) {
-    const int e1 = blockIdx.x, e2 = blockIdx.y;
-    const int i = b.ii[e1];
-    if (i != b.ii[e2] || !edge_ok(b, i, b.jj[e1]) || !edge_ok(b, i, b.jj[e2])) return;
-    __shared__ float s1[kSchurTile][12], s2[kSchurTile][12], sw[kSchurTile], sg[kSchurTile];
-    const int t = threadIdx.x;
-    const int a = t / 12, c = t % 12;       // product (a, c) of E(e1) E(e2)^T for t < 144
-    float acc = 0.f, racc = 0.f;            // racc: (E(e1) C'^-1 g_d)[t - 144] for e1 == e2
-    for (int p0 = 0; p0 < b.P; p0 += kSchurTile) {
-        const int np = min(kSchurTile, b.P - p0);
-        for (int k = t; k < np * 12; k += kSchurThreads) {
-            const int pp = k / 12, cc = k % 12;
-            s1[pp][cc] = b.Eb[((size_t)e1 * b.P + p0 + pp) * 12 + cc];
-            s2[pp][cc] = b.Eb[((size_t)e2 * b.P + p0 + pp) * 12 + cc];
+    __shared__ int s_out[kMaxOut];
+    __shared__ int s_deg;
+    // rows padded by 4 floats: 2 x 2 tiles of one warp read rows at different
+    // bank offsets instead of all starting at bank 0
+    __shared__ __align__(16) float s_v[kSchurRows][kSchurPix + 4];
+    __shared__ __align__(16) float s_u[kSchurRows][kSchurPix + 4];
+    __shared__ float s_w[kSchurPix];
+    const int i = blockIdx.y, t = threadIdx.x;
+    out_edges(b, i, s_out, &s_deg);
+    const int deg = s_deg;
+    if (deg == 0) return;
+    if (deg > kMaxOut) {
+        if (t == 0 && blockIdx.x == 0) atomicCAS(b.status, 0, GS_ERR_UNSUPPORTED);
+        return;
+    }
+    const int m = 6 * (1 + deg), T = m / 2 + 1, n_tiles = T * (T + 1) / 2;
+    int ta[kTilesPerThread], tb[kTilesPerThread];
+    float acc[kTilesPerThread][4];
+#pragma unroll
+    for (int s = 0; s < kTilesPerThread; s++) {
+        int rem = t + s * kSchurThreads, a = 0;
+        if (rem < n_tiles) {
+            while (rem >= T - a) { rem -= T - a; a++; }
+            ta[s] = a; tb[s] = a + rem;
+        } else {
+            ta[s] = -1; tb[s] = -1;
         }
-        for (int k = t; k < np; k += kSchurThreads) {
-            const float Cp = (1.0f + lambda) * b.C[(size_t)i * b.P + p0 + k] + eps;
-            sw[k] = 1.0f / Cp;
-            sg[k] = b.gd[(size_t)i * b.P + p0 + k];
+        acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+    }
+    // this thread's pixel and pair of record floats: pairs 0-2 are E_i (summed over
+    // the edges into slot 0), 3-5 E_j (slot 1 + k), 6 the C and g_d shares (summed)
+    const int spx = t / 8, f8 = t % 8;
+    if (t < kSchurPix) s_v[m + 1][t] = 0.f;      // row m is rewritten every round
+    const int p_lo = blockIdx.x * kSchurChunk, p_hi = min(b.P, p_lo + kSchurChunk);
+    for (int p0 = p_lo; p0 < p_hi; p0 += kSchurPix) {
+        const bool px_ok = spx < p_hi - p0;
+        // all of the round's loads are issued before the first store
+        float2 rv[kMaxOut];
+#pragma unroll
+        for (int k = 0; k < kMaxOut; k++) {
+            const bool ok = k < deg && px_ok && f8 < 7;
+            rv[k] = ok ? *reinterpret_cast<const float2*>(b.rec + ((size_t)s_out[ok ? k : 0] * b.P + p0 + spx) * kRec +
+                                                          2 * f8)
+                       : make_float2(0.f, 0.f);
+        }
+        if (f8 < 3 || f8 == 6) {
+            float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < kMaxOut; k++) { sum.x += rv[k].x; sum.y += rv[k].y; }
+            if (f8 < 3) {
+                s_v[2 * f8][spx] = sum.x;
+                s_v[2 * f8 + 1][spx] = sum.y;
+            } else {
+                s_w[spx] = px_ok ? 1.0f / ((1.0f + lambda) * sum.x + eps) : 0.f;
+                s_v[m][spx] = sum.y;
+            }
+        } else if (f8 < 6) {
+#pragma unroll
+            for (int k = 0; k < kMaxOut; k++) {
+                if (k < deg) {
+                    s_v[6 + 6 * k + 2 * (f8 - 3)][spx] = rv[k].x;
+                    s_v[6 + 6 * k + 2 * (f8 - 3) + 1][spx] = rv[k].y;
+                }
+            }
         }
         __syncthreads();
-        if (t < 144)
-            for (int pp = 0; pp < np; pp++) acc += sw[pp] * s1[pp][a] * s2[pp][c];
-        else if (t < 156 && e1 == e2)
-            for (int pp = 0; pp < np; pp++) racc += sw[pp] * sg[pp] * s1[pp][t - 144];
+        for (int idx = t; idx < m * kSchurPix; idx += kSchurThreads) {
+            const int a = idx / kSchurPix, px = idx % kSchurPix;
+            s_u[a][px] = s_v[a][px] * s_w[px];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kTilesPerThread; s++) {
+            if (ta[s] < 0 || 2 * ta[s] >= m) continue;     // rows m, m + 1 of u are not needed
+            const float4* u0 = reinterpret_cast<const float4*>(s_u[2 * ta[s]]);
+            const float4* u1 = reinterpret_cast<const float4*>(s_u[2 * ta[s] + 1]);
+            const float4* v0 = reinterpret_cast<const float4*>(s_v[2 * tb[s]]);
+            const float4* v1 = reinterpret_cast<const float4*>(s_v[2 * tb[s] + 1]);
+#pragma unroll
+            for (int q = 0; q < kSchurPix / 4; q++) {
+                const float4 a0 = u0[q], a1 = u1[q], c0 = v0[q], c1 = v1[q];
+                acc[s][0] += a0.x * c0.x + a0.y * c0.y + a0.z * c0.z + a0.w * c0.w;
+                acc[s][1] += a0.x * c1.x + a0.y * c1.y + a0.z * c1.z + a0.w * c1.w;
+                acc[s][2] += a1.x * c0.x + a1.y * c0.y + a1.z * c0.z + a1.w * c0.w;
+                acc[s][3] += a1.x * c1.x + a1.y * c1.y + a1.z * c1.z + a1.w * c1.w;
+            }
+        }
         __syncthreads();
     }
-    const int ji = b.jj[e1], jk = b.jj[e2];
-    // slots 0..5: source pose i, 6..11: target pose of the edge
-    if (t < 144) {
-        const int pa = a < 6 ? i : ji, pc = c < 6 ? i : jk;
-        if (pa >= b.n_fixed && pc >= b.n_fixed)
-            atomicAdd(b.S + (size_t)(6 * (pa - b.n_fixed) + a % 6) * b.n + 6 * (pc - b.n_fixed) + c % 6, -acc);
-    } else if (t < 156 && e1 == e2) {
-        const int s = t - 144, pa = s < 6 ? i : ji;
-        if (pa >= b.n_fixed) atomicAdd(b.rhs + 6 * (pa - b.n_fixed) + s % 6, racc);
+    auto slot_pose = [&](int slot) { return slot == 0 ? i : b.jj[s_out[slot - 1]]; };
+#pragma unroll
+    for (int s = 0; s < kTilesPerThread; s++) {
+        if (ta[s] < 0 || 2 * ta[s] >= m) continue;
+#pragma unroll
+        for (int xy = 0; xy < 4; xy++) {
+            const int a = 2 * ta[s] + (xy >> 1), c = 2 * tb[s] + (xy & 1);
+            if (a > c || c == m + 1) continue;         // the lower element of a diagonal tile; the zero row
+            const int pa = slot_pose(a / 6);
+            if (pa < b.n_fixed) continue;
+            const int ra = 6 * (pa - b.n_fixed) + a % 6;
+            if (c == m) {                               // E C'^-1 g_d
+                atomicAdd(b.rhs + ra, acc[s][xy]);
+                continue;
+            }
+            const int pc = slot_pose(c / 6);
+            if (pc < b.n_fixed) continue;
+            const int rc = 6 * (pc - b.n_fixed) + c % 6;
+            atomicAdd(b.SS + (size_t)ra * b.n + rc, -acc[s][xy]);
+            if (a != c) atomicAdd(b.SS + (size_t)rc * b.n + ra, -acc[s][xy]);
+        }
     }
 }
 
-// Dense Cholesky solve S x = rhs of the reduced system, one CTA, in shared memory.
-constexpr int kSolveThreads = 256;
+// Solve of the reduced system (B damped - E C'^-1 E^T) dxi = rhs, one CTA, in
+// shared memory: LU factorisation without pivoting (the matrix is symmetric
+// positive definite) of the augmented n x (n + 1) matrix [S | rhs], blocked by
+// 6 x 6 pose panels with two barriers per panel, then back substitution panel by
+// panel.  Per panel kb:
+//   (A) every thread of the panel phase factors the 6 x 6 diagonal block in its
+//       registers (the same operations in every thread, so no barrier); column
+//       threads form U12 = L11^-1 A12 (the right-hand side column included), row
+//       threads L21 = A21 U11^-1; thread 0 stores the factored block;
+//   (B) A22 -= L21 U12.
+constexpr int kSolveThreads = 512;
+constexpr int kNb = 6;
 
-__global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b) {
+// LU of a 6 x 6 block in registers: unit-lower multipliers below the diagonal,
+// U on and above it; inv[k] = 1 / U_kk.
+__device__ __forceinline__ void lu6(float (&a)[kNb][kNb], float (&inv)[kNb]) {
+#pragma unroll
+    for (int k = 0; k < kNb; k++) {
+        inv[k] = __frcp_rn(fmaxf(a[k][k], 1e-30f));
+#pragma unroll
+        for (int r = k + 1; r < kNb; r++) {
+            const float f = a[r][k] * inv[k];
+            a[r][k] = f;
+#pragma unroll
+            for (int c = k + 1; c < kNb; c++) a[r][c] -= f * a[k][c];
+        }
+    }
+}
+
+// CPL: columns of a lane in (B), ceil((n + 1 - 6) / 32), at most 6 (n <= 186)
+template <int CPL>
+__global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambda, float eps) {
     extern __shared__ float sm[];
-    const int n = b.n, t = threadIdx.x;
-    float* A = sm;                       // [n][n]
-    float* x = sm + n * n;               // [n]
-    for (int k = t; k < n * n; k += kSolveThreads) A[k] = b.S[k];
-    for (int k = t; k < n; k += kSolveThreads) x[k] = b.rhs[k];
-    __syncthreads();
+    const int n = b.n, ld = n + 1, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float* A = sm;                       // [n][n + 1]
+    float* x = sm + (size_t)n * ld;      // [n]
     __shared__ int s_bad;
+    __shared__ float s_inv[6 * 31];      // reciprocals of the pivots
+    // eight loads of each matrix in flight per thread before the stores
+    for (int k0 = 0; k0 < n * n; k0 += 8 * kSolveThreads) {
+        float vb[8], vs[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = k0 + u * kSolveThreads + t;
+            vb[u] = k < n * n ? b.SB[k] : 0.f;
+            vs[u] = k < n * n ? b.SS[k] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = k0 + u * kSolveThreads + t;
+            if (k < n * n) {
+                const int r = k / n, c = k - r * n;
+                A[(size_t)r * ld + c] = vs[u] + (r == c ? (1.0f + lambda) * vb[u] + eps : vb[u]);
+            }
+        }
+    }
+    for (int k = t; k < n; k += kSolveThreads) A[(size_t)k * ld + n] = b.rhs[k];
     if (t == 0) s_bad = 0;
     __syncthreads();
-    // right-looking Cholesky, lower triangle
-    for (int k = 0; k < n; k++) {
+    for (int kb = 0; kb < n; kb += kNb) {
+        const int k1 = kb + kNb;                  // first row / column after the panel
+        const int ncols = ld - k1, nrows = n - k1;
+        // (A) the diagonal block, U12 and L21 (thread 0 is always a column thread)
+        float a[kNb][kNb], inv[kNb];
+        if (t < ncols + nrows) {
+#pragma unroll
+            for (int r = 0; r < kNb; r++)
+#pragma unroll
+                for (int c = 0; c < kNb; c++) a[r][c] = A[(size_t)(kb + r) * ld + kb + c];
+            lu6(a, inv);
+            if (t < ncols) {
+                const int c = k1 + t;
+                float u[kNb];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) u[m] = A[(size_t)(kb + m) * ld + c];
+#pragma unroll
+                for (int m = 1; m < kNb; m++)
+#pragma unroll
+                    for (int q = 0; q < m; q++) u[m] -= a[m][q] * u[q];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) A[(size_t)(kb + m) * ld + c] = u[m];
+            } else {
+                const int r = k1 + (t - ncols);
+                float l[kNb];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) l[m] = A[(size_t)r * ld + kb + m];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) {
+#pragma unroll
+                    for (int q = 0; q < m; q++) l[m] -= l[q] * a[q][m];
+                    l[m] *= inv[m];
+                }
+#pragma unroll
+                for (int m = 0; m < kNb; m++) A[(size_t)r * ld + kb + m] = l[m];
+            }
+            if (t == 0) {
+#pragma unroll
+                for (int m = 0; m < kNb; m++) {
+                    if (!(a[m][m] > 0.f)) s_bad = 1;
+                    s_inv[kb + m] = inv[m];
+                }
+            }
+        }
+        __syncthreads();
+        // the factored diagonal block (read by every thread of (A) before the barrier;
+        // not read by (B))
         if (t == 0) {
-            const float dkk = A[k * n + k];
-            if (!(dkk > 0.f)) s_bad = 1;
-            A[k * n + k] = sqrtf(fmaxf(dkk, 1e-30f));
+#pragma unroll
+            for (int r = 0; r < kNb; r++)
+#pragma unroll
+                for (int c = 0; c < kNb; c++) A[(size_t)(kb + r) * ld + kb + c] = a[r][c];
+        }
+        // (B) trailing update, U12 of this lane's columns held in registers, two rows at a time
+        if (nrows > 0) {
+            float u[CPL][kNb];
+#pragma unroll
+            for (int j = 0; j < CPL; j++) {
+                const int c = k1 + lane + 32 * j;
+#pragma unroll
+                for (int m = 0; m < kNb; m++) u[j][m] = c < ld ? A[(size_t)(kb + m) * ld + c] : 0.f;
+            }
+            constexpr int kW = kSolveThreads / 32;
+            for (int r0 = k1 + warp; r0 < n; r0 += 2 * kW) {
+                const int r1 = r0 + kW;
+                const bool has1 = r1 < n;
+                float l0[kNb], l1[kNb];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) {
+                    l0[m] = A[(size_t)r0 * ld + kb + m];
+                    l1[m] = has1 ? A[(size_t)r1 * ld + kb + m] : 0.f;
+                }
+                float v0[CPL], v1[CPL];
+#pragma unroll
+                for (int j = 0; j < CPL; j++) {
+                    const int c = k1 + lane + 32 * j;
+                    v0[j] = c < ld ? A[(size_t)r0 * ld + c] : 0.f;
+                    v1[j] = (c < ld && has1) ? A[(size_t)r1 * ld + c] : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; j++) {
+#pragma unroll
+                    for (int m = 0; m < kNb; m++) {
+                        v0[j] -= l0[m] * u[j][m];
+                        v1[j] -= l1[m] * u[j][m];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; j++) {
+                    const int c = k1 + lane + 32 * j;
+                    if (c < ld) {
+                        A[(size_t)r0 * ld + c] = v0[j];
+                        if (has1) A[(size_t)r1 * ld + c] = v1[j];
+                    }
+                }
+            }
         }
         __syncthreads();
-        const float lkk = A[k * n + k];
-        for (int r = k + 1 + t; r < n; r += kSolveThreads) A[r * n + k] /= lkk;
-        __syncthreads();
-        for (int idx = t; idx < (n - k - 1) * (n - k - 1); idx += kSolveThreads) {
-            const int r = k + 1 + idx / (n - k - 1), c = k + 1 + idx % (n - k - 1);
-            if (c <= r) A[r * n + c] -= A[r * n + k] * A[c * n + k];
+    }
+    if (warp == 0) {
+        // U x = y (y in column n) panel by panel from the last: lane 0 solves the
+        // 6 x 6 triangle, then every lane removes the panel's x from the rows above
+        for (int k = lane; k < n; k += 32) x[k] = A[(size_t)k * ld + n];
+        __syncwarp();
+        for (int kb = n - kNb; kb >= 0; kb -= kNb) {
+            if (lane == 0) {
+                float xs[kNb];
+#pragma unroll
+                for (int m = kNb - 1; m >= 0; m--) {
+                    float v = x[kb + m];
+#pragma unroll
+                    for (int q = m + 1; q < kNb; q++) v -= A[(size_t)(kb + m) * ld + kb + q] * xs[q];
+                    xs[m] = v * s_inv[kb + m];
+                }
+#pragma unroll
+                for (int m = 0; m < kNb; m++) x[kb + m] = xs[m];
+            }
+            __syncwarp();
+            float xs[kNb];
+#pragma unroll
+            for (int m = 0; m < kNb; m++) xs[m] = x[kb + m];
+            for (int r = lane; r < kb; r += 32) {
+                float v = x[r];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) v -= A[(size_t)r * ld + kb + m] * xs[m];
+                x[r] = v;
+            }
+            __syncwarp();
         }
-        __syncthreads();
+        for (int k = lane; k < n; k += 32) b.dxi[k] = x[k];
+        if (lane == 0 && s_bad) atomicCAS(b.status, 0, GS_ERR_NUMERIC);
     }
-    // forward (L y = rhs) and backward (L^T x = y) substitution, one thread per row step
-    for (int k = 0; k < n; k++) {
-        if (t == 0) x[k] /= A[k * n + k];
-        __syncthreads();
-        for (int r = k + 1 + t; r < n; r += kSolveThreads) x[r] -= A[r * n + k] * x[k];
-        __syncthreads();
-    }
-    for (int k = n - 1; k >= 0; k--) {
-        if (t == 0) x[k] /= A[k * n + k];
-        __syncthreads();
-        for (int r = t; r < k; r += kSolveThreads) x[r] -= A[k * n + r] * x[k];
-        __syncthreads();
-    }
-    for (int k = t; k < n; k += kSolveThreads) b.dxi[k] = x[k];
-    if (t == 0 && s_bad) atomicCAS(b.status, 0, GS_ERR_NUMERIC);
 }
 
 __device__ __forceinline__ float pose_dxi(const BaDev& b, int k, int c) {
@@ -284,24 +547,41 @@ __device__ __forceinline__ float pose_dxi(const BaDev& b, int k, int c) {
 }
 
 // dd_p = C'_p^-1 (-g_d,p - sum_e E(e, p) . [dxi_i, dxi_j]) for every pixel of every
-// keyframe; then the poses T_k <- Exp(dxi_k) T_k (rotation exact, translation first order).
-__global__ void k_ba_update(BaDev b, float lambda, float eps) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
-    if (q < b.P) {
-        const float Cp = (1.0f + lambda) * b.C[(size_t)i * b.P + q] + eps;
-        float s = -b.gd[(size_t)i * b.P + q];
-        for (int e = 0; e < b.E; e++) {
-            if (b.ii[e] != i) continue;
-            const int j = b.jj[e];
-            if (j < 0 || j >= b.K) continue;
-            const float* Eo = b.Eb + ((size_t)e * b.P + q) * 12;
-            for (int c = 0; c < 6; c++) s -= Eo[c] * pose_dxi(b, i, c) + Eo[6 + c] * pose_dxi(b, j, c);
+// source keyframe; then the poses T_k <- Exp(dxi_k) T_k (rotation exact,
+// translation first order).
+constexpr int kUpdateThreads = 256;
+
+__global__ void __launch_bounds__(kUpdateThreads) k_ba_update(BaDev b, float lambda, float eps) {
+    __shared__ int s_out[kMaxOut];
+    __shared__ int s_deg;
+    __shared__ float s_dx[1 + kMaxOut][6];
+    const int i = blockIdx.y, t = threadIdx.x;
+    out_edges(b, i, s_out, &s_deg);
+    const int deg = s_deg;
+    if (deg <= kMaxOut && deg > 0) {
+        if (t < 6 * (1 + deg)) {
+            const int slot = t / 6, c = t % 6;
+            s_dx[slot][c] = pose_dxi(b, slot == 0 ? i : b.jj[s_out[slot - 1]], c);
         }
-        // a keyframe that is no edge's source keeps its inverse depths (C = 0 there)
-        if (b.C[(size_t)i * b.P + q] > 0.f) b.disp[(size_t)i * b.P + q] += s / Cp;
+        __syncthreads();
+        const int q = blockIdx.x * kUpdateThreads + t;
+        if (q < b.P) {
+            float C = 0.f, sacc = 0.f;
+            for (int k = 0; k < deg; k++) {
+                const float4* ro = reinterpret_cast<const float4*>(b.rec + ((size_t)s_out[k] * b.P + q) * kRec);
+                const float4 r0 = ro[0], r1 = ro[1], r2 = ro[2], r3 = ro[3];
+                C += r3.x;
+                sacc -= r3.y;
+                sacc -= r0.x * s_dx[0][0] + r0.y * s_dx[0][1] + r0.z * s_dx[0][2] + r0.w * s_dx[0][3] +
+                        r1.x * s_dx[0][4] + r1.y * s_dx[0][5];
+                sacc -= r1.z * s_dx[k + 1][0] + r1.w * s_dx[k + 1][1] + r2.x * s_dx[k + 1][2] +
+                        r2.y * s_dx[k + 1][3] + r2.z * s_dx[k + 1][4] + r2.w * s_dx[k + 1][5];
+            }
+            // an inverse depth no residual constrains (all weights 0) keeps its value
+            if (C > 0.f) b.disp[(size_t)i * b.P + q] += sacc / ((1.0f + lambda) * C + eps);
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && i >= b.n_fixed) {
+    if (blockIdx.x == 0 && t == 0 && i >= b.n_fixed) {
         float rho[3], phi[3];
         for (int c = 0; c < 3; c++) { rho[c] = pose_dxi(b, i, c); phi[c] = pose_dxi(b, i, 3 + c); }
         const float th = sqrtf(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
@@ -330,9 +610,9 @@ __global__ void k_ba_update(BaDev b, float lambda, float eps) {
 }  // namespace
 
 size_t ba_workspace(int K, int E, int P, int n) {
-    return align_up(sizeof(float) * (size_t)E * P * 12, 256) + 2 * align_up(sizeof(float) * (size_t)K * P, 256) +
-           align_up(sizeof(float) * (size_t)n * n, 256) + 2 * align_up(sizeof(float) * (size_t)(n + 1), 256) +
-           align_up(sizeof(float), 256);
+    (void)K;
+    return align_up(sizeof(float) * (size_t)E * P * kRec, 256) + 2 * align_up(sizeof(float) * (size_t)n * n, 256) +
+           2 * align_up(sizeof(float) * (size_t)(n + 1), 256);
 }
 
 cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, float* cost, void* ws,
@@ -344,32 +624,45 @@ cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, flo
     b.n_fixed = pr.n_fixed; b.n = 6 * (pr.n_keyframes - pr.n_fixed);
     b.fx = pr.fx; b.fy = pr.fy; b.cx = pr.cx; b.cy = pr.cy;
     char* p = static_cast<char*>(ws);
-    b.Eb = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.E * b.P * 12, 256);
-    b.C = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.K * b.P, 256);
-    b.gd = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.K * b.P, 256);
-    b.S = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.n * b.n, 256);
+    b.rec = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.E * b.P * kRec, 256);
+    b.SB = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.n * b.n, 256);
+    b.SS = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.n * b.n, 256);
     b.rhs = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)(b.n + 1), 256);
-    b.dxi = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)(b.n + 1), 256);
+    b.dxi = reinterpret_cast<float*>(p);
     b.cost = cost;
     b.status = pr.status;
-    // zero the accumulators (C, g_d, S, rhs are contiguous after Eb)
-    const size_t zero_bytes = 2 * align_up(sizeof(float) * (size_t)b.K * b.P, 256) +
-                              align_up(sizeof(float) * (size_t)b.n * b.n, 256) +
+    // zero the accumulators (SB, SS, rhs are contiguous after the records)
+    const size_t zero_bytes = 2 * align_up(sizeof(float) * (size_t)b.n * b.n, 256) +
                               align_up(sizeof(float) * (size_t)(b.n + 1), 256);
-    cudaError_t e = cudaMemsetAsync(b.C, 0, zero_bytes, s);
+    cudaError_t e = cudaMemsetAsync(b.SB, 0, zero_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cost, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
     if (b.E > 0) {
-        k_ba_terms<<<dim3((unsigned)ceil_div(b.P, kTermThreads), (unsigned)b.E), kTermThreads, 0, s>>>(b);
+        k_ba_terms<<<dim3((unsigned)ceil_div(b.P, kTermThreads * kTermPix), (unsigned)b.E), kTermThreads, 0, s>>>(b);
         if (b.n > 0) {
-            k_ba_damp<<<(unsigned)ceil_div(b.n, 256), 256, 0, s>>>(b, lambda, eps);
-            k_ba_schur<<<dim3((unsigned)b.E, (unsigned)b.E), kSchurThreads, 0, s>>>(b, lambda, eps);
-            const size_t smem = sizeof(float) * ((size_t)b.n * b.n + b.n);
-            e = cudaFuncSetAttribute(k_ba_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            k_ba_solve<<<1, kSolveThreads, smem, s>>>(b);
+            k_ba_schur<<<dim3((unsigned)ceil_div(b.P, kSchurChunk), (unsigned)b.K), kSchurThreads, 0, s>>>(b, lambda,
+                                                                                                     eps);
+            const size_t smem = sizeof(float) * ((size_t)b.n * (b.n + 1) + b.n);
+            const int cpl = (int)ceil_div((int64_t)b.n + 1 - kNb, 32);
+            switch (cpl) {
+#define GS_SOLVE(C)                                                                                      \
+    case C:                                                                                              \
+        e = cudaFuncSetAttribute(k_ba_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                  \
+        k_ba_solve<C><<<1, kSolveThreads, smem, s>>>(b, lambda, eps);                                    \
+        break;
+                GS_SOLVE(1)
+                GS_SOLVE(2)
+                GS_SOLVE(3)
+                GS_SOLVE(4)
+                GS_SOLVE(5)
+                GS_SOLVE(6)
+#undef GS_SOLVE
+                default: return cudaErrorInvalidValue;
+            }
         }
-        k_ba_update<<<dim3((unsigned)ceil_div(b.P, 256), (unsigned)b.K), 256, 0, s>>>(b, lambda, eps);
+        k_ba_update<<<dim3((unsigned)ceil_div(b.P, kUpdateThreads), (unsigned)b.K), kUpdateThreads, 0, s>>>(b, lambda,
+                                                                                                      eps);
     }
     return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ _lib = None
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA", 4: "GS_ERR_TIMEOUT",
           5: "GS_ERR_NUMERIC", 6: "GS_ERR_UNSUPPORTED"}
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA = 0, 1, 2, 3
+GS_ERR_TIMEOUT, GS_ERR_NUMERIC, GS_ERR_UNSUPPORTED = 4, 5, 6
 
 
 class GsError(RuntimeError):

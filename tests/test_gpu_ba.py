@@ -87,3 +87,20 @@ def test_bad_edge_is_reported():
                      np.concatenate([wts, wts[:1]]), 1)
     G.gs_ba_step(win)
     assert G.gs_read_device_status(win.status) == G.GS_ERR_INVALID_ARG
+
+
+def test_too_many_edges_out_of_one_keyframe_is_reported():
+    # 16 edges leave keyframe 0: above the 15 the Schur kernel stages per pixel
+    R, t, disp, intr, _, _ = synth.ba_scene(12, K=17, h=4, w=4)
+    edges = [(0, j) for j in range(1, 17)] + [(1, 0)]
+    targets = _exact_targets(R, t, disp, intr, edges)
+    wts = np.ones((len(edges), 4, 4, 2))
+    win = G.BAWindow(R, t, disp, intr, edges, targets, wts, 1)
+    G.gs_ba_step(win)
+    assert G.gs_read_device_status(win.status) == G.GS_ERR_UNSUPPORTED
+    # 15 edges out of keyframe 0 are within the limit
+    edges = [(0, j) for j in range(1, 16)] + [(1, 0)]
+    targets = _exact_targets(R, t, disp, intr, edges)
+    win = G.BAWindow(R, t, disp, intr, edges, targets, np.ones((len(edges), 4, 4, 2)), 1)
+    G.gs_ba_step(win)
+    assert G.gs_read_device_status(win.status) == G.GS_OK
