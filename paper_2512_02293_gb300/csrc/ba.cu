@@ -73,25 +73,31 @@ __device__ __forceinline__ void rel_pose(const BaDev& b, int i, int j, float* Ri
         tij[r] = Pj[9 + r] - (Rij[3 * r] * Pi[9] + Rij[3 * r + 1] * Pi[10] + Rij[3 * r + 2] * Pi[11]);
 }
 
-// sum over the CTA of kTermVals values per thread; thread t < kTermVals gets total t
-__device__ __forceinline__ float block_sum_vals(float (&v)[kTermVals], float* s_part) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// sum over the CTA of kTermVals values per thread; thread t < kTermVals gets
+// total t.  Every thread writes its values as a column of s_all; thread t then
+// sums row t (rows padded to an odd length: both passes are free of bank
+// conflicts).
+__device__ __forceinline__ float block_sum_vals(const float (&v)[kTermVals], float (*s_all)[kTermThreads + 1]) {
 #pragma unroll
-    for (int k = 0; k < kTermVals; k++) {
-        float x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) s_part[warp * kTermVals + k] = x;
-    }
+    for (int k = 0; k < kTermVals; k++) s_all[k][threadIdx.x] = v[k];
     __syncthreads();
     float tot = 0.f;
-    if ((int)threadIdx.x < kTermVals)
-        for (int w = 0; w < kTermThreads / 32; w++) tot += s_part[w * kTermVals + threadIdx.x];
+    if ((int)threadIdx.x < kTermVals) {
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < kTermThreads; j += 4) {
+            p0 += s_all[threadIdx.x][j];
+            p1 += s_all[threadIdx.x][j + 1];
+            p2 += s_all[threadIdx.x][j + 2];
+            p3 += s_all[threadIdx.x][j + 3];
+        }
+        tot = (p0 + p1) + (p2 + p3);
+    }
     return tot;
 }
 
 __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
-    __shared__ float s_part[(kTermThreads / 32) * kTermVals];
+    __shared__ float s_all[kTermVals][kTermThreads + 1];
     const int e = blockIdx.y;
     const int i = b.ii[e], j = b.jj[e];
     float v[kTermVals];
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
 #pragma unroll
         for (int m = 0; m < kRec / 4; m++) ro[m] = make_float4(rc[4 * m], rc[4 * m + 1], rc[4 * m + 2], rc[4 * m + 3]);
     }
-    const float tot = block_sum_vals(v, s_part);
+    const float tot = block_sum_vals(v, s_all);
     const int t = threadIdx.x;
     if (t < kTermVals) {
         const int bi = 6 * (i - b.n_fixed), bj = 6 * (j - b.n_fixed);
@@ -566,16 +572,30 @@ __global__ void __launch_bounds__(kUpdateThreads) k_ba_update(BaDev b, float lam
         __syncthreads();
         const int q = blockIdx.x * kUpdateThreads + t;
         if (q < b.P) {
+            // the records of four edges in flight at a time
             float C = 0.f, sacc = 0.f;
-            for (int k = 0; k < deg; k++) {
-                const float4* ro = reinterpret_cast<const float4*>(b.rec + ((size_t)s_out[k] * b.P + q) * kRec);
-                const float4 r0 = ro[0], r1 = ro[1], r2 = ro[2], r3 = ro[3];
-                C += r3.x;
-                sacc -= r3.y;
-                sacc -= r0.x * s_dx[0][0] + r0.y * s_dx[0][1] + r0.z * s_dx[0][2] + r0.w * s_dx[0][3] +
-                        r1.x * s_dx[0][4] + r1.y * s_dx[0][5];
-                sacc -= r1.z * s_dx[k + 1][0] + r1.w * s_dx[k + 1][1] + r2.x * s_dx[k + 1][2] +
-                        r2.y * s_dx[k + 1][3] + r2.z * s_dx[k + 1][4] + r2.w * s_dx[k + 1][5];
+            for (int k0 = 0; k0 < deg; k0 += 4) {
+                float4 rr[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u;
+                    const float4* ro =
+                        reinterpret_cast<const float4*>(b.rec + ((size_t)s_out[k < deg ? k : 0] * b.P + q) * kRec);
+#pragma unroll
+                    for (int h = 0; h < 4; h++) rr[u][h] = k < deg ? ro[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u;
+                    if (k >= deg) break;
+                    const float4 r0 = rr[u][0], r1 = rr[u][1], r2 = rr[u][2], r3 = rr[u][3];
+                    C += r3.x;
+                    sacc -= r3.y;
+                    sacc -= r0.x * s_dx[0][0] + r0.y * s_dx[0][1] + r0.z * s_dx[0][2] + r0.w * s_dx[0][3] +
+                            r1.x * s_dx[0][4] + r1.y * s_dx[0][5];
+                    sacc -= r1.z * s_dx[k + 1][0] + r1.w * s_dx[k + 1][1] + r2.x * s_dx[k + 1][2] +
+                            r2.y * s_dx[k + 1][3] + r2.z * s_dx[k + 1][4] + r2.w * s_dx[k + 1][5];
+                }
             }
             // an inverse depth no residual constrains (all weights 0) keeps its value
             if (C > 0.f) b.disp[(size_t)i * b.P + q] += sacc / ((1.0f + lambda) * C + eps);

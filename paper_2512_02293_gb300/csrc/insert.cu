@@ -36,38 +36,45 @@ __device__ __forceinline__ bool sample_pixel(const int32_t* uv, int64_t k, const
     return *u >= 0 && *u < c.W && *v >= 0 && *v < c.H;
 }
 
-__global__ void k_extract_patches(const float* __restrict__ color, const float* __restrict__ depth, Cam c,
-                                  const int32_t* __restrict__ uv, int64_t n, uint16_t* __restrict__ X,
-                                  int* status) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// One warp per sample: lane l forms window pixels l and l + 32 (8 bytes each: the
+// BF16 R, G, B and depth slot), so a row is written as contiguous 8-byte pieces;
+// pieces 49 .. 51 are the bias input and the padding.
+constexpr int kPatchWarps = 8;
+
+__global__ void __launch_bounds__(kPatchWarps * 32) k_extract_patches(
+        const float* __restrict__ color, const float* __restrict__ depth, Cam c, const int32_t* __restrict__ uv,
+        int64_t n, uint16_t* __restrict__ X, int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x * (int64_t)kPatchWarps + (threadIdx.x >> 5);
     if (k >= n) return;
+    uint2* row = reinterpret_cast<uint2*>(X + k * GS_MLP_IN_STRIDE);
+    constexpr int kPieces = GS_MLP_IN_STRIDE / 4;     // 52
     int u, v;
-    uint16_t* row = X + k * GS_MLP_IN_STRIDE;
     if (!sample_pixel(uv, k, c, &u, &v)) {
-        if (status) atomicCAS(status, 0, GS_ERR_INVALID_ARG);
-        for (int i = 0; i < GS_MLP_IN_STRIDE; i++) row[i] = 0;
+        if (status && lane == 0) atomicCAS(status, 0, GS_ERR_INVALID_ARG);
+        for (int q = lane; q < kPieces; q += 32) row[q] = make_uint2(0u, 0u);
         return;
     }
     const int HW = c.W * c.H;
     const float fbar = 0.5f * (c.fx + c.fy);
     const float dc = depth[v * c.W + u];
     const float dscale = dc > 0.f ? fbar / (7.f * dc) : 0.f;
-    uint32_t packed[GS_MLP_IN_STRIDE / 2];
-    for (int p = 0; p < 49; p++) {
-        const int x = min(max(u + p % 7 - 3, 0), c.W - 1), y = min(max(v + p / 7 - 3, 0), c.H - 1);
-        const int pix = y * c.W + x;
-        const float d = depth[pix];
-        float dz;
-        if (p == 24) dz = dc > 0.f ? logf(dc) : 0.f;
-        else dz = (d > 0.f && dc > 0.f) ? (d - dc) * dscale : 0.f;
-        packed[2 * p] = (uint32_t)f2bf16(color[pix]) | ((uint32_t)f2bf16(color[HW + pix]) << 16);
-        packed[2 * p + 1] = (uint32_t)f2bf16(color[2 * HW + pix]) | ((uint32_t)f2bf16(dz) << 16);
+    for (int q = lane; q < kPieces; q += 32) {
+        uint2 piece;
+        if (q < 49) {
+            const int x = min(max(u + q % 7 - 3, 0), c.W - 1), y = min(max(v + q / 7 - 3, 0), c.H - 1);
+            const int pix = y * c.W + x;
+            const float d = depth[pix];
+            float dz;
+            if (q == 24) dz = dc > 0.f ? logf(dc) : 0.f;
+            else dz = (d > 0.f && dc > 0.f) ? (d - dc) * dscale : 0.f;
+            piece.x = (uint32_t)f2bf16(color[pix]) | ((uint32_t)f2bf16(color[HW + pix]) << 16);
+            piece.y = (uint32_t)f2bf16(color[2 * HW + pix]) | ((uint32_t)f2bf16(dz) << 16);
+        } else {
+            piece = make_uint2(q == 49 ? 0x3F80u : 0u, 0u);   // column 196: the bias input 1; 197 .. 207: 0
+        }
+        row[q] = piece;
     }
-    packed[98] = 0x3F80u;     // column 196: the bias input 1, 197..207: 0
-    for (int i = 99; i < GS_MLP_IN_STRIDE / 2; i++) packed[i] = 0u;
-    uint4* out = reinterpret_cast<uint4*>(row);
-    for (int i = 0; i < GS_MLP_IN_STRIDE / 8; i++)
-        out[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
 }
 
 __global__ void k_insert(const float* __restrict__ color, const float* __restrict__ depth, Cam c,
@@ -82,8 +89,8 @@ __global__ void k_insert(const float* __restrict__ color, const float* __restric
     if (!inside && status) atomicCAS(status, 0, GS_ERR_INVALID_ARG);
     const float d = inside ? depth[v * c.W + u] : 0.f;
     float* col = dst.color + i * ncol;
-    for (int j = 0; j < ncol; j++) col[j] = 0.f;
     if (!(d > 0.f)) {
+        for (int j = 0; j < ncol; j++) col[j] = 0.f;
         // no depth: an inert Gaussian (transparent, tiny) at the camera centre
         for (int a = 0; a < 3; a++) { dst.mean[3 * i + a] = c.t[a]; dst.log_scale[3 * i + a] = -10.f; }
         dst.quat[4 * i] = 1.f; dst.quat[4 * i + 1] = dst.quat[4 * i + 2] = dst.quat[4 * i + 3] = 0.f;
@@ -97,6 +104,7 @@ __global__ void k_insert(const float* __restrict__ color, const float* __restric
     const int HW = c.W * c.H, pix = v * c.W + u;
     const float rgb[3] = {color[pix], color[HW + pix], color[2 * HW + pix]};
     for (int a = 0; a < 3; a++) col[a] = sh_degree == 3 ? (rgb[a] - 0.5f) / kSH0 : rgb[a];
+    for (int j = 3; j < ncol; j++) col[j] = 0.f;
     float q[4] = {1.f, 0.f, 0.f, 0.f}, ls[3] = {s0, s0, s0}, logit = 0.f;
     if (Y != nullptr) {
         const float* y = Y + k * GS_MLP_OUT;
@@ -128,7 +136,8 @@ Cam to_cam(const gs_camera& g) {
 cudaError_t launch_extract_patches(const float* color, const float* depth, const gs_camera& cam,
                                    const int32_t* uv, int64_t n, uint16_t* X, int* status, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_extract_patches<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(color, depth, to_cam(cam), uv, n, X, status);
+    k_extract_patches<<<(unsigned)((n + kPatchWarps - 1) / kPatchWarps), kPatchWarps * 32, 0, s>>>(
+        color, depth, to_cam(cam), uv, n, X, status);
     return cudaGetLastError();
 }
 
