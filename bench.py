@@ -493,7 +493,7 @@ def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
     """One Levenberg-Marquardt step of the dense visual bundle adjustment
     (Eq. 2 / Eq. 4) on a 16-keyframe window at the tracker's 1/8 resolution of
     640x480 (60 x 80 inverse depths per keyframe), every pair of keyframes at
-    most 3 apart as an edge; CUDA-event time of gs_ba_step."""
+    most 3 apart as an edge; device time of gs_ba_step by graph replay."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     from paper_2512_02293_gb300 import synth
@@ -502,15 +502,7 @@ def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
     targets = rng.normal(0.0, 0.5, (len(edges), h, w, 2)) + np.stack(np.meshgrid(np.arange(w) + 0.5,
                                                                              np.arange(h) + 0.5), -1)
     win = G.BAWindow(R, t, disp, intr, edges, targets, wts, 2, device)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for _ in range(3):
-        G.gs_ba_step(win, 1e-3, 1e-3)
-    ms = []
-    for _ in range(steps):
-        ev[0].record(); G.gs_ba_step(win, 1e-3, 1e-3); ev[1].record()
-        torch.cuda.synchronize()
-        ms.append(ev[0].elapsed_time(ev[1]))
-    m = statistics.median(ms)
+    m = graph_time_ms(lambda: G.gs_ba_step(win, 1e-3, 1e-3), steps=steps)
     n_res = len(edges) * h * w
     # algorithmic bytes: every residual's target and weight pair read once, every
     # inverse depth read and written once (the poses are negligible)
@@ -527,6 +519,28 @@ def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
                          "peak_basis": f"{kind} hbm_gbs",
                          "note": "four dependent launches and a one-CTA solve of the 84 x 84 reduced system: "
                                  "the step is latency bound at this size"}}
+
+
+def graph_time_ms(fn, reps=10, steps=10):
+    """Median device time of one call of fn: the call is captured reps times into
+    a CUDA graph and the replays are timed with CUDA events, so that the host's
+    argument marshalling of a short C-ABI call is not counted."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        for _ in range(reps):
+            fn()
+    graph.replay()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = []
+    for _ in range(steps):
+        ev[0].record(); graph.replay(); ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]) / reps)
+    return statistics.median(ms)
 
 
 def insertion_run(device, steps=20):
@@ -553,26 +567,8 @@ def insertion_run(device, steps=20):
                                                                          cfg.stride, g, 0),
     }
     # each call is tens of microseconds of GPU work, less than the host's ctypes
-    # marshalling, so it is captured ten times into a CUDA graph and the replays
-    # are timed
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    out = {}
-    reps = 10
-    for name, fn in calls.items():
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            for _ in range(reps):
-                fn()
-        graph.replay()
-        ms = []
-        for _ in range(steps):
-            ev[0].record(); graph.replay(); ev[1].record()
-            torch.cuda.synchronize()
-            ms.append(ev[0].elapsed_time(ev[1]) / reps)
-        out[name] = round(statistics.median(ms), 4)
+    # marshalling: timed by graph replay
+    out = {name: round(graph_time_ms(fn, steps=steps), 4) for name, fn in calls.items()}
     peaks, kind = _peaks()
     image_bytes = cam.n_pixels * 16                       # RGB + depth, read once
     ext_bytes = n * INSERT_PATCH_BYTES + image_bytes
@@ -599,8 +595,8 @@ LOOP_CLOSURE_BYTES = 12 + 16 + 12 + 4 + 12 + 16 + 12   # read mean, quat, log-sc
 def loop_closure_run(device, n=4_000_000, K=1000):
     """The loop-closure Gaussian update (Eq. 7, Eq. 8) over a 4M-Gaussian map
     anchored to 1000 keyframes, 4000 consecutive Gaussians per keyframe as
-    insertion lays them out (336 MB moved, more than L2), timed with CUDA
-    events; the roofline is HBM."""
+    insertion lays them out (336 MB moved, more than L2), device time by graph
+    replay; the roofline is HBM."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     rng = np.random.default_rng(11)
@@ -614,15 +610,7 @@ def loop_closure_run(device, n=4_000_000, K=1000):
                                           rng.uniform(-3, 3, (K, 3))], 1))
     pb, pa = pose(1), pose(2)
     ds = t(rng.uniform(0.9, 1.1, K))
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for _ in range(3):
-        G.gs_loop_closure_update(g, anchor, pb, pa, ds)
-    ms = []
-    for _ in range(10):
-        ev[0].record(); G.gs_loop_closure_update(g, anchor, pb, pa, ds); ev[1].record()
-        torch.cuda.synchronize()
-        ms.append(ev[0].elapsed_time(ev[1]))
-    m = statistics.median(ms)
+    m = graph_time_ms(lambda: G.gs_loop_closure_update(g, anchor, pb, pa, ds))
     peaks, kind = _peaks()
     gbs = n * LOOP_CLOSURE_BYTES / (m * 1e-3) / 1e9
     return {"workload": f"{n} Gaussians anchored to {K} keyframes ({n // K} consecutive per keyframe)",
