@@ -637,6 +637,8 @@ def main():
     ap.add_argument("--li-eval-rooms", type=int, default=5)
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
                     help="fix the tile size instead of autotuning over {8, 16, 32}")
+    ap.add_argument("--only", choices=["loop_closure", "pose_refinement", "bundle_adjustment", "keyframe_insertion"],
+                    default=None, help="run one extra section alone and print its line (for profiling runs)")
     args = ap.parse_args()
     args.tiles = (args.tile,) if args.tile else (8, 16, 32)
     rank = int(os.environ.get("RANK", "0"))
@@ -657,6 +659,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
+
+    if args.only is not None:
+        runs = {"loop_closure": loop_closure_run, "pose_refinement": tracking_run,
+                "bundle_adjustment": ba_run, "keyframe_insertion": insertion_run}
+        print(json.dumps({"section": args.only, args.only: runs[args.only](device)}), flush=True)
+        return 0
 
     from paper_2512_02293_gb300 import synth
     g, gt, cam = synth.cfg2_problem()
