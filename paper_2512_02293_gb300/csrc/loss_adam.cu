@@ -110,55 +110,106 @@ struct AdamArgs {
 constexpr int kAdamThreads = 256;
 
 __device__ __forceinline__ void adam_elem(float& p, float g, float& m, float& v, float b1, float b2, float ib1,
-                                          float ib2, float lr, float bc1, float bc2, float eps) {
+                                          float ib2, float lr, float rbc1, float rbc2, float eps) {
     m = b1 * m + ib1 * g;
     v = b2 * v + ib2 * g * g;
-    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    p -= lr * (m * rbc1) / (sqrtf(v * rbc2) + eps);
 }
 
-// Grid-stride over 4-element chunks of all groups; the last block to finish
-// advances the device step counter (each block reads it before finishing).
+// One float4 chunk c of the concatenated groups.
+__device__ __forceinline__ void adam_chunk(const AdamArgs& args, int64_t c, float b1, float b2, float ib1, float ib2,
+                                           float rbc1, float rbc2, float eps) {
+    int k = 0;
+    while (c >= args.chunk_end[k]) k++;
+    const gs_adam_group& G = args.g[k];
+    const int64_t i0 = 4 * (c - (k ? args.chunk_end[k - 1] : 0));
+    const float lr = G.lr;
+    const bool vec = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
+                       reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
+    if (vec && i0 + 3 < G.n) {
+        float4 p = *reinterpret_cast<const float4*>(G.param + i0);
+        const float4 g = *reinterpret_cast<const float4*>(G.grad + i0);
+        float4 m = *reinterpret_cast<const float4*>(G.m + i0);
+        float4 v = *reinterpret_cast<const float4*>(G.v + i0);
+        adam_elem(p.x, g.x, m.x, v.x, b1, b2, ib1, ib2, lr, rbc1, rbc2, eps);
+        adam_elem(p.y, g.y, m.y, v.y, b1, b2, ib1, ib2, lr, rbc1, rbc2, eps);
+        adam_elem(p.z, g.z, m.z, v.z, b1, b2, ib1, ib2, lr, rbc1, rbc2, eps);
+        adam_elem(p.w, g.w, m.w, v.w, b1, b2, ib1, ib2, lr, rbc1, rbc2, eps);
+        *reinterpret_cast<float4*>(G.param + i0) = p;
+        *reinterpret_cast<float4*>(G.m + i0) = m;
+        *reinterpret_cast<float4*>(G.v + i0) = v;
+    } else {
+        for (int64_t i = i0; i < i0 + 4 && i < G.n; i++) {
+            float p = G.param[i], m = G.m[i], v = G.v[i];
+            adam_elem(p, G.grad[i], m, v, b1, b2, ib1, ib2, lr, rbc1, rbc2, eps);
+            G.param[i] = p; G.m[i] = m; G.v[i] = v;
+        }
+    }
+}
+
+// Grid-stride over 4-element chunks of all groups, two chunks per thread and
+// round (their loads in flight together); the last block to finish advances the
+// device step counter (each block reads it before finishing).
 __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
     __shared__ float s_bc[2];
     __shared__ int s_t;
     if (threadIdx.x == 0) {
         const int t = args.d_step[0] + 1;
         s_t = t;
-        s_bc[0] = 1.0f - powf(args.b1, (float)t);
-        s_bc[1] = 1.0f - powf(args.b2, (float)t);
+        s_bc[0] = 1.0f / (1.0f - powf(args.b1, (float)t));
+        s_bc[1] = 1.0f / (1.0f - powf(args.b2, (float)t));
     }
     __syncthreads();
-    const float bc1 = s_bc[0], bc2 = s_bc[1];
+    const float rbc1 = s_bc[0], rbc2 = s_bc[1];
     const float b1 = args.b1, b2 = args.b2, eps = args.eps;
     const float ib1 = 1.0f - b1, ib2 = 1.0f - b2;
     const int64_t total = args.chunk_end[args.n_groups - 1];
-    for (int64_t c = (int64_t)blockIdx.x * kAdamThreads + threadIdx.x; c < total;
-         c += (int64_t)gridDim.x * kAdamThreads) {
-        int k = 0;
-        while (c >= args.chunk_end[k]) k++;
-        const gs_adam_group& G = args.g[k];
-        const int64_t i0 = 4 * (c - (k ? args.chunk_end[k - 1] : 0));
-        const float lr = G.lr;
-        const bool vec = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
-                           reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
-        if (vec && i0 + 3 < G.n) {
-            float4 p = *reinterpret_cast<const float4*>(G.param + i0);
-            const float4 g = *reinterpret_cast<const float4*>(G.grad + i0);
-            float4 m = *reinterpret_cast<const float4*>(G.m + i0);
-            float4 v = *reinterpret_cast<const float4*>(G.v + i0);
-            adam_elem(p.x, g.x, m.x, v.x, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
-            adam_elem(p.y, g.y, m.y, v.y, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
-            adam_elem(p.z, g.z, m.z, v.z, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
-            adam_elem(p.w, g.w, m.w, v.w, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
-            *reinterpret_cast<float4*>(G.param + i0) = p;
-            *reinterpret_cast<float4*>(G.m + i0) = m;
-            *reinterpret_cast<float4*>(G.v + i0) = v;
+    const int64_t stride = (int64_t)gridDim.x * kAdamThreads;
+    for (int64_t c = (int64_t)blockIdx.x * kAdamThreads + threadIdx.x; c < total; c += 2 * stride) {
+        const int64_t c1 = c + stride;
+        const bool has1 = c1 < total;
+        int k0 = 0, k1 = 0;
+        while (c >= args.chunk_end[k0]) k0++;
+        if (has1)
+            while (c1 >= args.chunk_end[k1]) k1++;
+        const gs_adam_group& G0 = args.g[k0];
+        const gs_adam_group& G1 = args.g[k1];
+        const int64_t i0 = 4 * (c - (k0 ? args.chunk_end[k0 - 1] : 0));
+        const int64_t i1 = has1 ? 4 * (c1 - (k1 ? args.chunk_end[k1 - 1] : 0)) : 0;
+        auto aligned4 = [](const gs_adam_group& G) {
+            return ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
+                     reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
+        };
+        const bool vec0 = aligned4(G0) && i0 + 3 < G0.n;
+        const bool vec1 = has1 && aligned4(G1) && i1 + 3 < G1.n;
+        if (vec0 && vec1) {
+            // both chunks' loads issued before any store
+            float4 p0 = *reinterpret_cast<const float4*>(G0.param + i0);
+            const float4 g0 = *reinterpret_cast<const float4*>(G0.grad + i0);
+            float4 m0 = *reinterpret_cast<const float4*>(G0.m + i0);
+            float4 v0 = *reinterpret_cast<const float4*>(G0.v + i0);
+            float4 p1 = *reinterpret_cast<const float4*>(G1.param + i1);
+            const float4 g1 = *reinterpret_cast<const float4*>(G1.grad + i1);
+            float4 m1 = *reinterpret_cast<const float4*>(G1.m + i1);
+            float4 v1 = *reinterpret_cast<const float4*>(G1.v + i1);
+            const float lr0 = G0.lr, lr1 = G1.lr;
+            adam_elem(p0.x, g0.x, m0.x, v0.x, b1, b2, ib1, ib2, lr0, rbc1, rbc2, eps);
+            adam_elem(p0.y, g0.y, m0.y, v0.y, b1, b2, ib1, ib2, lr0, rbc1, rbc2, eps);
+            adam_elem(p0.z, g0.z, m0.z, v0.z, b1, b2, ib1, ib2, lr0, rbc1, rbc2, eps);
+            adam_elem(p0.w, g0.w, m0.w, v0.w, b1, b2, ib1, ib2, lr0, rbc1, rbc2, eps);
+            adam_elem(p1.x, g1.x, m1.x, v1.x, b1, b2, ib1, ib2, lr1, rbc1, rbc2, eps);
+            adam_elem(p1.y, g1.y, m1.y, v1.y, b1, b2, ib1, ib2, lr1, rbc1, rbc2, eps);
+            adam_elem(p1.z, g1.z, m1.z, v1.z, b1, b2, ib1, ib2, lr1, rbc1, rbc2, eps);
+            adam_elem(p1.w, g1.w, m1.w, v1.w, b1, b2, ib1, ib2, lr1, rbc1, rbc2, eps);
+            *reinterpret_cast<float4*>(G0.param + i0) = p0;
+            *reinterpret_cast<float4*>(G0.m + i0) = m0;
+            *reinterpret_cast<float4*>(G0.v + i0) = v0;
+            *reinterpret_cast<float4*>(G1.param + i1) = p1;
+            *reinterpret_cast<float4*>(G1.m + i1) = m1;
+            *reinterpret_cast<float4*>(G1.v + i1) = v1;
         } else {
-            for (int64_t i = i0; i < i0 + 4 && i < G.n; i++) {
-                float p = G.param[i], m = G.m[i], v = G.v[i];
-                adam_elem(p, G.grad[i], m, v, b1, b2, ib1, ib2, lr, bc1, bc2, eps);
-                G.param[i] = p; G.m[i] = m; G.v[i] = v;
-            }
+            adam_chunk(args, c, b1, b2, ib1, ib2, rbc1, rbc2, eps);
+            if (has1) adam_chunk(args, c1, b1, b2, ib1, ib2, rbc1, rbc2, eps);
         }
     }
     __syncthreads();
@@ -236,7 +287,11 @@ cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, flo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = ceil_div(run > 0 ? run : 1, kAdamThreads);
-    const unsigned blocks = (unsigned)(want < 4 * sms ? want : 4 * sms);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adam, kAdamThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t full = (int64_t)per_sm * sms;                                // one resident wave
+    const unsigned blocks = (unsigned)(want < full ? want : full);
     a.total_blocks = blocks;
     k_adam<<<blocks, kAdamThreads, 0, s>>>(a);
     return cudaGetLastError();
