@@ -106,7 +106,7 @@ __device__ __forceinline__ int next_item(int* queue, int lane) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
+__global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         gs_image img, int* __restrict__ queue, int n_items) {
@@ -163,12 +163,8 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
             // transmittance cutoff) become predicates, so the warp never diverges
             const int cnt = __popc(kept);
             int last_k = -1;                         // batch slot of this lane's last blended splat
-            for (int k = 0; k < cnt; k++) {
-                const float2 m = s_xy[w][k];
-                const float4 q = s_q[w][k];
-                const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
-                const float p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-                const float a = fminf(amax, __fmul_rn(q.w, splat_weight(p2)));
+            // one compositing step of splat k given its power p2 and alpha a
+            auto step = [&](int k, float p2, float a) {
                 const float test = __fmaf_rn(-a, Tr, Tr);
                 const bool blend = !done && !(p2 > 0.f) && !(a < amin);
                 const bool stop = blend && test < tcut;
@@ -182,8 +178,33 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_render_fwd(
                 dd = __fmaf_rn(c.w, wgt, dd);
                 Tr = b ? test : Tr;
                 last_k = b ? k : last_k;
-                if (__all_sync(0xffffffffu, done)) break;
+            };
+            auto alpha = [&](int k, float* p2, float* a) {
+                const float2 m = s_xy[w][k];
+                const float4 q = s_q[w][k];
+                const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
+                *p2 = splat_power2(q.x, q.y, q.z, dx, dy);
+                *a = fminf(amax, __fmul_rn(q.w, splat_weight(p2[0])));
+            };
+            // groups of four: the four weights do not depend on the transmittance, so
+            // they are formed before the four serial steps; the warp checks for
+            // saturation once per group (a saturated lane blends nothing more either way)
+            int k = 0;
+            bool all_done = false;
+            for (; k + 4 <= cnt; k += 4) {
+                float p2[4], a[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) alpha(k + u, &p2[u], &a[u]);
+#pragma unroll
+                for (int u = 0; u < 4; u++) step(k + u, p2[u], a[u]);
+                if ((all_done = __all_sync(0xffffffffu, done))) break;
             }
+            if (!all_done)
+                for (; k < cnt; k++) {
+                    float p2, a;
+                    alpha(k, &p2, &a);
+                    step(k, p2, a);
+                }
             if (last_k >= 0) last = s_pos[w][last_k] + 1u;
             if (__all_sync(0xffffffffu, done)) break;
         }
