@@ -287,8 +287,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
 }
 
 // ---------------------------------------------------------------- backward
-// Shared-memory plan (bytes).  "x^T" operands are K-major over the tile's 128
-// samples (K = sample), the layout the weight-gradient GEMMs contract over.
+// Shared-memory plan (bytes).  "x^T" operands are contracted over the tile's 128
+// samples (K = sample) by the weight-gradient GEMMs; they are stored MN-major
+// (tc.cuh), so the thread that owns a sample writes 8 consecutive rows of one as
+// one 16-byte store.
 constexpr uint32_t kBwdW2t = 0;                                 // W2^T [128 i][128 j]         B of dH1
 constexpr uint32_t kBwdW3f = kBwdW2t + kHid * kHid * 2;         // W3 as float [8][128]
 constexpr uint32_t kBwdA2 = kBwdW3f + kOut * kHid * 4;          // dZ2 [128 b][128 j]           A of dH1
@@ -312,11 +314,6 @@ struct MlpBwdArgs {
     int* status;
 };
 
-// element (r, b) of a K-major operand over the 128 samples of a tile
-__device__ __forceinline__ void st_bf16(uint8_t* base, int r, int b, uint16_t v) {
-    *reinterpret_cast<uint16_t*>(base + tc::kmajor_offset(r, b, kTile)) = v;
-}
-
 __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,9 +332,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     for (int i = tid; i < kOut * kHid; i += kFwdThreads)
         sW3f[i] = bf2f(a.w.W3a[(i / kHid) * kK2 + (i % kHid)]);
     // constant rows of H1_aug^T: row 128 = 1 (the ones column of H1), rows 129..143 = 0
-    for (int k = tid; k < (kK2 - kHid) * kTile; k += kFwdThreads) {
-        const int rr = kHid + k / kTile, b = k % kTile;
-        st_bf16(sB2, rr, b, rr == kHid ? 0x3F80u : 0u);
+    for (int k = tid; k < 2 * kTile; k += kFwdThreads) {
+        const int b = k % kTile, q = k / kTile;
+        *reinterpret_cast<uint4*>(sB2 + tc::mnmajor_offset(kHid + 8 * q, b, kTile)) =
+            make_uint4(q == 0 ? 0x3F80u : 0u, 0u, 0u, 0u);
     }
     if (tid == 0) tc::mbar_init(bar, 1);
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
@@ -360,15 +358,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
         const bool valid = row < a.n;
         // (1) X_aug^T, dY and H2 (row-major, for the CUDA-core dW3) of this sample
 #pragma unroll 1
-        for (int c = cg; c < kK1 / 8; c += kColGroups) {
-            const uint4 v = x_chunk(a.X, row, a.n, c);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                st_bf16(sB1, 8 * c + 2 * i, r, (uint16_t)(w[i] & 0xFFFFu));
-                st_bf16(sB1, 8 * c + 2 * i + 1, r, (uint16_t)(w[i] >> 16));
-            }
-        }
+        for (int c = cg; c < kK1 / 8; c += kColGroups)
+            *reinterpret_cast<uint4*>(sB1 + tc::mnmajor_offset(8 * c, r, kTile)) = x_chunk(a.X, row, a.n, c);
         float dy[kOut];
         {
             float4 d0 = make_float4(0.f, 0.f, 0.f, 0.f), d1 = d0;
@@ -383,12 +374,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                 reinterpret_cast<float4*>(sDY + r * kOut)[1] = d1;
             }
         }
+        // this thread's hidden columns: chunks 4 cg .. 4 cg + 3 (32 values) of Z2 and Z1,
+        // loaded once here and used by steps (1), (3) and (5)
+        constexpr int kZc = kHid / 8 / kColGroups;
+        uint4 z2c[kZc], z1c[kZc];
+#pragma unroll
+        for (int q = 0; q < kZc; q++) {
+            const int c = kZc * cg + q;
+            z2c[q] = valid ? __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
+            z1c[q] = valid ? __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
+        }
         uint16_t* sH2 = reinterpret_cast<uint16_t*>(sA2t);   // [b][j], aliases dZ2^T until step (3)
-#pragma unroll 1
-        for (int c = cg; c < kHid / 8; c += kColGroups) {
-            uint4 z = make_uint4(0u, 0u, 0u, 0u);
-            if (valid) z = __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c);
-            const uint32_t w[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int q = 0; q < kZc; q++) {
+            const int c = kZc * cg + q;
+            const uint32_t w[4] = {z2c[q].x, z2c[q].y, z2c[q].z, z2c[q].w};
             uint32_t h[4];
 #pragma unroll
             for (int i = 0; i < 4; i++)
@@ -409,11 +409,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             for (int b = 0; b < kTile; b++) accb3 += sDY[b * kOut + tid];
         __syncthreads();
         // (3) dZ2 = bf16((dY W3) * gelu'(Z2)) as dZ2 rows and dZ2^T; H1 = bf16(gelu(Z1)) as H1_aug^T
-#pragma unroll 1
-        for (int c = cg; c < kHid / 8; c += kColGroups) {
-            uint4 z = make_uint4(0u, 0u, 0u, 0u);
-            if (valid) z = __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c);
-            const uint32_t w[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int q = 0; q < kZc; q++) {
+            const int c = kZc * cg + q;
+            const uint32_t w[4] = {z2c[q].x, z2c[q].y, z2c[q].z, z2c[q].w};
             uint16_t g[8];
 #pragma unroll
             for (int i = 0; i < 8; i++) {
@@ -423,18 +422,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                 for (int o = 0; o < kOut; o++) dh += dy[o] * sW3f[o * kHid + j];
                 const uint32_t zb = (i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu);
                 g[i] = f2bf(dh * __ldg(a.w.dgelu_tab + zb));
-                st_bf16(sA2t, j, r, g[i]);
             }
-            *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(r, 8 * c, kHid)) =
-                make_uint4(pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
-            uint4 z1 = make_uint4(0u, 0u, 0u, 0u);
-            if (valid) z1 = __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid) + c);
-            const uint32_t w1[4] = {z1.x, z1.y, z1.z, z1.w};
+            const uint4 gp = make_uint4(pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
+            *reinterpret_cast<uint4*>(sA2t + tc::mnmajor_offset(8 * c, r, kTile)) = gp;
+            *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(r, 8 * c, kHid)) = gp;
+            const uint32_t w1[4] = {z1c[q].x, z1c[q].y, z1c[q].z, z1c[q].w};
+            uint32_t hp[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                st_bf16(sB2, 8 * c + 2 * i, r, __ldg(a.w.gelu_tab + (w1[i] & 0xFFFFu)));
-                st_bf16(sB2, 8 * c + 2 * i + 1, r, __ldg(a.w.gelu_tab + (w1[i] >> 16)));
-            }
+            for (int i = 0; i < 4; i++)
+                hp[i] = pack2(__ldg(a.w.gelu_tab + (w1[i] & 0xFFFFu)), __ldg(a.w.gelu_tab + (w1[i] >> 16)));
+            *reinterpret_cast<uint4*>(sB2 + tc::mnmajor_offset(8 * c, r, kTile)) =
+                make_uint4(hp[0], hp[1], hp[2], hp[3]);
         }
         operands_ready();
         // (4) dH1 = dZ2 W2 and dW2_aug += dZ2^T H1_aug
@@ -445,27 +443,27 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                              tc::idesc_bf16(128, kHid), st > 0);
             for (int st = 0; st < kTile / 16; st++)
                 tc::mma_bf16(tbase + kTdW2, tc::kstep_desc(sa_a2t, kTile, st), tc::kstep_desc(sa_b2, kTile, st),
-                             tc::idesc_bf16(128, kK2), !first || st > 0);
+                             tc::idesc_bf16_mn(128, kK2, true, true), !first || st > 0);
             tc::mma_commit(bar);
         }
         if (!(ok = wait_all(bar, phase))) break;
         // (5) dZ1 = bf16(dH1 * gelu'(Z1)) as dZ1^T (over the dZ2 buffer, whose GEMM is done)
         uint8_t* sA1t = sA2;
-#pragma unroll 1
-        for (int c0 = cg * (kHid / kColGroups); c0 < (cg + 1) * (kHid / kColGroups); c0 += 16) {
+#pragma unroll
+        for (int h2 = 0; h2 < kZc / 2; h2++) {
+            const int c0 = 8 * kZc * cg + 16 * h2;
             float v[16];
             tc::tmem_ld16(tbase + kTdH1 + lane_off + (uint32_t)c0, v);
-            uint4 z[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
-            if (valid) {
-                z[0] = __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid + c0));
-                z[1] = __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid + c0) + 1);
-            }
-            const uint32_t w[8] = {z[0].x, z[0].y, z[0].z, z[0].w, z[1].x, z[1].y, z[1].z, z[1].w};
+            const uint32_t w[8] = {z1c[2 * h2].x, z1c[2 * h2].y, z1c[2 * h2].z, z1c[2 * h2].w,
+                                   z1c[2 * h2 + 1].x, z1c[2 * h2 + 1].y, z1c[2 * h2 + 1].z, z1c[2 * h2 + 1].w};
+            uint32_t gp[8];
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const uint32_t zb = (i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu);
-                st_bf16(sA1t, c0 + i, r, f2bf(v[i] * __ldg(a.w.dgelu_tab + zb)));
-            }
+            for (int i = 0; i < 8; i++)
+                gp[i] = pack2(f2bf(v[2 * i] * __ldg(a.w.dgelu_tab + (w[i] & 0xFFFFu))),
+                              f2bf(v[2 * i + 1] * __ldg(a.w.dgelu_tab + (w[i] >> 16))));
+            *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0, r, kTile)) = make_uint4(gp[0], gp[1], gp[2], gp[3]);
+            *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0 + 8, r, kTile)) =
+                make_uint4(gp[4], gp[5], gp[6], gp[7]);
         }
         operands_ready();
         // (6) dW1_aug += dZ1^T X_aug
@@ -473,7 +471,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             tc::fence_after_sync();
             for (int st = 0; st < kTile / 16; st++)
                 tc::mma_bf16(tbase + kTdW1, tc::kstep_desc(sa_a2, kTile, st), tc::kstep_desc(sa_b1, kTile, st),
-                             tc::idesc_bf16(128, kK1), !first || st > 0);
+                             tc::idesc_bf16_mn(128, kK1, true, true), !first || st > 0);
             tc::mma_commit(bar);
         }
         if (!(ok = wait_all(bar, phase))) break;

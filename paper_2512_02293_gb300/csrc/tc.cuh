@@ -11,6 +11,14 @@
 // byte offset) and those adjacent in rows SBO bytes apart (its stride byte
 // offset).  One MMA consumes K = 16 (two core matrices along K); step s of a
 // K loop starts 256 s bytes into the tile.
+//
+// MN-major operands (the instruction descriptor's transpose bit set) keep the
+// same descriptor: the leading byte offset still strides core matrices along K
+// and the stride byte offset along the rows (M or N); only each 128-byte core
+// matrix is transposed, its 16-byte lines holding 8 consecutive rows at one K:
+//     (r / 8) * SBO + (k / 8) * 128 + (k % 8) * 16 + (r % 8) * 2.
+// So a thread that owns one K index (a sample) and 8 consecutive rows writes
+// them as one 16-byte store.
 #pragma once
 #include <cstdint>
 
@@ -24,6 +32,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 // byte offset of element (r, k) in a K-major tile with K columns
 __device__ __forceinline__ uint32_t kmajor_offset(int r, int k, int K) {
     return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// byte offset of elements (r .. r + 7, k), r a multiple of 8, in an MN-major tile with K columns
+__device__ __forceinline__ uint32_t mnmajor_offset(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (k & 7) * 16);
 }
 
 // Shared-memory matrix descriptor (no swizzle): start address, leading byte
@@ -47,6 +60,11 @@ __device__ __forceinline__ uint64_t kstep_desc(uint32_t saddr, int K, int s) {
 // K-major, dense, shape M x N (N / 8 in bits 17-22, M / 16 in bits 24-28).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with A and / or B MN-major (transpose bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N, bool a_mn, bool b_mn) {
+    return idesc_bf16(M, N) | (a_mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
