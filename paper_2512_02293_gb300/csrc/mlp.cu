@@ -177,6 +177,14 @@ __device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t& phase) {
 
 // Sync point after this thread wrote shared-memory operands: visible to the
 // tensor core, prior tensor-memory reads ordered before the next MMA.
+// 16-byte asynchronous copy global -> shared (zero-filled when !valid; src must
+// then still be a readable address)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void operands_ready() {
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -337,6 +345,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
         *reinterpret_cast<uint4*>(sB2 + tc::mnmajor_offset(kHid + 8 * q, b, kTile)) =
             make_uint4(q == 0 ? 0x3F80u : 0u, 0u, 0u, 0u);
     }
+    for (int b = tid; b < kTile; b += kFwdThreads)       // X_aug^T rows 200..207: zeros
+        *reinterpret_cast<uint4*>(sB1 + tc::mnmajor_offset(kK1 - 8, b, kTile)) = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) tc::mbar_init(bar, 1);
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
     operands_ready();
@@ -358,8 +368,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
         const bool valid = row < a.n;
         // (1) X_aug^T, dY and H2 (row-major, for the CUDA-core dW3) of this sample
 #pragma unroll 1
-        for (int c = cg; c < kK1 / 8; c += kColGroups)
-            *reinterpret_cast<uint4*>(sB1 + tc::mnmajor_offset(8 * c, r, kTile)) = x_chunk(a.X, row, a.n, c);
+        for (int c = cg; c < kIn / 8 + 1; c += kColGroups) {
+            // the inputs are needed only by the dW1 GEMM at the end of the tile: copied
+            // asynchronously, waited for just before it; the partial chunk 24 (4 inputs,
+            // the ones column) by a plain store; chunk 25 holds zeros from the start
+            uint8_t* dst = sB1 + tc::mnmajor_offset(8 * c, r, kTile);
+            if (c < kIn / 8) cp_async16(tc::smem_addr(dst), a.X + (valid ? row : 0) * kK1 + 8 * c, valid);
+            else *reinterpret_cast<uint4*>(dst) = x_chunk(a.X, row, a.n, c);
+        }
         float dy[kOut];
         {
             float4 d0 = make_float4(0.f, 0.f, 0.f, 0.f), d1 = d0;
@@ -465,6 +481,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0 + 8, r, kTile)) =
                 make_uint4(gp[4], gp[5], gp[6], gp[7]);
         }
+        cp_async_wait_all();
         operands_ready();
         // (6) dW1_aug += dZ1^T X_aug
         if (tid == 0) {
