@@ -363,6 +363,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
     uint32_t phase = 0;
     bool ok = true, first = true;
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
+    // this thread's hidden columns: chunks 4 cg .. 4 cg + 3 (32 values) of Z2 and Z1,
+    // and its sample's dY, loaded for tile t + gridDim.x while tile t's last GEMM
+    // runs, and used by steps (1), (3) and (5) of the next tile
+    constexpr int kZc = kHid / 8 / kColGroups;
+    uint4 z2c[kZc], z1c[kZc];
+    float4 dy0, dy1;
+    auto load_rows = [&](int64_t tile) {
+        const int64_t rw = tile * kTile + r;
+        const bool v = tile < n_tiles && rw < a.n;
+#pragma unroll
+        for (int q = 0; q < kZc; q++) {
+            const int c = kZc * cg + q;
+            z2c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z2 + rw * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
+            z1c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z1 + rw * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        dy0 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dy1 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    load_rows(blockIdx.x);
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int64_t row = t * kTile + r;
         const bool valid = row < a.n;
@@ -376,29 +395,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             if (c < kIn / 8) cp_async16(tc::smem_addr(dst), a.X + (valid ? row : 0) * kK1 + 8 * c, valid);
             else *reinterpret_cast<uint4*>(dst) = x_chunk(a.X, row, a.n, c);
         }
-        float dy[kOut];
-        {
-            float4 d0 = make_float4(0.f, 0.f, 0.f, 0.f), d1 = d0;
-            if (valid) {
-                d0 = __ldg(reinterpret_cast<const float4*>(a.dY + row * kOut));
-                d1 = __ldg(reinterpret_cast<const float4*>(a.dY + row * kOut) + 1);
-            }
-            dy[0] = d0.x; dy[1] = d0.y; dy[2] = d0.z; dy[3] = d0.w;
-            dy[4] = d1.x; dy[5] = d1.y; dy[6] = d1.z; dy[7] = d1.w;
-            if (cg == 0) {
-                reinterpret_cast<float4*>(sDY + r * kOut)[0] = d0;
-                reinterpret_cast<float4*>(sDY + r * kOut)[1] = d1;
-            }
-        }
-        // this thread's hidden columns: chunks 4 cg .. 4 cg + 3 (32 values) of Z2 and Z1,
-        // loaded once here and used by steps (1), (3) and (5)
-        constexpr int kZc = kHid / 8 / kColGroups;
-        uint4 z2c[kZc], z1c[kZc];
-#pragma unroll
-        for (int q = 0; q < kZc; q++) {
-            const int c = kZc * cg + q;
-            z2c[q] = valid ? __ldg(reinterpret_cast<const uint4*>(a.Z2 + row * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
-            z1c[q] = valid ? __ldg(reinterpret_cast<const uint4*>(a.Z1 + row * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
+        const float dy[kOut] = {dy0.x, dy0.y, dy0.z, dy0.w, dy1.x, dy1.y, dy1.z, dy1.w};
+        if (cg == 0) {
+            reinterpret_cast<float4*>(sDY + r * kOut)[0] = dy0;
+            reinterpret_cast<float4*>(sDY + r * kOut)[1] = dy1;
         }
         uint16_t* sH2 = reinterpret_cast<uint16_t*>(sA2t);   // [b][j], aliases dZ2^T until step (3)
 #pragma unroll
@@ -481,6 +481,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
             *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0 + 8, r, kTile)) =
                 make_uint4(gp[4], gp[5], gp[6], gp[7]);
         }
+        load_rows(t + gridDim.x);          // the next tile's rows, in flight during the dW1 GEMM
         cp_async_wait_all();
         operands_ready();
         // (6) dW1_aug += dZ1^T X_aug
