@@ -104,3 +104,31 @@ def test_too_many_edges_out_of_one_keyframe_is_reported():
     win = G.BAWindow(R, t, disp, intr, edges, targets, np.ones((len(edges), 4, 4, 2)), 1)
     G.gs_ba_step(win)
     assert G.gs_read_device_status(win.status) == G.GS_OK
+
+
+def test_largest_system_31_free_poses():
+    # 32 keyframes with the first fixed: the reduced system is 186 x 186 (the
+    # limit), solved in 139 KB of shared memory with 6 columns per lane
+    R, t, disp, intr, edges, wts = synth.ba_scene(13, K=32, h=4, w=4, window=3)
+    rng = np.random.default_rng(14)
+    targets = _exact_targets(R, t, disp, intr, edges) + rng.normal(0, 0.3, (len(edges), 4, 4, 2))
+    win = G.BAWindow(R, t, disp, intr, edges, targets, wts, 1)
+    lam, eps = 1e-3, 1e-3
+    G.gs_ba_step(win, lam, eps)
+    torch.cuda.synchronize()
+    assert int(win.status[0].item()) == 0
+    R32, t32, d32, T32, W32 = _f32(R), _f32(t), _f32(disp), _f32(targets), _f32(wts)
+    intr32 = tuple(float(np.float32(x)) for x in intr)
+    dx, dd, H, g, cost = ba.lm_step(R32, t32, d32, intr32, edges, T32, W32, 1, lam=lam, eps=eps)
+    Rr, tr, dr = ba.apply_step(R32, t32, d32, dx, dd, 1)
+    assert win.cost.item() == pytest.approx(cost, rel=1e-4)
+    Rg, tg, dg = _gpu_state(win)
+    np.testing.assert_allclose(dg, dr, atol=2e-3 * np.abs(dd).max() + 1e-6)
+    np.testing.assert_allclose(tg, tr, atol=2e-3 * np.abs(dx).max() + 1e-6)
+    np.testing.assert_allclose(Rg, Rr, atol=2e-3 * np.abs(dx).max() + 1e-6)
+    # one more free pose is refused on the host
+    win33 = G.BAWindow(*synth.ba_scene(13, K=33, h=4, w=4, window=3)[:3], intr,
+                       [(i, j) for i in range(33) for j in range(33) if i != j and abs(i - j) <= 1],
+                       np.zeros((2 * 32, 4, 4, 2)), np.ones((2 * 32, 4, 4, 2)), 1)
+    with pytest.raises(G.GsError):
+        G.gs_ba_step(win33)
