@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the rasterisers
 # on this workload, from an ncu capture of the current kernels
 # (profiles/k_render_{bwd,fwd}_640x480_200k.md); keyed by (stage, tile).
-PROFILED_TRAFFIC = {("gs_render_bwd_raster", 16): 22.26e6, ("gs_render_fwd", 16): 9.27e6}
+PROFILED_TRAFFIC = {("gs_render_bwd_raster", 16): 22.28e6, ("gs_render_fwd", 16): 9.28e6}
 
 
 def _peaks():
@@ -197,6 +197,13 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
     return times, st, pairs, (clk.summary() if clk else None)
 
 
+def bwd_ctas_per_sm(step, tile) -> int:
+    """The backward rasteriser's occupancy variant the library picks: 2 CTAs per
+    SM up to 256 pixel blocks per SM, else 3."""
+    items = step.total_tiles * (tile // 8) * (tile // 4)
+    return 2 if items <= 256 * 152 else 3
+
+
 def launches_per_step(step) -> int:
     """Kernels of ours per iteration: project 1; bin/sort: entry scan 2,
     duplicate 1, 3 per radix pass (digits of at most 9 bits over 31 depth bits
@@ -312,7 +319,8 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     if st:
         roof = {}
         for stage, ops, kern in (("gs_render_fwd", FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"),
-                                 ("gs_render_bwd_raster", BWD_OPS_PER_PAIR, f"k_render_bwd<{params.tile}>")):
+                                 ("gs_render_bwd_raster", BWD_OPS_PER_PAIR,
+                                  f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}>")):
             ach = pairs * ops / (st[stage] * 1e-3) / 1e12
             roof[stage] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
                            "frac": ach / alu_peak, "work": f"{pairs} visited pairs x {ops} FP32 ops per launch",
@@ -764,7 +772,8 @@ def main():
     if st:
         dominant = max(st, key=st.get)
         if dominant == "gs_render_bwd_raster":
-            ms, ops, kern = st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR, f"k_render_bwd<{params.tile}> (+ its grad2d memset)"
+            ms, ops, kern = (st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR,
+                             f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}> (+ its grad2d memset)")
         else:
             ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"
         ach = pairs * ops / (ms * 1e-3) / 1e12

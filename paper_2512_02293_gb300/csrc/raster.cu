@@ -432,8 +432,11 @@ __device__ __forceinline__ void bwd_item(
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(kRasterThreads, 4) k_render_bwd(
+// Two occupancies (kCtas CTAs per SM): few work items per SM (a single 640x480
+// view: ~60) run best with 2 CTAs and 90 registers, where the deepest blocks'
+// chains are shorter; many (a keyframe window: ~900) with 3 CTAs and 80.
+template <int T, int kCtas>
+__global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
@@ -505,12 +508,20 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     int* queue = bins.status + 2;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    constexpr int kBwdFewItemsPerSm = 256;
     switch (rc.tile) {
 #define GS_BWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        k_render_bwd<TT><<<persistent_grid(k_render_bwd<TT>, n_items), kRasterThreads, 0, s>>>(       \
-            xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
+        if (n_items <= kBwdFewItemsPerSm * sms)                                                        \
+            k_render_bwd<TT, 2><<<persistent_grid(k_render_bwd<TT, 2>, n_items), kRasterThreads, 0, s>>>( \
+                xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
+        else                                                                                           \
+            k_render_bwd<TT, 3><<<persistent_grid(k_render_bwd<TT, 3>, n_items), kRasterThreads, 0, s>>>( \
+                xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
         break;                                                                                         \
     }
         GS_BWD(8)
