@@ -440,6 +440,54 @@ def gs_adam_step(groups, beta1: float, beta2: float, eps: float, d_step, stream=
                                        _stream(stream)), "gs_adam_step")
 
 
+class BoundCall:
+    """One C-ABI call with every argument but the stream marshalled once.  The
+    tensors it points at must stay allocated and keep their storage; the
+    ctypes structures the arguments refer to are held here."""
+    __slots__ = ("fn", "args", "name", "keep")
+
+    def __init__(self, name: str, args: tuple, keep: tuple = ()):
+        self.fn = getattr(load_library(), name)
+        self.args = args
+        self.name = name
+        self.keep = keep
+
+    def __call__(self, stream=None):
+        _check(self.fn(*self.args, _stream(stream)), self.name)
+
+
+def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cams, params: RenderParams,
+                      target_color, target_depth, lambda_c: float, lambda_d: float, dL_dcolor, dL_ddepth,
+                      loss_terms, lambda_iso: float, grads: Grads, iso_loss, ws, adam_groups,
+                      beta1: float, beta2: float, eps: float, d_step):
+    """The seven calls of one mapping iteration (gs_project, gs_bin_sort,
+    gs_render_fwd, gs_loss, gs_render_bwd_raster, gs_project_bwd, gs_adam_step)
+    as BoundCall objects, in order.  ws doubles as grad2d, as in the staged
+    iteration."""
+    arr = camera_array(cams); V = len(cams); p = params.struct()
+    gg = g.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct(); gr = grads.struct()
+    wsb = ws.numel() * ws.element_size()
+    groups = (gs_adam_group * len(adam_groups))()
+    for k, (pp, gd, m, v, lr) in enumerate(adam_groups):
+        groups[k] = gs_adam_group(_ptr(pp), _ptr(gd), _ptr(m), _ptr(v), pp.numel(), float(lr), 0)
+    keep = (arr, p, gg, pr, b, im, gr, groups)
+    by = ctypes.byref
+    return [
+        BoundCall("gs_project", (by(gg), arr, V, by(p), by(pr)), keep),
+        BoundCall("gs_bin_sort", (by(pr), g.n, arr, V, by(p), by(b), _ptr(ws), wsb), keep),
+        BoundCall("gs_render_fwd", (by(pr), by(b), arr, V, by(p), by(im)), keep),
+        BoundCall("gs_loss", (by(im), _ptr(target_color), _ptr(target_depth), arr, V, float(lambda_c),
+                              float(lambda_d), _ptr(dL_dcolor), _ptr(dL_ddepth), _ptr(loss_terms), _ptr(ws), wsb),
+                  keep),
+        BoundCall("gs_render_bwd_raster", (by(pr), by(b), by(im), _ptr(dL_dcolor), _ptr(dL_ddepth), arr, V, by(p),
+                                           g.n, _ptr(ws)), keep),
+        BoundCall("gs_project_bwd", (by(gg), arr, V, by(p), _ptr(ws), float(lambda_iso), by(gr), _ptr(iso_loss)),
+                  keep),
+        BoundCall("gs_adam_step", (groups, len(adam_groups), float(beta1), float(beta2), float(eps), _ptr(d_step)),
+                  keep),
+    ]
+
+
 def gs_read_device_status(d_status, stream=None) -> int:
     out = ctypes.c_int32(0)
     _check(load_library().gs_read_device_status(_ptr(d_status), _stream(stream), ctypes.byref(out)),

@@ -65,6 +65,8 @@ class MappingStep:
         self.d_step = torch.zeros(2, device=dev, dtype=torch.int32)
         self.headroom = headroom
         self.graph = None
+        self._bound = None          # the seven calls marshalled once (eager step); rebuilt when stale
+        self._bound_key = None
         self._alloc_bins(key_capacity if key_capacity is not None else self._measure_keys())
 
     # -------------------------------------------------------------- buffers
@@ -74,6 +76,7 @@ class MappingStep:
         ws = G.gs_workspace_size(self.n, self.cams, self.params, capacity)
         self.ws = torch.empty((ws + 255) // 256 * 64, device=self.device, dtype=torch.float32)
         self.graph = None
+        self._bound = None
 
     def _measure_keys(self) -> int:
         """Project once and count the keys (host read; outside any graph)."""
@@ -115,14 +118,32 @@ class MappingStep:
                   zip(self.g.tensors(), self.grads.tensors(), self.m, self.v, self.mp.lr)]
         G.gs_adam_step(groups, self.mp.beta1, self.mp.beta2, self.mp.eps, self.d_step)
 
+    def _bound_calls(self):
+        """The iteration's seven C-ABI calls with their arguments marshalled once;
+        rebuilt when the cameras, the buffers or the mapping parameters change."""
+        mp = self.mp
+        key = (tuple(id(c) for c in self.cams), id(self.bins), id(self.ws), id(self.target_color),
+               id(self.target_depth), mp.lambda_c, mp.lambda_d, mp.lambda_iso, tuple(mp.lr), mp.beta1, mp.beta2,
+               mp.eps, self.g.n)
+        if self._bound is None or self._bound_key != key:
+            groups = list(zip(self.g.tensors(), self.grads.tensors(), self.m, self.v, mp.lr))
+            self._bound = G.bind_mapping_step(self.g, self.proj, self.bins, self.img, self.cams, self.params,
+                                              self.target_color, self.target_depth, mp.lambda_c, mp.lambda_d,
+                                              self.dL_dcolor, self.dL_ddepth, self.loss_terms, mp.lambda_iso,
+                                              self.grads, self.iso, self.ws, groups, mp.beta1, mp.beta2, mp.eps,
+                                              self.d_step)
+            self._bound_key = key
+        return self._bound
+
     def step(self):
-        """One full mapping iteration (no host synchronisation)."""
+        """One full mapping iteration (no host synchronisation): the captured graph
+        if capture() was called, else the seven C-ABI calls (arguments marshalled
+        once and reused)."""
         if self.graph is not None:
             self.graph.replay()
             return
-        self.render()
-        self.loss_and_backward()
-        self.optimizer_step()
+        for call in self._bound_calls():
+            call()
 
     STAGES = ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
               "gs_adam_step")
