@@ -346,6 +346,16 @@ def cfg4_problem(trial: int = 0, n=1_000_000, views=16, width=1280, height=1024,
     return g, perturb_map(g, seed + 1), cams
 
 
+def refinement_problem(trial: int = 0, n=200_000, views=16, width=640, height=480, f=525.0):
+    """A keyframe list for the final colour refinement: `views` keyframes of one
+    resolution along a 5 m path inside an n-Gaussian room; the map to refine and
+    the perturbed copy whose renders are the targets."""
+    seed = 6000 + trial
+    cams, ctrl = trajectory_cameras(seed, [(width, height, f)] * views)
+    g = room_scene(n, seed, keep_out=[c.t_wc for c in cams])
+    return g, perturb_map(g, seed + 1), cams
+
+
 def mlp_params(seed: int, n_in: int = 196, n_hid: int = 128, n_out: int = 8, bias_sd: float = 0.1) -> dict:
     """Seeded float32 weights of the 196 -> 128 -> 128 -> 8 initialiser network:
     W ~ N(0, 1 / fan_in), biases ~ N(0, bias_sd^2)."""
