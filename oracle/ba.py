@@ -26,9 +26,31 @@ The oracle builds the full dense Jacobian and solves the full system (no
 Schur complement), so it checks the GPU's block elimination of the diagonal
 depth block C (Eq. 4) by the plain definition.
 
-Parity status (tests/test_oracle_ba.py): Jacobian against central differences
-of the residual; Gauss-Newton converging to the generating poses and depths on
-exact synthetic correspondences; the solve against a least-squares routine.
+Inertial factor (Eq. 3), between consecutive keyframes i, j = i + 1, on the
+body-to-world rotation R_i = R_cw,i^T, position p_i = -R_i t_cw,i, velocity v_i
+and IMU bias b_i = (b_g, b_a) (camera and body frames taken as one, as the
+paper's equations do), with pre-integrated dR, dp, dv, Jacobians J_rot (3x3,
+gyro bias), J_pos and J_vel (3x6, full bias), time step dt, gravity g and a
+15 x 15 information matrix:
+  r_rot  = Log((dR Exp(J_rot (b_g,i - bh_g,i)))^T R_i^T R_j)
+  r_pos  = R_i^T (p_j - p_i - v_i dt - g dt^2 / 2) - (dp + J_pos (b_i - bh_i))
+  r_vel  = R_i^T (v_j - v_i - g dt) - (dv + J_vel (b_i - bh_i))
+  r_bias = b_j - b_i
+(reading: the velocity term's bias correction uses the full bias, as the
+position term's does; the printed equation writes the gyro part there).  The
+variables of a keyframe become (rho, phi, v, b): 15; the inertial Jacobian is
+taken by central differences of these residuals under the same perturbation
+as the visual part (T_cw <- Exp(xi) T_cw; v, b additive), so it rests on the
+residual's definition alone.
+
+Parity status (tests/test_oracle_ba.py): as above, plus the inertial residual
+vanishing on a consistent synthetic trajectory and Gauss-Newton over the
+joint visual-inertial objective recovering it.
+
+Parity status of the visual part (tests/test_oracle_ba.py): Jacobian against
+central differences of the residual; Gauss-Newton converging to the generating
+poses and depths on exact synthetic correspondences; the solve against a
+least-squares routine.
 """
 from __future__ import annotations
 
@@ -133,3 +155,119 @@ def apply_step(R, t, disp, dxi, ddisp, n_fixed):
         R[k] = Rphi @ R[k]
         t[k] = Rphi @ t[k] + rho
     return R, t, disp + ddisp
+
+
+# ------------------------------------------------------------------ inertial
+
+IMU_FLOATS = 9 + 3 + 3 + 9 + 18 + 18 + 1 + 225     # one pair's record (see imu_record)
+
+
+def so3_log(M):
+    """Rotation vector of a rotation matrix."""
+    M = np.asarray(M, np.float64)
+    c = np.clip((np.trace(M) - 1.0) / 2.0, -1.0, 1.0)
+    th = np.arccos(c)
+    w = np.array([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]]) / 2.0
+    if th < 1e-8:
+        return w
+    return w * th / np.sin(th)
+
+
+def body_states(R, t):
+    """Body-to-world rotations R_i = R_cw^T and positions p_i = -R_i t_cw."""
+    Rb = np.transpose(np.asarray(R, np.float64), (0, 2, 1))
+    return Rb, -np.einsum("kab,kb->ka", Rb, np.asarray(t, np.float64))
+
+
+def imu_record(dR, dp, dv, Jrot, Jpos, Jvel, dt, info):
+    """One consecutive pair's pre-integration record in the library's layout."""
+    return np.concatenate([np.asarray(dR, np.float64).reshape(9), dp, dv, np.asarray(Jrot).reshape(9),
+                           np.asarray(Jpos).reshape(18), np.asarray(Jvel).reshape(18), [dt],
+                           np.asarray(info).reshape(225)])
+
+
+def _unpack(rec):
+    rec = np.asarray(rec, np.float64)
+    o = 0
+    def take(k, shape):
+        nonlocal o
+        v = rec[o:o + k].reshape(shape); o += k
+        return v
+    dR = take(9, (3, 3)); dp = take(3, 3); dv = take(3, 3); Jrot = take(9, (3, 3))
+    Jpos = take(18, (3, 6)); Jvel = take(18, (3, 6)); dt = take(1, 1)[0]; info = take(225, (15, 15))
+    return dR, dp, dv, Jrot, Jpos, Jvel, dt, info
+
+
+def inertial_residual(R, t, vel, bias, bias_hat, imu, gravity, i):
+    """r (15) of the pair (i, i + 1), Eq. 3."""
+    dR, dp, dv, Jrot, Jpos, Jvel, dt, _ = _unpack(imu[i])
+    Rb, pb = body_states(R, t)
+    j = i + 1
+    g = np.asarray(gravity, np.float64)
+    db = np.asarray(bias[i], np.float64) - np.asarray(bias_hat[i], np.float64)
+    A = dR @ so3_exp(Jrot @ db[:3])
+    r_rot = so3_log(A.T @ Rb[i].T @ Rb[j])
+    r_pos = Rb[i].T @ (pb[j] - pb[i] - vel[i] * dt - 0.5 * g * dt * dt) - (dp + Jpos @ db)
+    r_vel = Rb[i].T @ (vel[j] - vel[i] - g * dt) - (dv + Jvel @ db)
+    r_bias = np.asarray(bias[j], np.float64) - np.asarray(bias[i], np.float64)
+    return np.concatenate([r_rot, r_pos, r_vel, r_bias])
+
+
+def apply_step_vi(R, t, disp, vel, bias, dx, ddisp, n_fixed):
+    """dx [K - n_fixed, 15] = (rho, phi, dv, db) per free keyframe: poses by
+    apply_step, velocities and biases additively."""
+    dx = np.asarray(dx, np.float64)
+    R2, t2, d2 = apply_step(R, t, disp, dx[:, :6], ddisp, n_fixed)
+    v2 = np.array(vel, np.float64); b2 = np.array(bias, np.float64)
+    v2[n_fixed:] += dx[:, 6:9]
+    b2[n_fixed:] += dx[:, 9:15]
+    return R2, t2, d2, v2, b2
+
+
+def inertial_jacobian(R, t, vel, bias, bias_hat, imu, gravity, n_fixed, h=1e-6):
+    """Dense J [15 (K - 1), 15 (K - n_fixed)] of all pairs' residuals by central
+    differences over the free keyframes' (rho, phi, v, b)."""
+    K = np.asarray(R).shape[0]
+    nv = 15 * (K - n_fixed)
+    disp0 = np.zeros((K, 1, 1))
+    def all_res(dx):
+        R2, t2, _, v2, b2 = apply_step_vi(R, t, disp0, vel, bias, dx.reshape(K - n_fixed, 15), 0.0, n_fixed)
+        return np.concatenate([inertial_residual(R2, t2, v2, b2, bias_hat, imu, gravity, i) for i in range(K - 1)])
+    J = np.zeros((15 * (K - 1), nv))
+    for c in range(nv):
+        e = np.zeros(nv); e[c] = h
+        J[:, c] = (all_res(e) - all_res(-e)) / (2 * h)
+    return J
+
+
+def lm_step_vi(R, t, disp, vel, bias, bias_hat, intr, edges, targets, weights, imu, gravity, n_fixed,
+               lam=1e-4, eps=1e-4):
+    """One damped Gauss-Newton step of the joint visual (Eq. 2) + inertial
+    (Eq. 3) objective by the full dense solve.  Returns (dx [K - n_fixed, 15],
+    ddisp [K, h, w], cost)."""
+    K = np.asarray(R).shape[0]
+    h, w = disp.shape[1:]
+    P = h * w
+    nx6 = 6 * (K - n_fixed)
+    # visual part, its pose columns spread into the 15-wide keyframe blocks
+    rv = residuals(R, t, disp, intr, edges, targets).reshape(-1)
+    Wv = np.asarray(weights, np.float64).reshape(-1)
+    Jv6 = jacobian(R, t, disp, intr, edges, n_fixed)
+    nx = 15 * (K - n_fixed)
+    Jv = np.zeros((Jv6.shape[0], nx + K * P))
+    for k in range(K - n_fixed):
+        Jv[:, 15 * k:15 * k + 6] = Jv6[:, 6 * k:6 * k + 6]
+    Jv[:, nx:] = Jv6[:, nx6:]
+    # inertial part
+    ri = np.concatenate([inertial_residual(R, t, vel, bias, bias_hat, imu, gravity, i) for i in range(K - 1)])
+    Ji = np.zeros((15 * (K - 1), nx + K * P))
+    Ji[:, :nx] = inertial_jacobian(R, t, vel, bias, bias_hat, imu, gravity, n_fixed)
+    Wi = np.zeros((15 * (K - 1), 15 * (K - 1)))
+    for i in range(K - 1):
+        Wi[15 * i:15 * i + 15, 15 * i:15 * i + 15] = _unpack(imu[i])[7]
+    H = Jv.T @ (Wv[:, None] * Jv) + Ji.T @ Wi @ Ji
+    g = Jv.T @ (Wv * rv) + Ji.T @ Wi @ ri
+    A = H + lam * np.diag(np.diag(H)) + eps * np.eye(H.shape[0])
+    delta = np.linalg.solve(A, -g)
+    cost = float(np.sum(Wv * rv * rv) + ri @ Wi @ ri)
+    return delta[:nx].reshape(K - n_fixed, 15), delta[nx:].reshape(K, h, w), cost

@@ -346,6 +346,51 @@ def cfg4_problem(trial: int = 0, n=1_000_000, views=16, width=1280, height=1024,
     return g, perturb_map(g, seed + 1), cams
 
 
+def vi_scene(seed: int, K: int = 4, h: int = 12, w: int = 16, f: float = 20.0, window: int = 2, dt: float = 0.5):
+    """ba_scene plus the inertial quantities of Eq. 3 for consecutive keyframes:
+    velocities [K, 3], IMU biases [K, 6] (constant along the window, so the bias
+    term vanishes), the biases the pre-integration was linearised at [K, 6]
+    (a small offset, so the bias corrections are exercised), gravity [3], and
+    one pre-integration record per pair [K - 1, 286] (dR, dp, dv, J_rot, J_pos,
+    J_vel, dt, 15 x 15 information; see oracle.ba.imu_record) built so that
+    every inertial residual is zero at this state.  The pre-integration's own
+    Jacobians and information are seeded random values of plausible size (the
+    factor is exact for any of them)."""
+    R, t, disp, intr, edges, weights = ba_scene(seed, K=K, h=h, w=w, f=f, window=window)
+    rng = np.random.default_rng(seed + 17)
+    Rb = np.transpose(R, (0, 2, 1))
+    pb = -np.einsum("kab,kb->ka", Rb, t)
+    vel = rng.normal(0.0, 0.3, (K, 3))
+    b = np.concatenate([rng.normal(0, 0.01, 3), rng.normal(0, 0.05, 3)])
+    bias = np.tile(b, (K, 1))
+    bias_hat = bias + np.concatenate([rng.normal(0, 0.003, (K, 3)), rng.normal(0, 0.01, (K, 3))], 1)
+    gravity = np.array([0.0, 0.0, -9.81])
+
+    def exp3(phi):
+        th = np.linalg.norm(phi)
+        Kx = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+        if th < 1e-12:
+            return np.eye(3) + Kx
+        return np.eye(3) + np.sin(th) / th * Kx + (1 - np.cos(th)) / th ** 2 * Kx @ Kx
+
+    recs = []
+    for i in range(K - 1):
+        j = i + 1
+        Jrot = -dt * np.eye(3) + rng.normal(0, 0.02, (3, 3))
+        Jpos = np.concatenate([rng.normal(0, 0.05, (3, 3)), -0.5 * dt * dt * np.eye(3)], 1)
+        Jvel = np.concatenate([rng.normal(0, 0.1, (3, 3)), -dt * np.eye(3)], 1)
+        db = bias[i] - bias_hat[i]
+        dR = Rb[i].T @ Rb[j] @ exp3(Jrot @ db[:3]).T
+        dp = Rb[i].T @ (pb[j] - pb[i] - vel[i] * dt - 0.5 * gravity * dt * dt) - Jpos @ db
+        dv = Rb[i].T @ (vel[j] - vel[i] - gravity * dt) - Jvel @ db
+        Lm = rng.normal(0, 0.3, (15, 15))
+        info = Lm @ Lm.T + np.diag(np.concatenate([np.full(3, 400.0), np.full(3, 100.0), np.full(3, 100.0),
+                                                   np.full(6, 1000.0)]))
+        recs.append(np.concatenate([dR.reshape(9), dp, dv, Jrot.reshape(9), Jpos.reshape(18), Jvel.reshape(18),
+                                    [dt], info.reshape(225)]))
+    return R, t, disp, intr, edges, weights, vel, bias, bias_hat, gravity, np.stack(recs)
+
+
 def refinement_problem(trial: int = 0, n=200_000, views=16, width=640, height=480, f=525.0):
     """A keyframe list for the final colour refinement: `views` keyframes of one
     resolution along a 5 m path inside an n-Gaussian room; the map to refine and

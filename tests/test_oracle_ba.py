@@ -66,3 +66,55 @@ def test_step_solves_the_damped_least_squares_problem():
     b = np.concatenate([-sw * r, np.zeros(J.shape[1])])
     delta = np.linalg.lstsq(A, b, rcond=None)[0]
     np.testing.assert_allclose(np.concatenate([dx.reshape(-1), dd.reshape(-1)]), delta, rtol=1e-7, atol=1e-10)
+
+
+# ------------------------------------------------------------ inertial (Eq. 3)
+
+def test_inertial_residual_vanishes_on_a_consistent_trajectory():
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(5, K=5)
+    for i in range(4):
+        np.testing.assert_allclose(ba.inertial_residual(R, t, vel, bias, bh, imu, g, i), 0.0, atol=1e-9)
+
+
+def test_inertial_residual_terms():
+    # each term moves with its own variable: a velocity offset moves r_pos by
+    # -R_i^T dv dt and r_vel by -R_i^T dv; a common bias offset leaves r_bias at 0
+    # and moves r_pos by -J_pos db; a rotation of keyframe j about its own frame
+    # moves r_rot by that angle
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(6, K=3)
+    Rb, _ = ba.body_states(R, t)
+    dR, dp, dv, Jrot, Jpos, Jvel, dt, info = ba._unpack(imu[0])
+    d = np.array([0.1, -0.2, 0.05])
+    v2 = vel.copy(); v2[0] += d
+    r = ba.inertial_residual(R, t, v2, bias, bh, imu, g, 0)
+    np.testing.assert_allclose(r[3:6], -Rb[0].T @ d * dt, atol=1e-12)
+    np.testing.assert_allclose(r[6:9], -Rb[0].T @ d, atol=1e-12)
+    db = np.array([0, 0, 0, 0.02, -0.01, 0.03])
+    b2 = bias + db
+    r = ba.inertial_residual(R, t, vel, b2, bh, imu, g, 0)
+    np.testing.assert_allclose(r[12:], 0.0, atol=1e-12)
+    np.testing.assert_allclose(r[3:6], -Jpos @ db, atol=1e-12)
+    phi = np.array([0.01, -0.02, 0.015])
+    R2 = R.copy(); R2[1] = (Rb[1] @ ba.so3_exp(phi)).T          # R_j <- R_j Exp(phi)
+    r = ba.inertial_residual(R2, t - 0 * t, vel, bias, bh, imu, g, 0)
+    np.testing.assert_allclose(r[:3], phi, atol=1e-9)
+
+
+def test_visual_inertial_gauss_newton_recovers_the_window():
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(7, K=5, h=6, w=8)
+    targets = _exact_targets(R, t, disp, intr, edges)
+    rng = np.random.default_rng(8)
+    n_fixed = 1
+    dx0 = np.concatenate([rng.normal(0, 0.01, (4, 6)), rng.normal(0, 0.05, (4, 3)), rng.normal(0, 0.005, (4, 6))], 1)
+    R1, t1, d1, v1, b1 = ba.apply_step_vi(R, t, disp, vel, bias, dx0, rng.normal(0, 0.01, disp.shape), n_fixed)
+    costs = []
+    for _ in range(8):
+        dx, dd, cost = ba.lm_step_vi(R1, t1, d1, v1, b1, bh, intr, edges, targets, wts, imu, g, n_fixed,
+                                     lam=1e-6, eps=1e-8)
+        costs.append(cost)
+        R1, t1, d1, v1, b1 = ba.apply_step_vi(R1, t1, d1, v1, b1, dx, dd, n_fixed)
+    assert costs[-1] < 1e-10 * costs[0]
+    np.testing.assert_allclose(d1, disp, atol=1e-7)
+    np.testing.assert_allclose(t1, t, atol=1e-7)
+    np.testing.assert_allclose(v1, vel, atol=1e-6)
+    np.testing.assert_allclose(b1, bias, atol=1e-7)
