@@ -500,16 +500,21 @@ def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
     """One Levenberg-Marquardt step of the dense visual bundle adjustment
     (Eq. 2 / Eq. 4) on a 16-keyframe window at the tracker's 1/8 resolution of
     640x480 (60 x 80 inverse depths per keyframe), every pair of keyframes at
-    most 3 apart as an edge; device time of gs_ba_step by graph replay."""
+    most 3 apart as an edge; device time of gs_ba_step by graph replay.  Also
+    the same window with the inertial factor of Eq. 3 between consecutive
+    keyframes and one keyframe fixed (225 pose, velocity and bias unknowns)."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     from paper_2512_02293_gb300 import synth
-    R, t, disp, intr, edges, wts = synth.ba_scene(21, K=K, h=h, w=w, f=70.0, window=window)
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(21, K=K, h=h, w=w, f=70.0, window=window)
     rng = np.random.default_rng(22)
     targets = rng.normal(0.0, 0.5, (len(edges), h, w, 2)) + np.stack(np.meshgrid(np.arange(w) + 0.5,
                                                                              np.arange(h) + 0.5), -1)
     win = G.BAWindow(R, t, disp, intr, edges, targets, wts, 2, device)
     m = graph_time_ms(lambda: G.gs_ba_step(win, 1e-3, 1e-3), steps=steps)
+    win_vi = G.BAWindow(R, t, disp, intr, edges, targets, wts, 1, device, imu=imu, vel=vel, bias=bias, bias_hat=bh,
+                        gravity=g)
+    m_vi = graph_time_ms(lambda: G.gs_ba_step(win_vi, 1e-3, 1e-3), steps=steps)
     n_res = len(edges) * h * w
     # algorithmic bytes: every residual's target and weight pair read once, every
     # inverse depth read and written once (the poses are negligible)
@@ -525,7 +530,10 @@ def ba_run(device, K=16, h=60, w=80, window=3, steps=10):
                                  f"inverse depth ({nbytes} B per step)",
                          "peak_basis": f"{kind} hbm_gbs",
                          "note": "four dependent launches and a one-CTA solve of the 84 x 84 reduced system: "
-                                 "the step is latency bound at this size"}}
+                                 "the step is latency bound at this size"},
+            "visual_inertial": {"workload": f"the same window with the inertial factor between the {K - 1} "
+                                            f"consecutive pairs, 1 keyframe fixed (225 x 225 reduced system)",
+                                "ms_per_step": round(m_vi, 4), "status": int(win_vi.status[0].item())}}
 
 
 def mlp_kernels_run(device, n=2_457_600, steps=5):

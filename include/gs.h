@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 1
+#define GS_ABI_VERSION 2
 #define GS_MAX_VIEWS 32
 
 typedef enum gs_status {
@@ -432,17 +432,39 @@ typedef struct gs_ba_problem {
                                 GS_ERR_INVALID_ARG, more than 15 edges out of one
                                 keyframe GS_ERR_UNSUPPORTED, a reduced system
                                 that is not positive definite GS_ERR_NUMERIC */
+    /* Inertial factor (Eq. 3) between consecutive keyframes k, k + 1; imu NULL
+     * = vision only.  The camera frame is taken as the IMU body frame.  With the
+     * factor, every free keyframe also has a velocity and a bias variable.
+     * imu: [K - 1][GS_BA_IMU_FLOATS] per pair: dR (9, row-major), dp (3), dv (3),
+     *      J_rot (9, w.r.t. the gyro bias), J_pos (18, 3 x 6 w.r.t. the bias
+     *      (b_g, b_a)), J_vel (18), dt (1), information (225, 15 x 15 over
+     *      (r_rot, r_pos, r_vel, r_bias)); the velocity term's bias correction
+     *      takes the full bias, as the position term's does.
+     * vel: [K][3] world-frame velocities, updated; bias: [K][6] (b_g, b_a),
+     * updated; bias_hat: [K][6] the biases the pre-integration was linearised
+     * at; gravity: g in the world frame. */
+    const float* imu;
+    float* vel;
+    float* bias;
+    const float* bias_hat;
+    float gravity[3];
 } gs_ba_problem;
 
-/* Workspace bytes of gs_ba_step. */
-size_t gs_ba_workspace_size(int32_t n_keyframes, int32_t n_edges, int32_t height, int32_t width, int32_t n_fixed);
+#define GS_BA_IMU_FLOATS 286
+
+/* Workspace bytes of gs_ba_step (inertial != 0: with the inertial factor). */
+size_t gs_ba_workspace_size(int32_t n_keyframes, int32_t n_edges, int32_t height, int32_t width, int32_t n_fixed,
+                            int32_t inertial);
 
 /* One step; *cost (device float) receives sum w r^2 at the poses and inverse
- * depths before the step.  At most 31 free poses (n_keyframes - n_fixed <= 31)
- * and at most 15 edges with the same source keyframe.
+ * depths (and the inertial terms) before the step.  At most 31 free keyframes
+ * (15 with the inertial factor) and at most 15 edges with the same source
+ * keyframe.  With the inertial factor the first n_fixed keyframes keep their
+ * pose, velocity and bias.
  * Errors: GS_ERR_INVALID_ARG on NULL pointers, bad sizes, a too-small or
- * misaligned workspace, lambda < 0, eps < 0; GS_ERR_UNSUPPORTED above 31 free
- * poses. */
+ * misaligned workspace, lambda < 0, eps < 0, imu given without vel, bias or
+ * bias_hat; GS_ERR_UNSUPPORTED above 31 free keyframes (15 with the inertial
+ * factor). */
 int32_t gs_ba_step(const gs_ba_problem* problem, float lambda, float eps, float* cost, void* ws, size_t ws_bytes,
                    void* stream);
 

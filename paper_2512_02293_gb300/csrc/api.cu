@@ -356,9 +356,9 @@ int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, c
                                            d_status, static_cast<cudaStream_t>(stream)));
 }
 
-size_t gs_ba_workspace_size(int32_t K, int32_t E, int32_t h, int32_t w, int32_t n_fixed) {
+size_t gs_ba_workspace_size(int32_t K, int32_t E, int32_t h, int32_t w, int32_t n_fixed, int32_t inertial) {
     if (K < 1 || E < 0 || h < 1 || w < 1 || n_fixed < 0 || n_fixed > K) return 0;
-    return ba_workspace(K, E, h * w, 6 * (K - n_fixed));
+    return ba_workspace(K, E, h * w, (inertial ? 15 : 6) * (K - n_fixed));
 }
 
 int32_t gs_ba_step(const gs_ba_problem* pr, float lambda, float eps, float* cost, void* ws, size_t ws_bytes,
@@ -373,8 +373,13 @@ int32_t gs_ba_step(const gs_ba_problem* pr, float lambda, float eps, float* cost
         return GS_ERR_INVALID_ARG;
     if (!pr->poses || !pr->disp || !pr->status || (E > 0 && (!pr->targets || !pr->weights || !pr->ii || !pr->jj)))
         return GS_ERR_INVALID_ARG;
-    if (K - pr->n_fixed > 31) return GS_ERR_UNSUPPORTED;
-    if (ws == nullptr || !aligned(ws, 256) || ws_bytes < ba_workspace(K, E, h * w, 6 * (K - pr->n_fixed)))
+    const bool inertial = pr->imu != nullptr;
+    if (inertial && (!pr->vel || !pr->bias || !pr->bias_hat)) return GS_ERR_INVALID_ARG;
+    if (inertial && (!isfinite(pr->gravity[0]) || !isfinite(pr->gravity[1]) || !isfinite(pr->gravity[2])))
+        return GS_ERR_INVALID_ARG;
+    if (K - pr->n_fixed > (inertial ? 15 : 31)) return GS_ERR_UNSUPPORTED;
+    const int bs = inertial ? 15 : 6;
+    if (ws == nullptr || !aligned(ws, 256) || ws_bytes < ba_workspace(K, E, h * w, bs * (K - pr->n_fixed)))
         return GS_ERR_INVALID_ARG;
     return cuda_status(launch_ba_step(*pr, lambda, eps, cost, ws, static_cast<cudaStream_t>(stream)));
 }

@@ -48,7 +48,13 @@ struct BaDev {
     const float* weights;  // [E][P][2]
     const int32_t* ii;
     const int32_t* jj;
-    int K, E, h, w, P, n_fixed, n;   // n = 6 (K - n_fixed)
+    int K, E, h, w, P, n_fixed, n;   // n = bs (K - n_fixed)
+    int bs;                          // variables per free keyframe: 6 (pose), 15 with the inertial factor
+    const float* imu;                // [K - 1][GS_BA_IMU_FLOATS] or null
+    float* vel;                      // [K][3]
+    float* bias;                     // [K][6]
+    const float* bias_hat;           // [K][6]
+    float gx, gy, gz;                // gravity (world)
     float fx, fy, cx, cy;
     float* rec;            // [E][P][kRec]
     float* SB;             // [n][n] B (undamped)
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
     const float tot = block_sum_vals(v, s_all);
     const int t = threadIdx.x;
     if (t < kTermVals) {
-        const int bi = 6 * (i - b.n_fixed), bj = 6 * (j - b.n_fixed);
+        const int bi = b.bs * (i - b.n_fixed), bj = b.bs * (j - b.n_fixed);
         if (t < 21) {
             if (i >= b.n_fixed) {
                 int a = 0, c = t, rem = t;          // t -> (a, c), c >= a
@@ -201,6 +207,219 @@ __global__ void __launch_bounds__(kTermThreads) k_ba_terms(BaDev b) {
         } else {
             atomicAdd(b.cost, tot);
         }
+    }
+}
+
+// ------------------------------------------------------------ inertial factor
+// Eq. 3 between consecutive keyframes i, j = i + 1, on the body-to-world rotation
+// R_i = R_cw,i^T, position p_i = -R_i t_cw,i, velocity v_i and bias b_i = (b_g, b_a)
+// (the camera frame taken as the body frame).  Under the perturbation of the
+// visual part (T_cw <- Exp(xi) T_cw, xi = (rho, phi)) R_i <- R_i Exp(-phi) and
+// p_i <- p_i - R_i rho to first order; v and b are additive.  With E = R_i^T R_j,
+// A = dR Exp(J_rot db_g), M = A^T E, r_rot = Log(M), J_r the right Jacobian of
+// SO(3) and Jri = J_r(r_rot)^-1:
+//   d r_rot / d phi_i = Jri M^T A^T,  d r_rot / d phi_j = -Jri,
+//   d r_rot / d b_g,i = -Jri M^T J_r(J_rot db_g) J_rot,
+//   r_pos = q - (dp + J_pos db), q = R_i^T (p_j - p_i - v_i dt - g dt^2 / 2):
+//     d / d rho_i = I, d / d phi_i = -[q]x, d / d rho_j = -E, d / d v_i = -R_i^T dt,
+//     d / d b_i = -J_pos,
+//   r_vel = q' - (dv + J_vel db), q' = R_i^T (v_j - v_i - g dt):
+//     d / d phi_i = -[q']x, d / d v_i = -R_i^T, d / d v_j = R_i^T, d / d b_i = -J_vel,
+//   r_bias = b_j - b_i.
+// Keyframe variables (15): rho 0-2, phi 3-5, v 6-8, b_g 9-11, b_a 12-14.
+
+__device__ __forceinline__ void skew3(const float* w, float* K) {
+    K[0] = 0.f;   K[1] = -w[2]; K[2] = w[1];
+    K[3] = w[2];  K[4] = 0.f;   K[5] = -w[0];
+    K[6] = -w[1]; K[7] = w[0];  K[8] = 0.f;
+}
+__device__ __forceinline__ void mat3mul(const float* A, const float* B, float* C) {     // C = A B
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+__device__ __forceinline__ void mat3tmul(const float* A, const float* B, float* C) {    // C = A^T B
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) C[3 * r + c] = A[r] * B[c] + A[3 + r] * B[3 + c] + A[6 + r] * B[6 + c];
+}
+// I + a K + b K^2 for K = [w]x
+__device__ __forceinline__ void so3_poly(const float* w, float a, float bcoef, float* M) {
+    float K[9], K2[9];
+    skew3(w, K);
+    mat3mul(K, K, K2);
+    for (int k = 0; k < 9; k++) M[k] = (k % 4 == 0 ? 1.f : 0.f) + a * K[k] + bcoef * K2[k];
+}
+__device__ __forceinline__ void so3_exp_f(const float* w, float* M) {
+    const float th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2], th = sqrtf(th2);
+    const float a = th < 1e-4f ? 1.f - th2 / 6.f : sinf(th) / th;
+    const float bc = th < 1e-4f ? 0.5f - th2 / 24.f : (1.f - cosf(th)) / th2;
+    so3_poly(w, a, bc, M);
+}
+__device__ __forceinline__ void so3_log_f(const float* M, float* w) {
+    const float c = fminf(1.f, fmaxf(-1.f, 0.5f * (M[0] + M[4] + M[8] - 1.f)));
+    const float th = acosf(c);
+    const float f = th < 1e-4f ? 0.5f * (1.f + th * th / 6.f) : 0.5f * th / sinf(th);
+    w[0] = f * (M[7] - M[5]); w[1] = f * (M[2] - M[6]); w[2] = f * (M[3] - M[1]);
+}
+// right Jacobian J_r(x) = I - (1 - cos t) / t^2 [x]x + (t - sin t) / t^3 [x]x^2
+__device__ __forceinline__ void so3_jr(const float* x, float* J) {
+    const float th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2], th = sqrtf(th2);
+    const float a = th < 1e-3f ? 0.5f - th2 / 24.f : (1.f - cosf(th)) / th2;
+    const float bc = th < 1e-3f ? 1.f / 6.f - th2 / 120.f : (th - sinf(th)) / (th2 * th);
+    so3_poly(x, -a, bc, J);
+}
+// its inverse: I + [r]x / 2 + (1 / t^2 - (1 + cos t) / (2 t sin t)) [r]x^2
+__device__ __forceinline__ void so3_jr_inv(const float* r, float* J) {
+    const float th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], th = sqrtf(th2);
+    const float bc = th < 1e-3f ? 1.f / 12.f + th2 / 720.f : 1.f / th2 - (1.f + cosf(th)) / (2.f * th * sinf(th));
+    so3_poly(r, 0.5f, bc, J);
+}
+
+constexpr int kImuFloats = GS_BA_IMU_FLOATS;
+constexpr int kInerThreads = 256;
+
+// One CTA per consecutive pair (i, i + 1): thread 0 forms the residual r (15) and
+// the Jacobian J (15 x 30) in shared memory; then H += J^T W J, rhs -= J^T W r and
+// the cost += r^T W r over the free keyframes' blocks.
+__global__ void __launch_bounds__(kInerThreads) k_ba_inertial(BaDev b) {
+    __shared__ float sJ[15][30], sWJ[15][30], sW[15][15], sr[15], sWr[15];
+    const int i = blockIdx.x, j = i + 1, t = threadIdx.x;
+    const float* rec = b.imu + (size_t)i * kImuFloats;
+    for (int k = t; k < 225; k += kInerThreads) sW[k / 15][k % 15] = rec[61 + k];
+    for (int k = t; k < 450; k += kInerThreads) sJ[k / 30][k % 30] = 0.f;
+    __syncthreads();
+    if (t == 0) {
+        const float* dR = rec;
+        const float* dp = rec + 9;
+        const float* dv = rec + 12;
+        const float* Jrot = rec + 15;
+        const float* Jpos = rec + 24;        // 3 x 6
+        const float* Jvel = rec + 42;        // 3 x 6
+        const float dt = rec[60];
+        // body-to-world rotations and positions from the world-to-camera poses
+        const float* Pi = b.poses + 12 * i;
+        const float* Pj = b.poses + 12 * j;
+        float Ri[9], Rj[9], pi_[3], pj_[3];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) { Ri[3 * r + c] = Pi[3 * c + r]; Rj[3 * r + c] = Pj[3 * c + r]; }
+        for (int r = 0; r < 3; r++) {
+            pi_[r] = -(Ri[3 * r] * Pi[9] + Ri[3 * r + 1] * Pi[10] + Ri[3 * r + 2] * Pi[11]);
+            pj_[r] = -(Rj[3 * r] * Pj[9] + Rj[3 * r + 1] * Pj[10] + Rj[3 * r + 2] * Pj[11]);
+        }
+        const float* vi = b.vel + 3 * i;
+        const float* vj = b.vel + 3 * j;
+        const float* bi = b.bias + 6 * i;
+        const float* bj = b.bias + 6 * j;
+        float db[6];
+        for (int k = 0; k < 6; k++) db[k] = bi[k] - b.bias_hat[6 * i + k];
+        const float g[3] = {b.gx, b.gy, b.gz};
+        // rotation
+        float jd[3], Ej[9], A[9], E[9], M[9], rr[3], Jri[9];
+        for (int r = 0; r < 3; r++) jd[r] = Jrot[3 * r] * db[0] + Jrot[3 * r + 1] * db[1] + Jrot[3 * r + 2] * db[2];
+        so3_exp_f(jd, Ej);
+        mat3mul(dR, Ej, A);
+        mat3tmul(Ri, Rj, E);
+        mat3tmul(A, E, M);
+        so3_log_f(M, rr);
+        so3_jr_inv(rr, Jri);
+        float MtAt[9], T1[9], Jrd[9], T2[9];
+        {
+            float AM[9];
+            mat3mul(A, M, AM);                          // (A M)^T = M^T A^T
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) MtAt[3 * r + c] = AM[3 * c + r];
+        }
+        mat3mul(Jri, MtAt, T1);                         // d r_rot / d phi_i
+        so3_jr(jd, Jrd);
+        {
+            float JrdJrot[9], Mt[9];
+            mat3mul(Jrd, Jrot, JrdJrot);
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) Mt[3 * r + c] = M[3 * c + r];
+            float MtJ[9];
+            mat3mul(Mt, JrdJrot, MtJ);
+            mat3mul(Jri, MtJ, T2);                      // -(d r_rot / d b_g,i)
+        }
+        for (int r = 0; r < 3; r++) {
+            sr[r] = rr[r];
+            for (int c = 0; c < 3; c++) {
+                sJ[r][3 + c] = T1[3 * r + c];
+                sJ[r][15 + 3 + c] = -Jri[3 * r + c];
+                sJ[r][9 + c] = -T2[3 * r + c];
+            }
+        }
+        // position and velocity
+        float sp[3], sv[3], q[3], qv[3];
+        for (int r = 0; r < 3; r++) {
+            sp[r] = pj_[r] - pi_[r] - vi[r] * dt - 0.5f * g[r] * dt * dt;
+            sv[r] = vj[r] - vi[r] - g[r] * dt;
+        }
+        for (int r = 0; r < 3; r++) {
+            q[r] = Ri[r] * sp[0] + Ri[3 + r] * sp[1] + Ri[6 + r] * sp[2];
+            qv[r] = Ri[r] * sv[0] + Ri[3 + r] * sv[1] + Ri[6 + r] * sv[2];
+        }
+        float Kq[9], Kqv[9];
+        skew3(q, Kq);
+        skew3(qv, Kqv);
+        for (int r = 0; r < 3; r++) {
+            float cp = 0.f, cv = 0.f;
+            for (int k = 0; k < 6; k++) { cp += Jpos[6 * r + k] * db[k]; cv += Jvel[6 * r + k] * db[k]; }
+            sr[3 + r] = q[r] - (dp[r] + cp);
+            sr[6 + r] = qv[r] - (dv[r] + cv);
+            for (int c = 0; c < 3; c++) {
+                sJ[3 + r][c] = r == c ? 1.f : 0.f;                      // rho_i
+                sJ[3 + r][3 + c] = -Kq[3 * r + c];                      // phi_i
+                sJ[3 + r][15 + c] = -E[3 * r + c];                      // rho_j
+                sJ[3 + r][6 + c] = -Ri[3 * c + r] * dt;                  // v_i
+                sJ[6 + r][3 + c] = -Kqv[3 * r + c];                     // phi_i
+                sJ[6 + r][6 + c] = -Ri[3 * c + r];                      // v_i
+                sJ[6 + r][15 + 6 + c] = Ri[3 * c + r];                  // v_j
+            }
+            for (int k = 0; k < 6; k++) {
+                sJ[3 + r][9 + k] = -Jpos[6 * r + k];
+                sJ[6 + r][9 + k] = -Jvel[6 * r + k];
+            }
+        }
+        // bias smoothness
+        for (int k = 0; k < 6; k++) {
+            sr[9 + k] = bj[k] - bi[k];
+            sJ[9 + k][9 + k] = -1.f;
+            sJ[9 + k][15 + 9 + k] = 1.f;
+        }
+    }
+    __syncthreads();
+    // W J and W r
+    for (int k = t; k < 15 * 30 + 15; k += kInerThreads) {
+        const int r = k < 450 ? k / 30 : k - 450, c = k < 450 ? k % 30 : 0;
+        float acc = 0.f;
+        for (int m = 0; m < 15; m++) acc += sW[r][m] * (k < 450 ? sJ[m][c] : sr[m]);
+        if (k < 450) sWJ[r][c] = acc;
+        else sWr[r] = acc;
+    }
+    __syncthreads();
+    // J^T W J into the free blocks, J^T W r into the right-hand side, r^T W r into the cost
+    auto row_of = [&](int c) {
+        const int kf = c < 15 ? i : j;
+        return kf >= b.n_fixed ? b.bs * (kf - b.n_fixed) + c % 15 : -1;
+    };
+    for (int k = t; k < 30 * 30; k += kInerThreads) {
+        const int a = k / 30, c = k % 30;
+        const int ra = row_of(a), rc = row_of(c);
+        if (ra < 0 || rc < 0) continue;
+        float acc = 0.f;
+        for (int m = 0; m < 15; m++) acc += sJ[m][a] * sWJ[m][c];
+        atomicAdd(b.SB + (size_t)ra * b.n + rc, acc);
+    }
+    if (t < 30) {
+        const int ra = row_of(t);
+        if (ra >= 0) {
+            float acc = 0.f;
+            for (int m = 0; m < 15; m++) acc += sJ[m][t] * sWr[m];
+            atomicAdd(b.rhs + ra, -acc);
+        }
+    } else if (t == 32) {
+        float acc = 0.f;
+        for (int m = 0; m < 15; m++) acc += sr[m] * sWr[m];
+        atomicAdd(b.cost, acc);
     }
 }
 
@@ -341,14 +560,14 @@ __global__ void __launch_bounds__(kSchurThreads) k_ba_schur(BaDev b, float lambd
             if (a > c || c == m + 1) continue;         // the lower element of a diagonal tile; the zero row
             const int pa = slot_pose(a / 6);
             if (pa < b.n_fixed) continue;
-            const int ra = 6 * (pa - b.n_fixed) + a % 6;
+            const int ra = b.bs * (pa - b.n_fixed) + a % 6;
             if (c == m) {                               // E C'^-1 g_d
                 atomicAdd(b.rhs + ra, acc[s][xy]);
                 continue;
             }
             const int pc = slot_pose(c / 6);
             if (pc < b.n_fixed) continue;
-            const int rc = 6 * (pc - b.n_fixed) + c % 6;
+            const int rc = b.bs * (pc - b.n_fixed) + c % 6;
             atomicAdd(b.SS + (size_t)ra * b.n + rc, -acc[s][xy]);
             if (a != c) atomicAdd(b.SS + (size_t)rc * b.n + ra, -acc[s][xy]);
         }
@@ -367,6 +586,7 @@ __global__ void __launch_bounds__(kSchurThreads) k_ba_schur(BaDev b, float lambd
 //   (B) A22 -= L21 U12.
 constexpr int kSolveThreads = 512;
 constexpr int kNb = 6;
+constexpr int kMaxSolve = 228;          // largest padded system: 15 free keyframes with the inertial factor
 
 // LU of a 6 x 6 block in registers: unit-lower multipliers below the diagonal,
 // U on and above it; inv[k] = 1 / U_kk.
@@ -384,34 +604,42 @@ __device__ __forceinline__ void lu6(float (&a)[kNb][kNb], float (&inv)[kNb]) {
     }
 }
 
-// CPL: columns of a lane in (B), ceil((n + 1 - 6) / 32), at most 6 (n <= 186)
+// CPL: columns of a lane in (B), ceil((n + 1 - 6) / 32) for the padded n, at most 7 (n <= 228)
 template <int CPL>
 __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambda, float eps) {
     extern __shared__ float sm[];
-    const int n = b.n, ld = n + 1, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // the system is padded to a multiple of the panel width with identity rows
+    const int n0 = b.n, n = (n0 + kNb - 1) / kNb * kNb, ld = n + 1, t = threadIdx.x, warp = t >> 5, lane = t & 31;
     float* A = sm;                       // [n][n + 1]
     float* x = sm + (size_t)n * ld;      // [n]
     __shared__ int s_bad;
-    __shared__ float s_inv[6 * 31];      // reciprocals of the pivots
+    __shared__ float s_inv[kMaxSolve];   // reciprocals of the pivots
     // eight loads of each matrix in flight per thread before the stores
-    for (int k0 = 0; k0 < n * n; k0 += 8 * kSolveThreads) {
+    for (int k0 = 0; k0 < n0 * n0; k0 += 8 * kSolveThreads) {
         float vb[8], vs[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             const int k = k0 + u * kSolveThreads + t;
-            vb[u] = k < n * n ? b.SB[k] : 0.f;
-            vs[u] = k < n * n ? b.SS[k] : 0.f;
+            vb[u] = k < n0 * n0 ? b.SB[k] : 0.f;
+            vs[u] = k < n0 * n0 ? b.SS[k] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             const int k = k0 + u * kSolveThreads + t;
-            if (k < n * n) {
-                const int r = k / n, c = k - r * n;
+            if (k < n0 * n0) {
+                const int r = k / n0, c = k - r * n0;
                 A[(size_t)r * ld + c] = vs[u] + (r == c ? (1.0f + lambda) * vb[u] + eps : vb[u]);
             }
         }
     }
-    for (int k = t; k < n; k += kSolveThreads) A[(size_t)k * ld + n] = b.rhs[k];
+    const int pad = n - n0;
+    for (int k = t; k < pad * n; k += kSolveThreads) {                 // padding rows: identity
+        const int r = n0 + k / n, c = k % n;
+        A[(size_t)r * ld + c] = (r == c) ? 1.f : 0.f;
+    }
+    for (int k = t; k < n0 * pad; k += kSolveThreads)                  // padding columns of the real rows
+        A[(size_t)(k / pad) * ld + n0 + k % pad] = 0.f;
+    for (int k = t; k < n; k += kSolveThreads) A[(size_t)k * ld + n] = k < n0 ? b.rhs[k] : 0.f;
     if (t == 0) s_bad = 0;
     __syncthreads();
     for (int kb = 0; kb < n; kb += kNb) {
@@ -543,13 +771,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambd
             }
             __syncwarp();
         }
-        for (int k = lane; k < n; k += 32) b.dxi[k] = x[k];
+        for (int k = lane; k < n0; k += 32) b.dxi[k] = x[k];
         if (lane == 0 && s_bad) atomicCAS(b.status, 0, GS_ERR_NUMERIC);
     }
 }
 
 __device__ __forceinline__ float pose_dxi(const BaDev& b, int k, int c) {
-    return k >= b.n_fixed ? b.dxi[6 * (k - b.n_fixed) + c] : 0.f;
+    return k >= b.n_fixed ? b.dxi[b.bs * (k - b.n_fixed) + c] : 0.f;
 }
 
 // dd_p = C'_p^-1 (-g_d,p - sum_e E(e, p) . [dxi_i, dxi_j]) for every pixel of every
@@ -614,6 +842,10 @@ __global__ void __launch_bounds__(kUpdateThreads) k_ba_update(BaDev b, float lam
                 for (int m = 0; m < 3; m++) kk += Kx[3 * r + m] * Kx[3 * m + c];
                 Rp[3 * r + c] = (r == c ? 1.f : 0.f) + A * Kx[3 * r + c] + Bc * kk;
             }
+        if (b.bs == 15) {
+            for (int c = 0; c < 3; c++) b.vel[3 * i + c] += b.dxi[15 * (i - b.n_fixed) + 6 + c];
+            for (int c = 0; c < 6; c++) b.bias[6 * i + c] += b.dxi[15 * (i - b.n_fixed) + 9 + c];
+        }
         // no CTA of this kernel reads the poses (only dxi), so keyframe i's pose can
         // be rewritten here by one thread
         float* P = b.poses + 12 * i;
@@ -641,7 +873,11 @@ cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, flo
     b.poses = pr.poses; b.disp = pr.disp; b.targets = pr.targets; b.weights = pr.weights;
     b.ii = pr.ii; b.jj = pr.jj;
     b.K = pr.n_keyframes; b.E = pr.n_edges; b.h = pr.height; b.w = pr.width; b.P = pr.height * pr.width;
-    b.n_fixed = pr.n_fixed; b.n = 6 * (pr.n_keyframes - pr.n_fixed);
+    b.n_fixed = pr.n_fixed;
+    b.imu = pr.imu; b.vel = pr.vel; b.bias = pr.bias; b.bias_hat = pr.bias_hat;
+    b.gx = pr.gravity[0]; b.gy = pr.gravity[1]; b.gz = pr.gravity[2];
+    b.bs = pr.imu != nullptr ? 15 : 6;
+    b.n = b.bs * (pr.n_keyframes - pr.n_fixed);
     b.fx = pr.fx; b.fy = pr.fy; b.cx = pr.cx; b.cy = pr.cy;
     char* p = static_cast<char*>(ws);
     b.rec = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * (size_t)b.E * b.P * kRec, 256);
@@ -657,13 +893,18 @@ cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, flo
     cudaError_t e = cudaMemsetAsync(b.SB, 0, zero_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cost, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
-    if (b.E > 0) {
+    if (b.imu != nullptr && b.K > 1)
+        k_ba_inertial<<<(unsigned)(b.K - 1), kInerThreads, 0, s>>>(b);
+    if (b.E > 0 || b.imu != nullptr) {
+        if (b.E > 0)
         k_ba_terms<<<dim3((unsigned)ceil_div(b.P, kTermThreads * kTermPix), (unsigned)b.E), kTermThreads, 0, s>>>(b);
         if (b.n > 0) {
-            k_ba_schur<<<dim3((unsigned)ceil_div(b.P, kSchurChunk), (unsigned)b.K), kSchurThreads, 0, s>>>(b, lambda,
-                                                                                                     eps);
-            const size_t smem = sizeof(float) * ((size_t)b.n * (b.n + 1) + b.n);
-            const int cpl = (int)ceil_div((int64_t)b.n + 1 - kNb, 32);
+            if (b.E > 0)
+                k_ba_schur<<<dim3((unsigned)ceil_div(b.P, kSchurChunk), (unsigned)b.K), kSchurThreads, 0, s>>>(
+                    b, lambda, eps);
+            const int n_pad = (int)ceil_div(b.n, kNb) * kNb;
+            const size_t smem = sizeof(float) * ((size_t)n_pad * (n_pad + 1) + n_pad);
+            const int cpl = (int)ceil_div((int64_t)n_pad + 1 - kNb, 32);
             switch (cpl) {
 #define GS_SOLVE(C)                                                                                      \
     case C:                                                                                              \
@@ -677,6 +918,7 @@ cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, flo
                 GS_SOLVE(4)
                 GS_SOLVE(5)
                 GS_SOLVE(6)
+                GS_SOLVE(7)
 #undef GS_SOLVE
                 default: return cudaErrorInvalidValue;
             }

@@ -89,7 +89,12 @@ class gs_ba_problem(ctypes.Structure):
                 ("weights", ctypes.c_void_p), ("ii", ctypes.c_void_p), ("jj", ctypes.c_void_p),
                 ("n_keyframes", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("width", ctypes.c_int32), ("n_fixed", ctypes.c_int32), ("fx", ctypes.c_float),
-                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("status", ctypes.c_void_p)]
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("status", ctypes.c_void_p),
+                ("imu", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("bias", ctypes.c_void_p),
+                ("bias_hat", ctypes.c_void_p), ("gravity", ctypes.c_float * 3)]
+
+
+GS_BA_IMU_FLOATS = 286
 
 
 class gs_mlp_params(ctypes.Structure):
@@ -162,7 +167,7 @@ def load_library(path: str | None = None):
     lib.gs_extract_patches.restype = ctypes.c_int32
     lib.gs_extract_patches.argtypes = [V, V, V, V, ctypes.c_int64, V, V, V]
     lib.gs_ba_workspace_size.restype = ctypes.c_size_t
-    lib.gs_ba_workspace_size.argtypes = [ctypes.c_int32] * 5
+    lib.gs_ba_workspace_size.argtypes = [ctypes.c_int32] * 6
     lib.gs_ba_step.restype = ctypes.c_int32
     lib.gs_ba_step.argtypes = [V, ctypes.c_float, ctypes.c_float, V, V, ctypes.c_size_t, V]
     lib.gs_loop_closure_update.restype = ctypes.c_int32
@@ -170,7 +175,7 @@ def load_library(path: str | None = None):
     lib.gs_insert_gaussians.restype = ctypes.c_int32
     lib.gs_insert_gaussians.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_float, V, V, ctypes.c_int64,
                                         ctypes.c_int32, V, V]
-    if lib.gs_abi_version() != 1:
+    if lib.gs_abi_version() != 2:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
         _lib = lib
@@ -582,9 +587,13 @@ def gs_loop_closure_update(g: "Gaussians", anchor, pose_before, pose_after, scal
 class BAWindow:
     """Device state of a bundle-adjustment window (see gs_ba_step): poses
     [K, 12] (world-to-camera R row-major, t), inverse depths [K, h, w], targets
-    and weights [E, h, w, 2], edges ii / jj [E], intrinsics of the grid."""
+    and weights [E, h, w, 2], edges ii / jj [E], intrinsics of the grid.  With
+    `imu` ([K - 1, GS_BA_IMU_FLOATS] pre-integration records) the window also
+    holds velocities [K, 3], biases [K, 6] (b_g, b_a), the linearisation biases
+    [K, 6] and gravity, and each step includes the inertial factor of Eq. 3."""
 
-    def __init__(self, R, t, disp, intr, edges, targets, weights, n_fixed, device="cuda"):
+    def __init__(self, R, t, disp, intr, edges, targets, weights, n_fixed, device="cuda", imu=None, vel=None,
+                 bias=None, bias_hat=None, gravity=None):
         import torch
         f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
         K, h, w = np.asarray(disp).shape
@@ -600,18 +609,32 @@ class BAWindow:
         self.n_fixed = int(n_fixed)
         self.status = torch.zeros(4, device=device, dtype=torch.int32)
         self.cost = torch.zeros(1, device=device)
-        nbytes = gs_ba_workspace_size(K, self.E, h, w, n_fixed)
+        self.imu = None
+        if imu is not None:
+            if vel is None or bias is None or bias_hat is None or gravity is None:
+                raise ValueError("the inertial factor needs velocities, biases, linearisation biases and gravity")
+            self.imu = f(np.asarray(imu).reshape(K - 1, GS_BA_IMU_FLOATS))
+            self.vel = f(np.asarray(vel).reshape(K, 3))
+            self.bias = f(np.asarray(bias).reshape(K, 6))
+            self.bias_hat = f(np.asarray(bias_hat).reshape(K, 6))
+            self.gravity = tuple(float(x) for x in np.asarray(gravity).reshape(3))
+        nbytes = gs_ba_workspace_size(K, self.E, h, w, n_fixed, self.imu is not None)
         self.ws = torch.empty((nbytes + 255) // 256 * 64 + 64, device=device, dtype=torch.float32)
 
     def struct(self):
         fx, fy, cx, cy = self.intr
-        return gs_ba_problem(_ptr(self.poses), _ptr(self.disp), _ptr(self.targets), _ptr(self.weights), _ptr(self.ii),
-                             _ptr(self.jj), self.K, self.E, self.h, self.w, self.n_fixed, fx, fy, cx, cy,
-                             _ptr(self.status))
+        pr = gs_ba_problem(_ptr(self.poses), _ptr(self.disp), _ptr(self.targets), _ptr(self.weights), _ptr(self.ii),
+                           _ptr(self.jj), self.K, self.E, self.h, self.w, self.n_fixed, fx, fy, cx, cy,
+                           _ptr(self.status))
+        if self.imu is not None:
+            pr.imu, pr.vel, pr.bias, pr.bias_hat = (_ptr(self.imu), _ptr(self.vel), _ptr(self.bias),
+                                                    _ptr(self.bias_hat))
+            pr.gravity[:] = self.gravity
+        return pr
 
 
-def gs_ba_workspace_size(K: int, E: int, h: int, w: int, n_fixed: int) -> int:
-    return int(load_library().gs_ba_workspace_size(K, E, h, w, n_fixed))
+def gs_ba_workspace_size(K: int, E: int, h: int, w: int, n_fixed: int, inertial: bool = False) -> int:
+    return int(load_library().gs_ba_workspace_size(K, E, h, w, n_fixed, int(bool(inertial))))
 
 
 def gs_ba_step(win: BAWindow, lam: float = 1e-4, eps: float = 1e-4, stream=None):
