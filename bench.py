@@ -207,13 +207,14 @@ def bwd_ctas_per_sm(step, tile) -> int:
 def launches_per_step(step) -> int:
     """Kernels of ours per iteration: project 1; bin/sort: entry scan 2,
     duplicate 1, 3 per radix pass (digits of at most 9 bits over 31 depth bits
-    and the tile bits), tile ranges 1; render 1; loss 2; backward raster 1 +
-    projection backward 1; Adam 1."""
+    and the tile bits), tile ranges 1; render 1; loss: accumulator zeroing 1 +
+    2; backward: gradient zeroing 1 + raster 1, pose/iso zeroing 1 + projection
+    backward 1; Adam 1."""
     tb = 0
     while (1 << tb) < step.total_tiles:
         tb += 1
     passes = math.ceil((31 + tb) / 9)
-    return 1 + (2 + 1 + 3 * passes + 1) + 1 + 2 + 2 + 1
+    return 1 + (2 + 1 + 3 * passes + 1) + 1 + 3 + 4 + 1
 
 
 def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):

@@ -227,7 +227,7 @@ int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, cons
     if (E >= (1ll << 31)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (E == 0) return GS_OK;
-    cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float) * kGradStride * (size_t)E, s);
+    cudaError_t e = launch_zero(grad2d, kGradStride * E, nullptr, 0, nullptr, 0, s);
     if (e == cudaSuccess)
         e = launch_render_bwd(*proj, *bins, *img, dL_dcolor, dL_ddepth, views, make_consts(params), grad2d, s);
     return cuda_status(e);
@@ -244,8 +244,7 @@ int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_v
     if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    if (grads->pose) e = cudaMemsetAsync(grads->pose, 0, sizeof(float) * 6 * (size_t)n_views, s);
-    if (e == cudaSuccess && iso_loss) e = cudaMemsetAsync(iso_loss, 0, sizeof(float), s);
+    e = launch_zero(grads->pose, 6 * (int64_t)n_views, iso_loss, 1, nullptr, 0, s);
     if (e == cudaSuccess && g->n > 0)
         e = launch_project_bwd(*g, views, make_consts(params), grad2d, lambda_iso, *grads, iso_loss, s);
     return cuda_status(e);

@@ -73,9 +73,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
     return r;
 }
 
+// Also zeroes the tile ranges (k_tile_ranges writes only the tiles that have keys).
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt, int64_t E,
-                                                             uint32_t* __restrict__ block_sums) {
+                                                             uint32_t* __restrict__ block_sums,
+                                                             uint32_t* __restrict__ ranges, int64_t n_range_words) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    pdl_enter();
+    for (int64_t k = (int64_t)blockIdx.x * kScanThreads + threadIdx.x; k < n_range_words;
+         k += (int64_t)gridDim.x * kScanThreads)
+        ranges[k] = 0u;
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
@@ -92,6 +98,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blo
                                                       uint32_t* __restrict__ num_keys, int64_t capacity,
                                                       int32_t* __restrict__ status) {
     __shared__ uint32_t s_warp[1024 / 32 + 1];
+    pdl_enter();
     const int chunk = (nb + 1023) / 1024;
     const int lo = threadIdx.x * chunk;
     uint32_t s = 0;
@@ -134,6 +141,7 @@ __global__ void __launch_bounds__(kScanThreads) k_duplicate(const uint32_t* __re
                                                            int64_t capacity, uint64_t* __restrict__ keys,
                                                            uint32_t* __restrict__ vals) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     uint32_t carry = block_offsets[blockIdx.x];
     for (int k = 0; k < kScanItems; k++) {
@@ -188,6 +196,7 @@ __device__ __forceinline__ int64_t sort_count(const uint32_t* num_keys, int64_t 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
                                                             const uint32_t* __restrict__ num_keys, int64_t capacity,
                                                             int shift, int bits, uint32_t* __restrict__ counts) {
+    pdl_enter();
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
     if ((int)blockIdx.x >= nb) return;
@@ -228,6 +237,7 @@ __global__ void __launch_bounds__(kDigitScanThreads) k_radix_scan(uint32_t* __re
                                                                  uint32_t* __restrict__ digit_total,
                                                                  const uint32_t* __restrict__ num_keys,
                                                                  int64_t capacity, int radix) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * kDigitScanWarps + (threadIdx.x >> 5);
     if (d >= radix) return;
@@ -262,6 +272,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
                                                                const uint32_t* __restrict__ digit_total,
                                                                const uint32_t* __restrict__ num_keys,
                                                                int64_t capacity, int shift, int bits) {
+    pdl_enter();
     const int64_t M = sort_count(num_keys, capacity);
     const int nb = (int)ceil_div(M, kSortBlock);
     if ((int)blockIdx.x >= nb) return;
@@ -334,6 +345,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
 
 __global__ void k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
                               int64_t capacity, uint2* __restrict__ ranges) {
+    pdl_enter();
     const int64_t M = sort_count(num_keys, capacity);
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= M) return;
@@ -383,9 +395,12 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     p += align_up(sizeof(uint64_t) * (size_t)cap, 256);
     uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
 
-    cudaError_t err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)views.total_tiles, s);
-    if (err != cudaSuccess) return err;
-    if (E == 0) return cudaMemsetAsync(bins.num_keys, 0, sizeof(uint32_t), s);
+    cudaError_t err = cudaSuccess;
+    if (E == 0) {
+        err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)views.total_tiles, s);
+        if (err != cudaSuccess) return err;
+        return cudaMemsetAsync(bins.num_keys, 0, sizeof(uint32_t), s);
+    }
     // passes over the compacted key (tile << 31 | z bits), digits of at most 9 bits
     int tile_bits = 0;
     while ((1ll << tile_bits) < (int64_t)plan.total_tiles) tile_bits++;
@@ -398,29 +413,39 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
         sh += width[k];
     }
     const int nb_scan = (int)ceil_div(E, kScanBlock);
-    k_scan_reduce<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, E, block_sums);
-    k_scan_blocks<<<1, 1024, 0, s>>>(block_sums, nb_scan, bins.num_keys, cap, bins.status);
+    err = launch_pdl(k_scan_reduce, nb_scan, kScanThreads, 0, s, pr.tiles_touched, E, block_sums, bins.ranges,
+                     2 * (int64_t)views.total_tiles);
+    if (err == cudaSuccess)
+        err = launch_pdl(k_scan_blocks, 1, 1024, 0, s, block_sums, nb_scan, bins.num_keys, cap, bins.status);
+    if (err != cudaSuccess) return err;
     // The duplicated list goes into the buffer that makes the last pass land in bins.keys.
     uint64_t* k0 = (n_passes % 2 == 0) ? bins.keys : keys_alt;
     uint32_t* v0 = (n_passes % 2 == 0) ? bins.vals : vals_alt;
     uint64_t* k1 = (n_passes % 2 == 0) ? keys_alt : bins.keys;
     uint32_t* v1 = (n_passes % 2 == 0) ? vals_alt : bins.vals;
-    k_duplicate<<<nb_scan, kScanThreads, 0, s>>>(pr.tiles_touched, reinterpret_cast<const int4*>(pr.rect),
-                                                 reinterpret_cast<const float4*>(pr.rgbd), E, n, block_sums, views,
-                                                 cap, k0, v0);
+    err = launch_pdl(k_duplicate, nb_scan, kScanThreads, 0, s, pr.tiles_touched,
+                     reinterpret_cast<const int4*>(pr.rect), reinterpret_cast<const float4*>(pr.rgbd), E, n,
+                     block_sums, views, cap, k0, v0);
+    if (err != cudaSuccess) return err;
     const int nb_sort = (int)ceil_div(cap, kSortBlock);
     for (int pass = 0; pass < n_passes; pass++) {
-        k_radix_hist<<<nb_sort, kSortThreads, 0, s>>>(k0, bins.num_keys, cap, shift[pass], width[pass], counts);
+        err = launch_pdl(k_radix_hist, nb_sort, kSortThreads, 0, s, k0, bins.num_keys, cap, shift[pass], width[pass],
+                         counts);
         const int radix = 1 << width[pass];
-        k_radix_scan<<<(unsigned)ceil_div(radix, kDigitScanWarps), kDigitScanThreads, 0, s>>>(counts, digit_total,
-                                                                                             bins.num_keys, cap, radix);
-        k_radix_scatter<<<nb_sort, kSortThreads, 0, s>>>(k0, v0, k1, v1, counts, digit_total, bins.num_keys, cap,
-                                                         shift[pass], width[pass]);
+        if (err == cudaSuccess)
+            err = launch_pdl(k_radix_scan, (unsigned)ceil_div(radix, kDigitScanWarps), kDigitScanThreads, 0, s, counts,
+                             digit_total, bins.num_keys, cap, radix);
+        if (err == cudaSuccess)
+            err = launch_pdl(k_radix_scatter, nb_sort, kSortThreads, 0, s, k0, v0, k1, v1, counts, digit_total,
+                             bins.num_keys, cap, shift[pass], width[pass]);
+        if (err != cudaSuccess) return err;
         uint64_t* tk = k0; k0 = k1; k1 = tk;
         uint32_t* tv = v0; v0 = v1; v1 = tv;
     }
     const int nb_rng = (int)ceil_div(cap, 256);
-    k_tile_ranges<<<nb_rng, 256, 0, s>>>(bins.keys, bins.num_keys, cap, reinterpret_cast<uint2*>(bins.ranges));
+    err = launch_pdl(k_tile_ranges, nb_rng, 256, 0, s, bins.keys, bins.num_keys, cap,
+                     reinterpret_cast<uint2*>(bins.ranges));
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 

@@ -53,6 +53,31 @@ constexpr int kGradStride = 12;                  // floats per entry of the 2D-g
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Programmatic dependent launch.  The mapping kernels are launched with
+// programmatic stream serialisation, so a kernel's CTAs may be dispatched while
+// the previous kernel on the stream drains.  Every such kernel calls pdl_wait()
+// (griddepcontrol.wait: returns once every prerequisite grid has completed and
+// its memory is visible) before its first global memory access, then
+// pdl_trigger() (griddepcontrol.launch_dependents) so that the next kernel can
+// be dispatched in turn.  Without a programmatic prerequisite both are no-ops.
+#ifdef __CUDACC__
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+#endif
+
 // Launchers (one translation unit each).
 cudaError_t launch_project(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                            const gs_projected& out, cudaStream_t s);
@@ -69,6 +94,8 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const 
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s);
 cudaError_t noalloc_loss_scratch(float** out);
+// zero na, nb, nc floats at a, b, c (null or 0: skipped) with one kernel launch
+cudaError_t launch_zero(float* a, int64_t na, float* b, int64_t nb, float* c, int64_t nc, cudaStream_t s);
 cudaError_t launch_extract_patches(const float* color, const float* depth, const gs_camera& cam,
                                    const int32_t* uv, int64_t n, uint16_t* X, int* status, cudaStream_t s);
 cudaError_t launch_insert(const float* color, const float* depth, const gs_camera& cam, const int32_t* uv,
@@ -92,6 +119,14 @@ cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, flo
 #ifdef __CUDACC__
 // log2(e): the splat weight is evaluated as exp2(power * log2 e).
 constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// first statement of every kernel launched by launch_pdl
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

@@ -25,6 +25,7 @@ __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f
 __global__ void __launch_bounds__(kLossThreads) k_loss_reduce(gs_image img, const float* __restrict__ tc,
                                                              const float* __restrict__ td, Views views,
                                                              float* __restrict__ acc) {
+    pdl_enter();
     const int v = blockIdx.y;
     const ViewParams& vp = views.v[v];
     const int HW = vp.W * vp.H;
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(gs_image img, const 
                                                            const float* __restrict__ acc, float lc, float ld,
                                                            float* __restrict__ dc, float* __restrict__ dd,
                                                            float* __restrict__ terms) {
+    pdl_enter();
     const int v = blockIdx.y;
     const ViewParams& vp = views.v[v];
     const int HW = vp.W * vp.H;
@@ -153,6 +155,7 @@ __device__ __forceinline__ void adam_chunk(const AdamArgs& args, int64_t c, floa
 __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
     __shared__ float s_bc[2];
     __shared__ int s_t;
+    pdl_enter();
     if (threadIdx.x == 0) {
         const int t = args.d_step[0] + 1;
         s_t = t;
@@ -224,20 +227,56 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
     }
 }
 
+// Zero-fill of up to three float buffers (float4 stores for a 16-byte aligned
+// first buffer): the accumulators a following kernel adds into.  A kernel rather
+// than memset nodes, so that the launch chain stays programmatic.
+__global__ void __launch_bounds__(256) k_zero(float* a, int64_t na, float* b, int64_t nb, float* c, int64_t nc) {
+    pdl_enter();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
+        head = na / 4 * 4;
+        for (int64_t k = t0; k < na / 4; k += stride) reinterpret_cast<float4*>(a)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int64_t k = head + t0; k < na; k += stride) a[k] = 0.f;
+    for (int64_t k = t0; k < nb; k += stride) b[k] = 0.f;
+    for (int64_t k = t0; k < nc; k += stride) c[k] = 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_zero(float* a, int64_t na, float* b, int64_t nb, float* c, int64_t nc, cudaStream_t s) {
+    if (a == nullptr) na = 0;
+    if (b == nullptr) nb = 0;
+    if (c == nullptr) nc = 0;
+    int64_t work = na / 4 + 4;
+    if (nb > work) work = nb;
+    if (nc > work) work = nc;
+    if (na + nb + nc == 0) return cudaSuccess;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = ceil_div(work, 256), cap = 4 * (int64_t)sms;
+    const cudaError_t e = launch_pdl(k_zero, (unsigned)(want < cap ? want : cap), 256, 0, s, a, na, b, nb, c, nc);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
 size_t loss_workspace(int32_t n_views) { return align_up(sizeof(float) * 4 * (size_t)n_views, 256); }
 
 cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, const Views& views, float lc, float ld,
                         float* dc, float* dd, float* terms, void* ws, cudaStream_t s) {
     float* acc = static_cast<float*>(ws);
-    cudaError_t err = cudaMemsetAsync(acc, 0, sizeof(float) * 4 * (size_t)views.n, s);
+    cudaError_t err = launch_zero(acc, 4 * (int64_t)views.n, nullptr, 0, nullptr, 0, s);
     if (err != cudaSuccess) return err;
     int max_hw = 0;
     for (int v = 0; v < views.n; v++) max_hw = max(max_hw, views.v[v].W * views.v[v].H);
     dim3 grid((unsigned)ceil_div(max_hw, kLossThreads * kLossItems), (unsigned)views.n);
-    k_loss_reduce<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc);
-    k_loss_grad<<<grid, kLossThreads, 0, s>>>(img, tc, td, views, acc, lc, ld, dc, dd, terms);
+    err = launch_pdl(k_loss_reduce, grid, kLossThreads, 0, s, img, tc, td, views, acc);
+    if (err == cudaSuccess)
+        err = launch_pdl(k_loss_grad, grid, kLossThreads, 0, s, img, tc, td, views, acc, lc, ld, dc, dd, terms);
+    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 
@@ -293,7 +332,8 @@ cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, flo
     const int64_t full = (int64_t)per_sm * sms;                                // one resident wave
     const unsigned blocks = (unsigned)(want < full ? want : full);
     a.total_blocks = blocks;
-    k_adam<<<blocks, kAdamThreads, 0, s>>>(a);
+    const cudaError_t e = launch_pdl(k_adam, blocks, kAdamThreads, 0, s, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -200,6 +200,7 @@ __device__ __forceinline__ void view_colour(const gs_gaussians& g, int i, const 
 template <int SH>
 __global__ void __launch_bounds__(kProjThreads) k_project(gs_gaussians g, Views views, RenderConsts rc,
                                                           gs_projected out) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = (int)g.n;
     if (i >= n) return;
@@ -246,6 +247,7 @@ template <int SH>
 __global__ void __launch_bounds__(kProjThreads) k_project_bwd(gs_gaussians g, Views views, RenderConsts rc,
                                                               const float* __restrict__ g2d, float lambda_iso,
                                                               float inv_n, gs_grads grads, float* iso_loss) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = (int)g.n;
     const bool active = i < n;
@@ -469,10 +471,9 @@ cudaError_t launch_project(const gs_gaussians& g, const Views& views, const Rend
                            const gs_projected& out, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
     const int blocks = (int)ceil_div(g.n, kProjThreads);
-    if (rc.sh_degree == 0)
-        k_project<0><<<blocks, kProjThreads, 0, s>>>(g, views, rc, out);
-    else
-        k_project<3><<<blocks, kProjThreads, 0, s>>>(g, views, rc, out);
+    const cudaError_t e = rc.sh_degree == 0 ? launch_pdl(k_project<0>, blocks, kProjThreads, 0, s, g, views, rc, out)
+                                            : launch_pdl(k_project<3>, blocks, kProjThreads, 0, s, g, views, rc, out);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -482,10 +483,13 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const 
     if (g.n == 0) return cudaSuccess;
     const int blocks = (int)ceil_div(g.n, kProjThreads);
     const float inv_n = 1.0f / (float)g.n;
-    if (rc.sh_degree == 0)
-        k_project_bwd<0><<<blocks, kProjThreads, 0, s>>>(g, views, rc, g2d, lambda_iso, inv_n, grads, iso_loss);
-    else
-        k_project_bwd<3><<<blocks, kProjThreads, 0, s>>>(g, views, rc, g2d, lambda_iso, inv_n, grads, iso_loss);
+    const cudaError_t e =
+        rc.sh_degree == 0
+            ? launch_pdl(k_project_bwd<0>, blocks, kProjThreads, 0, s, g, views, rc, g2d, lambda_iso, inv_n, grads,
+                         iso_loss)
+            : launch_pdl(k_project_bwd<3>, blocks, kProjThreads, 0, s, g, views, rc, g2d, lambda_iso, inv_n, grads,
+                         iso_loss);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

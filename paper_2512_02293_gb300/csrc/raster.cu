@@ -99,9 +99,15 @@ __device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
 
-__device__ __forceinline__ int next_item(int* queue, int lane) {
+// Every warp takes items until it draws one >= n_items, so a launch makes
+// exactly n_items + (its warps) increments; the warp that draws the last value
+// returns the counter to zero for the next launch (no reset on the stream).
+__device__ __forceinline__ int next_item(int* queue, int lane, int n_items) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(queue, 1);
+    if (lane == 0) {
+        item = atomicAdd(queue, 1);
+        if (item == n_items + (int)(gridDim.x * kRasterWarps) - 1) *queue = 0;
+    }
     return __shfl_sync(0xffffffffu, item, 0);
 }
 
@@ -115,10 +121,11 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
     __shared__ float4 s_q[kRasterWarps][32];
     __shared__ float4 s_cd[kRasterWarps][32];
     __shared__ uint32_t s_pos[kRasterWarps][32];
+    pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const float amin = rc.alpha_min, amax = rc.alpha_max, tcut = rc.T_cut;
-    for (int item = next_item(queue, lane); item < n_items; item = next_item(queue, lane)) {
+    for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
         const int g = item / W, blk = item % W;
         const int v = view_of_tile(views, g);
         const ViewParams& vp = views.v[v];
@@ -447,8 +454,9 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
     __shared__ float4 s_q[kRasterWarps][32];      // scaled conic + opacity
     __shared__ float4 s_cd[kRasterWarps][32];     // r, g, b, z
     __shared__ float4 s_c[kRasterWarps][32];      // raw conic A, B, C
+    pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int item = next_item(queue, lane); item < n_items; item = next_item(queue, lane)) {
+    for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
         bwd_item<T>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
                     views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d);
         __syncwarp();
@@ -478,15 +486,14 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
-    int* queue = bins.status + 1;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
+    int* queue = bins.status + 1;      // zero between launches (see next_item)
+    cudaError_t e = cudaSuccess;
     switch (rc.tile) {
 #define GS_FWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        k_render_fwd<TT><<<persistent_grid(k_render_fwd<TT>, n_items), kRasterThreads, 0, s>>>(       \
-            xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items);                               \
+        e = launch_pdl(k_render_fwd<TT>, persistent_grid(k_render_fwd<TT>, n_items), kRasterThreads, 0, s, \
+                       xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items);                    \
         break;                                                                                         \
     }
         GS_FWD(8)
@@ -495,6 +502,7 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 #undef GS_FWD
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -505,9 +513,8 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
-    int* queue = bins.status + 2;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
+    int* queue = bins.status + 2;      // zero between launches (see next_item)
+    cudaError_t e = cudaSuccess;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -517,11 +524,13 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
         if (n_items <= kBwdFewItemsPerSm * sms)                                                        \
-            k_render_bwd<TT, 2><<<persistent_grid(k_render_bwd<TT, 2>, n_items), kRasterThreads, 0, s>>>( \
-                xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
+            e = launch_pdl(k_render_bwd<TT, 2>, persistent_grid(k_render_bwd<TT, 2>, n_items), kRasterThreads, \
+                           0, s, xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, \
+                           queue, n_items);                                                            \
         else                                                                                           \
-            k_render_bwd<TT, 3><<<persistent_grid(k_render_bwd<TT, 3>, n_items), kRasterThreads, 0, s>>>( \
-                xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items); \
+            e = launch_pdl(k_render_bwd<TT, 3>, persistent_grid(k_render_bwd<TT, 3>, n_items), kRasterThreads, \
+                           0, s, xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, \
+                           queue, n_items);                                                            \
         break;                                                                                         \
     }
         GS_BWD(8)
@@ -530,6 +539,7 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
 #undef GS_BWD
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
