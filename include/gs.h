@@ -109,7 +109,9 @@ typedef struct gs_bins {
     uint32_t* ranges;         /* [total_tiles][2] [start, end) of each tile's list */
     uint32_t* num_keys;       /* [1] number of keys M the projection produced */
     int32_t* status;          /* [4] [0] device status word (gs_status), sticky; [1..3]
-                                 work counters of the persistent rasterisers */
+                                 work counters of the persistent rasterisers: zero
+                                 before the first render call, and every render
+                                 launch leaves them zero */
 } gs_bins;
 
 /* Rendered images and the per-pixel checkpoint the backward pass uses. */

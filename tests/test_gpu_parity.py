@@ -405,6 +405,37 @@ def test_full_iteration_end_to_end_matches_oracle(lambdas):
     assert rel_l2(got["pose"][0], ref.pose_grads[0]) < GRAD_RTOL
 
 
+def test_repeated_launches_leave_work_counters_zero():
+    # the persistent rasterisers' work counters are returned to zero by the last
+    # warp of each launch (no reset on the stream): eager calls and graph replays
+    # of the step reproduce the first result bit for bit and leave them zero
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, cam = _problem(1)
+    params = G.RenderParams()
+    targets = _oracle_targets(gt, [cam], params)
+    tc, td = pack_images([targets[0][0]], [targets[0][1]])
+    # zero learning rates: the graph's Adam step leaves the map as it is
+    mp = MapParams(0.9, 0.1, 10.0, lr=(0.0,) * 5)
+    step = MappingStep(G.Gaussians.from_numpy(g), [cam], tc, td, params, mp)
+    outs = []
+    for k in range(4):
+        if k == 2:
+            step.capture(warmup=0)
+        if k >= 2:
+            step.step()                      # graph replay: project ... Adam
+        else:
+            step.render()
+            step.loss_and_backward()
+        torch.cuda.synchronize()
+        assert step.bins.status[1:].cpu().tolist() == [0, 0, 0]
+        outs.append((step.img.color.clone(), step.img.n_contrib.clone(), step.grads.mean.clone()))
+    for c, n, gm in outs[1:]:
+        assert torch.equal(c, outs[0][0]) and torch.equal(n, outs[0][1])
+    # gradient accumulation order is not fixed (atomics): equal to fp32 rounding
+    for _, _, gm in outs[1:]:
+        assert rel_l2(gm.cpu().numpy(), outs[0][2].cpu().numpy()) < 1e-5
+
+
 def test_multiview_gradients_are_the_sum_of_single_views():
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
     g, gt, _ = _problem(4)

@@ -79,7 +79,7 @@ def test_inertial_residual_vanishes_on_a_consistent_trajectory():
 def test_inertial_residual_terms():
     # each term moves with its own variable: a velocity offset moves r_pos by
     # -R_i^T dv dt and r_vel by -R_i^T dv; a common bias offset leaves r_bias at 0
-    # and moves r_pos by -J_pos db; a rotation of keyframe j about its own frame
+    # and moves r_pos by -J_pos db and r_vel by -J_vel db; a rotation of keyframe j about its own frame
     # moves r_rot by that angle
     R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(6, K=3)
     Rb, _ = ba.body_states(R, t)
@@ -94,6 +94,9 @@ def test_inertial_residual_terms():
     r = ba.inertial_residual(R, t, vel, b2, bh, imu, g, 0)
     np.testing.assert_allclose(r[12:], 0.0, atol=1e-12)
     np.testing.assert_allclose(r[3:6], -Jpos @ db, atol=1e-12)
+    # the velocity term's correction takes the accelerometer bias too (3 x 6 J_vel)
+    np.testing.assert_allclose(r[6:9], -Jvel @ db, atol=1e-12)
+    assert np.abs(Jvel[:, 3:] @ db[3:]).max() > 1e-3
     phi = np.array([0.01, -0.02, 0.015])
     R2 = R.copy(); R2[1] = (Rb[1] @ ba.so3_exp(phi)).T          # R_j <- R_j Exp(phi)
     r = ba.inertial_residual(R2, t - 0 * t, vel, bias, bh, imu, g, 0)
