@@ -695,14 +695,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambd
 #pragma unroll
                 for (int c = 0; c < kNb; c++) A[(size_t)(kb + r) * ld + kb + c] = a[r][c];
         }
-        // (B) trailing update, U12 of this lane's columns held in registers, two rows at a time
+        // (B) trailing update, U12 of this lane's columns held in registers, two rows at a time;
+        // only the jn column groups that still hold columns (uniform over the CTA) are touched
         if (nrows > 0) {
+            const int jn = (ncols + 31) >> 5;
             float u[CPL][kNb];
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
                 const int c = k1 + lane + 32 * j;
+                if (j < jn) {
 #pragma unroll
-                for (int m = 0; m < kNb; m++) u[j][m] = c < ld ? A[(size_t)(kb + m) * ld + c] : 0.f;
+                    for (int m = 0; m < kNb; m++) u[j][m] = c < ld ? A[(size_t)(kb + m) * ld + c] : 0.f;
+                }
             }
             constexpr int kW = kSolveThreads / 32;
             for (int r0 = k1 + warp; r0 < n; r0 += 2 * kW) {
@@ -718,21 +722,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambd
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
                     const int c = k1 + lane + 32 * j;
-                    v0[j] = c < ld ? A[(size_t)r0 * ld + c] : 0.f;
-                    v1[j] = (c < ld && has1) ? A[(size_t)r1 * ld + c] : 0.f;
+                    if (j < jn) {
+                        v0[j] = c < ld ? A[(size_t)r0 * ld + c] : 0.f;
+                        v1[j] = (c < ld && has1) ? A[(size_t)r1 * ld + c] : 0.f;
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
+                    if (j < jn) {
 #pragma unroll
-                    for (int m = 0; m < kNb; m++) {
-                        v0[j] -= l0[m] * u[j][m];
-                        v1[j] -= l1[m] * u[j][m];
+                        for (int m = 0; m < kNb; m++) {
+                            v0[j] -= l0[m] * u[j][m];
+                            v1[j] -= l1[m] * u[j][m];
+                        }
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
                     const int c = k1 + lane + 32 * j;
-                    if (c < ld) {
+                    if (j < jn && c < ld) {
                         A[(size_t)r0 * ld + c] = v0[j];
                         if (has1) A[(size_t)r1 * ld + c] = v1[j];
                     }
