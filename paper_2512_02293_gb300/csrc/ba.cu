@@ -1,5 +1,6 @@
-// ba.cu -- one Levenberg-Marquardt step of the tracker's dense visual bundle
-// adjustment (Sec. 3.2: vision residual Eq. 2 over the edges of the frame graph,
+// ba.cu -- one Levenberg-Marquardt step of the tracker's dense visual-inertial
+// bundle adjustment (Sec. 3.2: vision residual Eq. 2 over the edges of the frame
+// graph, optionally the inertial residual Eq. 3 between consecutive keyframes,
 // normal equations solved by the Schur complement of the diagonal depth block,
 // Eq. 4).
 //
@@ -24,11 +25,16 @@
 //                 of i] (summed over the edges for pose i), C'_p and g_d,p from the
 //                 records; sum_p v_p v_p^T / C'_p in 2 x 2 register tiles and
 //                 sum_p v_p g_d,p / C'_p, added once per CTA into the reduced system.
-//   k_ba_solve  : one CTA: damping of B, then Gaussian elimination of the
-//                 symmetric positive definite reduced system in shared memory
-//                 (no pivoting; one barrier per column) and back substitution by
-//                 one warp.
-//   k_ba_update : inverse depths by back-substitution, poses by Exp.
+//   k_ba_inertial: one CTA per consecutive keyframe pair: the 15 residuals of
+//                 Eq. 3 and their Jacobian, added into the 15-wide keyframe blocks.
+//   k_ba_solve_cluster: a cluster of 8 CTAs: damping, then block Gauss-Jordan
+//                 elimination of the symmetric positive definite reduced system
+//                 (no pivoting; 6-wide panels read across the cluster through
+//                 distributed shared memory; one cluster barrier per panel).
+//   k_ba_update : inverse depths by back-substitution, poses by Exp (velocities
+//                 and biases added).
+#include <cooperative_groups.h>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -574,19 +580,9 @@ __global__ void __launch_bounds__(kSchurThreads) k_ba_schur(BaDev b, float lambd
     }
 }
 
-// Solve of the reduced system (B damped - E C'^-1 E^T) dxi = rhs, one CTA, in
-// shared memory: LU factorisation without pivoting (the matrix is symmetric
-// positive definite) of the augmented n x (n + 1) matrix [S | rhs], blocked by
-// 6 x 6 pose panels with two barriers per panel, then back substitution panel by
-// panel.  Per panel kb:
-//   (A) every thread of the panel phase factors the 6 x 6 diagonal block in its
-//       registers (the same operations in every thread, so no barrier); column
-//       threads form U12 = L11^-1 A12 (the right-hand side column included), row
-//       threads L21 = A21 U11^-1; thread 0 stores the factored block;
-//   (B) A22 -= L21 U12.
-constexpr int kSolveThreads = 512;
+// Solve of the reduced system (B damped - E C'^-1 E^T) dxi = rhs in 6 x 6 pose
+// panels (a system that is not a multiple of 6 is padded with identity rows).
 constexpr int kNb = 6;
-constexpr int kMaxSolve = 228;          // largest padded system: 15 free keyframes with the inertial factor
 
 // LU of a 6 x 6 block in registers: unit-lower multipliers below the diagonal,
 // U on and above it; inv[k] = 1 / U_kk.
@@ -604,184 +600,177 @@ __device__ __forceinline__ void lu6(float (&a)[kNb][kNb], float (&inv)[kNb]) {
     }
 }
 
-// CPL: columns of a lane in (B), ceil((n + 1 - 6) / 32) for the padded n, at most 7 (n <= 228)
+// ------------------------------------------------------- cluster solve
+// The same damped system solved by a cluster of kClusterCtas CTAs with block
+// Gauss-Jordan elimination.  CTA q keeps the row panels p = q, q + C, ... in its
+// shared memory.  Step k: every CTA copies panel k's rows (columns kb .. n) out of
+// the owner's shared memory, forms W = A_kk^-1 A[panel k, k1 ..] (one column per
+// thread, the 6 x 6 factorisation redundantly in registers) and eliminates the
+// panel's columns from all of its own rows above and below the panel:
+// A[r, k1 ..] -= A[r, panel k] W.  Panel k's rows are not written during step k,
+// and a cluster barrier ends every step, so each copy reads finished rows.  After
+// the last step the system is block diagonal and each CTA solves its own panels,
+// A_pp x_p = rhs_p, with A_pp as it stood at step p (later steps only touch the
+// columns to the right of their panel).
+namespace cg = cooperative_groups;
+constexpr int kClusterCtas = 8;
+constexpr int kClSolveThreads = 256;
+constexpr int kClWarps = kClSolveThreads / 32;
+
+__host__ __device__ inline int cl_panels(int np, int q) { return (np - q + kClusterCtas - 1) / kClusterCtas; }
+
 template <int CPL>
-__global__ void __launch_bounds__(kSolveThreads) k_ba_solve(BaDev b, float lambda, float eps) {
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClSolveThreads)
+    k_ba_solve_cluster(BaDev b, float lambda, float eps) {
+    cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float sm[];
-    // the system is padded to a multiple of the panel width with identity rows
-    const int n0 = b.n, n = (n0 + kNb - 1) / kNb * kNb, ld = n + 1, t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    float* A = sm;                       // [n][n + 1]
-    float* x = sm + (size_t)n * ld;      // [n]
+    const int q = (int)cl.block_rank();
+    const int n0 = b.n, n = (n0 + kNb - 1) / kNb * kNb, ld = n + 1, np = n / kNb;
+    const int mine = cl_panels(np, q), rows = mine * kNb;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float* R = sm;                                  // [rows][ld] this CTA's rows
+    float* P = R + (size_t)rows * ld;               // [6][ld] the current panel's rows
+    float* W = P + (size_t)kNb * ld;                // [6][ld] A_kk^-1 A[panel k, k1 ..]
     __shared__ int s_bad;
-    __shared__ float s_inv[kMaxSolve];   // reciprocals of the pivots
-    // eight loads of each matrix in flight per thread before the stores
-    for (int k0 = 0; k0 < n0 * n0; k0 += 8 * kSolveThreads) {
-        float vb[8], vs[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int k = k0 + u * kSolveThreads + t;
-            vb[u] = k < n0 * n0 ? b.SB[k] : 0.f;
-            vs[u] = k < n0 * n0 ? b.SS[k] : 0.f;
+    // own rows of the damped system; padding rows are identity, padding columns zero
+    for (int k = t; k < rows * ld; k += kClSolveThreads) {
+        const int lr = k / ld, c = k - lr * ld;
+        const int r = kNb * (q + kClusterCtas * (lr / kNb)) + lr % kNb;
+        float v;
+        if (c == n) {
+            v = r < n0 ? b.rhs[r] : 0.f;
+        } else if (r < n0 && c < n0) {
+            const size_t g = (size_t)r * n0 + c;
+            v = b.SS[g] + (r == c ? (1.0f + lambda) * b.SB[g] + eps : b.SB[g]);
+        } else {
+            v = r == c ? 1.f : 0.f;
         }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int k = k0 + u * kSolveThreads + t;
-            if (k < n0 * n0) {
-                const int r = k / n0, c = k - r * n0;
-                A[(size_t)r * ld + c] = vs[u] + (r == c ? (1.0f + lambda) * vb[u] + eps : vb[u]);
-            }
-        }
+        R[k] = v;
     }
-    const int pad = n - n0;
-    for (int k = t; k < pad * n; k += kSolveThreads) {                 // padding rows: identity
-        const int r = n0 + k / n, c = k % n;
-        A[(size_t)r * ld + c] = (r == c) ? 1.f : 0.f;
-    }
-    for (int k = t; k < n0 * pad; k += kSolveThreads)                  // padding columns of the real rows
-        A[(size_t)(k / pad) * ld + n0 + k % pad] = 0.f;
-    for (int k = t; k < n; k += kSolveThreads) A[(size_t)k * ld + n] = k < n0 ? b.rhs[k] : 0.f;
     if (t == 0) s_bad = 0;
-    __syncthreads();
-    for (int kb = 0; kb < n; kb += kNb) {
-        const int k1 = kb + kNb;                  // first row / column after the panel
-        const int ncols = ld - k1, nrows = n - k1;
-        // (A) the diagonal block, U12 and L21 (thread 0 is always a column thread)
-        float a[kNb][kNb], inv[kNb];
-        if (t < ncols + nrows) {
+    cl.sync();
+    for (int k = 0; k < np; k++) {
+        const int kb = kNb * k, k1 = kb + kNb, owner = k % kClusterCtas, lpk = k / kClusterCtas;
+        const int ncols = ld - k1;
+        {
+            // all remote loads of a thread issued before its stores (wdt <= ld <= 229 < 2 * 256)
+            const float* src = cl.map_shared_rank(R, owner) + (size_t)lpk * kNb * ld;
+            float v[kNb][2];
+#pragma unroll
+            for (int m = 0; m < kNb; m++)
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int c = kb + t + h * kClSolveThreads;
+                    v[m][h] = c < ld ? src[(size_t)m * ld + c] : 0.f;
+                }
+#pragma unroll
+            for (int m = 0; m < kNb; m++)
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int c = kb + t + h * kClSolveThreads;
+                    if (c < ld) P[m * ld + c] = v[m][h];
+                }
+        }
+        __syncthreads();
+        if (t < ncols || t == 0) {
+            float a[kNb][kNb], inv[kNb];
 #pragma unroll
             for (int r = 0; r < kNb; r++)
 #pragma unroll
-                for (int c = 0; c < kNb; c++) a[r][c] = A[(size_t)(kb + r) * ld + kb + c];
+                for (int c = 0; c < kNb; c++) a[r][c] = P[r * ld + kb + c];
             lu6(a, inv);
-            if (t < ncols) {
-                const int c = k1 + t;
-                float u[kNb];
+            if (t == 0 && q == owner) {
 #pragma unroll
-                for (int m = 0; m < kNb; m++) u[m] = A[(size_t)(kb + m) * ld + c];
+                for (int m = 0; m < kNb; m++)
+                    if (!(a[m][m] > 0.f)) s_bad = 1;
+            }
+            for (int j = t; j < ncols; j += kClSolveThreads) {
+                const int c = k1 + j;
+                float y[kNb];
+#pragma unroll
+                for (int m = 0; m < kNb; m++) y[m] = P[m * ld + c];
 #pragma unroll
                 for (int m = 1; m < kNb; m++)
 #pragma unroll
-                    for (int q = 0; q < m; q++) u[m] -= a[m][q] * u[q];
+                    for (int u = 0; u < m; u++) y[m] -= a[m][u] * y[u];
 #pragma unroll
-                for (int m = 0; m < kNb; m++) A[(size_t)(kb + m) * ld + c] = u[m];
-            } else {
-                const int r = k1 + (t - ncols);
-                float l[kNb];
+                for (int m = kNb - 1; m >= 0; m--) {
 #pragma unroll
-                for (int m = 0; m < kNb; m++) l[m] = A[(size_t)r * ld + kb + m];
-#pragma unroll
-                for (int m = 0; m < kNb; m++) {
-#pragma unroll
-                    for (int q = 0; q < m; q++) l[m] -= l[q] * a[q][m];
-                    l[m] *= inv[m];
+                    for (int u = m + 1; u < kNb; u++) y[m] -= a[m][u] * y[u];
+                    y[m] *= inv[m];
                 }
 #pragma unroll
-                for (int m = 0; m < kNb; m++) A[(size_t)r * ld + kb + m] = l[m];
-            }
-            if (t == 0) {
-#pragma unroll
-                for (int m = 0; m < kNb; m++) {
-                    if (!(a[m][m] > 0.f)) s_bad = 1;
-                    s_inv[kb + m] = inv[m];
-                }
+                for (int m = 0; m < kNb; m++) W[m * ld + c] = y[m];
             }
         }
         __syncthreads();
-        // the factored diagonal block (read by every thread of (A) before the barrier;
-        // not read by (B))
-        if (t == 0) {
-#pragma unroll
-            for (int r = 0; r < kNb; r++)
-#pragma unroll
-                for (int c = 0; c < kNb; c++) A[(size_t)(kb + r) * ld + kb + c] = a[r][c];
-        }
-        // (B) trailing update, U12 of this lane's columns held in registers, two rows at a time;
-        // only the jn column groups that still hold columns (uniform over the CTA) are touched
-        if (nrows > 0) {
+        if (ncols > 0 && rows > 0) {
             const int jn = (ncols + 31) >> 5;
-            float u[CPL][kNb];
+            float w[CPL][kNb];
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
                 const int c = k1 + lane + 32 * j;
                 if (j < jn) {
 #pragma unroll
-                    for (int m = 0; m < kNb; m++) u[j][m] = c < ld ? A[(size_t)(kb + m) * ld + c] : 0.f;
+                    for (int m = 0; m < kNb; m++) w[j][m] = c < ld ? W[m * ld + c] : 0.f;
                 }
             }
-            constexpr int kW = kSolveThreads / 32;
-            for (int r0 = k1 + warp; r0 < n; r0 += 2 * kW) {
-                const int r1 = r0 + kW;
-                const bool has1 = r1 < n;
-                float l0[kNb], l1[kNb];
+            for (int lr = warp; lr < rows; lr += kClWarps) {
+                if (q == owner && lr / kNb == lpk) continue;      // the panel's own rows (warp-uniform)
+                float* row = R + (size_t)lr * ld;
+                float l[kNb];
 #pragma unroll
-                for (int m = 0; m < kNb; m++) {
-                    l0[m] = A[(size_t)r0 * ld + kb + m];
-                    l1[m] = has1 ? A[(size_t)r1 * ld + kb + m] : 0.f;
-                }
-                float v0[CPL], v1[CPL];
+                for (int m = 0; m < kNb; m++) l[m] = row[kb + m];
+                float v[CPL];
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
                     const int c = k1 + lane + 32 * j;
-                    if (j < jn) {
-                        v0[j] = c < ld ? A[(size_t)r0 * ld + c] : 0.f;
-                        v1[j] = (c < ld && has1) ? A[(size_t)r1 * ld + c] : 0.f;
-                    }
+                    if (j < jn) v[j] = c < ld ? row[c] : 0.f;
                 }
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
                     if (j < jn) {
 #pragma unroll
-                        for (int m = 0; m < kNb; m++) {
-                            v0[j] -= l0[m] * u[j][m];
-                            v1[j] -= l1[m] * u[j][m];
-                        }
+                        for (int m = 0; m < kNb; m++) v[j] -= l[m] * w[j][m];
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < CPL; j++) {
                     const int c = k1 + lane + 32 * j;
-                    if (j < jn && c < ld) {
-                        A[(size_t)r0 * ld + c] = v0[j];
-                        if (has1) A[(size_t)r1 * ld + c] = v1[j];
-                    }
+                    if (j < jn && c < ld) row[c] = v[j];
                 }
             }
         }
-        __syncthreads();
+        cl.sync();
     }
-    if (warp == 0) {
-        // U x = y (y in column n) panel by panel from the last: lane 0 solves the
-        // 6 x 6 triangle, then every lane removes the panel's x from the rows above
-        for (int k = lane; k < n; k += 32) x[k] = A[(size_t)k * ld + n];
-        __syncwarp();
-        for (int kb = n - kNb; kb >= 0; kb -= kNb) {
-            if (lane == 0) {
-                float xs[kNb];
+    // x_p = A_pp^-1 rhs_p for this CTA's panels
+    if (t < mine) {
+        const int p = q + kClusterCtas * t, kb = kNb * p;
+        const float* rp = R + (size_t)t * kNb * ld;
+        float a[kNb][kNb], inv[kNb], y[kNb];
 #pragma unroll
-                for (int m = kNb - 1; m >= 0; m--) {
-                    float v = x[kb + m];
+        for (int r = 0; r < kNb; r++) {
 #pragma unroll
-                    for (int q = m + 1; q < kNb; q++) v -= A[(size_t)(kb + m) * ld + kb + q] * xs[q];
-                    xs[m] = v * s_inv[kb + m];
-                }
-#pragma unroll
-                for (int m = 0; m < kNb; m++) x[kb + m] = xs[m];
-            }
-            __syncwarp();
-            float xs[kNb];
-#pragma unroll
-            for (int m = 0; m < kNb; m++) xs[m] = x[kb + m];
-            for (int r = lane; r < kb; r += 32) {
-                float v = x[r];
-#pragma unroll
-                for (int m = 0; m < kNb; m++) v -= A[(size_t)r * ld + kb + m] * xs[m];
-                x[r] = v;
-            }
-            __syncwarp();
+            for (int c = 0; c < kNb; c++) a[r][c] = rp[r * ld + kb + c];
+            y[r] = rp[r * ld + n];
         }
-        for (int k = lane; k < n0; k += 32) b.dxi[k] = x[k];
-        if (lane == 0 && s_bad) atomicCAS(b.status, 0, GS_ERR_NUMERIC);
+        lu6(a, inv);
+#pragma unroll
+        for (int m = 1; m < kNb; m++)
+#pragma unroll
+            for (int u = 0; u < m; u++) y[m] -= a[m][u] * y[u];
+#pragma unroll
+        for (int m = kNb - 1; m >= 0; m--) {
+#pragma unroll
+            for (int u = m + 1; u < kNb; u++) y[m] -= a[m][u] * y[u];
+            y[m] *= inv[m];
+        }
+#pragma unroll
+        for (int m = 0; m < kNb; m++)
+            if (kb + m < n0) b.dxi[kb + m] = y[m];
     }
+    __syncthreads();
+    if (t == 0 && s_bad) atomicCAS(b.status, 0, GS_ERR_NUMERIC);
 }
 
 __device__ __forceinline__ float pose_dxi(const BaDev& b, int k, int c) {
@@ -911,14 +900,16 @@ cudaError_t launch_ba_step(const gs_ba_problem& pr, float lambda, float eps, flo
                 k_ba_schur<<<dim3((unsigned)ceil_div(b.P, kSchurChunk), (unsigned)b.K), kSchurThreads, 0, s>>>(
                     b, lambda, eps);
             const int n_pad = (int)ceil_div(b.n, kNb) * kNb;
-            const size_t smem = sizeof(float) * ((size_t)n_pad * (n_pad + 1) + n_pad);
+            const int cl_rows = cl_panels(n_pad / kNb, 0) * kNb;
+            const size_t smem = sizeof(float) * (size_t)(cl_rows + 2 * kNb) * (n_pad + 1);
             const int cpl = (int)ceil_div((int64_t)n_pad + 1 - kNb, 32);
             switch (cpl) {
 #define GS_SOLVE(C)                                                                                      \
     case C:                                                                                              \
-        e = cudaFuncSetAttribute(k_ba_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = cudaFuncSetAttribute(k_ba_solve_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 (int)smem);                                                             \
         if (e != cudaSuccess) return e;                                                                  \
-        k_ba_solve<C><<<1, kSolveThreads, smem, s>>>(b, lambda, eps);                                    \
+        k_ba_solve_cluster<C><<<kClusterCtas, kClSolveThreads, smem, s>>>(b, lambda, eps);               \
         break;
                 GS_SOLVE(1)
                 GS_SOLVE(2)
