@@ -65,6 +65,7 @@ class MappingStep:
         self.d_step = torch.zeros(2, device=dev, dtype=torch.int32)
         self.headroom = headroom
         self.graph = None
+        self._io_stream = None
         self._bound = None          # the seven calls marshalled once (eager step); rebuilt when stale
         self._bound_key = None
         self._alloc_bins(key_capacity if key_capacity is not None else self._measure_keys())
@@ -148,17 +149,33 @@ class MappingStep:
     STAGES = ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
               "gs_adam_step")
 
-    def _staged(self, events=None):
+    def _staged(self, events=None, host_io=None):
         """The iteration as its seven C-ABI calls; if `events` (len 8) is given,
-        events[k] is recorded before call k and events[7] after the last."""
+        events[k] is recorded before call k and events[7] after the last.  With
+        `host_io` = (color, depth, loss_terms, iso) pinned host tensors, the
+        targets are first copied in from the first two and the loss terms and
+        the iso term copied out to the last two."""
         rec = (lambda k: events[k].record()) if events is not None else (lambda k: None)
         grad2d = self.ws
+        main = torch.cuda.current_stream()
+        if host_io is not None:
+            # the targets are first read by the loss: their upload runs on a side
+            # branch beside projection, binning and the forward pass
+            if self._io_stream is None:
+                self._io_stream = torch.cuda.Stream()
+            side = self._io_stream
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                self.target_color.copy_(host_io[0], non_blocking=True)
+                self.target_depth.copy_(host_io[1], non_blocking=True)
         rec(0)
         G.gs_project(self.g, self.cams, self.params, self.proj)
         rec(1)
         G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
         rec(2)
         G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
+        if host_io is not None:
+            main.wait_stream(side)
         rec(3)
         G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c, self.mp.lambda_d,
                   self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
@@ -167,14 +184,31 @@ class MappingStep:
                                self.n, grad2d)
         rec(5)
         G.gs_project_bwd(self.g, self.cams, self.params, grad2d, self.mp.lambda_iso, self.grads, self.iso)
+        if host_io is not None:
+            # the loss terms and the iso term are final: read back beside Adam
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                host_io[2].copy_(self.loss_terms, non_blocking=True)
+                host_io[3].copy_(self.iso, non_blocking=True)
         rec(6)
         self.optimizer_step()
         rec(7)
+        if host_io is not None:
+            main.wait_stream(side)
 
-    def capture(self, warmup: int = 1, events=None):
+    def capture(self, warmup: int = 1, events=None, host_io=None):
         """Capture the iteration into a CUDA graph (replayed by step()).  With
         `events` (8 torch.cuda.Event created with external=True) the graph also
-        records them around each of the seven calls, for per-stage timing."""
+        records them around each of the seven calls, for per-stage timing.  With
+        `host_io` = (color, depth, loss_terms, iso), pinned host tensors shaped
+        like target_color, target_depth, loss_terms and iso, every replay also
+        copies that step's targets in and its loss out (memcpy nodes of the same
+        graph); the host values are valid after the stream is synchronised."""
+        if host_io is not None:
+            want = (self.target_color, self.target_depth, self.loss_terms, self.iso)
+            for h, d in zip(host_io, want):
+                if not h.is_pinned() or h.shape != d.shape or h.dtype != d.dtype:
+                    raise ValueError("host_io needs pinned host tensors shaped like the targets, loss terms and iso")
         self.graph = None
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -184,7 +218,7 @@ class MappingStep:
         torch.cuda.current_stream().wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self._staged(events)
+            self._staged(events, host_io)
         self.graph = g
         return g
 

@@ -436,6 +436,34 @@ def test_repeated_launches_leave_work_counters_zero():
         assert rel_l2(gm.cpu().numpy(), outs[0][2].cpu().numpy()) < 1e-5
 
 
+def test_capture_with_host_copies():
+    # MappingStep.capture(host_io=...): each replay copies the pinned host targets
+    # in and the loss terms out, inside the graph
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, cam = _problem(2)
+    params = G.RenderParams()
+    targets = _oracle_targets(gt, [cam], params)
+    tc, td = pack_images([targets[0][0]], [targets[0][1]])
+    step = MappingStep(G.Gaussians.from_numpy(g), [cam], torch.zeros_like(tc), torch.zeros_like(td), params,
+                       MapParams(0.9, 0.1, 10.0, lr=(0.0,) * 5))
+    h = (tc.cpu().pin_memory(), td.cpu().pin_memory(), torch.empty(1, 2).pin_memory(), torch.empty(1).pin_memory())
+    step.capture(warmup=0, host_io=h)
+    step.step()
+    torch.cuda.synchronize()
+    assert torch.equal(step.target_color.cpu(), h[0]) and torch.equal(step.target_depth.cpu(), h[1])
+    assert torch.equal(h[2], step.loss_terms.cpu()) and torch.equal(h[3], step.iso.cpu())
+    first = h[2].clone()
+    ref = oracle.mapping_loss_and_grads(g, [cam], targets, prm_dict(params), (0.9, 0.1, 10.0))
+    np.testing.assert_allclose(first.numpy()[0], ref.loss_terms[0], rtol=1e-5)
+    h[0].mul_(0.5)                           # a new target in the host buffer reaches the next replay
+    step.step()
+    torch.cuda.synchronize()
+    assert torch.equal(step.target_color.cpu(), h[0])
+    assert torch.equal(h[2], step.loss_terms.cpu()) and h[2][0, 0] != first[0, 0]
+    with pytest.raises(ValueError):
+        step.capture(warmup=0, host_io=(tc, h[1], h[2], h[3]))       # not pinned host memory
+
+
 def test_multiview_gradients_are_the_sum_of_single_views():
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
     g, gt, _ = _problem(4)
