@@ -133,7 +133,7 @@ def build_step(device, g, gt, cams, candidates=(8, 16, 32)):
 
 def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
     """Graph-replayed iterations, each from the same map and Adam state (restored
-    before the step) after an L2 flush.  Two graphs of the same seven C-ABI calls
+    before the step) after an L2 flush.  Two graphs of the same C-ABI calls
     are captured: a plain one, whose replays are timed by CUDA events recorded on
     the launch stream around each replay (the per-step times), and one with an
     event-record node before and after each call, replayed as many times again for
@@ -146,7 +146,7 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
         step.step()
         assert not step.ensure_capacity()
     pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
-    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(8)]
+    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(step.stages) + 1)]
     staged_graph = step.capture(warmup=1, events=evs)
     step.capture(warmup=0)                          # the plain graph, replayed by step()
     for _ in range(warmup):
@@ -165,7 +165,7 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
 
     s = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    per_stage = {k: [] for k in step.STAGES}
+    per_stage = {k: [] for k in step.stages}
     times = []
     clk = ClockSampler(clock_index) if clock_index is not None else None
     if clk:
@@ -186,7 +186,7 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
         flush()
         staged_graph.replay()
         torch.cuda.synchronize()
-        for j, nm in enumerate(step.STAGES):
+        for j, nm in enumerate(step.stages):
             per_stage[nm].append(evs[j].elapsed_time(evs[j + 1]))
     if dist is not None:
         dist.barrier()
@@ -207,14 +207,21 @@ def bwd_ctas_per_sm(step, tile) -> int:
 def launches_per_step(step) -> int:
     """Kernels of ours per iteration: project 1; bin/sort: entry scan 2,
     duplicate 1, 3 per radix pass (digits of at most 9 bits over 31 depth bits
-    and the tile bits), tile ranges 1; render 1; loss: accumulator zeroing 1 +
-    2; backward: gradient zeroing 1 + raster 1, pose/iso zeroing 1 + projection
-    backward 1; Adam 1."""
+    and the tile bits), tile ranges 1; render 1 (with the fused loss); loss
+    (unfused only): accumulator zeroing 1 + 2; backward: gradient zeroing 1 +
+    raster 1, pose/iso zeroing 1 + projection backward 1; Adam 1."""
     tb = 0
     while (1 << tb) < step.total_tiles:
         tb += 1
     passes = math.ceil((31 + tb) / 9)
-    return 1 + (2 + 1 + 3 * passes + 1) + 1 + 3 + 4 + 1
+    return 1 + (2 + 1 + 3 * passes + 1) + 1 + (0 if step.fused_loss else 3) + 4 + 1
+
+
+def raster_stages(step):
+    """Names of the forward and backward raster stages of this step's calls."""
+    if step.fused_loss:
+        return "gs_render_fwd_loss", "gs_render_bwd_raster_loss"
+    return "gs_render_fwd", "gs_render_bwd_raster"
 
 
 def cpu_baseline(g, gt, cam, params, mp, budget_s=20.0):
@@ -319,9 +326,11 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     roof = None
     if st:
         roof = {}
-        for stage, ops, kern in (("gs_render_fwd", FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"),
-                                 ("gs_render_bwd_raster", BWD_OPS_PER_PAIR,
-                                  f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}>")):
+        fwd_st, bwd_st = raster_stages(step)
+        fl = str(step.fused_loss).lower()
+        for stage, ops, kern in ((fwd_st, FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}, {fl}>"),
+                                 (bwd_st, BWD_OPS_PER_PAIR,
+                                  f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}>")):
             ach = pairs * ops / (st[stage] * 1e-3) / 1e12
             roof[stage] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
                            "frac": ach / alu_peak, "work": f"{pairs} visited pairs x {ops} FP32 ops per launch",
@@ -332,7 +341,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
             "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
             "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
             "pixels_per_iter": step.total_pixels, "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
-            "gpix_splats_per_s": pairs / (st["gs_render_fwd"] * 1e-3) / 1e9 if st else None,
+            "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
             "stages_ms": st, "graph": True, "persistent_raster": True}
 
 
@@ -815,7 +824,7 @@ def main():
             total += time.perf_counter() - t0
         return total
 
-    # eager: the seven C-ABI calls issued from Python every step
+    # eager: the C-ABI calls issued from Python every step
     eager_rate, _ = whole_job_rate(e2e_loop() * 1000.0, args.steps, world, dist, device)
     # captured: MappingStep.capture() once, then every step() replays the graph,
     # the per-step host copies (targets in, loss out) included in it as memcpy nodes
@@ -830,7 +839,7 @@ def main():
                    "pinned-host target image and depth copied in, the step, the loss terms read back, stream "
                    "synchronised; value with the step captured once together with its host copies "
                    "(MappingStep.capture(host_io=...): memcpy nodes of the same graph) and replayed, "
-                   "eager_value with the two copies in, the seven C-ABI calls and the two copies out issued "
+                   "eager_value with the two copies in, the C-ABI calls and the two copies out issued "
                    "each step"}
 
     peaks, peak_kind = _peaks()
@@ -839,11 +848,14 @@ def main():
     roofline = None
     if st:
         dominant = max(st, key=st.get)
-        if dominant == "gs_render_bwd_raster":
-            ms, ops, kern = (st["gs_render_bwd_raster"], BWD_OPS_PER_PAIR,
-                             f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}> (+ its grad2d memset)")
+        fwd_st, bwd_st = raster_stages(step)
+        fl = str(step.fused_loss).lower()
+        if dominant == bwd_st:
+            ms, ops, kern = (st[bwd_st], BWD_OPS_PER_PAIR,
+                             f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> "
+                             f"(+ its grad2d zero-fill)")
         else:
-            ms, ops, kern = st["gs_render_fwd"], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}>"
+            ms, ops, kern = st[fwd_st], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}, {fl}>"
         ach = pairs * ops / (ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
                     "frac": ach / alu_peak, "traffic": PROFILED_TRAFFIC.get((dominant, params.tile)),
@@ -860,7 +872,7 @@ def main():
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
                        "per_step_state": "map and Adam state restored before every timed step (identical work per step)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpix_splats_per_s": pairs / (st["gs_render_fwd"] * 1e-3) / 1e9 if st else None,
+            "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
             "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "stages_ms": st, "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}

@@ -5,6 +5,9 @@
  *
  * One mapping iteration is
  *     gs_project -> gs_bin_sort -> gs_render_fwd -> gs_loss -> gs_render_bwd -> gs_adam_step
+ * or, with the loss fused into the rasterisers,
+ *     gs_project -> gs_bin_sort -> gs_render_fwd_loss -> gs_render_bwd_raster_loss
+ *     -> gs_project_bwd -> gs_adam_step
  * over one or more keyframe views ("views").
  *
  * Conventions that hold for every call
@@ -41,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 2
+#define GS_ABI_VERSION 3
 #define GS_MAX_VIEWS 32
 
 typedef enum gs_status {
@@ -267,6 +270,36 @@ int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, cons
 int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
                        const gs_render_params* params, const float* grad2d, float lambda_iso,
                        gs_grads* grads, float* iso_loss, void* stream);
+
+/* The colour and depth terms of Eq. 6 fused into the rasterisers (the same
+ * values as gs_render_fwd + gs_loss + gs_render_bwd_raster, without the two
+ * loss passes over the images and without materialised gradient images).
+ *
+ * gs_render_fwd_loss: gs_render_fwd, and per view sum |I_hat - I|,
+ * sum over D > 0 of |D_hat - D| and the count of D > 0 into loss_ws (per-CTA
+ * partial sums, added up by the launch's last CTA); writes loss_terms[2 v] = L_c,
+ * [2 v + 1] = L_d as gs_loss does.  Uses bins->status[3] as its ticket (zero
+ * before the first call, left zero).
+ * gs_render_bwd_raster_loss: gs_render_bwd_raster with each pixel's dL/dI_hat =
+ * lambda_c sign(I_hat - I) / (3 W H) and dL/dD_hat = lambda_d sign(D_hat - D) /
+ * n_valid (0 where D <= 0) formed from img, the targets and the totals that the
+ * preceding gs_render_fwd_loss left in loss_ws (bit-identical to gs_loss's).
+ * Follow it with gs_project_bwd.
+ * loss_ws: device, 256-byte aligned, gs_fused_loss_workspace_size(n_views)
+ * bytes; it carries the totals from the forward to the backward call, so the
+ * two calls must use the same workspace, targets and views.
+ * Errors: GS_ERR_INVALID_ARG on NULL or misaligned pointers, non-finite lambdas
+ * or a small workspace. */
+size_t gs_fused_loss_workspace_size(int32_t n_views);
+int32_t gs_render_fwd_loss(const gs_projected* proj, const gs_bins* bins, const gs_camera* cams,
+                           int32_t n_views, const gs_render_params* params, gs_image* img,
+                           const float* target_color, const float* target_depth, float* loss_terms,
+                           void* loss_ws, size_t loss_ws_bytes, void* stream);
+int32_t gs_render_bwd_raster_loss(const gs_projected* proj, const gs_bins* bins, const gs_image* img,
+                                  const float* target_color, const float* target_depth, float lambda_c,
+                                  float lambda_d, const void* loss_ws, size_t loss_ws_bytes,
+                                  const gs_camera* cams, int32_t n_views, const gs_render_params* params,
+                                  int64_t n, float* grad2d, void* stream);
 
 /* Adam with bias correction over n_groups parameter groups in one launch (the
  * optimiser step of each mapping iteration, Sec. 3.3 "Map Management"; the

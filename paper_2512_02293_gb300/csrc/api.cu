@@ -187,6 +187,57 @@ int32_t gs_render_fwd(const gs_projected* proj, const gs_bins* bins, const gs_ca
                                          static_cast<cudaStream_t>(stream)));
 }
 
+size_t gs_fused_loss_workspace_size(int32_t n_views) {
+    if (n_views < 1 || n_views > GS_MAX_VIEWS) return 0;
+    return fused_loss_workspace(n_views);
+}
+
+int32_t gs_render_fwd_loss(const gs_projected* proj, const gs_bins* bins, const gs_camera* cams, int32_t n_views,
+                           const gs_render_params* params, gs_image* img, const float* target_color,
+                           const float* target_depth, float* loss_terms, void* loss_ws, size_t loss_ws_bytes,
+                           void* stream) {
+    if (!params_ok(params) || !bins_ok(bins) || !projected_ok(proj) || !image_ok(img)) return GS_ERR_INVALID_ARG;
+    if (!target_color || !target_depth || !loss_terms) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    if (loss_ws == nullptr || !aligned(loss_ws, 256) || loss_ws_bytes < fused_loss_workspace(n_views))
+        return GS_ERR_INVALID_ARG;
+    FusedLoss fl = {};
+    fl.tc = target_color; fl.td = target_depth;
+    fl.terms = loss_terms;
+    fl.ticket = bins->status + 3;
+    fused_loss_layout(loss_ws, n_views, &fl.acc, &fl.partial);
+    return cuda_status(launch_render_fwd(*proj, *bins, views, make_consts(params), *img,
+                                         static_cast<cudaStream_t>(stream), &fl));
+}
+
+int32_t gs_render_bwd_raster_loss(const gs_projected* proj, const gs_bins* bins, const gs_image* img,
+                                  const float* target_color, const float* target_depth, float lambda_c,
+                                  float lambda_d, const void* loss_ws, size_t loss_ws_bytes, const gs_camera* cams,
+                                  int32_t n_views, const gs_render_params* params, int64_t n, float* grad2d,
+                                  void* stream) {
+    if (!params_ok(params) || !bins_ok(bins) || !projected_ok(proj) || !image_ok(img)) return GS_ERR_INVALID_ARG;
+    if (!target_color || !target_depth || !grad2d || !aligned(grad2d, 16) || n < 0) return GS_ERR_INVALID_ARG;
+    if (!isfinite(lambda_c) || !isfinite(lambda_d)) return GS_ERR_INVALID_ARG;
+    Views views;
+    if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
+    if (loss_ws == nullptr || !aligned(loss_ws, 256) || loss_ws_bytes < fused_loss_workspace(n_views))
+        return GS_ERR_INVALID_ARG;
+    const int64_t E = n * n_views;
+    if (E >= (1ll << 31)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (E == 0) return GS_OK;
+    FusedLoss fl = {};
+    fl.tc = target_color; fl.td = target_depth;
+    fl.color = img->color; fl.depth = img->depth;
+    fl.lc = lambda_c; fl.ld = lambda_d;
+    fused_loss_layout(const_cast<void*>(loss_ws), n_views, &fl.acc, &fl.partial);
+    cudaError_t e = launch_zero(grad2d, kGradStride * E, nullptr, 0, nullptr, 0, s);
+    if (e == cudaSuccess)
+        e = launch_render_bwd(*proj, *bins, *img, nullptr, nullptr, views, make_consts(params), grad2d, s, &fl);
+    return cuda_status(e);
+}
+
 int32_t gs_loss(const gs_image* img, const float* target_color, const float* target_depth, const gs_camera* cams,
                 int32_t n_views, float lambda_c, float lambda_d, float* dL_dcolor, float* dL_ddepth, float* loss_terms,
                 void* ws, size_t ws_bytes, void* stream) {

@@ -83,13 +83,35 @@ cudaError_t launch_project(const gs_gaussians& g, const Views& views, const Rend
                            const gs_projected& out, cudaStream_t s);
 cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n_entries, const Views& views,
                             const SortPlan& plan, const gs_bins& bins, void* ws, cudaStream_t s);
+// The Eq. 6 colour and depth L1 terms fused into the rasterisers: the forward
+// pass sums |I_hat - I|, |D_hat - D| over D > 0 and the count of D > 0 per view
+// (per-CTA partials, finished by the last CTA into acc and the loss terms); the
+// backward pass forms each pixel's dL/dI_hat and dL/dD_hat from the images and
+// those totals instead of reading gradient images.
+struct FusedLoss {
+    const float* tc;        // target colour, planar per view like gs_image.color
+    const float* td;        // target depth
+    const float* color;     // rendered colour (read by the backward pass)
+    const float* depth;     // rendered depth (read by the backward pass)
+    float* partial;         // [forward CTAs][n_views][3]
+    float* acc;             // [n_views][4]: sum |I_hat - I|, sum_{D > 0} |D_hat - D|, count D > 0, 0
+    float* terms;           // [n_views][2]: L_c, L_d (unweighted means)
+    int* ticket;            // zero between launches (the last CTA resets it)
+    float lc, ld;
+};
+constexpr int kFusedMaxCtas = 4096;              // bound on a forward raster grid (partial slots)
+size_t fused_loss_workspace(int32_t n_views);
+// acc and partial inside a fused-loss workspace
+void fused_loss_layout(void* ws, int32_t n_views, float** acc, float** partial);
+
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
-                              const RenderConsts& rc, const gs_image& img, cudaStream_t s);
+                              const RenderConsts& rc, const gs_image& img, cudaStream_t s,
+                              const FusedLoss* fl = nullptr);
 cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, const Views& views,
                         float lc, float ld, float* dc, float* dd, float* terms, void* ws, cudaStream_t s);
 cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img,
                               const float* dc, const float* dd, const Views& views, const RenderConsts& rc,
-                              float* g2d, cudaStream_t s);
+                              float* g2d, cudaStream_t s, const FusedLoss* fl = nullptr);
 cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s);

@@ -36,6 +36,21 @@ __device__ __forceinline__ int view_of_tile(const Views& views, int g) {
     return v;
 }
 
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// 4-byte asynchronous copy global -> shared (no register held while in flight)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 // A tile of T x T pixels is covered by (T / 8) x (T / 4) warps; lane l of warp w
 // is pixel (8 (w % (T/8)) + l % 8, 4 (w / (T/8)) + l / 8) of the tile.
 template <int T>
@@ -99,6 +114,46 @@ __device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
 
+// Fused loss, end of the forward launch: this CTA's per-view sums go to its
+// partial slot; the last CTA to finish adds all slots into acc and writes the
+// loss terms (the same expressions as the stand-alone loss), then resets the
+// ticket.  Called by every thread of the CTA after its item loop.
+__device__ void fused_loss_finish(const FusedLoss& fl, const Views& views, const float* s_loss) {
+    __shared__ int s_last;
+    __shared__ float s_red[kRasterThreads / 32][3];
+    __syncthreads();
+    float* mine = fl.partial + (size_t)blockIdx.x * views.n * 3;
+    for (int k = threadIdx.x; k < views.n * 3; k += kRasterThreads) mine[k] = s_loss[k];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(fl.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int v = 0; v < views.n; v++) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int c = threadIdx.x; c < (int)gridDim.x; c += kRasterThreads) {
+            const float* p = fl.partial + ((size_t)c * views.n + v) * 3;
+            a0 += __ldcg(p); a1 += __ldcg(p + 1); a2 += __ldcg(p + 2);
+        }
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+        if (lane == 0) { s_red[w][0] = a0; s_red[w][1] = a1; s_red[w][2] = a2; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            for (int k = 0; k < kRasterThreads / 32; k++) { t0 += s_red[k][0]; t1 += s_red[k][1]; t2 += s_red[k][2]; }
+            const int HW = views.v[v].W * views.v[v].H;
+            fl.acc[4 * v] = t0; fl.acc[4 * v + 1] = t1; fl.acc[4 * v + 2] = t2; fl.acc[4 * v + 3] = 0.f;
+            fl.terms[2 * v] = t0 / (3.0f * (float)HW);
+            fl.terms[2 * v + 1] = t2 > 0.f ? t1 / t2 : 0.f;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *fl.ticket = 0;
+}
+
+
 // Every warp takes items until it draws one >= n_items, so a launch makes
 // exactly n_items + (its warps) increments; the warp that draws the last value
 // returns the counter to zero for the next launch (no reset on the stream).
@@ -111,18 +166,36 @@ __device__ __forceinline__ int next_item(int* queue, int lane, int n_items) {
     return __shfl_sync(0xffffffffu, item, 0);
 }
 
-template <int T>
+template <int T, bool LOSS>
 __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
-        gs_image img, int* __restrict__ queue, int n_items) {
+        gs_image img, int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;     // pixel blocks per tile
     __shared__ float2 s_xy[kRasterWarps][32];
     __shared__ float4 s_q[kRasterWarps][32];
     __shared__ float4 s_cd[kRasterWarps][32];
     __shared__ uint32_t s_pos[kRasterWarps][32];
+    __shared__ float s_loss[LOSS ? GS_MAX_VIEWS * 3 : 1];    // per-view sums of this CTA (fused loss)
+    __shared__ float s_tgt[LOSS ? kRasterWarps : 1][4][32];   // each lane's targets, fetched at the item's start
+    __shared__ float s_lacc[LOSS ? kRasterWarps : 1][3][32];  // each lane's running sums for the warp's view lv
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int lv = -1;                                               // view of the sums in s_lacc (warp-uniform)
+    if constexpr (LOSS) {
+        for (int k = threadIdx.x; k < views.n * 3; k += kRasterThreads) s_loss[k] = 0.f;
+        for (int k = 0; k < 3; k++) s_lacc[w][k][lane] = 0.f;
+        __syncthreads();
+    }
+    // the warp's lane sums of view lv into the CTA's per-view sums
+    auto flush_lanes = [&]() {
+        if (lv < 0) return;
+        for (int k = 0; k < 3; k++) {
+            const float x = warp_sum(s_lacc[w][k][lane]);
+            s_lacc[w][k][lane] = 0.f;
+            if (lane == 0) atomicAdd(&s_loss[3 * lv + k], x);
+        }
+    };
     const uint32_t lt_mask = (1u << lane) - 1u;
     const float amin = rc.alpha_min, amax = rc.alpha_max, tcut = rc.T_cut;
     for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
@@ -136,6 +209,16 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const int px = tx * T + ox, py = ty * T + oy;
         const bool inside = px < vp.W && py < vp.H;
         if (!__any_sync(0xffffffffu, inside)) continue;      // block entirely outside the image
+        if constexpr (LOSS) {
+            if (inside) {
+                const int HW = vp.W * vp.H, pix = py * vp.W + px;
+                const float* t = fl.tc + 3 * (size_t)vp.pix_base;
+                cp_async4(&s_tgt[w][0][lane], t + pix);
+                cp_async4(&s_tgt[w][1][lane], t + HW + pix);
+                cp_async4(&s_tgt[w][2][lane], t + 2 * HW + pix);
+                cp_async4(&s_tgt[w][3][lane], fl.td + vp.pix_base + pix);
+            }
+        }
         const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
         // sample rectangle of this 8 x 4 block
         const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f;
@@ -215,18 +298,42 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             if (last_k >= 0) last = s_pos[w][last_k] + 1u;
             if (__all_sync(0xffffffffu, done)) break;
         }
+        float ec = 0.f, ed = 0.f, nv = 0.f;
         if (inside) {
             const int HW = vp.W * vp.H;
             const int pix = py * vp.W + px;
             float* col = img.color + 3 * (size_t)vp.pix_base;
-            col[pix] = cr + Tr * rc.bg[0];
-            col[HW + pix] = cg + Tr * rc.bg[1];
-            col[2 * HW + pix] = cb + Tr * rc.bg[2];
+            const float fr = cr + Tr * rc.bg[0], fg = cg + Tr * rc.bg[1], fb = cb + Tr * rc.bg[2];
+            col[pix] = fr;
+            col[HW + pix] = fg;
+            col[2 * HW + pix] = fb;
             img.depth[vp.pix_base + pix] = dd;
             img.T_final[vp.pix_base + pix] = Tr;
             img.n_contrib[vp.pix_base + pix] = last;
+            if constexpr (LOSS) {
+                cp_async_wait_all();             // this lane's own copies
+                ec = fabsf(fr - s_tgt[w][0][lane]) + fabsf(fg - s_tgt[w][1][lane]) + fabsf(fb - s_tgt[w][2][lane]);
+                const float tdv = s_tgt[w][3][lane];
+                if (tdv > 0.f) {
+                    ed = fabsf(dd - tdv);
+                    nv = 1.f;
+                }
+            }
+        }
+        if constexpr (LOSS) {
+            if (v != lv) {                       // items come in global tile order: rare
+                flush_lanes();
+                lv = v;
+            }
+            s_lacc[w][0][lane] += ec;
+            s_lacc[w][1][lane] += ed;
+            s_lacc[w][2][lane] += nv;
         }
         __syncwarp();
+    }
+    if constexpr (LOSS) {
+        flush_lanes();
+        fused_loss_finish(fl, views, s_loss);
     }
 }
 
@@ -333,13 +440,14 @@ __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const f
 
 // Backward of one work item (pixel block blk of tile g) by one warp, using the
 // warp's shared-memory slot (s_m .. s_c: 32 entries each).
-template <int T>
+template <int T, bool LOSS>
 __device__ __forceinline__ void bwd_item(
         int g, int blk, float4* s_m, float4* s_q, float4* s_cd, float4* s_c,
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, const Views& views,
         const RenderConsts& rc, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-        const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d) {
+        const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
+        const FusedLoss& fl) {
     const int lane = threadIdx.x & 31;
     const int v = view_of_tile(views, g);
     const ViewParams& vp = views.v[v];
@@ -363,11 +471,25 @@ __device__ __forceinline__ void bwd_item(
     if (inside) {
         const int HW = vp.W * vp.H;
         const int pix = py * vp.W + px;
-        const float* dc = dL_dcolor + 3 * (size_t)vp.pix_base;
         P.T = T_final[vp.pix_base + pix];
         P.np = n_contrib[vp.pix_base + pix];
-        P.gr = dc[pix]; P.gg = dc[HW + pix]; P.gb = dc[2 * HW + pix];
-        P.gd = dL_ddepth[vp.pix_base + pix];
+        if constexpr (LOSS) {
+            // the gradient of Eq. 6's colour and depth L1 terms, as the stand-alone loss forms it
+            const float* c = fl.color + 3 * (size_t)vp.pix_base;
+            const float* t = fl.tc + 3 * (size_t)vp.pix_base;
+            const float kc = fl.lc / (3.0f * (float)HW);
+            const float nvalid = fl.acc[4 * v + 2];
+            const float kd = nvalid > 0.f ? fl.ld / nvalid : 0.f;
+            P.gr = kc * sgnf(c[pix] - t[pix]);
+            P.gg = kc * sgnf(c[HW + pix] - t[HW + pix]);
+            P.gb = kc * sgnf(c[2 * HW + pix] - t[2 * HW + pix]);
+            const float tdv = fl.td[vp.pix_base + pix];
+            P.gd = tdv > 0.f ? kd * sgnf(fl.depth[vp.pix_base + pix] - tdv) : 0.f;
+        } else {
+            const float* dc = dL_dcolor + 3 * (size_t)vp.pix_base;
+            P.gr = dc[pix]; P.gg = dc[HW + pix]; P.gb = dc[2 * HW + pix];
+            P.gd = dL_ddepth[vp.pix_base + pix];
+        }
     }
     // this warp needs the list only up to its deepest pixel (a checkpoint never points past the list)
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, P.np);
@@ -442,13 +564,13 @@ __device__ __forceinline__ void bwd_item(
 // Two occupancies (kCtas CTAs per SM): few work items per SM (a single 640x480
 // view: ~60) run best with 2 CTAs and 90 registers, where the deepest blocks'
 // chains are shorter; many (a keyframe window: ~900) with 3 CTAs and 80.
-template <int T, int kCtas>
+template <int T, int kCtas, bool LOSS>
 __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
-        int* __restrict__ queue, int n_items) {
+        int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;
     __shared__ float4 s_m[kRasterWarps][32];      // mean x, y, list position, entry (bit patterns)
     __shared__ float4 s_q[kRasterWarps][32];      // scaled conic + opacity
@@ -457,8 +579,8 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
-        bwd_item<T>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
-                    views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d);
+        bwd_item<T, LOSS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
+                          views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
         __syncwarp();
     }
 }
@@ -479,8 +601,17 @@ static int persistent_grid(K kernel, int n_items) {
     return want < g ? want : g;
 }
 
+size_t fused_loss_workspace(int32_t n_views) {
+    return align_up(sizeof(float) * 4 * (size_t)n_views, 256) + sizeof(float) * (size_t)kFusedMaxCtas * n_views * 3;
+}
+
+void fused_loss_layout(void* ws, int32_t n_views, float** acc, float** partial) {
+    *acc = static_cast<float*>(ws);
+    *partial = reinterpret_cast<float*>(static_cast<char*>(ws) + align_up(sizeof(float) * 4 * (size_t)n_views, 256));
+}
+
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
-                              const RenderConsts& rc, const gs_image& img, cudaStream_t s) {
+                              const RenderConsts& rc, const gs_image& img, cudaStream_t s, const FusedLoss* fl) {
     if (views.total_tiles == 0) return cudaSuccess;
     const float2* xy = reinterpret_cast<const float2*>(pr.xy);
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
@@ -492,8 +623,15 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 #define GS_FWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        e = launch_pdl(k_render_fwd<TT>, persistent_grid(k_render_fwd<TT>, n_items), kRasterThreads, 0, s, \
-                       xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items);                    \
+        if (fl) {                                                                                      \
+            const int grid = persistent_grid(k_render_fwd<TT, true>, n_items);                        \
+            if (grid > kFusedMaxCtas) return cudaErrorInvalidConfiguration;                           \
+            e = launch_pdl(k_render_fwd<TT, true>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, \
+                           views, rc, img, queue, n_items, *fl);                                       \
+        } else                                                                                         \
+            e = launch_pdl(k_render_fwd<TT, false>, persistent_grid(k_render_fwd<TT, false>, n_items), \
+                           kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items, \
+                           FusedLoss{});                                                               \
         break;                                                                                         \
     }
         GS_FWD(8)
@@ -507,7 +645,8 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 }
 
 cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img, const float* dc,
-                              const float* dd, const Views& views, const RenderConsts& rc, float* g2d, cudaStream_t s) {
+                              const float* dd, const Views& views, const RenderConsts& rc, float* g2d, cudaStream_t s,
+                              const FusedLoss* fl) {
     if (views.total_tiles == 0) return cudaSuccess;
     const float2* xy = reinterpret_cast<const float2*>(pr.xy);
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
@@ -519,24 +658,29 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     constexpr int kBwdFewItemsPerSm = 256;
+#define GS_BWD_LAUNCH(TT, C, L, F)                                                                     \
+    launch_pdl(k_render_bwd<TT, C, L>, persistent_grid(k_render_bwd<TT, C, L>, n_items), kRasterThreads, 0, s, \
+               xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items, F)
     switch (rc.tile) {
 #define GS_BWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        if (n_items <= kBwdFewItemsPerSm * sms)                                                        \
-            e = launch_pdl(k_render_bwd<TT, 2>, persistent_grid(k_render_bwd<TT, 2>, n_items), kRasterThreads, \
-                           0, s, xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, \
-                           queue, n_items);                                                            \
+        const bool few = n_items <= kBwdFewItemsPerSm * sms;                                          \
+        if (few && fl)                                                                                 \
+            e = GS_BWD_LAUNCH(TT, 2, true, *fl);                                                       \
+        else if (few)                                                                                  \
+            e = GS_BWD_LAUNCH(TT, 2, false, FusedLoss{});                                              \
+        else if (fl)                                                                                   \
+            e = GS_BWD_LAUNCH(TT, 3, true, *fl);                                                       \
         else                                                                                           \
-            e = launch_pdl(k_render_bwd<TT, 3>, persistent_grid(k_render_bwd<TT, 3>, n_items), kRasterThreads, \
-                           0, s, xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, \
-                           queue, n_items);                                                            \
+            e = GS_BWD_LAUNCH(TT, 3, false, FusedLoss{});                                              \
         break;                                                                                         \
     }
         GS_BWD(8)
         GS_BWD(16)
         GS_BWD(32)
 #undef GS_BWD
+#undef GS_BWD_LAUNCH
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

@@ -114,7 +114,7 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_render_bwd_raster",
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
            "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
-           "gs_ba_step"]
+           "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss"]
 
 
 def load_library(path: str | None = None):
@@ -175,7 +175,14 @@ def load_library(path: str | None = None):
     lib.gs_insert_gaussians.restype = ctypes.c_int32
     lib.gs_insert_gaussians.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_float, V, V, ctypes.c_int64,
                                         ctypes.c_int32, V, V]
-    if lib.gs_abi_version() != 2:
+    lib.gs_fused_loss_workspace_size.restype = ctypes.c_size_t
+    lib.gs_fused_loss_workspace_size.argtypes = [ctypes.c_int32]
+    lib.gs_render_fwd_loss.restype = ctypes.c_int32
+    lib.gs_render_fwd_loss.argtypes = [V, V, V, ctypes.c_int32, V, V, V, V, V, V, ctypes.c_size_t, V]
+    lib.gs_render_bwd_raster_loss.restype = ctypes.c_int32
+    lib.gs_render_bwd_raster_loss.argtypes = [V, V, V, V, V, ctypes.c_float, ctypes.c_float, V, ctypes.c_size_t, V,
+                                              ctypes.c_int32, V, ctypes.c_int64, V, V]
+    if lib.gs_abi_version() != 3:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
         _lib = lib
@@ -428,6 +435,32 @@ def gs_render_bwd_raster(proj: Projected, bins: Bins, img: Image, dL_dcolor, dL_
                                                _stream(stream)), "gs_render_bwd_raster")
 
 
+def gs_fused_loss_workspace_size(n_views: int) -> int:
+    return int(load_library().gs_fused_loss_workspace_size(n_views))
+
+
+def gs_render_fwd_loss(proj: Projected, bins: Bins, cams, params: RenderParams, img: Image, target_color,
+                       target_depth, loss_terms, loss_ws, stream=None):
+    """gs_render_fwd with the Eq. 6 colour/depth L1 sums fused in (see gs.h)."""
+    arr = camera_array(cams); p = params.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct()
+    _check(load_library().gs_render_fwd_loss(ctypes.byref(pr), ctypes.byref(b), arr, len(cams), ctypes.byref(p),
+                                             ctypes.byref(im), _ptr(target_color), _ptr(target_depth),
+                                             _ptr(loss_terms), _ptr(loss_ws), loss_ws.numel() * loss_ws.element_size(),
+                                             _stream(stream)), "gs_render_fwd_loss")
+
+
+def gs_render_bwd_raster_loss(proj: Projected, bins: Bins, img: Image, target_color, target_depth, lambda_c: float,
+                              lambda_d: float, loss_ws, cams, params: RenderParams, n: int, grad2d, stream=None):
+    """gs_render_bwd_raster with the image gradients of the fused loss formed per pixel (see gs.h)."""
+    arr = camera_array(cams); p = params.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct()
+    _check(load_library().gs_render_bwd_raster_loss(ctypes.byref(pr), ctypes.byref(b), ctypes.byref(im),
+                                                    _ptr(target_color), _ptr(target_depth), float(lambda_c),
+                                                    float(lambda_d), _ptr(loss_ws),
+                                                    loss_ws.numel() * loss_ws.element_size(), arr, len(cams),
+                                                    ctypes.byref(p), n, _ptr(grad2d), _stream(stream)),
+           "gs_render_bwd_raster_loss")
+
+
 def gs_project_bwd(g: Gaussians, cams, params: RenderParams, grad2d, lambda_iso: float, grads: Grads, iso_loss,
                    stream=None):
     arr = camera_array(cams); p = params.struct(); gg = g.struct(); gr = grads.struct()
@@ -464,11 +497,12 @@ class BoundCall:
 def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cams, params: RenderParams,
                       target_color, target_depth, lambda_c: float, lambda_d: float, dL_dcolor, dL_ddepth,
                       loss_terms, lambda_iso: float, grads: Grads, iso_loss, ws, adam_groups,
-                      beta1: float, beta2: float, eps: float, d_step):
-    """The seven calls of one mapping iteration (gs_project, gs_bin_sort,
-    gs_render_fwd, gs_loss, gs_render_bwd_raster, gs_project_bwd, gs_adam_step)
-    as BoundCall objects, in order.  ws doubles as grad2d, as in the staged
-    iteration."""
+                      beta1: float, beta2: float, eps: float, d_step, loss_ws=None):
+    """The calls of one mapping iteration as BoundCall objects, in order: with
+    loss_ws (a fused-loss workspace) the six of the fused iteration (gs_project,
+    gs_bin_sort, gs_render_fwd_loss, gs_render_bwd_raster_loss, gs_project_bwd,
+    gs_adam_step), else the seven with gs_render_fwd, gs_loss and
+    gs_render_bwd_raster.  ws doubles as grad2d, as in the staged iteration."""
     arr = camera_array(cams); V = len(cams); p = params.struct()
     gg = g.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct(); gr = grads.struct()
     wsb = ws.numel() * ws.element_size()
@@ -477,6 +511,21 @@ def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cam
         groups[k] = gs_adam_group(_ptr(pp), _ptr(gd), _ptr(m), _ptr(v), pp.numel(), float(lr), 0)
     keep = (arr, p, gg, pr, b, im, gr, groups)
     by = ctypes.byref
+    if loss_ws is not None:
+        lwb = loss_ws.numel() * loss_ws.element_size()
+        return [
+            BoundCall("gs_project", (by(gg), arr, V, by(p), by(pr)), keep),
+            BoundCall("gs_bin_sort", (by(pr), g.n, arr, V, by(p), by(b), _ptr(ws), wsb), keep),
+            BoundCall("gs_render_fwd_loss", (by(pr), by(b), arr, V, by(p), by(im), _ptr(target_color),
+                                             _ptr(target_depth), _ptr(loss_terms), _ptr(loss_ws), lwb), keep),
+            BoundCall("gs_render_bwd_raster_loss", (by(pr), by(b), by(im), _ptr(target_color), _ptr(target_depth),
+                                                    float(lambda_c), float(lambda_d), _ptr(loss_ws), lwb, arr, V,
+                                                    by(p), g.n, _ptr(ws)), keep),
+            BoundCall("gs_project_bwd", (by(gg), arr, V, by(p), _ptr(ws), float(lambda_iso), by(gr),
+                                         _ptr(iso_loss)), keep),
+            BoundCall("gs_adam_step", (groups, len(adam_groups), float(beta1), float(beta2), float(eps),
+                                       _ptr(d_step)), keep),
+        ]
     return [
         BoundCall("gs_project", (by(gg), arr, V, by(p), by(pr)), keep),
         BoundCall("gs_bin_sort", (by(pr), g.n, arr, V, by(p), by(b), _ptr(ws), wsb), keep),

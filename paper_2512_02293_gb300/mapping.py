@@ -38,8 +38,9 @@ class MapParams:
 class MappingStep:
     def __init__(self, gaussians: G.Gaussians, cams, target_color: torch.Tensor, target_depth: torch.Tensor,
                  params: G.RenderParams | None = None, mparams: MapParams | None = None,
-                 key_capacity: int | None = None, headroom: float = 1.3):
+                 key_capacity: int | None = None, headroom: float = 1.3, fused_loss: bool = True):
         self.g = gaussians
+        self.fused_loss = bool(fused_loss)
         self.cams = list(cams)
         self.params = params or G.RenderParams()
         self.mp = mparams or MapParams()
@@ -63,10 +64,14 @@ class MappingStep:
         self.m = [torch.zeros_like(t) for t in gaussians.tensors()]
         self.v = [torch.zeros_like(t) for t in gaussians.tensors()]
         self.d_step = torch.zeros(2, device=dev, dtype=torch.int32)
+        # fused loss: per-view totals carried from the forward to the backward call
+        self.loss_ws = (torch.empty((G.gs_fused_loss_workspace_size(self.V) + 3) // 4, device=dev,
+                                    dtype=torch.float32) if self.fused_loss else None)
+        self.stages = self.FUSED_STAGES if self.fused_loss else self.STAGES
         self.headroom = headroom
         self.graph = None
         self._io_stream = None
-        self._bound = None          # the seven calls marshalled once (eager step); rebuilt when stale
+        self._bound = None          # the calls marshalled once (eager step); rebuilt when stale
         self._bound_key = None
         self._alloc_bins(key_capacity if key_capacity is not None else self._measure_keys())
 
@@ -104,11 +109,24 @@ class MappingStep:
 
     # ------------------------------------------------------------ iteration
     def render(self):
+        """Projection, binning and the forward pass (with the fused loss, also the
+        loss terms against the current targets)."""
         G.gs_project(self.g, self.cams, self.params, self.proj)
         G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
-        G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
+        if self.fused_loss:
+            G.gs_render_fwd_loss(self.proj, self.bins, self.cams, self.params, self.img, self.target_color,
+                                 self.target_depth, self.loss_terms, self.loss_ws)
+        else:
+            G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
 
     def loss_and_backward(self):
+        """Eq. 6 loss and the gradients of every parameter and pose tangent (after render())."""
+        if self.fused_loss:
+            G.gs_render_bwd_raster_loss(self.proj, self.bins, self.img, self.target_color, self.target_depth,
+                                        self.mp.lambda_c, self.mp.lambda_d, self.loss_ws, self.cams, self.params,
+                                        self.n, self.ws)
+            G.gs_project_bwd(self.g, self.cams, self.params, self.ws, self.mp.lambda_iso, self.grads, self.iso)
+            return
         G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c, self.mp.lambda_d,
                   self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
         G.gs_render_bwd(self.g, self.proj, self.bins, self.img, self.dL_dcolor, self.dL_ddepth, self.cams,
@@ -120,7 +138,7 @@ class MappingStep:
         G.gs_adam_step(groups, self.mp.beta1, self.mp.beta2, self.mp.eps, self.d_step)
 
     def _bound_calls(self):
-        """The iteration's seven C-ABI calls with their arguments marshalled once;
+        """The iteration's C-ABI calls with their arguments marshalled once;
         rebuilt when the cameras, the buffers or the mapping parameters change."""
         mp = self.mp
         key = (tuple(id(c) for c in self.cams), id(self.bins), id(self.ws), id(self.target_color),
@@ -132,14 +150,14 @@ class MappingStep:
                                               self.target_color, self.target_depth, mp.lambda_c, mp.lambda_d,
                                               self.dL_dcolor, self.dL_ddepth, self.loss_terms, mp.lambda_iso,
                                               self.grads, self.iso, self.ws, groups, mp.beta1, mp.beta2, mp.eps,
-                                              self.d_step)
+                                              self.d_step, loss_ws=self.loss_ws)
             self._bound_key = key
         return self._bound
 
     def step(self):
         """One full mapping iteration (no host synchronisation): the captured graph
-        if capture() was called, else the seven C-ABI calls (arguments marshalled
-        once and reused)."""
+        if capture() was called, else the C-ABI calls (arguments marshalled once
+        and reused)."""
         if self.graph is not None:
             self.graph.replay()
             return
@@ -148,19 +166,22 @@ class MappingStep:
 
     STAGES = ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_loss", "gs_render_bwd_raster", "gs_project_bwd",
               "gs_adam_step")
+    FUSED_STAGES = ("gs_project", "gs_bin_sort", "gs_render_fwd_loss", "gs_render_bwd_raster_loss", "gs_project_bwd",
+                    "gs_adam_step")
 
     def _staged(self, events=None, host_io=None):
-        """The iteration as its seven C-ABI calls; if `events` (len 8) is given,
-        events[k] is recorded before call k and events[7] after the last.  With
-        `host_io` = (color, depth, loss_terms, iso) pinned host tensors, the
-        targets are first copied in from the first two and the loss terms and
-        the iso term copied out to the last two."""
+        """The iteration as its C-ABI calls (the names in self.stages); if
+        `events` (len(self.stages) + 1) is given, events[k] is recorded before
+        call k and the last one after the last call.  With `host_io` = (color,
+        depth, loss_terms, iso) pinned host tensors, the targets are first copied
+        in from the first two and the loss terms and the iso term copied out to
+        the last two."""
         rec = (lambda k: events[k].record()) if events is not None else (lambda k: None)
         grad2d = self.ws
         main = torch.cuda.current_stream()
         if host_io is not None:
-            # the targets are first read by the loss: their upload runs on a side
-            # branch beside projection, binning and the forward pass
+            # the targets are first read by the loss (fused: the forward pass); their
+            # upload runs on a side branch beside projection and binning
             if self._io_stream is None:
                 self._io_stream = torch.cuda.Stream()
             side = self._io_stream
@@ -168,21 +189,33 @@ class MappingStep:
             with torch.cuda.stream(side):
                 self.target_color.copy_(host_io[0], non_blocking=True)
                 self.target_depth.copy_(host_io[1], non_blocking=True)
-        rec(0)
+        k = 0
+        rec(k)
         G.gs_project(self.g, self.cams, self.params, self.proj)
-        rec(1)
+        k += 1; rec(k)
         G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
-        rec(2)
-        G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
-        if host_io is not None:
-            main.wait_stream(side)
-        rec(3)
-        G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c, self.mp.lambda_d,
-                  self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
-        rec(4)
-        G.gs_render_bwd_raster(self.proj, self.bins, self.img, self.dL_dcolor, self.dL_ddepth, self.cams, self.params,
-                               self.n, grad2d)
-        rec(5)
+        if self.fused_loss:
+            if host_io is not None:
+                main.wait_stream(side)
+            k += 1; rec(k)
+            G.gs_render_fwd_loss(self.proj, self.bins, self.cams, self.params, self.img, self.target_color,
+                                 self.target_depth, self.loss_terms, self.loss_ws)
+            k += 1; rec(k)
+            G.gs_render_bwd_raster_loss(self.proj, self.bins, self.img, self.target_color, self.target_depth,
+                                        self.mp.lambda_c, self.mp.lambda_d, self.loss_ws, self.cams, self.params,
+                                        self.n, grad2d)
+        else:
+            k += 1; rec(k)
+            G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
+            if host_io is not None:
+                main.wait_stream(side)
+            k += 1; rec(k)
+            G.gs_loss(self.img, self.target_color, self.target_depth, self.cams, self.mp.lambda_c,
+                      self.mp.lambda_d, self.dL_dcolor, self.dL_ddepth, self.loss_terms, self.ws)
+            k += 1; rec(k)
+            G.gs_render_bwd_raster(self.proj, self.bins, self.img, self.dL_dcolor, self.dL_ddepth, self.cams,
+                                   self.params, self.n, grad2d)
+        k += 1; rec(k)
         G.gs_project_bwd(self.g, self.cams, self.params, grad2d, self.mp.lambda_iso, self.grads, self.iso)
         if host_io is not None:
             # the loss terms and the iso term are final: read back beside Adam
@@ -190,16 +223,17 @@ class MappingStep:
             with torch.cuda.stream(side):
                 host_io[2].copy_(self.loss_terms, non_blocking=True)
                 host_io[3].copy_(self.iso, non_blocking=True)
-        rec(6)
+        k += 1; rec(k)
         self.optimizer_step()
-        rec(7)
+        k += 1; rec(k)
         if host_io is not None:
             main.wait_stream(side)
 
     def capture(self, warmup: int = 1, events=None, host_io=None):
         """Capture the iteration into a CUDA graph (replayed by step()).  With
-        `events` (8 torch.cuda.Event created with external=True) the graph also
-        records them around each of the seven calls, for per-stage timing.  With
+        `events` (len(self.stages) + 1 torch.cuda.Event created with
+        external=True) the graph also records them around each call, for
+        per-stage timing.  With
         `host_io` = (color, depth, loss_terms, iso), pinned host tensors shaped
         like target_color, target_depth, loss_terms and iso, every replay also
         copies that step's targets in and its loss out (memcpy nodes of the same

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gs_abi_version() == 2
+    assert lib.gs_abi_version() == 3
     assert lib.gs_status_string(0) == b"GS_OK"
     assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
     assert lib.gs_status_string(99) == b"GS_ERR_UNKNOWN"

@@ -381,8 +381,9 @@ def test_render_bwd_deep_lists(tile):
     assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("lambdas", [(1.0, 1.0, 0.0), (0.9, 0.1, 10.0)])
-def test_full_iteration_end_to_end_matches_oracle(lambdas):
+def test_full_iteration_end_to_end_matches_oracle(lambdas, fused):
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
     g, gt, cam = _problem(0)
     params = G.RenderParams()
@@ -390,7 +391,7 @@ def test_full_iteration_end_to_end_matches_oracle(lambdas):
     targets = _oracle_targets(gt, cams, params)
     tc, td = pack_images([t[0] for t in targets], [t[1] for t in targets])
     mp = MapParams(lambda_c=lambdas[0], lambda_d=lambdas[1], lambda_iso=lambdas[2])
-    step = MappingStep(G.Gaussians.from_numpy(g), cams, tc, td, params, mp)
+    step = MappingStep(G.Gaussians.from_numpy(g), cams, tc, td, params, mp, fused_loss=fused)
     step.render()
     step.loss_and_backward()
     torch.cuda.synchronize()
@@ -403,6 +404,45 @@ def test_full_iteration_end_to_end_matches_oracle(lambdas):
     for k in oracle.PARAM_NAMES:
         assert rel_l2(got[k], ref.grads[k]) < GRAD_RTOL, k
     assert rel_l2(got["pose"][0], ref.pose_grads[0]) < GRAD_RTOL
+
+
+def test_fused_loss_matches_separate_calls():
+    # gs_render_fwd_loss + gs_render_bwd_raster_loss against gs_render_fwd +
+    # gs_loss + gs_render_bwd_raster on two views whose depth targets are partly
+    # invalid (D <= 0): identical images, loss terms to fp32 summation order,
+    # gradients to atomic accumulation order
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, _ = _problem(4)
+    R, e = synth.look_at([0.3, 0.2, -0.2], [0.0, 0.0, 2.0])
+    cams = [synth.Camera(60.0, 60.0, 32.0, 24.0, 64, 48), synth.Camera(45.0, 45.0, 20.0, 15.0, 40, 30, R, e)]
+    params = G.RenderParams()
+    targets = _oracle_targets(gt, cams, params)
+    tds = []
+    for k, (_, d) in enumerate(targets):
+        d = np.array(d, copy=True)
+        d.reshape(-1)[k::3] = 0.0                  # a third of the depth targets invalid
+        tds.append(d)
+    tc, td = pack_images([t[0] for t in targets], tds)
+    mp = MapParams(0.9, 0.1, 10.0)
+    steps = [MappingStep(G.Gaussians.from_numpy(g), cams, tc, td, params, mp, fused_loss=f) for f in (True, False)]
+    for st in steps:
+        st.render()
+        st.loss_and_backward()
+    torch.cuda.synchronize()
+    a, b = steps
+    assert torch.equal(a.img.color, b.img.color) and torch.equal(a.img.n_contrib, b.img.n_contrib)
+    assert int(a.bins.status[3].item()) == 0                      # the fused forward's ticket is back at zero
+    np.testing.assert_allclose(a.loss_terms.cpu().numpy(), b.loss_terms.cpu().numpy(), rtol=2e-6)
+    ga, gb = grads_to_numpy(a.grads), grads_to_numpy(b.grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(ga[k], gb[k]) < 1e-5, k
+    for v in range(2):
+        assert rel_l2(ga["pose"][v], gb["pose"][v]) < 1e-5
+    ref = oracle.mapping_loss_and_grads(g, cams, [(t[0], d) for t, d in zip(targets, tds)], prm_dict(params),
+                                        (0.9, 0.1, 10.0))
+    np.testing.assert_allclose(a.loss_terms.cpu().numpy(), np.asarray(ref.loss_terms), rtol=1e-5)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(ga[k], ref.grads[k]) < GRAD_RTOL, k
 
 
 def test_repeated_launches_leave_work_counters_zero():
