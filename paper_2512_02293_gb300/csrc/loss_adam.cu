@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_grad(gs_image img, const 
 struct AdamArgs {
     gs_adam_group g[8];
     int64_t chunk_end[8];      // cumulative float4 chunks per group
+    int vec[8];                // the group's four arrays are 16-byte aligned (float4 loads and stores)
     int n_groups;
     float b1, b2, eps;
     int32_t* d_step;
@@ -115,7 +116,8 @@ __device__ __forceinline__ void adam_elem(float& p, float g, float& m, float& v,
                                           float ib2, float lr, float rbc1, float rbc2, float eps) {
     m = b1 * m + ib1 * g;
     v = b2 * v + ib2 * g * g;
-    p -= lr * (m * rbc1) / (sqrtf(v * rbc2) + eps);
+    // fast division (numerator times the approximate reciprocal, within 2 ulp), IEEE square root
+    p -= lr * __fdividef(m * rbc1, __fsqrt_rn(v * rbc2) + eps);
 }
 
 // One float4 chunk c of the concatenated groups.
@@ -126,9 +128,7 @@ __device__ __forceinline__ void adam_chunk(const AdamArgs& args, int64_t c, floa
     const gs_adam_group& G = args.g[k];
     const int64_t i0 = 4 * (c - (k ? args.chunk_end[k - 1] : 0));
     const float lr = G.lr;
-    const bool vec = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
-                       reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
-    if (vec && i0 + 3 < G.n) {
+    if (args.vec[k] && i0 + 3 < G.n) {
         float4 p = *reinterpret_cast<const float4*>(G.param + i0);
         const float4 g = *reinterpret_cast<const float4*>(G.grad + i0);
         float4 m = *reinterpret_cast<const float4*>(G.m + i0);
@@ -152,7 +152,7 @@ __device__ __forceinline__ void adam_chunk(const AdamArgs& args, int64_t c, floa
 // Grid-stride over 4-element chunks of all groups, two chunks per thread and
 // round (their loads in flight together); the last block to finish advances the
 // device step counter (each block reads it before finishing).
-__global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
+__global__ void __launch_bounds__(kAdamThreads, 4) k_adam(AdamArgs args) {
     __shared__ float s_bc[2];
     __shared__ int s_t;
     pdl_enter();
@@ -179,12 +179,8 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(AdamArgs args) {
         const gs_adam_group& G1 = args.g[k1];
         const int64_t i0 = 4 * (c - (k0 ? args.chunk_end[k0 - 1] : 0));
         const int64_t i1 = has1 ? 4 * (c1 - (k1 ? args.chunk_end[k1 - 1] : 0)) : 0;
-        auto aligned4 = [](const gs_adam_group& G) {
-            return ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
-                     reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
-        };
-        const bool vec0 = aligned4(G0) && i0 + 3 < G0.n;
-        const bool vec1 = has1 && aligned4(G1) && i1 + 3 < G1.n;
+        const bool vec0 = args.vec[k0] && i0 + 3 < G0.n;
+        const bool vec1 = has1 && args.vec[k1] && i1 + 3 < G1.n;
         if (vec0 && vec1) {
             // both chunks' loads issued before any store
             float4 p0 = *reinterpret_cast<const float4*>(G0.param + i0);
@@ -318,6 +314,9 @@ cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, flo
         a.g[k] = k < n_groups ? groups[k] : gs_adam_group{};
         if (k < n_groups) run += ceil_div(groups[k].n, 4);
         a.chunk_end[k] = run;
+        const gs_adam_group& G = a.g[k];
+        a.vec[k] = ((reinterpret_cast<uintptr_t>(G.param) | reinterpret_cast<uintptr_t>(G.grad) |
+                     reinterpret_cast<uintptr_t>(G.m) | reinterpret_cast<uintptr_t>(G.v)) & 15u) == 0;
     }
     a.n_groups = n_groups;
     a.b1 = b1; a.b2 = b2; a.eps = eps;

@@ -244,7 +244,8 @@ __device__ __forceinline__ float warp_sum(float x) {
 // pose tangent (rho, phi) of T_cw <- Exp(xi) T_cw; plus the isotropic
 // regulariser on the scales.
 template <int SH>
-__global__ void __launch_bounds__(kProjThreads) k_project_bwd(gs_gaussians g, Views views, RenderConsts rc,
+__global__ void __launch_bounds__(kProjThreads, SH == 0 ? 3 : 1) k_project_bwd(gs_gaussians g, Views views,
+                                                                               RenderConsts rc,
                                                               const float* __restrict__ g2d, float lambda_iso,
                                                               float inv_n, gs_grads grads, float* iso_loss) {
     pdl_enter();
