@@ -102,3 +102,30 @@ def test_mlp_entry_points_reject_bad_arguments(lib):
     g = G.gs_mlp_grads(V(256), V(256), V(256), V(256), V(256), None)
     assert lib.gs_mlp_bwd(ctypes.byref(q), V(256), V(256), V(256), V(256), 4, ctypes.byref(g), None, None) == 1
     assert lib.gs_mlp_bwd(ctypes.byref(q), V(256), V(256), V(256), V(256), 4, None, None, None) == 1
+
+
+def test_fused_loss_and_inertial_arguments_rejected_on_the_host(lib):
+    # the fused-loss calls and the inertial factor of gs_ba_step check their
+    # arguments before any launch
+    V = ctypes.c_void_p
+    assert lib.gs_fused_loss_workspace_size(0) == 0
+    assert lib.gs_fused_loss_workspace_size(G.GS_MAX_VIEWS + 1) == 0
+    one, two = lib.gs_fused_loss_workspace_size(1), lib.gs_fused_loss_workspace_size(2)
+    assert 0 < one < two
+    cams = G.camera_array([synth.identity_camera()])
+    p = G.RenderParams().struct()
+    assert lib.gs_render_fwd_loss(None, None, cams, 1, ctypes.byref(p), None, V(256), V(256), V(256), V(256),
+                                  one, None) == 1
+    assert lib.gs_render_bwd_raster_loss(None, None, None, V(256), V(256), 0.9, 0.1, V(256), one, cams, 1,
+                                         ctypes.byref(p), 10, V(256), None) == 1
+    # inertial factor: records without velocities, and 16 free keyframes
+    pr = G.gs_ba_problem(V(256), V(256), V(256), V(256), V(256), V(256), 17, 0, 4, 4, 1, 20.0, 20.0, 2.0, 2.0,
+                         V(256))
+    pr.imu = V(256)
+    assert lib.gs_ba_step(ctypes.byref(pr), 1e-3, 1e-3, V(256), V(256), 1 << 30, None) == 1
+    pr.vel, pr.bias, pr.bias_hat = V(256), V(256), V(256)
+    assert lib.gs_ba_step(ctypes.byref(pr), 1e-3, 1e-3, V(256), V(256), 1 << 30, None) == 6   # unsupported
+    pr.gravity[2] = float("nan")
+    assert lib.gs_ba_step(ctypes.byref(pr), 1e-3, 1e-3, V(256), V(256), 1 << 30, None) == 1
+    # workspace sizes grow with the inertial unknowns (15 instead of 6 per free keyframe)
+    assert lib.gs_ba_workspace_size(8, 10, 4, 4, 1, 1) > lib.gs_ba_workspace_size(8, 10, 4, 4, 1, 0)
