@@ -286,8 +286,13 @@ int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_v
  * preceding gs_render_fwd_loss left in loss_ws (bit-identical to gs_loss's).
  * Follow it with gs_project_bwd.
  * loss_ws: device, 256-byte aligned, gs_fused_loss_workspace_size(n_views)
- * bytes; it carries the totals from the forward to the backward call, so the
- * two calls must use the same workspace, targets and views.
+ * bytes, zero-filled before its first use; it carries the totals from the
+ * forward to the backward call, so the two calls must use the same workspace,
+ * targets and views.  It also carries the order in which the rasterisers take
+ * their 8 x 4 pixel blocks when a launch has few of them per SM (at most 65536
+ * blocks): the backward pass sorts the blocks by the forward's per-block depth,
+ * deepest first, and the next forward pass on the same workspace and block count
+ * reuses that order.  The order changes only which warp takes which block.
  * Errors: GS_ERR_INVALID_ARG on NULL or misaligned pointers, non-finite lambdas
  * or a small workspace. */
 size_t gs_fused_loss_workspace_size(int32_t n_views);

@@ -206,7 +206,7 @@ int32_t gs_render_fwd_loss(const gs_projected* proj, const gs_bins* bins, const 
     fl.tc = target_color; fl.td = target_depth;
     fl.terms = loss_terms;
     fl.ticket = bins->status + 3;
-    fused_loss_layout(loss_ws, n_views, &fl.acc, &fl.partial);
+    fused_loss_layout(loss_ws, n_views, &fl);
     return cuda_status(launch_render_fwd(*proj, *bins, views, make_consts(params), *img,
                                          static_cast<cudaStream_t>(stream), &fl));
 }
@@ -231,7 +231,7 @@ int32_t gs_render_bwd_raster_loss(const gs_projected* proj, const gs_bins* bins,
     fl.tc = target_color; fl.td = target_depth;
     fl.color = img->color; fl.depth = img->depth;
     fl.lc = lambda_c; fl.ld = lambda_d;
-    fused_loss_layout(const_cast<void*>(loss_ws), n_views, &fl.acc, &fl.partial);
+    fused_loss_layout(const_cast<void*>(loss_ws), n_views, &fl);
     cudaError_t e = launch_zero(grad2d, kGradStride * E, nullptr, 0, nullptr, 0, s);
     if (e == cudaSuccess)
         e = launch_render_bwd(*proj, *bins, *img, nullptr, nullptr, views, make_consts(params), grad2d, s, &fl);

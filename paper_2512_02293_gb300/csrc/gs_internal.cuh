@@ -97,12 +97,17 @@ struct FusedLoss {
     float* acc;             // [n_views][4]: sum |I_hat - I|, sum_{D > 0} |D_hat - D|, count D > 0, 0
     float* terms;           // [n_views][2]: L_c, L_d (unweighted means)
     int* ticket;            // zero between launches (the last CTA resets it)
+    uint32_t* item_cost;    // [work items] deepest n_contrib of each 8 x 4 block (forward), or null
+    uint32_t* order;        // [work items] item order, deepest blocks first (backward; next forward), or null
+    uint32_t* order_tag;    // [2] (n, n ^ kOrderTagMagic) once order holds a permutation of n items
     float lc, ld;
 };
 constexpr int kFusedMaxCtas = 4096;              // bound on a forward raster grid (partial slots)
+constexpr int kOrderMaxItems = 65536;            // work items the cost-ordered rasterisers handle
+constexpr uint32_t kOrderTagMagic = 0x9E3779B9u;
 size_t fused_loss_workspace(int32_t n_views);
-// acc and partial inside a fused-loss workspace
-void fused_loss_layout(void* ws, int32_t n_views, float** acc, float** partial);
+// acc, partial, item_cost and order inside a fused-loss workspace
+void fused_loss_layout(void* ws, int32_t n_views, FusedLoss* fl);
 
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
                               const RenderConsts& rc, const gs_image& img, cudaStream_t s,

@@ -198,7 +198,17 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
     };
     const uint32_t lt_mask = (1u << lane) - 1u;
     const float amin = rc.alpha_min, amax = rc.alpha_max, tcut = rc.T_cut;
-    for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
+    // the order the previous backward pass left, if it is a permutation of these items
+    bool ordered = false;
+    if constexpr (LOSS)
+        ordered = fl.order != nullptr && fl.order_tag[0] == (uint32_t)n_items &&
+                  fl.order_tag[1] == ((uint32_t)n_items ^ kOrderTagMagic);
+    for (int raw = next_item(queue, lane, n_items); raw < n_items; raw = next_item(queue, lane, n_items)) {
+        int item = raw;
+        if (ordered) {                           // (an index out of range can only come from a foreign workspace)
+            const uint32_t o = fl.order[raw];
+            item = o < (uint32_t)n_items ? (int)o : raw;
+        }
         const int g = item / W, blk = item % W;
         const int v = view_of_tile(views, g);
         const ViewParams& vp = views.v[v];
@@ -208,7 +218,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         lane_pixel(T, blk * 32 + lane, &ox, &oy);
         const int px = tx * T + ox, py = ty * T + oy;
         const bool inside = px < vp.W && py < vp.H;
-        if (!__any_sync(0xffffffffu, inside)) continue;      // block entirely outside the image
+        if (!__any_sync(0xffffffffu, inside)) {               // block entirely outside the image
+            if (LOSS && fl.item_cost != nullptr && lane == 0) fl.item_cost[item] = 0u;
+            continue;
+        }
         if constexpr (LOSS) {
             if (inside) {
                 const int HW = vp.W * vp.H, pix = py * vp.W + px;
@@ -321,6 +334,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             }
         }
         if constexpr (LOSS) {
+            if (fl.item_cost != nullptr) {       // the block's deepest walk, for the backward's item order
+                const uint32_t deepest = __reduce_max_sync(0xffffffffu, inside ? last : 0u);
+                if (lane == 0) fl.item_cost[item] = deepest;
+            }
             if (v != lv) {                       // items come in global tile order: rare
                 flush_lanes();
                 lv = v;
@@ -578,7 +595,8 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
     __shared__ float4 s_c[kRasterWarps][32];      // raw conic A, B, C
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int item = next_item(queue, lane, n_items); item < n_items; item = next_item(queue, lane, n_items)) {
+    for (int raw = next_item(queue, lane, n_items); raw < n_items; raw = next_item(queue, lane, n_items)) {
+        const int item = (LOSS && fl.order != nullptr) ? (int)fl.order[raw] : raw;
         bwd_item<T, LOSS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
                           views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
         __syncwarp();
@@ -586,6 +604,58 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
 }
 
 }  // namespace
+
+// The backward's item order: the forward's per-item costs (deepest n_contrib of
+// the 8 x 4 block) counting-sorted in descending order (costs above the last
+// bucket share it; items of one bucket in any order), so that the longest
+// walks start first and the launch does not end on one deep block.  One CTA.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 2048;
+
+__global__ void __launch_bounds__(kOrderThreads) k_item_order(const uint32_t* __restrict__ cost,
+                                                              uint32_t* __restrict__ order, uint32_t* tag, int n) {
+    __shared__ uint32_t h[kOrderBuckets];
+    __shared__ uint32_t s_warp[kOrderThreads / 32];
+    pdl_enter();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    auto bucket = [](uint32_t c) { return (uint32_t)(kOrderBuckets - 1) - min(c, (uint32_t)(kOrderBuckets - 1)); };
+    for (int k = t; k < kOrderBuckets; k += kOrderThreads) h[k] = 0u;
+    __syncthreads();
+    for (int i = t; i < n; i += kOrderThreads) atomicAdd(&h[bucket(cost[i])], 1u);
+    __syncthreads();
+    // exclusive scan of the 2048 buckets, two per thread
+    const uint32_t a = h[2 * t], b = h[2 * t + 1];
+    uint32_t inc = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t wv = s_warp[lane];
+        uint32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_warp[lane] = wi - wv;
+    }
+    __syncthreads();
+    const uint32_t excl = s_warp[warp] + inc - (a + b);
+    h[2 * t] = excl;
+    h[2 * t + 1] = excl + a;
+    __syncthreads();
+    for (int i = t; i < n; i += kOrderThreads) order[atomicAdd(&h[bucket(cost[i])], 1u)] = (uint32_t)i;
+    __syncthreads();
+    if (t == 0) {                                 // the order now holds a permutation of the n items
+        tag[0] = (uint32_t)n;
+        tag[1] = (uint32_t)n ^ kOrderTagMagic;
+    }
+}
+static_assert(kOrderBuckets == 2 * kOrderThreads, "two buckets per thread in the scan");
 
 // CTAs of a persistent raster launch: every SM filled to the kernel's occupancy
 // (host-side occupancy query; no stream operation, so it may run during capture).
@@ -602,12 +672,21 @@ static int persistent_grid(K kernel, int n_items) {
 }
 
 size_t fused_loss_workspace(int32_t n_views) {
-    return align_up(sizeof(float) * 4 * (size_t)n_views, 256) + sizeof(float) * (size_t)kFusedMaxCtas * n_views * 3;
+    return align_up(sizeof(float) * 4 * (size_t)n_views, 256) +
+           align_up(sizeof(float) * (size_t)kFusedMaxCtas * n_views * 3, 256) + 256 +
+           2 * sizeof(uint32_t) * kOrderMaxItems;
 }
 
-void fused_loss_layout(void* ws, int32_t n_views, float** acc, float** partial) {
-    *acc = static_cast<float*>(ws);
-    *partial = reinterpret_cast<float*>(static_cast<char*>(ws) + align_up(sizeof(float) * 4 * (size_t)n_views, 256));
+void fused_loss_layout(void* ws, int32_t n_views, FusedLoss* fl) {
+    char* p = static_cast<char*>(ws);
+    fl->acc = reinterpret_cast<float*>(p);
+    p += align_up(sizeof(float) * 4 * (size_t)n_views, 256);
+    fl->partial = reinterpret_cast<float*>(p);
+    p += align_up(sizeof(float) * (size_t)kFusedMaxCtas * n_views * 3, 256);
+    fl->order_tag = reinterpret_cast<uint32_t*>(p);
+    p += 256;
+    fl->item_cost = reinterpret_cast<uint32_t*>(p);
+    fl->order = fl->item_cost + kOrderMaxItems;
 }
 
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
@@ -626,8 +705,10 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
         if (fl) {                                                                                      \
             const int grid = persistent_grid(k_render_fwd<TT, true>, n_items);                        \
             if (grid > kFusedMaxCtas) return cudaErrorInvalidConfiguration;                           \
+            FusedLoss f = *fl;                                                                         \
+            if (n_items > kOrderMaxItems) f.item_cost = f.order = nullptr;                             \
             e = launch_pdl(k_render_fwd<TT, true>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, \
-                           views, rc, img, queue, n_items, *fl);                                       \
+                           views, rc, img, queue, n_items, f);                                         \
         } else                                                                                         \
             e = launch_pdl(k_render_fwd<TT, false>, persistent_grid(k_render_fwd<TT, false>, n_items), \
                            kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items, \
@@ -666,12 +747,20 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
         const bool few = n_items <= kBwdFewItemsPerSm * sms;                                          \
+        FusedLoss f = fl ? *fl : FusedLoss{};                                                          \
+        /* few items per SM: deepest blocks first (costs from the fused forward) */                    \
+        if (fl && few && n_items <= kOrderMaxItems)                                                    \
+            e = launch_pdl(k_item_order, 1, kOrderThreads, 0, s, (const uint32_t*)f.item_cost, f.order, \
+                           f.order_tag, n_items);                                                      \
+        else                                                                                           \
+            f.order = nullptr;                                                                         \
+        if (e != cudaSuccess) return e;                                                                \
         if (few && fl)                                                                                 \
-            e = GS_BWD_LAUNCH(TT, 2, true, *fl);                                                       \
+            e = GS_BWD_LAUNCH(TT, 2, true, f);                                                         \
         else if (few)                                                                                  \
             e = GS_BWD_LAUNCH(TT, 2, false, FusedLoss{});                                              \
         else if (fl)                                                                                   \
-            e = GS_BWD_LAUNCH(TT, 3, true, *fl);                                                       \
+            e = GS_BWD_LAUNCH(TT, 3, true, f);                                                         \
         else                                                                                           \
             e = GS_BWD_LAUNCH(TT, 3, false, FusedLoss{});                                              \
         break;                                                                                         \

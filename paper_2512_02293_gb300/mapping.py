@@ -65,7 +65,7 @@ class MappingStep:
         self.v = [torch.zeros_like(t) for t in gaussians.tensors()]
         self.d_step = torch.zeros(2, device=dev, dtype=torch.int32)
         # fused loss: per-view totals carried from the forward to the backward call
-        self.loss_ws = (torch.empty((G.gs_fused_loss_workspace_size(self.V) + 3) // 4, device=dev,
+        self.loss_ws = (torch.zeros((G.gs_fused_loss_workspace_size(self.V) + 3) // 4, device=dev,
                                     dtype=torch.float32) if self.fused_loss else None)
         self.stages = self.FUSED_STAGES if self.fused_loss else self.STAGES
         self.headroom = headroom
