@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # on this workload, from an ncu capture of the current kernels
 # (profiles/k_render_{bwd,fwd}_640x480_200k.md); keyed by (stage, tile).
 PROFILED_TRAFFIC = {("gs_render_bwd_raster", 16): 22.28e6, ("gs_render_fwd", 16): 9.28e6,
-                    ("gs_render_bwd_raster_loss", 16): 27.20e6, ("gs_render_fwd_loss", 16): 14.21e6}
+                    ("gs_render_bwd_raster_loss", 16): 27.23e6, ("gs_render_fwd_loss", 16): 14.25e6}
 
 
 def _peaks():
