@@ -858,7 +858,7 @@ def main():
         if dominant == bwd_st:
             ms, ops, kern = (st[bwd_st], BWD_OPS_PER_PAIR,
                              f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> "
-                             f"(+ its grad2d zero-fill)")
+                             f"(+ its grad2d zero-fill and block ordering)")
         else:
             ms, ops, kern = st[fwd_st], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}, {fl}>"
         ach = pairs * ops / (ms * 1e-3) / 1e12
