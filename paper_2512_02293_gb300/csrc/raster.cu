@@ -24,6 +24,12 @@
 // transposed butterfly (10 values in 12 shuffles; each lane ends with one
 // finished sum); two splats are reduced together so that their shuffle chains
 // overlap, and the ten sums go to global memory as ten atomics.
+//
+// With the loss fused in (gs_render_fwd_loss / gs_render_bwd_raster_loss) the
+// forward pass also sums the Eq. 6 L1 terms per view and records each block's
+// deepest n_contrib; when a launch has few blocks per SM, one CTA sorts the
+// blocks by that depth and both passes take the deepest blocks first, so that
+// no long walk starts when the queue is nearly empty.
 #include "gs_internal.cuh"
 
 namespace gs {
