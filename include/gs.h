@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 3
+#define GS_ABI_VERSION 4
 #define GS_MAX_VIEWS 32
 
 typedef enum gs_status {
@@ -315,6 +315,38 @@ int32_t gs_render_bwd_raster_loss(const gs_projected* proj, const gs_bins* bins,
  * Errors: GS_ERR_INVALID_ARG on NULL pointers, n < 0, n_groups outside [1, 8]. */
 int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1, float beta2,
                      float eps, int32_t* d_step, void* stream);
+
+/* One whole mapping iteration of the fused path in one call: gs_project,
+ * gs_bin_sort (workspace ws), gs_render_fwd_loss (loss_ws),
+ * gs_render_bwd_raster_loss (2D gradients in ws, which the sort no longer
+ * needs), gs_project_bwd and gs_adam_step, issued in that order on `stream`
+ * with the arguments below (each as documented for its call).  ws must hold
+ * gs_workspace_size() bytes.  Returns the first non-GS_OK status of the six;
+ * the calls after it are not issued. */
+typedef struct gs_mapping_step_args {
+    const gs_gaussians* gaussians;
+    const gs_camera* cams;
+    const gs_render_params* params;
+    gs_projected* proj;
+    gs_bins* bins;
+    gs_image* img;
+    gs_grads* grads;
+    const float* target_color;
+    const float* target_depth;
+    float* loss_terms;            /* [n_views][2] */
+    float* iso_loss;              /* device scalar or NULL */
+    void* ws;
+    size_t ws_bytes;
+    void* loss_ws;
+    size_t loss_ws_bytes;
+    const gs_adam_group* adam_groups;
+    int32_t* d_step;
+    int32_t n_views;
+    int32_t n_adam_groups;
+    float lambda_c, lambda_d, lambda_iso;
+    float beta1, beta2, adam_eps;
+} gs_mapping_step_args;
+int32_t gs_mapping_step(const gs_mapping_step_args* args, void* stream);
 
 /* ------------------------------------------------------------------------
  * Learned initialiser of inserted Gaussians (keyframe insertion, Sec. 3.3

@@ -326,6 +326,28 @@ int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1,
     return cuda_status(launch_adam(groups, n_groups, beta1, beta2, eps, d_step, static_cast<cudaStream_t>(stream)));
 }
 
+int32_t gs_mapping_step(const gs_mapping_step_args* a, void* stream) {
+    if (a == nullptr || a->gaussians == nullptr || a->bins == nullptr || a->ws == nullptr) return GS_ERR_INVALID_ARG;
+    const int64_t n = a->gaussians->n;
+    float* grad2d = static_cast<float*>(a->ws);
+    int32_t st = gs_project(a->gaussians, a->cams, a->n_views, a->params, a->proj, stream);
+    if (st == GS_OK)
+        st = gs_bin_sort(a->proj, n, a->cams, a->n_views, a->params, a->bins, a->ws, a->ws_bytes, stream);
+    if (st == GS_OK)
+        st = gs_render_fwd_loss(a->proj, a->bins, a->cams, a->n_views, a->params, a->img, a->target_color,
+                                a->target_depth, a->loss_terms, a->loss_ws, a->loss_ws_bytes, stream);
+    if (st == GS_OK)
+        st = gs_render_bwd_raster_loss(a->proj, a->bins, a->img, a->target_color, a->target_depth, a->lambda_c,
+                                       a->lambda_d, a->loss_ws, a->loss_ws_bytes, a->cams, a->n_views, a->params, n,
+                                       grad2d, stream);
+    if (st == GS_OK)
+        st = gs_project_bwd(a->gaussians, a->cams, a->n_views, a->params, grad2d, a->lambda_iso, a->grads,
+                            a->iso_loss, stream);
+    if (st == GS_OK)
+        st = gs_adam_step(a->adam_groups, a->n_adam_groups, a->beta1, a->beta2, a->adam_eps, a->d_step, stream);
+    return st;
+}
+
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status) {
     if (d_status == nullptr || host_status == nullptr) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

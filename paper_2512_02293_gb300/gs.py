@@ -97,6 +97,15 @@ class gs_ba_problem(ctypes.Structure):
 GS_BA_IMU_FLOATS = 286
 
 
+class gs_mapping_step_args(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("gaussians", "cams", "params", "proj", "bins", "img", "grads",
+                                                "target_color", "target_depth", "loss_terms", "iso_loss")] + \
+               [("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t), ("loss_ws", ctypes.c_void_p),
+                ("loss_ws_bytes", ctypes.c_size_t), ("adam_groups", ctypes.c_void_p), ("d_step", ctypes.c_void_p),
+                ("n_views", ctypes.c_int32), ("n_adam_groups", ctypes.c_int32)] + \
+               [(k, ctypes.c_float) for k in ("lambda_c", "lambda_d", "lambda_iso", "beta1", "beta2", "adam_eps")]
+
+
 class gs_mlp_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
 
@@ -114,7 +123,8 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_render_bwd_raster",
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
            "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
-           "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss"]
+           "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss",
+           "gs_mapping_step"]
 
 
 def load_library(path: str | None = None):
@@ -182,7 +192,9 @@ def load_library(path: str | None = None):
     lib.gs_render_bwd_raster_loss.restype = ctypes.c_int32
     lib.gs_render_bwd_raster_loss.argtypes = [V, V, V, V, V, ctypes.c_float, ctypes.c_float, V, ctypes.c_size_t, V,
                                               ctypes.c_int32, V, ctypes.c_int64, V, V]
-    if lib.gs_abi_version() != 3:
+    lib.gs_mapping_step.restype = ctypes.c_int32
+    lib.gs_mapping_step.argtypes = [V, V]
+    if lib.gs_abi_version() != 4:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
         _lib = lib
@@ -497,12 +509,13 @@ class BoundCall:
 def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cams, params: RenderParams,
                       target_color, target_depth, lambda_c: float, lambda_d: float, dL_dcolor, dL_ddepth,
                       loss_terms, lambda_iso: float, grads: Grads, iso_loss, ws, adam_groups,
-                      beta1: float, beta2: float, eps: float, d_step, loss_ws=None):
+                      beta1: float, beta2: float, eps: float, d_step, loss_ws=None, one_call: bool = True):
     """The calls of one mapping iteration as BoundCall objects, in order: with
-    loss_ws (a fused-loss workspace) the six of the fused iteration (gs_project,
-    gs_bin_sort, gs_render_fwd_loss, gs_render_bwd_raster_loss, gs_project_bwd,
-    gs_adam_step), else the seven with gs_render_fwd, gs_loss and
-    gs_render_bwd_raster.  ws doubles as grad2d, as in the staged iteration."""
+    loss_ws (a fused-loss workspace) the single native gs_mapping_step (or, with
+    one_call=False, its six calls gs_project, gs_bin_sort, gs_render_fwd_loss,
+    gs_render_bwd_raster_loss, gs_project_bwd, gs_adam_step), else the seven with
+    gs_render_fwd, gs_loss and gs_render_bwd_raster.  ws doubles as grad2d, as
+    in the staged iteration."""
     arr = camera_array(cams); V = len(cams); p = params.struct()
     gg = g.struct(); pr = proj.struct(); b = bins.struct(); im = img.struct(); gr = grads.struct()
     wsb = ws.numel() * ws.element_size()
@@ -511,6 +524,16 @@ def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cam
         groups[k] = gs_adam_group(_ptr(pp), _ptr(gd), _ptr(m), _ptr(v), pp.numel(), float(lr), 0)
     keep = (arr, p, gg, pr, b, im, gr, groups)
     by = ctypes.byref
+    if loss_ws is not None and one_call:
+        # the whole fused iteration as one native call (gs_mapping_step)
+        lwb = loss_ws.numel() * loss_ws.element_size()
+        ad = ctypes.addressof
+        args = gs_mapping_step_args(ad(gg), ad(arr), ad(p), ad(pr), ad(b), ad(im), ad(gr), _ptr(target_color),
+                                    _ptr(target_depth), _ptr(loss_terms), _ptr(iso_loss), _ptr(ws), wsb,
+                                    _ptr(loss_ws), lwb, ad(groups), _ptr(d_step), V, len(adam_groups),
+                                    float(lambda_c), float(lambda_d), float(lambda_iso), float(beta1), float(beta2),
+                                    float(eps))
+        return [BoundCall("gs_mapping_step", (ctypes.byref(args),), keep + (args,))]
     if loss_ws is not None:
         lwb = loss_ws.numel() * loss_ws.element_size()
         return [

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gs_abi_version() == 3
+    assert lib.gs_abi_version() == 4
     assert lib.gs_status_string(0) == b"GS_OK"
     assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
     assert lib.gs_status_string(99) == b"GS_ERR_UNKNOWN"
@@ -48,6 +48,8 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(G.gs_gaussians) == 6 * 8
     assert ctypes.sizeof(G.gs_bins) == 6 * 8
     assert ctypes.sizeof(G.gs_adam_group) == 4 * 8 + 8 + 8
+    # 11 pointers, (ws, bytes), (loss_ws, bytes), 2 pointers, 2 int32, 6 floats
+    assert ctypes.sizeof(G.gs_mapping_step_args) == 11 * 8 + 2 * 16 + 2 * 8 + 2 * 4 + 6 * 4
 
 
 def test_tiles_pixels_workspace_host_only(lib):
@@ -129,3 +131,15 @@ def test_fused_loss_and_inertial_arguments_rejected_on_the_host(lib):
     assert lib.gs_ba_step(ctypes.byref(pr), 1e-3, 1e-3, V(256), V(256), 1 << 30, None) == 1
     # workspace sizes grow with the inertial unknowns (15 instead of 6 per free keyframe)
     assert lib.gs_ba_workspace_size(8, 10, 4, 4, 1, 1) > lib.gs_ba_workspace_size(8, 10, 4, 4, 1, 0)
+
+
+def test_mapping_step_rejects_missing_arguments(lib):
+    assert lib.gs_mapping_step(None, None) == 1
+    a = G.gs_mapping_step_args()
+    assert lib.gs_mapping_step(ctypes.byref(a), None) == 1          # no Gaussians, bins or workspace
+    g = G.gs_gaussians(None, None, None, None, None, 10)
+    bins = G.gs_bins()
+    a.gaussians = ctypes.addressof(g)
+    a.bins = ctypes.addressof(bins)
+    a.ws = 256
+    assert lib.gs_mapping_step(ctypes.byref(a), None) == 1          # the projection's checks reject NULL arrays

@@ -445,6 +445,29 @@ def test_fused_loss_matches_separate_calls():
         assert rel_l2(ga[k], ref.grads[k]) < GRAD_RTOL, k
 
 
+def test_native_mapping_step_matches_the_six_calls():
+    # gs_mapping_step (one C call, the eager MappingStep.step) against its six
+    # calls issued one by one on an identical map
+    from paper_2512_02293_gb300.mapping import MapParams, MappingStep
+    g, gt, cam = _problem(3)
+    params = G.RenderParams()
+    targets = _oracle_targets(gt, [cam], params)
+    tc, td = pack_images([targets[0][0]], [targets[0][1]])
+    mp = MapParams(0.9, 0.1, 10.0)
+    a, b = (MappingStep(G.Gaussians.from_numpy(g), [cam], tc, td, params, mp) for _ in range(2))
+    assert [c.name for c in a._bound_calls()] == ["gs_mapping_step"]
+    a.step()
+    b.render(); b.loss_and_backward(); b.optimizer_step()
+    torch.cuda.synchronize()
+    assert a.check() == 0 and b.check() == 0
+    assert torch.equal(a.img.color, b.img.color) and torch.equal(a.img.n_contrib, b.img.n_contrib)
+    np.testing.assert_allclose(a.loss_terms.cpu().numpy(), b.loss_terms.cpu().numpy(), rtol=2e-6)
+    ga, gb = grads_to_numpy(a.grads), grads_to_numpy(b.grads)
+    for k in oracle.PARAM_NAMES:
+        assert rel_l2(ga[k], gb[k]) < 1e-5, k
+    assert int(a.d_step[0].item()) == 1 and int(b.d_step[0].item()) == 1
+
+
 def test_repeated_launches_leave_work_counters_zero():
     # the persistent rasterisers' work counters are returned to zero by the last
     # warp of each launch (no reset on the stream): eager calls and graph replays
