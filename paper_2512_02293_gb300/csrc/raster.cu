@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 const uint32_t deepest = __reduce_max_sync(0xffffffffu, inside ? last : 0u);
                 if (lane == 0) fl.item_cost[item] = deepest;
             }
-            if (v != lv) {                       // items come in global tile order: rare
+            if (v != lv) {                       // rare: items of one view are taken together, except
+                                                 // that the depth order may interleave views
                 flush_lanes();
                 lv = v;
             }
