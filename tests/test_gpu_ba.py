@@ -232,3 +232,26 @@ def test_vi_largest_system_15_free_keyframes():
     # as are inertial records without velocities
     with pytest.raises(ValueError):
         G.BAWindow(o["R"], o["t"], o["disp"], o["intr"], o["edges"], o["targets"], o["weights"], 1, imu=o["imu"])
+
+
+def test_vi_convergence_at_the_benchmark_size():
+    # the benchmark's window (16 keyframes at 60 x 80, edges up to 3 apart, one
+    # keyframe fixed, the inertial factor between consecutive keyframes): from a
+    # perturbed state of an exactly consistent window, damped Gauss-Newton steps
+    # drive the joint cost down by more than four orders of magnitude (the state
+    # itself settles within ~1e-3 of the generating one along a weakly observable
+    # direction, so it is not compared here; the small windows above compare it)
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(31, K=16, h=60, w=80, f=70.0, window=3)
+    targets = _exact_targets(R, t, disp, intr, edges)
+    rng = np.random.default_rng(32)
+    dx = np.concatenate([rng.normal(0, 0.005, (15, 6)), rng.normal(0, 0.01, (15, 3)),
+                         rng.normal(0, 0.001, (15, 6))], 1)
+    R1, t1, d1, v1, b1 = ba.apply_step_vi(R, t, disp, vel, bias, dx, rng.normal(0, 0.005, disp.shape), 1)
+    win = G.BAWindow(R1, t1, d1, intr, edges, targets, wts, 1, imu=imu, vel=v1, bias=b1, bias_hat=bh, gravity=g)
+    costs = []
+    for _ in range(15):
+        G.gs_ba_step(win, 1e-5, 1e-6)
+        costs.append(win.cost.item())
+    torch.cuda.synchronize()
+    assert int(win.status[0].item()) == 0
+    assert costs[-1] < 1e-4 * costs[0]
