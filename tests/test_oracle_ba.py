@@ -121,3 +121,32 @@ def test_visual_inertial_gauss_newton_recovers_the_window():
     np.testing.assert_allclose(t1, t, atol=1e-7)
     np.testing.assert_allclose(v1, vel, atol=1e-6)
     np.testing.assert_allclose(b1, bias, atol=1e-7)
+
+
+def test_inertial_jacobian_closed_form_blocks():
+    # blocks of the Eq. 3 Jacobian that are exact closed forms at any state, for
+    # the pair (1, 2) of a perturbed 4-keyframe window with keyframe 0 fixed:
+    # perturbation R_k <- R_k Exp(-phi), p_k <- p_k - R_k rho, v and b additive
+    R, t, disp, intr, edges, wts, vel, bias, bh, g, imu = synth.vi_scene(8, K=4)
+    rng = np.random.default_rng(9)
+    dx0 = np.concatenate([rng.normal(0, 0.05, (3, 6)), rng.normal(0, 0.1, (3, 3)), rng.normal(0, 0.01, (3, 6))], 1)
+    R, t, _, vel, bias = ba.apply_step_vi(R, t, disp, vel, bias, dx0, 0.0, 1)
+    J = ba.inertial_jacobian(R, t, vel, bias, bh, imu, g, 1)
+    Rb, _ = ba.body_states(R, t)
+    _, _, _, _, Jpos, Jvel, dt, _ = ba._unpack(imu[1])
+    rows = slice(15, 30)                       # residuals of pair (1, 2)
+    Ji, Jj = J[rows, 0:15], J[rows, 15:30]     # columns of keyframes 1 and 2
+    Ri, Rj = Rb[1], Rb[2]
+    tol = dict(atol=1e-6)
+    np.testing.assert_allclose(Ji[3:6, 0:3], np.eye(3), **tol)                 # d r_pos / d rho_i
+    np.testing.assert_allclose(Jj[3:6, 0:3], -Ri.T @ Rj, **tol)                # d r_pos / d rho_j
+    np.testing.assert_allclose(Ji[3:6, 6:9], -Ri.T * dt, **tol)                # d r_pos / d v_i
+    np.testing.assert_allclose(Ji[6:9, 6:9], -Ri.T, **tol)                     # d r_vel / d v_i
+    np.testing.assert_allclose(Jj[6:9, 6:9], Ri.T, **tol)                      # d r_vel / d v_j
+    np.testing.assert_allclose(Ji[3:6, 9:15], -Jpos, **tol)                    # d r_pos / d b_i
+    np.testing.assert_allclose(Ji[6:9, 9:15], -Jvel, **tol)                    # d r_vel / d b_i
+    np.testing.assert_allclose(Ji[9:15, 9:15], -np.eye(6), **tol)              # d r_bias / d b_i
+    np.testing.assert_allclose(Jj[9:15, 9:15], np.eye(6), **tol)               # d r_bias / d b_j
+    for blk in (Ji[0:3, 0:3], Jj[0:3, 0:3], Ji[6:9, 0:3], Jj[6:9, 0:3], Ji[9:15, 0:9], Jj[9:15, 0:9],
+                Jj[0:3, 6:15], Jj[3:9, 9:15]):
+        np.testing.assert_allclose(blk, 0.0, **tol)                            # no dependence
