@@ -20,7 +20,8 @@
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
  *    NULL = the legacy default stream), performs no host synchronisation and no
  *    allocation, and may be captured into a CUDA graph.  Exceptions:
- *    gs_read_device_status synchronises `stream`.
+ *    gs_read_device_status synchronises `stream`; gs_loss_noalloc and the
+ *    test hook gs_mlp_set_wait_polls carry their own notes.
  *  - Errors detectable on the host (NULL pointers, negative sizes, unsupported
  *    tile sizes, too many views, a too-small workspace) return a non-zero
  *    gs_status before anything is launched.  Errors found on the device
@@ -177,7 +178,10 @@ size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams,
 int32_t gs_project(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
                    const gs_render_params* params, gs_projected* out, void* stream);
 
-/* Tile binning and depth sort: one key (global tile << 32) | bits(float z) per
+/* Tile binning and depth sort.  The paper does not describe this step: Sec. 3.3
+ * renders with the 3D Gaussian splatting rasteriser it builds on, whose
+ * compositing visits each tile's splats front to back.  Here: one key
+ * (global tile << 32) | bits(float z) per
  * (entry, covered tile), keys sorted ascending by a stable LSD radix sort of
  * the entry-ordered list (ties in z keep entry order), and [start, end) of each
  * tile in the sorted list.  Global tile of view v = tile_base(v) + ty * tiles_x(v)
@@ -215,11 +219,11 @@ int32_t gs_loss(const gs_image* img, const float* target_color, const float* tar
 
 /* Allocation-free variant of gs_loss, for callers that cannot allocate device
  * memory for a workspace (no counterpart in the paper; it exists for such
- * callers only).  Examples: code that runs while a CUDA graph is being
- * captured in global mode, where allocation calls are illegal; processes that
- * must keep a fixed, pre-planned device-memory budget (an embedded or
- * real-time tracker); a plugin inside a host application that owns the
- * allocator and forbids other allocations.
+ * callers only).  Examples: processes that must keep a fixed, pre-planned
+ * device-memory budget (an embedded or real-time tracker that may not grow its
+ * footprint after start-up); a plugin inside a host application that owns the
+ * device allocator and forbids any other allocation; code running where an
+ * allocation call is not allowed at that moment.
  * Same arguments, outputs and errors as gs_loss, without the workspace: the
  * per-view accumulators live in a static device array of
  * GS_NOALLOC_LOSS_MAX_VIEWS x 4 floats that every device loading the library
@@ -227,7 +231,11 @@ int32_t gs_loss(const gs_image* img, const float* target_color, const float* tar
  * GS_ERR_INVALID_ARG.  The call allocates nothing (no cudaMalloc / cudaFree /
  * allocating library routine).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  Each call zeroes the
+ * make that first call before any stream capture.  The address is cached for
+ * the life of the process: after cudaDeviceReset (or anything else that
+ * destroys the device's primary context and reloads the library's module) the
+ * cached address is stale, and calling gs_loss_noalloc again is not supported.
+ * Each call zeroes the
  * accumulators before use, but all calls on a device share them: calls whose
  * executions overlap on the GPU (different streams, no ordering) race. */
 #define GS_NOALLOC_LOSS_MAX_VIEWS 32
@@ -321,8 +329,9 @@ int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1,
  * gs_render_bwd_raster_loss (2D gradients in ws, which the sort no longer
  * needs), gs_project_bwd and gs_adam_step, issued in that order on `stream`
  * with the arguments below (each as documented for its call).  ws must hold
- * gs_workspace_size() bytes.  Returns the first non-GS_OK status of the six;
- * the calls after it are not issued. */
+ * gs_workspace_size() bytes for these Gaussians, views and key capacity and be
+ * 256-byte aligned, else GS_ERR_INVALID_ARG before anything is issued.  Returns
+ * the first non-GS_OK status of the six; the calls after it are not issued. */
 typedef struct gs_mapping_step_args {
     const gs_gaussians* gaussians;
     const gs_camera* cams;
@@ -417,6 +426,19 @@ int32_t gs_mlp_fwd(const gs_mlp_packed* packed, const uint16_t* X, int64_t n, fl
 int32_t gs_mlp_bwd(const gs_mlp_packed* packed, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
                    const float* dY, int64_t n, const gs_mlp_grads* grads, int32_t* d_status, void* stream);
 
+/* Test hook of the bounded device-side waits (no counterpart in the paper).
+ * gs_mlp_fwd and gs_mlp_bwd wait on mbarriers for their tensor-core MMAs, each
+ * wait at most this many polls; a wait that runs out lets the kernel wait
+ * (bounded again) for the MMAs and copies it has in flight, record
+ * GS_ERR_TIMEOUT in *d_status, release its tensor memory and return, so the
+ * context stays usable.  Sets the limit of the launches issued after the call
+ * (process-wide; 0 makes the first wait give up at once; a negative value
+ * restores the default GS_MLP_WAIT_POLLS_DEFAULT) and returns the previous
+ * limit, or -1 (nothing changed) above 2^32 - 1.  The limit is read when a
+ * launch is issued, so a captured graph keeps the value of its capture. */
+#define GS_MLP_WAIT_POLLS_DEFAULT 67108864u
+int64_t gs_mlp_set_wait_polls(int64_t polls);
+
 /* ------------------------------------------------------------------------
  * Keyframe insertion (Sec. 3.3 "Map Management").  A keyframe is one view:
  * colour [3][H][W] and depth [H][W] (device, FP32, planar), its gs_camera, and
@@ -489,7 +511,9 @@ int32_t gs_loop_closure_update(const gs_map_slots* map, const int32_t* anchor, c
  *   order) and every inverse depth of every keyframe that is an edge source.
  *   (H + lambda diag(H) + eps I) delta = -g with H = J^T W J, g = J^T W r,
  *   solved through the Schur complement of the diagonal inverse-depth block.
- * The inertial factor of Eq. 3 is not part of this call. */
+ * With gs_ba_problem.imu set, the inertial factor of Eq. 3 between consecutive
+ * keyframes joins the same system (each free keyframe then also has a velocity
+ * and a bias variable); see the fields below. */
 typedef struct gs_ba_problem {
     float* poses;            /* [K][12] world-to-camera R (row-major) and t; updated */
     float* disp;             /* [K][h][w] inverse depths; updated */

@@ -251,6 +251,10 @@ int32_t gs_loss(const gs_image* img, const float* target_color, const float* tar
                                    loss_terms, ws, static_cast<cudaStream_t>(stream)));
 }
 
+// the static scratch array of gs_loss_noalloc must cover every view count the
+// view checks (make_views) accept below its own limit
+static_assert(GS_NOALLOC_LOSS_MAX_VIEWS <= GS_MAX_VIEWS, "no-alloc loss limit above the view limit");
+
 int32_t gs_loss_noalloc(const gs_image* img, const float* target_color, const float* target_depth,
                         const gs_camera* cams, int32_t n_views, float lambda_c, float lambda_d, float* dL_dcolor,
                         float* dL_ddepth, float* loss_terms, void* stream) {
@@ -329,6 +333,11 @@ int32_t gs_adam_step(const gs_adam_group* groups, int32_t n_groups, float beta1,
 int32_t gs_mapping_step(const gs_mapping_step_args* a, void* stream) {
     if (a == nullptr || a->gaussians == nullptr || a->bins == nullptr || a->ws == nullptr) return GS_ERR_INVALID_ARG;
     const int64_t n = a->gaussians->n;
+    // ws serves the sort and then the 2D-gradient scratch of the backward pass,
+    // so it must hold the larger of the two (gs_workspace_size), not just what
+    // gs_bin_sort checks for
+    const size_t need = gs_workspace_size(n, a->n_views, a->cams, a->params, a->bins->key_capacity);
+    if (need == 0 || a->ws_bytes < need || !aligned(a->ws, 256)) return GS_ERR_INVALID_ARG;
     float* grad2d = static_cast<float*>(a->ws);
     int32_t st = gs_project(a->gaussians, a->cams, a->n_views, a->params, a->proj, stream);
     if (st == GS_OK)
@@ -388,6 +397,11 @@ int32_t gs_mlp_bwd(const gs_mlp_packed* q, const uint16_t* X, const uint16_t* Z1
                   !aligned(dY, 16)))
         return GS_ERR_INVALID_ARG;
     return cuda_status(launch_mlp_bwd(*q, X, Z1, Z2, dY, n, *g, d_status, static_cast<cudaStream_t>(stream)));
+}
+
+int64_t gs_mlp_set_wait_polls(int64_t polls) {
+    if (polls > (int64_t)UINT32_MAX) return -1;
+    return (int64_t)set_mlp_wait_polls(polls < 0 ? GS_MLP_WAIT_POLLS_DEFAULT : (uint32_t)polls);
 }
 
 static bool keyframe_ok(const float* color, const float* depth, const gs_camera* cam, const int32_t* uv, int64_t n) {

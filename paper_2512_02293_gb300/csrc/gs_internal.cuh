@@ -138,6 +138,7 @@ cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n,
                            cudaStream_t s);
 cudaError_t launch_mlp_bwd(const gs_mlp_packed& w, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
                            const float* dY, int64_t n, const gs_mlp_grads& g, int* status, cudaStream_t s);
+uint32_t set_mlp_wait_polls(uint32_t polls);    // returns the previous limit
 cudaError_t launch_adam(const gs_adam_group* groups, int n_groups, float b1, float b2, float eps,
                         int32_t* d_step, cudaStream_t s);
 

@@ -21,6 +21,8 @@
 // sample row r (tensor-memory lane r of every accumulator) split its columns.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "gs_internal.cuh"
 #include "tc.cuh"
 
@@ -33,7 +35,11 @@ constexpr int kTile = 128;
 // 32 (w % 4) + 31 (sample rows) and takes column group w / 4 of every epilogue.
 constexpr int kFwdThreads = 512, kColGroups = kFwdThreads / 128;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kWaitPolls = 1u << 26;     // bounded mbarrier polls before GS_ERR_TIMEOUT
+constexpr uint32_t kWaitPolls = GS_MLP_WAIT_POLLS_DEFAULT;   // mbarrier polls before GS_ERR_TIMEOUT (default)
+constexpr uint32_t kDrainPolls = 1u << 26;    // bound of the wait for in-flight MMAs after a timeout
+
+// Poll limit of the mbarrier waits of the next launches (gs_mlp_set_wait_polls).
+std::atomic<uint32_t> g_wait_polls{kWaitPolls};
 
 __device__ __forceinline__ uint16_t f2bf(float x) {
     __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -128,6 +134,7 @@ struct MlpFwdArgs {
     float* loss;         // += loss_scale * sum (Y - T)^2, when T is given
     float loss_scale;
     int* status;
+    uint32_t wait_polls; // mbarrier polls before a wait gives up
 };
 
 // Hidden-layer epilogue for this thread's sample row and columns [c_lo, c_hi):
@@ -166,11 +173,19 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t sa, uint32_
     tc::mma_commit(bar);
 }
 
-// Every thread waits for the barrier phase; the outcome is made uniform.
-__device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t& phase) {
-    const bool ok = tc::mbar_wait(bar, phase, kWaitPolls);
-    phase ^= 1u;
+// Every thread waits (at most `polls` polls) for the barrier phase; the outcome
+// is made uniform.  If any thread gave up, the MMAs of that phase may still be
+// running: thread 0 then waits for them (bounded again) before the CTA goes on
+// to report the timeout and release its tensor memory, so nothing is freed
+// under an MMA in flight.
+__device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t& phase, uint32_t polls) {
+    const bool ok = tc::mbar_wait(bar, phase, polls);
     const bool all = __syncthreads_and(ok) != 0;
+    if (!all) {
+        if (threadIdx.x == 0) tc::mbar_wait(bar, phase, kDrainPolls);
+        __syncthreads();
+    }
+    phase ^= 1u;
     tc::fence_after_sync();
     return all;
 }
@@ -244,15 +259,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
         operands_ready();
         if (tid == 0) issue_gemm(tD1, sa_x, sa_w1, kK1, tc::idesc_bf16(128, kHid), false, bar);
         if (t + gridDim.x < n_tiles) load_x(t + gridDim.x);     // in flight during the epilogues
-        if (!(ok = wait_all(bar, phase))) break;
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi, a.w.gelu_tab);
         operands_ready();
         if (tid == 0) issue_gemm(tD2, sa_h, sa_w2, kK2, tc::idesc_bf16(128, kHid), false, bar);
-        if (!(ok = wait_all(bar, phase))) break;
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         hidden_epilogue(tD2 + lane_off, sH, r, row, a.n, a.Z2, c_lo, c_hi, a.w.gelu_tab);
         operands_ready();
         if (tid == 0) issue_gemm(tD3, sa_h, sa_w3, kK2, tc::idesc_bf16(128, kN3), false, bar);
-        if (!(ok = wait_all(bar, phase))) break;
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         if (cg == 0) {                       // the 8 outputs: one column group (warp-uniform)
             float y[16];
             tc::tmem_ld16(tD3 + lane_off, y);
@@ -320,6 +335,7 @@ struct MlpBwdArgs {
     int64_t n;
     gs_mlp_grads g;      // zeroed before the launch; accumulated with atomics
     int* status;
+    uint32_t wait_polls; // mbarrier polls before a wait gives up
 };
 
 __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
@@ -462,7 +478,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                              tc::idesc_bf16_mn(128, kK2, true, true), !first || st > 0);
             tc::mma_commit(bar);
         }
-        if (!(ok = wait_all(bar, phase))) break;
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         // (5) dZ1 = bf16(dH1 * gelu'(Z1)) as dZ1^T (over the dZ2 buffer, whose GEMM is done)
         uint8_t* sA1t = sA2;
 #pragma unroll
@@ -492,10 +508,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                              tc::idesc_bf16_mn(128, kK1, true, true), !first || st > 0);
             tc::mma_commit(bar);
         }
-        if (!(ok = wait_all(bar, phase))) break;
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         first = false;
     }
     if (!ok && tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
+    cp_async_wait_all();     // after a timeout this thread's input copies may still be in flight
     if (ok && !first) {
         // accumulated weight gradients of this CTA -> global (row r of dW1_aug, dW2_aug; every fourth chunk)
 #pragma unroll 1
@@ -534,6 +551,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
 
 }  // namespace
 
+uint32_t set_mlp_wait_polls(uint32_t polls) { return g_wait_polls.exchange(polls); }
+
 static int sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -554,7 +573,7 @@ cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n,
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-    MlpFwdArgs a{w, X, n, Y, Z1, Z2, T, dY, loss, loss_scale, status};
+    MlpFwdArgs a{w, X, n, Y, Z1, Z2, T, dY, loss, loss_scale, status, g_wait_polls.load()};
     k_mlp_fwd<<<grid, kFwdThreads, kFwdSmem, s>>>(a);
     return cudaGetLastError();
 }
@@ -573,7 +592,7 @@ cudaError_t launch_mlp_bwd(const gs_mlp_packed& w, const uint16_t* X, const uint
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-    MlpBwdArgs a{w, X, Z1, Z2, dY, n, g, status};
+    MlpBwdArgs a{w, X, Z1, Z2, dY, n, g, status, g_wait_polls.load()};
     k_mlp_bwd<<<grid, kFwdThreads, kBwdSmem, s>>>(a);
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgs.so")
 GS_MAX_VIEWS = 32
+GS_NOALLOC_LOSS_MAX_VIEWS = 32     # views gs_loss_noalloc's static scratch array holds
 _lib = None
 
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA", 4: "GS_ERR_TIMEOUT",
@@ -124,7 +125,7 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
            "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
            "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss",
-           "gs_mapping_step"]
+           "gs_mapping_step", "gs_mlp_set_wait_polls"]
 
 
 def load_library(path: str | None = None):
@@ -194,6 +195,8 @@ def load_library(path: str | None = None):
                                               ctypes.c_int32, V, ctypes.c_int64, V, V]
     lib.gs_mapping_step.restype = ctypes.c_int32
     lib.gs_mapping_step.argtypes = [V, V]
+    lib.gs_mlp_set_wait_polls.restype = ctypes.c_int64
+    lib.gs_mlp_set_wait_polls.argtypes = [ctypes.c_int64]
     if lib.gs_abi_version() != 4:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
@@ -620,6 +623,18 @@ def gs_mlp_bwd(packed: MlpPacked, X, Z1, Z2, dY, grads: dict, status=None, strea
     g = gs_mlp_grads(*[_ptr(grads[k]) for k in MLP_PARAM_NAMES])
     _check(load_library().gs_mlp_bwd(ctypes.byref(q), _ptr(X), _ptr(Z1), _ptr(Z2), _ptr(dY), X.shape[0],
                                      ctypes.byref(g), _ptr(status), _stream(stream)), "gs_mlp_bwd")
+
+
+MLP_WAIT_POLLS_DEFAULT = 1 << 26
+
+
+def gs_mlp_set_wait_polls(polls: int) -> int:
+    """Poll limit of the MLP kernels' mbarrier waits for later launches (a test
+    hook of the timeout path; negative = the default); returns the previous one."""
+    prev = int(load_library().gs_mlp_set_wait_polls(int(polls)))
+    if prev < 0:
+        raise GsError(GS_ERR_INVALID_ARG, "gs_mlp_set_wait_polls")
+    return prev
 
 
 # ------------------------------------------------------- keyframe insertion

@@ -143,3 +143,52 @@ def test_mapping_step_rejects_missing_arguments(lib):
     a.bins = ctypes.addressof(bins)
     a.ws = 256
     assert lib.gs_mapping_step(ctypes.byref(a), None) == 1          # the projection's checks reject NULL arrays
+
+
+def test_mapping_step_rejects_a_workspace_smaller_than_gs_workspace_size(lib):
+    # The whole-iteration call reuses its workspace as the backward's 2D-gradient
+    # scratch (48 B per entry), which can be larger than what the sort alone
+    # needs; a buffer of exactly the sort's size must be refused before any launch.
+    V = ctypes.c_void_p
+    cam = synth.identity_camera(64, 48)
+    cams = G.camera_array([cam])
+    p = G.RenderParams().struct()
+    n, cap = 4096, 1024                               # few keys per entry: the scratch dominates
+    need = lib.gs_workspace_size(n, 1, cams, ctypes.byref(p), cap)
+    sort_only = lib.gs_workspace_size(0, 1, cams, ctypes.byref(p), cap)
+    assert need >= 12 * 4 * n > sort_only
+    g = G.gs_gaussians(V(256), V(256), V(256), V(256), V(256), n)
+    bins = G.gs_bins(V(256), V(256), cap, V(256), V(256), V(256))
+    a = G.gs_mapping_step_args()
+    a.gaussians = ctypes.addressof(g)
+    a.cams = ctypes.addressof(cams)
+    a.params = ctypes.addressof(p)
+    a.bins = ctypes.addressof(bins)
+    a.n_views = 1
+    a.ws = 256
+    for size in (sort_only, need - 256):
+        a.ws_bytes = size
+        assert lib.gs_mapping_step(ctypes.byref(a), None) == G.GS_ERR_INVALID_ARG, size
+    a.ws, a.ws_bytes = 257, need                      # misaligned
+    assert lib.gs_mapping_step(ctypes.byref(a), None) == G.GS_ERR_INVALID_ARG
+
+
+def test_noalloc_loss_view_limit_is_checked_on_the_host(lib):
+    V = ctypes.c_void_p
+    n = G.GS_NOALLOC_LOSS_MAX_VIEWS + 1
+    cams = G.camera_array([synth.identity_camera(8, 8)] * n)
+    im = G.gs_image(V(256), V(256), V(256), V(256))
+    assert lib.gs_loss_noalloc(ctypes.byref(im), V(256), V(256), cams, n, 1.0, 1.0, V(256), V(256), V(256),
+                               None) == G.GS_ERR_INVALID_ARG
+
+
+def test_mlp_wait_poll_limit_is_set_and_restored(lib):
+    prev = G.gs_mlp_set_wait_polls(0)
+    try:
+        assert prev == G.MLP_WAIT_POLLS_DEFAULT
+        assert G.gs_mlp_set_wait_polls(7) == 0
+        assert lib.gs_mlp_set_wait_polls(1 << 33) == -1          # out of range: unchanged
+        assert G.gs_mlp_set_wait_polls(-1) == 7                  # negative: back to the default
+        assert G.gs_mlp_set_wait_polls(-1) == G.MLP_WAIT_POLLS_DEFAULT
+    finally:
+        G.gs_mlp_set_wait_polls(-1)

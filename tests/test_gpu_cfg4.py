@@ -3,7 +3,8 @@
 coefficients), gradients to every parameter and every keyframe's 6-DoF pose
 tangent, from the per-pixel (T_final, n_contrib) checkpoint.
 
-- colour / depth of tile-aligned windows of two views against the FP64 oracle;
+- colour / depth / T_final, and n_contrib bit-exact, on tile-aligned windows of
+  two views against the FP64 oracle;
 - every parameter gradient (incl. all SH coefficients) and the pose gradient of
   a loss that lives in one view's window; the 15 other poses get exactly 0;
 - on the 4k-Gaussian, 160x128 sub-sample the oracle's differences pin
@@ -65,8 +66,12 @@ def test_forward_windows(full, v, win):
     assert ok.mean() > 0.95
     c = _view(cams, v, col.detach(), 3).cpu().numpy()[:, y0:y0 + h, x0:x0 + w]
     d = _view(cams, v, dep.detach(), 1).cpu().numpy()[y0:y0 + h, x0:x0 + w]
+    Tf = _view(cams, v, rast.img.T_final, 1).cpu().numpy()[y0:y0 + h, x0:x0 + w]
+    nc = _view(cams, v, rast.img.n_contrib, 1).cpu().numpy().view(np.uint32)[y0:y0 + h, x0:x0 + w]
     np.testing.assert_allclose(c[:, ok], img["color"][:, ok], atol=COLOR_TOL)
     np.testing.assert_allclose(d[ok], img["depth"][ok], atol=COLOR_TOL)
+    np.testing.assert_allclose(Tf[ok], img["T_final"][ok], atol=1e-5)
+    np.testing.assert_array_equal(nc[ok], img["n_contrib"][ok])
 
 
 def test_backward_window_all_parameters_and_poses(full):

@@ -4,8 +4,9 @@ piecewise:
 
 - projection of every Gaussian, element by element;
 - keys / order / ranges bit-exact on the oracle's fp32-rounded projection;
-- colour / depth / checkpoint on tile-aligned windows (the oracle renders the
-  window as its own camera, cx and cy shifted by the window offset);
+- colour / depth / checkpoint (T_final, and n_contrib bit-exact) on
+  tile-aligned windows (the oracle renders the window as its own camera, cx
+  and cy shifted by the window offset);
 - every parameter gradient and the pose gradient for a loss whose image
   gradient lives inside a window;
 - properties of the GPU's own keys that hold at any size.
@@ -115,10 +116,13 @@ def test_window_forward_and_backward(setup, win):
     dep = step.depth_image(0).cpu().numpy()[y0:y0 + h, x0:x0 + w]
     P = cam.n_pixels
     Tf = step.img.T_final.cpu().numpy().reshape(cam.height, cam.width)[y0:y0 + h, x0:x0 + w]
+    nc = step.img.n_contrib.cpu().numpy().view(np.uint32).reshape(cam.height, cam.width)[y0:y0 + h, x0:x0 + w]
     ok = ~ex
     np.testing.assert_allclose(col[:, ok], img["color"][:, ok], atol=COLOR_TOL)
     np.testing.assert_allclose(dep[ok], img["depth"][ok], atol=COLOR_TOL)
     np.testing.assert_allclose(Tf[ok], img["T_final"][ok], atol=1e-5)
+    # the checkpoint's integer half: the list position of each pixel's last blended splat
+    np.testing.assert_array_equal(nc[ok], img["n_contrib"][ok])
     # backward for an image gradient supported on the window's non-excused pixels
     rng = np.random.default_rng(x0 + y0)
     dcw = rng.standard_normal((3, h, w)) * 1e-3 * ok[None]

@@ -164,3 +164,36 @@ def test_adam_training_reduces_the_loss():
         G.gs_adam_step([(params[k], grads[k], m[k], v[k], 3e-3) for k in G.MLP_PARAM_NAMES], 0.9, 0.999, 1e-8, d_step)
         losses.append(loss.item())
     assert losses[-1] < 0.3 * losses[0]
+
+
+def test_bounded_waits_run_out_report_timeout_and_leave_the_gpu_usable():
+    """With the poll limit set to 0 the first mbarrier wait of each kernel gives
+    up at once: the kernel waits (bounded) for its MMAs and copies in flight,
+    records GS_ERR_TIMEOUT, frees its tensor memory and returns.  The host reads
+    the status through gs_read_device_status; afterwards the same context runs
+    the kernels normally and matches the oracle."""
+    n = 640
+    p = synth.mlp_params(33)
+    X, T = synth.mlp_batch(34, n)
+    packed = G.MlpPacked()
+    G.gs_mlp_pack(_device_params(p), packed)
+    Xd = _device_x(X)
+    Y = torch.empty(n, 8, device="cuda")
+    Z1 = torch.zeros(n, 128, device="cuda", dtype=torch.bfloat16); Z2 = torch.zeros_like(Z1)
+    dY = torch.zeros(n, 8, device="cuda")
+    grads = _grads_dev()
+    st_f = torch.zeros(1, device="cuda", dtype=torch.int32)
+    st_b = torch.zeros(1, device="cuda", dtype=torch.int32)
+    prev = G.gs_mlp_set_wait_polls(0)
+    try:
+        G.gs_mlp_fwd(packed, Xd, Y=Y, Z1=Z1, Z2=Z2, status=st_f)
+        G.gs_mlp_bwd(packed, Xd, Z1, Z2, dY, grads, status=st_b)
+    finally:
+        G.gs_mlp_set_wait_polls(prev)
+    assert G.gs_read_device_status(st_f) == G.GS_ERR_TIMEOUT
+    assert G.gs_read_device_status(st_b) == G.GS_ERR_TIMEOUT
+    # the default limit again: normal results on the same GPU context
+    _, _, Y2, _, _, _ = _run_fwd(p, X)
+    ref = M.forward(X, p, bf16=True)
+    err = np.abs(Y2.cpu().numpy() - ref["Y"])
+    assert (err > 1e-4).mean() < 0.01 and err.max() < 5e-3

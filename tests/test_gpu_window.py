@@ -4,9 +4,11 @@ one launch over all views, tile 16 (the shapes bench.py's window line times).
 
 - each view of the batched render equals the same view rendered alone,
   bit for bit (identical per-tile lists and arithmetic);
-- colour / depth on tile-aligned windows of two views against the FP64 oracle;
+- colour / depth / T_final, and n_contrib bit-exact, on tile-aligned windows of
+  two views against the FP64 oracle;
 - every parameter gradient and all eight pose gradients for a loss whose image
-  gradient lives in a window of one view (the other poses get exactly zero).
+  gradient lives in a window of one view (the other poses get exactly zero), for
+  one view of each of the three resolutions.
 """
 import numpy as np
 import pytest
@@ -66,14 +68,22 @@ def test_window_views_forward(window, v, win):
     ok = ~ex
     col = step.color_image(v).cpu().numpy()[:, y0:y0 + h, x0:x0 + w]
     dep = step.depth_image(v).cpu().numpy()[y0:y0 + h, x0:x0 + w]
+    base = sum(c.n_pixels for c in cams[:v])
+    W, H = cams[v].width, cams[v].height
+    Tf = step.img.T_final[base:base + W * H].cpu().numpy().reshape(H, W)[y0:y0 + h, x0:x0 + w]
+    nc = step.img.n_contrib[base:base + W * H].cpu().numpy().view(np.uint32).reshape(H, W)[y0:y0 + h, x0:x0 + w]
     assert ok.mean() > 0.95
     np.testing.assert_allclose(col[:, ok], img["color"][:, ok], atol=COLOR_TOL)
     np.testing.assert_allclose(dep[ok], img["depth"][ok], atol=COLOR_TOL)
+    np.testing.assert_allclose(Tf[ok], img["T_final"][ok], atol=1e-5)
+    np.testing.assert_array_equal(nc[ok], img["n_contrib"][ok])
 
 
-def test_window_backward_one_view(window):
+@pytest.mark.parametrize("v,win", [(0, (320, 224, 64, 64)), (4, (352, 224, 64, 64)), (6, (608, 480, 64, 64))])
+def test_window_backward_one_view(window, v, win):
+    """One view of each resolution (640x480, 752x480, 1280x1024)."""
     g, cams, params, step = window
-    v, (x0, y0, w, h) = 6, (608, 480, 64, 64)
+    x0, y0, w, h = win
     crop = _crop(cams[v], x0, y0, w, h)
     prm = prm_dict(params)
     pr = oracle.project(g, crop, prm)

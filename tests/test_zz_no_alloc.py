@@ -1,6 +1,6 @@
 """gs_loss_noalloc: the loss entry point for callers that cannot allocate a
-device workspace (for example code running while a CUDA graph is captured in
-global mode, or a tracker held to a fixed device-memory budget).  Its scratch
+device workspace (for example a tracker held to a fixed device-memory budget,
+or a plugin whose host application owns the device allocator).  Its scratch
 is a static device array inside the library, so the caller passes only
 inputs and outputs.
 
@@ -55,7 +55,7 @@ def test_noalloc_loss_matches_workspace_loss_twice():
 def test_noalloc_loss_rejects_too_many_views():
     B.build()
     G.load_library()
-    n = G.GS_MAX_VIEWS + 1          # one view more than the scratch array holds
+    n = G.GS_NOALLOC_LOSS_MAX_VIEWS + 1          # one view more than the scratch array holds
     cams = [synth.identity_camera(8, 8)] * n
     P = 64 * n
     buf = torch.zeros(3 * P, device="cuda")
