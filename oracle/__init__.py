@@ -37,11 +37,16 @@ DEFAULT_PARAMS = dict(tile=16, near=0.2, alpha_min=1.0 / 255.0, alpha_max=0.99, 
 
 
 def build(force: bool = False) -> str:
-    """Compile gs_oracle.c into _build/liboracle.so (gcc, -O2, no FMA contraction)."""
+    """Compile gs_oracle.c into _build/liboracle.so (gcc, -O2, no FMA contraction,
+    OpenMP for the optional host threads; without OpenMP the loops run serially)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,7 +59,21 @@ def _load():
         _lib.or_bin_sort.restype = ctypes.c_long
         _lib.or_iso_loss.restype = ctypes.c_double
         _lib.or_tile_rect.restype = ctypes.c_int
+        _lib.or_set_threads.restype = ctypes.c_int
+        _lib.or_set_threads.argtypes = [ctypes.c_int]
+        _lib.or_num_procs.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's parallel loops (results are bit-identical
+    for every count); returns the previous count."""
+    return int(_load().or_set_threads(int(n)))
+
+
+def num_procs() -> int:
+    """Processors the parallel loops can use (1 if built without OpenMP)."""
+    return int(_load().or_num_procs())
 
 
 def _p(a):
@@ -267,3 +286,24 @@ def mapping_loss_and_grads(g, cams, targets, prm: dict, lambdas=(1.0, 1.0, 0.0))
         grads["log_scale"] += gi
         total += lam_iso * iso
     return StepResult(images, projs, terms, iso, total, grads, pose, g2ds)
+
+
+def mapping_iteration(g, cams, targets, prm: dict, lambdas, lrs, state: dict, beta1=0.9, beta2=0.999,
+                      eps=1e-15) -> StepResult:
+    """One whole mapping iteration (Sec. 3.3 "Map Management"): the loss and
+    gradients of mapping_loss_and_grads, then one Adam step of every parameter
+    group with its learning rate (lrs in PARAM_NAMES order).  state holds the
+    float64 parameters ("params": dict by name), the moments ("m", "v") and the
+    step count ("step"); all are updated in place."""
+    res = mapping_loss_and_grads(g, cams, targets, prm, lambdas)
+    state["step"] += 1
+    for k, lr in zip(PARAM_NAMES, lrs):
+        adam(state["params"][k], res.grads[k], state["m"][k], state["v"][k], lr, beta1, beta2, eps, state["step"])
+    return res
+
+
+def adam_state(g) -> dict:
+    """float64 copies of the map's parameters and zero Adam moments."""
+    params = {k: np.array(a, dtype=np.float64, copy=True) for k, a in zip(PARAM_NAMES, g.arrays())}
+    return {"params": params, "m": {k: np.zeros_like(a) for k, a in params.items()},
+            "v": {k: np.zeros_like(a) for k, a in params.items()}, "step": 0}

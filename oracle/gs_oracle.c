@@ -40,11 +40,38 @@
  * prm[12] = {tile, near, alpha_min, alpha_max, T_cut, dilation, k_sigma,
  *            bg_r, bg_g, bg_b, smooth, sh_degree}.
  * Images are planar: colour [3][H][W], depth / T_final / n_contrib [H][W].
+ *
+ * Threads (or_set_threads): the loops over Gaussians and tiles may run on
+ * several host threads (OpenMP).  Each such loop either writes outputs that no
+ * other iteration touches, or records its contributions to shared sums and
+ * adds them up afterwards in the serial loop's order, so every result is
+ * bit-identical to the one-thread run.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+/* Host threads of the parallel loops (>= 1); returns the previous count. */
+int or_set_threads(int n) {
+    int prev = g_threads;
+    g_threads = n < 1 ? 1 : n;
+    return prev;
+}
+
+/* Processors available to the parallel loops (1 without OpenMP). */
+int or_num_procs(void) {
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 typedef struct {
     double fx, fy, cx, cy;
@@ -300,6 +327,7 @@ void or_project(long n, const double* mean, const double* quat, const double* lo
     Cam c = cam_from(cam);
     Prm p = prm_from(prm);
     int nc = p.sh_degree == 0 ? 3 : 48;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (long i = 0; i < n; i++) {
         Proj o;
         project_one(mean + 3 * i, quat + 4 * i, log_scale + 3 * i, logit[i], color + nc * i, &c, &p, &o);
@@ -475,9 +503,13 @@ void or_render_fwd(long n, const double* xy, const double* conic, const double* 
     Prm p = prm_from(prm);
     int t = p.tile, tx = tiles_x_of(&c, &p), ty = tiles_y_of(&c, &p);
     long HW = (long)c.W * c.H;
-    ZI* list = (ZI*)malloc(sizeof(ZI) * (n > 0 ? n : 1));
-    for (int by = 0; by < ty; by++)
-        for (int bx = 0; bx < tx; bx++) {
+    /* tiles in row-major order; each pixel is written by its own tile only */
+#pragma omp parallel num_threads(g_threads)
+    {
+        ZI* list = (ZI*)malloc(sizeof(ZI) * (n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (long b = 0; b < (long)tx * ty; b++) {
+            int by = (int)(b / tx), bx = (int)(b % tx);
             long m = tile_list(n, depth, rect, bx, by, list);
             for (int py = by * t; py < (by + 1) * t && py < c.H; py++)
                 for (int px = bx * t; px < (bx + 1) * t && px < c.W; px++) {
@@ -493,14 +525,100 @@ void or_render_fwd(long n, const double* xy, const double* conic, const double* 
                     out_margin[pix] = mg;
                 }
         }
-    free(list);
+        free(list);
+    }
+}
+
+/* One blended (pixel, splat) pair's additions to the per-Gaussian gradients
+ * of the compositing backward, in the form the serial loop adds them. */
+typedef struct {
+    long idx;
+    int clamped;                  /* alpha = alpha_max: no opacity / conic / xy terms */
+    double rgb[3], depth, opacity, conic[3], xy[2];
+} Contrib;
+
+typedef struct {
+    Contrib* c;
+    long n, cap;
+} ContribList;
+
+static void contrib_push(ContribList* L, const Contrib* x) {
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 1024;
+        L->c = (Contrib*)realloc(L->c, sizeof(Contrib) * L->cap);
+    }
+    L->c[L->n++] = *x;
+}
+
+/* The contributions of every pixel of tile (bx, by), pixels in row-major
+ * order, each pixel's blended splats front to back.  d colour / d alpha_j is
+ * taken straight from the product form C = sum_i c_i alpha_i T_i + bg T_final
+ * with T_i = prod_{k<i} (1 - alpha_k). */
+static void tile_backward(long n, int bx, int by, const double* xy, const double* conic, const double* opacity,
+                          const double* rgb, const double* depth, const int* rect, const Cam* c, const Prm* p,
+                          const double* dL_dcolor, const double* dL_ddepth, ZI* list, Blend* bl, double* sufC,
+                          double* sufD, ContribList* out) {
+    int t = p->tile;
+    long HW = (long)c->W * c->H;
+    long m = tile_list(n, depth, rect, bx, by, list);
+    for (int py = by * t; py < (by + 1) * t && py < c->H; py++)
+        for (int px = bx * t; px < (bx + 1) * t && px < c->W; px++) {
+            double C3[3], D, T, mg;
+            int np;
+            long nb = composite_pixel(list, m, px + 0.5, py + 0.5, xy, conic, opacity, rgb, depth, p, C3, &D,
+                                      &T, &np, &mg, bl);
+            long pix = (long)py * c->W + px;
+            double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
+            double gD = dL_ddepth[pix];
+            /* suffix sums of the contributions behind blended splat j, plus background */
+            for (int ch = 0; ch < 3; ch++) sufC[3 * nb + ch] = p->bg[ch] * T;
+            sufD[nb] = 0.0;
+            for (long j = nb - 1; j >= 0; j--) {
+                long i = bl[j].idx;
+                double w = bl[j].alpha * bl[j].T_before;
+                for (int ch = 0; ch < 3; ch++) sufC[3 * j + ch] = sufC[3 * (j + 1) + ch] + rgb[3 * i + ch] * w;
+                sufD[j] = sufD[j + 1] + depth[i] * w;
+            }
+            for (long j = 0; j < nb; j++) {
+                long i = bl[j].idx;
+                double a = bl[j].alpha, Tb = bl[j].T_before, w = a * Tb;
+                double dC_da[3], dD_da;
+                Contrib r;
+                memset(&r, 0, sizeof(r));
+                r.idx = i;
+                for (int ch = 0; ch < 3; ch++)
+                    dC_da[ch] = rgb[3 * i + ch] * Tb - sufC[3 * (j + 1) + ch] / (1.0 - a);
+                dD_da = depth[i] * Tb - sufD[j + 1] / (1.0 - a);
+                double dL_da = gD * dD_da;
+                for (int ch = 0; ch < 3; ch++) {
+                    dL_da += gC[ch] * dC_da[ch];
+                    r.rgb[ch] = gC[ch] * w;
+                }
+                r.depth = gD * w;
+                r.clamped = bl[j].clamped;
+                if (!r.clamped) {    /* alpha = alpha_max is flat in o and power */
+                    double G = bl[j].G;
+                    r.opacity = dL_da * G;
+                    double dL_dpow = dL_da * opacity[i] * G;
+                    double dx = bl[j].dx, dy = bl[j].dy;
+                    double A = conic[3 * i], B = conic[3 * i + 1], Cc = conic[3 * i + 2];
+                    /* power = -1/2 (A dx^2 + C dy^2) - B dx dy, dx = sample - mean */
+                    r.conic[0] = dL_dpow * (-0.5 * dx * dx);
+                    r.conic[1] = dL_dpow * (-dx * dy);
+                    r.conic[2] = dL_dpow * (-0.5 * dy * dy);
+                    r.xy[0] = dL_dpow * (A * dx + B * dy);
+                    r.xy[1] = dL_dpow * (B * dx + Cc * dy);
+                }
+                contrib_push(out, &r);
+            }
+        }
 }
 
 /* Backward of the compositing for one view: accumulates (+=) the gradient of
  * sum_pix <dL_dcolor, colour> + <dL_ddepth, depth> into per-Gaussian
- * gradients of xy (2), conic (3), opacity (1), rgb (3) and depth (1).
- * d colour / d alpha_j is taken straight from the product form
- * C = sum_i c_i alpha_i T_i + bg T_final with T_i = prod_{k<i} (1 - alpha_k). */
+ * gradients of xy (2), conic (3), opacity (1), rgb (3) and depth (1).  The
+ * tiles' contributions are formed (in parallel when threads > 1) and added in
+ * tile order, pixel order, splat order: the order of one serial pass. */
 void or_render_bwd(long n, const double* xy, const double* conic, const double* opacity,
                    const double* rgb, const double* depth, const int* rect,
                    const double* cam, const double* prm,
@@ -508,62 +626,43 @@ void or_render_bwd(long n, const double* xy, const double* conic, const double* 
                    double* g_xy, double* g_conic, double* g_opacity, double* g_rgb, double* g_depth) {
     Cam c = cam_from(cam);
     Prm p = prm_from(prm);
-    int t = p.tile, tx = tiles_x_of(&c, &p), ty = tiles_y_of(&c, &p);
-    long HW = (long)c.W * c.H;
-    ZI* list = (ZI*)malloc(sizeof(ZI) * (n > 0 ? n : 1));
-    Blend* bl = (Blend*)malloc(sizeof(Blend) * (n > 0 ? n : 1));
-    double* sufC = (double*)malloc(sizeof(double) * 3 * (n + 1));
-    double* sufD = (double*)malloc(sizeof(double) * (n + 1));
-    for (int by = 0; by < ty; by++)
-        for (int bx = 0; bx < tx; bx++) {
-            long m = tile_list(n, depth, rect, bx, by, list);
-            for (int py = by * t; py < (by + 1) * t && py < c.H; py++)
-                for (int px = bx * t; px < (bx + 1) * t && px < c.W; px++) {
-                    double C3[3], D, T, mg;
-                    int np;
-                    long nb = composite_pixel(list, m, px + 0.5, py + 0.5, xy, conic, opacity, rgb, depth,
-                                              &p, C3, &D, &T, &np, &mg, bl);
-                    long pix = (long)py * c.W + px;
-                    double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
-                    double gD = dL_ddepth[pix];
-                    /* suffix sums of the contributions behind blended splat j, plus background */
-                    for (int ch = 0; ch < 3; ch++) sufC[3 * nb + ch] = p.bg[ch] * T;
-                    sufD[nb] = 0.0;
-                    for (long j = nb - 1; j >= 0; j--) {
-                        long i = bl[j].idx;
-                        double w = bl[j].alpha * bl[j].T_before;
-                        for (int ch = 0; ch < 3; ch++) sufC[3 * j + ch] = sufC[3 * (j + 1) + ch] + rgb[3 * i + ch] * w;
-                        sufD[j] = sufD[j + 1] + depth[i] * w;
-                    }
-                    for (long j = 0; j < nb; j++) {
-                        long i = bl[j].idx;
-                        double a = bl[j].alpha, Tb = bl[j].T_before, w = a * Tb;
-                        double dC_da[3], dD_da;
-                        for (int ch = 0; ch < 3; ch++)
-                            dC_da[ch] = rgb[3 * i + ch] * Tb - sufC[3 * (j + 1) + ch] / (1.0 - a);
-                        dD_da = depth[i] * Tb - sufD[j + 1] / (1.0 - a);
-                        double dL_da = gD * dD_da;
-                        for (int ch = 0; ch < 3; ch++) {
-                            dL_da += gC[ch] * dC_da[ch];
-                            g_rgb[3 * i + ch] += gC[ch] * w;
-                        }
-                        g_depth[i] += gD * w;
-                        if (bl[j].clamped) continue;   /* alpha = alpha_max: flat in o and power */
-                        double G = bl[j].G;
-                        g_opacity[i] += dL_da * G;
-                        double dL_dpow = dL_da * opacity[i] * G;
-                        double dx = bl[j].dx, dy = bl[j].dy;
-                        double A = conic[3 * i], B = conic[3 * i + 1], Cc = conic[3 * i + 2];
-                        /* power = -1/2 (A dx^2 + C dy^2) - B dx dy, dx = sample - mean */
-                        g_conic[3 * i] += dL_dpow * (-0.5 * dx * dx);
-                        g_conic[3 * i + 1] += dL_dpow * (-dx * dy);
-                        g_conic[3 * i + 2] += dL_dpow * (-0.5 * dy * dy);
-                        g_xy[2 * i] += dL_dpow * (A * dx + B * dy);
-                        g_xy[2 * i + 1] += dL_dpow * (B * dx + Cc * dy);
-                    }
-                }
+    int tx = tiles_x_of(&c, &p), ty = tiles_y_of(&c, &p);
+    long n_tiles = (long)tx * ty;
+    long chunk = g_threads > 1 ? 4L * g_threads : 1L;      /* tiles whose contributions are held at once */
+    ContribList* lists = (ContribList*)calloc((size_t)chunk, sizeof(ContribList));
+    for (long b0 = 0; b0 < n_tiles; b0 += chunk) {
+        long b1 = b0 + chunk < n_tiles ? b0 + chunk : n_tiles;
+#pragma omp parallel num_threads(g_threads)
+        {
+            ZI* list = (ZI*)malloc(sizeof(ZI) * (n > 0 ? n : 1));
+            Blend* bl = (Blend*)malloc(sizeof(Blend) * (n > 0 ? n : 1));
+            double* sufC = (double*)malloc(sizeof(double) * 3 * (n + 1));
+            double* sufD = (double*)malloc(sizeof(double) * (n + 1));
+#pragma omp for schedule(dynamic, 1)
+            for (long b = b0; b < b1; b++) {
+                lists[b - b0].n = 0;
+                tile_backward(n, (int)(b % tx), (int)(b / tx), xy, conic, opacity, rgb, depth, rect, &c, &p,
+                              dL_dcolor, dL_ddepth, list, bl, sufC, sufD, &lists[b - b0]);
+            }
+            free(list); free(bl); free(sufC); free(sufD);
         }
-    free(list); free(bl); free(sufC); free(sufD);
+        for (long b = b0; b < b1; b++) {
+            const ContribList* L = &lists[b - b0];
+            for (long k = 0; k < L->n; k++) {
+                const Contrib* r = &L->c[k];
+                long i = r->idx;
+                for (int ch = 0; ch < 3; ch++) g_rgb[3 * i + ch] += r->rgb[ch];
+                g_depth[i] += r->depth;
+                if (r->clamped) continue;
+                g_opacity[i] += r->opacity;
+                for (int q = 0; q < 3; q++) g_conic[3 * i + q] += r->conic[q];
+                g_xy[2 * i] += r->xy[0];
+                g_xy[2 * i + 1] += r->xy[1];
+            }
+        }
+    }
+    for (long k = 0; k < chunk; k++) free(lists[k].c);
+    free(lists);
 }
 
 /* Backward of the projection for one view: accumulates (+=) into parameter
@@ -579,11 +678,16 @@ void or_project_bwd(long n, const double* mean, const double* quat, const double
     Cam c = cam_from(cam);
     Prm p = prm_from(prm);
     int nc = p.sh_degree == 0 ? 3 : 48;
+    /* each Gaussian's pose-gradient terms, added up in Gaussian order afterwards */
+    double* pose_terms = g_pose ? (double*)malloc(sizeof(double) * 6 * (n > 0 ? n : 1)) : NULL;
+    char* visible = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (long i = 0; i < n; i++) {
         Proj o;
         const double* q = quat + 4 * i;
         project_one(mean + 3 * i, q, log_scale + 3 * i, logit[i], color + nc * i, &c, &p, &o);
         if (!o.visible) continue;
+        visible[i] = 1;
         double z = o.pc[2], x = o.pc[0], y = o.pc[1];
         double a = o.cov2[0], b = o.cov2[1], cc = o.cov2[2], det = o.det, det2 = det * det;
         const double* gq = g_conic + 3 * i;
@@ -693,9 +797,19 @@ void or_project_bwd(long n, const double* mean, const double* quat, const double
             /* camera centre C = -R_cw^T t_cw moves by -R_cw^T rho under rho */
             for (int r = 0; r < 3; r++)
                 for (int k = 0; k < 3; k++) grho[r] -= c.Rcw[r * 3 + k] * Gcenter[k];
-            for (int k = 0; k < 3; k++) { g_pose[k] += grho[k]; g_pose[3 + k] += gphi[k]; }
+            for (int k = 0; k < 3; k++) { pose_terms[6 * i + k] = grho[k]; pose_terms[6 * i + 3 + k] = gphi[k]; }
         }
     }
+    if (g_pose)
+        for (long i = 0; i < n; i++) {
+            if (!visible[i]) continue;
+            for (int k = 0; k < 3; k++) {
+                g_pose[k] += pose_terms[6 * i + k];
+                g_pose[3 + k] += pose_terms[6 * i + 3 + k];
+            }
+        }
+    free(pose_terms);
+    free(visible);
 }
 
 /* ------------------------------------------------------------------ losses */
@@ -755,6 +869,7 @@ double or_iso_loss(long n, const double* log_scale, double lambda, double* g_log
 void or_adam(long n, double* param, const double* grad, double* m, double* v,
              double lr, double beta1, double beta2, double eps, int step) {
     double bc1 = 1.0 - pow(beta1, step), bc2 = 1.0 - pow(beta2, step);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (long k = 0; k < n; k++) {
         m[k] = beta1 * m[k] + (1.0 - beta1) * grad[k];
         v[k] = beta2 * v[k] + (1.0 - beta2) * grad[k] * grad[k];
