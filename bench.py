@@ -206,20 +206,15 @@ def bwd_ctas_per_sm(step, tile) -> int:
 
 
 def launches_per_step(step) -> int:
-    """Kernels of ours per iteration: project 1; bin/sort: entry scan 2,
-    duplicate 1, 3 per radix pass (digits of at most 9 bits over 31 depth bits
-    and the tile bits), tile ranges 1; render 1 (with the fused loss); loss
-    (unfused only): accumulator zeroing 1 + 2; backward: gradient zeroing 1 +
-    block order 1 (fused, few blocks per SM) + raster 1, pose/iso zeroing 1 +
-    projection backward 1; Adam 1."""
-    tb = 0
-    while (1 << tb) < step.total_tiles:
-        tb += 1
-    passes = math.ceil((31 + tb) / 9)
+    """Kernels of ours per iteration: project 1; bin/sort 5 (count zeroing, tile
+    counts, tile offsets, scatter, per-tile sort); render 1 (with the fused
+    loss); loss (unfused only): accumulator zeroing 1 + 2; backward: gradient
+    zeroing 1 + block order 1 (fused, few blocks per SM) + raster 1, pose/iso
+    zeroing 1 + projection backward 1; Adam 1."""
     tile = step.params.tile
     items = step.total_tiles * (tile // 8) * (tile // 4)
     order = 1 if step.fused_loss and items <= 256 * 152 and items <= 65536 else 0   # k_item_order
-    return 1 + (2 + 1 + 3 * passes + 1) + 1 + (0 if step.fused_loss else 3) + 4 + order + 1
+    return 1 + 5 + 1 + (0 if step.fused_loss else 3) + 4 + order + 1
 
 
 def raster_stages(step):

@@ -1,41 +1,59 @@
 // binsort.cu -- tile binning and depth sort of the projected splats.
 //
-//   1. k_scan_reduce   : per-block sums of tiles_touched (256 entries a block)
-//   2. k_scan_blocks   : exclusive scan of the block sums (one CTA), M, overflow flag
-//   3. k_duplicate     : block-local scan + emission of one key per (entry, tile):
-//                        key = (global tile << 32) | bits(float z), value = entry.
-//                        Entries covering many tiles are emitted by their whole
-//                        warp, so a large splat near the camera does not leave
-//                        one thread writing hundreds of keys alone.
-//   4. LSD radix sort  : passes of up to 9-bit digits over the 31 depth bits and
-//                        the tile bits; each pass is k_radix_hist (per-block
-//                        digit counts) -> k_radix_scan (one CTA per digit) ->
-//                        k_radix_scatter (stable: per-warp ranks from match_any,
-//                        per-digit warp prefixes in shared memory).  Blocks hold
-//                        1024 keys, so even a few hundred thousand keys give
-//                        several blocks per SM and short serial chains.
-//   5. k_tile_ranges   : [start, end) of every tile in the sorted list
+// The paper does not describe this step (Sec. 3.3 renders with the 3D Gaussian
+// splatting rasteriser it builds on, whose compositing walks each tile's splats
+// front to back).  The result is the list of keys (global tile << 32) | bits(z),
+// one per (entry, covered tile), in ascending key order with equal keys in entry
+// order, and each tile's [start, end) in it.  Since (tile, z bits, entry) is
+// unique, the order is unique, so it does not matter how it is reached:
 //
-// The key's bit 31 (the sign of z > 0) is always 0, so the sort runs over the
-// 31 depth bits and the tile bits only.  Kernels never read M on the host: grids
-// are sized for the key capacity and blocks past M return at once, which keeps
-// the whole sequence free of host synchronisation (capturable in a CUDA graph).
+//   1. k_bin_zero    : zero the per-tile key counts (workspace)
+//   2. k_bin_count   : one atomic increment of a tile's count per (entry, covered
+//                      tile); entries covering many tiles are counted by their
+//                      whole warp.  Each tile has kStripes counters (the lane
+//                      picks one), so that the thousands of keys of a deep tile
+//                      do not queue on one address
+//   3. k_bin_stripes : per tile, the exclusive scan of its stripe counters (each
+//                      becomes its stripe's offset inside the tile) and the total
+//   4. k_bin_offsets : one CTA: exclusive scan of the tile totals in coalesced
+//                      rounds -> ranges [start, end) of every tile (clamped to
+//                      the key capacity), M, the overflow flag; the totals
+//                      become the tiles' starts
+//   5. k_bin_scatter : every (entry, tile) pair claims a slot of its tile's
+//                      segment with an atomic on its stripe's cursor and writes
+//                      the composite (z bits << 32) | entry there (in no fixed
+//                      order)
+//   6. k_tile_sort   : sorts every tile's segment by the composite, i.e. by
+//                      (z, entry), and writes key = (tile << 32) | z bits and
+//                      value = entry: a CTA of 1024 threads sorts one tile of more
+//                      than kSmallCap keys (a bitonic network in shared memory up
+//                      to kSegCap keys, a stable LSD radix sort through the
+//                      workspace's second key buffer above that) or, split into
+//                      four groups of 256 threads with their own barriers, four
+//                      smaller tiles at once.
+//
+// z > near > 0, so the fp32 bits of z are positive and ordered like z.  Kernels
+// never read M on the host: grids are sized by entries and tiles, every write
+// is bounded by the key capacity, so the sequence is free of host
+// synchronisation (capturable in a CUDA graph).
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 1;
-constexpr int kScanBlock = kScanThreads * kScanItems;
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 4;
-constexpr int kSortBlock = kSortThreads * kSortItems;
-constexpr int kMaxDigitBits = 9;
-constexpr int kRadixMax = 1 << kMaxDigitBits;            // buckets of the widest digit
-constexpr int kDigitsPerThread = kRadixMax / kSortThreads;
-constexpr int kBigEntry = 8;                             // keys an entry emits by itself
+constexpr int kBinThreads = 256;
+constexpr int kBigEntry = 8;                             // keys an entry handles by itself
+constexpr int kScanThreads = 1024;
+constexpr int kSortThreads = 1024;                       // a tile-sort CTA
+constexpr int kGroup = 256;                              // threads of a small-tile group
+constexpr int kGroups = kSortThreads / kGroup;
+constexpr int kSmallCap = 2 * kGroup;                    // keys a group sorts (one pair per thread)
+constexpr int kSegCap = 4 * kSortThreads;                // keys a CTA sorts (two pairs per thread)
+constexpr int kRadixThreads = 256;                       // threads that work in the radix path
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kStripes = 32;                             // counters per tile (stripe = lane)
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -73,285 +91,328 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
     return r;
 }
 
-// Also zeroes the tile ranges (k_tile_ranges writes only the tiles that have keys).
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt, int64_t E,
-                                                             uint32_t* __restrict__ block_sums,
-                                                             uint32_t* __restrict__ ranges, int64_t n_range_words) {
-    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+__global__ void __launch_bounds__(kBinThreads) k_bin_zero(uint32_t* __restrict__ cnt, int64_t words) {
     pdl_enter();
-    for (int64_t k = (int64_t)blockIdx.x * kScanThreads + threadIdx.x; k < n_range_words;
-         k += (int64_t)gridDim.x * kScanThreads)
-        ranges[k] = 0u;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        const int64_t e = (int64_t)blockIdx.x * kScanBlock + (int64_t)k * kScanThreads + threadIdx.x;
-        if (e < E) s += tt[e];
-    }
-    uint32_t total;
-    block_exclusive_scan<kScanThreads>(s, &total, s_warp);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+    for (int64_t t = (int64_t)blockIdx.x * kBinThreads + threadIdx.x; t < words; t += (int64_t)gridDim.x * kBinThreads)
+        cnt[t] = 0u;
 }
 
-// One CTA: exclusive scan of nb block sums in place; M = total.
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ block_sums, int nb,
-                                                      uint32_t* __restrict__ num_keys, int64_t capacity,
-                                                      int32_t* __restrict__ status) {
-    __shared__ uint32_t s_warp[1024 / 32 + 1];
+// Global tile of the k-th covered tile (row-major over the rectangle r) of an
+// entry of a view with tile base tb and tx tiles per row.
+__device__ __forceinline__ uint32_t covered_tile(int4 r, int tb, int tx, int k) {
+    const int w = r.z - r.x;
+    return (uint32_t)(tb + (r.y + k / w) * tx + r.x + k % w);
+}
+
+// Calls f(tile, entry, z bits) once for every (entry, covered tile) pair of this
+// thread's entry e; entries with more than kBigEntry tiles are enumerated by
+// the whole warp (32 tiles at a time), so one large splat near the camera does
+// not leave a single thread looping over hundreds of tiles.
+template <typename F>
+__device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
+                                             const float4* __restrict__ rgbd, int64_t E, int64_t n,
+                                             const Views& views, F f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const uint32_t cnt = e < E ? tt[e] : 0u;
+    int4 r = make_int4(0, 0, 1, 1);
+    int tb = 0, tx = 1;
+    uint32_t zbits = 0;
+    if (cnt > 0) {
+        const int v = (int)(e / n);
+        r = rect[e];
+        tb = views.v[v].tile_base;
+        tx = views.v[v].tiles_x;
+        if (rgbd != nullptr) zbits = __float_as_uint(rgbd[e].w);
+    }
+    if (cnt > 0 && cnt <= (uint32_t)kBigEntry)
+        for (int k = 0; k < (int)cnt; k++) f(covered_tile(r, tb, tx, k), (uint32_t)e, zbits);
+    uint32_t big = __ballot_sync(0xffffffffu, cnt > (uint32_t)kBigEntry);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        int4 br;
+        br.x = __shfl_sync(0xffffffffu, r.x, src);
+        br.y = __shfl_sync(0xffffffffu, r.y, src);
+        br.z = __shfl_sync(0xffffffffu, r.z, src);
+        br.w = __shfl_sync(0xffffffffu, r.w, src);
+        const int bcnt = (int)__shfl_sync(0xffffffffu, cnt, src);
+        const int btb = __shfl_sync(0xffffffffu, tb, src), btx = __shfl_sync(0xffffffffu, tx, src);
+        const uint32_t bz = __shfl_sync(0xffffffffu, zbits, src);
+        const uint32_t be = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)e, src);
+        for (int k = lane; k < bcnt; k += 32) f(covered_tile(br, btb, btx, k), be, bz);
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
+                                                          int64_t E, int64_t n, Views views,
+                                                          uint32_t* __restrict__ cnt) {
     pdl_enter();
-    const int chunk = (nb + 1023) / 1024;
-    const int lo = threadIdx.x * chunk;
-    uint32_t s = 0;
-    for (int k = 0; k < chunk; k++)
-        if (lo + k < nb) s += block_sums[lo + k];
-    uint32_t total;
-    uint32_t run = block_exclusive_scan<1024>(s, &total, s_warp);
-    for (int k = 0; k < chunk; k++) {
-        if (lo + k < nb) {
-            uint32_t v = block_sums[lo + k];
-            block_sums[lo + k] = run;
-            run += v;
+    uint32_t* mine = cnt + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles;     // this lane's stripe
+    for_each_key(tt, rect, nullptr, E, n, views, [&](uint32_t g, uint32_t, uint32_t) { atomicAdd(mine + g, 1u); });
+}
+
+// Per tile: each stripe counter becomes the exclusive prefix of the stripes
+// before it (its offset inside the tile); total[t] = the tile's key count.
+__global__ void __launch_bounds__(kBinThreads) k_bin_stripes(uint32_t* __restrict__ cnt, int total_tiles,
+                                                            uint32_t* __restrict__ total) {
+    pdl_enter();
+    const int t = blockIdx.x * kBinThreads + threadIdx.x;
+    if (t >= total_tiles) return;
+    uint32_t run = 0;
+#pragma unroll 8
+    for (int s = 0; s < kStripes; s++) {
+        uint32_t* c = cnt + (size_t)s * total_tiles + t;
+        const uint32_t v = *c;
+        *c = run;
+        run += v;
+    }
+    total[t] = run;
+}
+
+// One CTA: ranges[t] = [start, start + count) of every tile with keys (both
+// clamped to the capacity, so that no reader of the ranges leaves the key
+// buffers after an overflow) and (0, 0) for an empty tile, cnt[t] = start (the
+// tile's first slot for the scatter), M, the overflow flag.
+__global__ void __launch_bounds__(kScanThreads) k_bin_offsets(uint32_t* __restrict__ cnt, int total_tiles,
+                                                             uint2* __restrict__ ranges,
+                                                             uint32_t* __restrict__ num_keys, int64_t capacity,
+                                                             int32_t* __restrict__ status) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    pdl_enter();
+    const uint32_t cap = (uint32_t)capacity;     // < 2^32 (host check)
+    uint32_t carry = 0;
+    for (int base = 0; base < total_tiles; base += kScanThreads) {
+        const int t = base + (int)threadIdx.x;
+        const uint32_t c = t < total_tiles ? cnt[t] : 0u;
+        uint32_t total;
+        const uint32_t st = carry + block_exclusive_scan<kScanThreads>(c, &total, s_warp);
+        if (t < total_tiles) {
+            ranges[t] = c > 0 ? make_uint2(min(st, cap), min(st + c, cap)) : make_uint2(0u, 0u);   // (0, 0): empty
+            cnt[t] = st;
         }
+        carry += total;
     }
     if (threadIdx.x == 0) {
-        *num_keys = total;
-        if ((int64_t)total > capacity) *status = GS_ERR_CAPACITY;
+        *num_keys = carry;
+        if ((int64_t)carry > capacity) *status = GS_ERR_CAPACITY;
     }
 }
 
-// Emission of the keys of one entry: key = (tile << 32) | z bits, value =
-// entry, written at [off, off + cnt) in row-major order over its rectangle.
-__device__ __forceinline__ void emit_keys(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
-                                          uint32_t off, int k0, int k1, int kstep, int4 r, int tb, int tx,
-                                          uint32_t zbits, uint32_t e) {
-    const int w = r.z - r.x;
-    for (int k = k0; k < k1; k += kstep) {
-        const int64_t pos = (int64_t)off + k;
-        if (pos < capacity) {
-            const uint64_t g = (uint64_t)(tb + (r.y + k / w) * tx + r.x + k % w);
-            keys[pos] = (g << 32) | (uint64_t)zbits;
-            vals[pos] = e;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_duplicate(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
-                                                           const float4* __restrict__ rgbd, int64_t E, int64_t n,
-                                                           const uint32_t* __restrict__ block_offsets, Views views,
-                                                           int64_t capacity, uint64_t* __restrict__ keys,
-                                                           uint32_t* __restrict__ vals) {
-    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const uint32_t* __restrict__ tt,
+                                                            const int4* __restrict__ rect,
+                                                            const float4* __restrict__ rgbd, int64_t E, int64_t n,
+                                                            Views views, const uint32_t* __restrict__ start,
+                                                            uint32_t* __restrict__ stripes, int64_t capacity,
+                                                            uint64_t* __restrict__ comp) {
     pdl_enter();
-    const int lane = threadIdx.x & 31;
-    uint32_t carry = block_offsets[blockIdx.x];
-    for (int k = 0; k < kScanItems; k++) {
-        const int64_t e = (int64_t)blockIdx.x * kScanBlock + (int64_t)k * kScanThreads + threadIdx.x;
-        const uint32_t cnt = e < E ? tt[e] : 0u;
-        uint32_t total;
-        const uint32_t off = carry + block_exclusive_scan<kScanThreads>(cnt, &total, s_warp);
-        carry += total;
-        int4 r = make_int4(0, 0, 1, 1);
-        int tb = 0, tx = 1;
-        uint32_t zbits = 0;
-        if (cnt > 0) {
-            const int v = (int)(e / n);
-            r = rect[e];
-            zbits = __float_as_uint(rgbd[e].w);
-            tb = views.v[v].tile_base;
-            tx = views.v[v].tiles_x;
-        }
-        if (cnt > 0 && cnt <= (uint32_t)kBigEntry)
-            emit_keys(keys, vals, capacity, off, 0, (int)cnt, 1, r, tb, tx, zbits, (uint32_t)e);
-        uint32_t big = __ballot_sync(0xffffffffu, cnt > (uint32_t)kBigEntry);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            int4 br;
-            br.x = __shfl_sync(0xffffffffu, r.x, src);
-            br.y = __shfl_sync(0xffffffffu, r.y, src);
-            br.z = __shfl_sync(0xffffffffu, r.z, src);
-            br.w = __shfl_sync(0xffffffffu, r.w, src);
-            const uint32_t boff = __shfl_sync(0xffffffffu, off, src);
-            const int bcnt = (int)__shfl_sync(0xffffffffu, cnt, src);
-            const int btb = __shfl_sync(0xffffffffu, tb, src), btx = __shfl_sync(0xffffffffu, tx, src);
-            const uint32_t bz = __shfl_sync(0xffffffffu, zbits, src);
-            const uint32_t be = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)e, src);
-            emit_keys(keys, vals, capacity, boff, lane, bcnt, 32, br, btb, btx, bz, be);
-        }
+    uint32_t* mine = stripes + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles;   // this lane's stripe
+    for_each_key(tt, rect, rgbd, E, n, views, [&](uint32_t g, uint32_t e, uint32_t zbits) {
+        const uint32_t pos = start[g] + atomicAdd(mine + g, 1u);
+        if ((int64_t)pos < capacity) comp[pos] = ((uint64_t)zbits << 32) | e;
+    });
+}
+
+// Shared memory of k_tile_sort: the groups' keys, one large tile's keys, or the
+// radix path's bookkeeping (one at a time).
+struct RadixSmem {
+    uint32_t hist[kRadix];
+    uint32_t base[kRadix];
+    uint32_t rbase[kRadix];
+    uint32_t cnt[2][kRadixWarps][kRadix];
+    uint32_t warp[kRadixThreads / 32 + 1];
+};
+union SortSmem {
+    uint64_t group_keys[kGroups][kSmallCap];    // the groups' own sorts
+    uint64_t keys[kSegCap];                     // a CTA's sort of one larger tile
+    RadixSmem rx;
+};
+
+// Exclusive scan of one value per thread over the first kRadixThreads threads;
+// every thread of the CTA must call it (it contains CTA barriers).
+__device__ __forceinline__ uint32_t radix_exclusive_scan(uint32_t x, uint32_t* s_warp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool act = tid < kRadixThreads;
+    uint32_t inc = act ? x : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
-}
-
-// digit of the compacted key ((tile << 31) | z bits) at [shift, shift + bits)
-__device__ __forceinline__ uint32_t key_digit(uint64_t key, int shift, uint32_t mask) {
-    const uint64_t c = ((key >> 32) << 31) | (key & 0x7fffffffull);
-    return (uint32_t)(c >> shift) & mask;
-}
-
-__device__ __forceinline__ int64_t sort_count(const uint32_t* num_keys, int64_t capacity) {
-    const int64_t m = (int64_t)*num_keys;
-    return m < capacity ? m : capacity;
-}
-
-// Per-block digit counts, stored digit-major: counts[d * nb + b].
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
-                                                            const uint32_t* __restrict__ num_keys, int64_t capacity,
-                                                            int shift, int bits, uint32_t* __restrict__ counts) {
-    pdl_enter();
-    const int64_t M = sort_count(num_keys, capacity);
-    const int nb = (int)ceil_div(M, kSortBlock);
-    if ((int)blockIdx.x >= nb) return;
-    __shared__ uint32_t h[kSortWarps][kRadixMax];
-    const int radix = 1 << bits;
-    for (int k = threadIdx.x; k < kSortWarps * kRadixMax; k += kSortThreads) (&h[0][0])[k] = 0u;
+    if (act && lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    const uint32_t mask = (uint32_t)radix - 1u;
-    const int warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    uint64_t key[kSortItems];
-#pragma unroll
-    for (int r = 0; r < kSortItems; r++) {
-        const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        key[r] = idx < M ? keys[idx] : 0ull;
-    }
-#pragma unroll
-    for (int r = 0; r < kSortItems; r++) {
-        const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-        if (idx < M) atomicAdd(&h[warp][key_digit(key[r], shift, mask)], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kSortThreads) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; w++) s += h[w][d];
-        counts[(int64_t)d * nb + blockIdx.x] = s;
-    }
-}
-
-// One warp per digit: exclusive scan (in place) of that digit's per-block
-// counts counts[d * nb .. d * nb + nb) with shuffle scans over chunks of 32 and
-// a running carry; the digit's total goes to digit_total[d].
-constexpr int kDigitScanThreads = 256;
-constexpr int kDigitScanWarps = kDigitScanThreads / 32;
-
-__global__ void __launch_bounds__(kDigitScanThreads) k_radix_scan(uint32_t* __restrict__ counts,
-                                                                 uint32_t* __restrict__ digit_total,
-                                                                 const uint32_t* __restrict__ num_keys,
-                                                                 int64_t capacity, int radix) {
-    pdl_enter();
-    const int lane = threadIdx.x & 31;
-    const int d = blockIdx.x * kDigitScanWarps + (threadIdx.x >> 5);
-    if (d >= radix) return;
-    const int64_t M = sort_count(num_keys, capacity);
-    const int nb = (int)ceil_div(M, kSortBlock);
-    uint32_t* c = counts + (int64_t)d * nb;
-    uint32_t carry = 0;
-    for (int i0 = 0; i0 < nb; i0 += 32) {
-        const int i = i0 + lane;
-        const uint32_t x = i < nb ? c[i] : 0u;
-        uint32_t inc = x;
+    if (warp == 0) {
+        uint32_t w = lane < kRadixWarps ? s_warp[lane] : 0u;
+        uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
-        if (i < nb) c[i] = carry + inc - x;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
+        if (lane < kRadixWarps) s_warp[lane] = wi - w;
     }
-    if (lane == 0) digit_total[d] = carry;
-}
-
-// Stable scatter.  Each round places 256 consecutive keys: ranks inside a warp
-// come from match_any, the offsets of earlier warps from a per-digit prefix in
-// shared memory, and s_base carries the digit's running position across rounds.
-// Counts are double-buffered so that a round needs two barriers.  Thread t owns
-// digits t and t + 256 of the bookkeeping.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* __restrict__ kin,
-                                                               const uint32_t* __restrict__ vin,
-                                                               uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                               const uint32_t* __restrict__ offsets,
-                                                               const uint32_t* __restrict__ digit_total,
-                                                               const uint32_t* __restrict__ num_keys,
-                                                               int64_t capacity, int shift, int bits) {
-    pdl_enter();
-    const int64_t M = sort_count(num_keys, capacity);
-    const int nb = (int)ceil_div(M, kSortBlock);
-    if ((int)blockIdx.x >= nb) return;
-    __shared__ uint32_t s_base[kRadixMax];
-    __shared__ uint32_t s_rbase[kRadixMax];
-    __shared__ uint32_t s_cnt[2][kSortWarps][kRadixMax];
-    __shared__ uint32_t s_warp[kSortThreads / 32 + 1];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int radix = 1 << bits;
-    const uint32_t mask = (uint32_t)radix - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
-#pragma unroll
-    for (int r = 0; r < kSortItems; r++) {
-        const int64_t idx = base + (int64_t)r * kSortThreads + tid;
-        key[r] = idx < M ? kin[idx] : 0ull;
-        val[r] = idx < M ? vin[idx] : 0u;
-    }
-    // digit base = keys of smaller digits in the whole list + this digit's keys in earlier blocks
-    uint32_t dt[kDigitsPerThread];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int q = 0; q < kDigitsPerThread; q++) {
-        const int d = tid * kDigitsPerThread + q;
-        dt[q] = d < radix ? digit_total[d] : 0u;
-        sum += dt[q];
-    }
-    uint32_t tot;
-    uint32_t run0 = block_exclusive_scan<kSortThreads>(sum, &tot, s_warp);
-#pragma unroll
-    for (int q = 0; q < kDigitsPerThread; q++) {
-        const int d = tid * kDigitsPerThread + q;
-        if (d < radix) s_base[d] = run0 + offsets[(int64_t)d * nb + blockIdx.x];
-        run0 += dt[q];
-    }
-    for (int k = tid; k < 2 * kSortWarps * kRadixMax; k += kSortThreads) (&s_cnt[0][0][0])[k] = 0u;
     __syncthreads();
+    const uint32_t r = act ? s_warp[warp] + inc - x : 0u;
+    __syncthreads();
+    return r;
+}
+
+// Stable LSD radix sort of the n composites at a (scratch b, same length) by
+// 8-bit digits over bits [0, ebits) (the entry) and [32, 63) (the z bits).  The
+// first kRadixThreads threads do the work, the others take part in the CTA
+// barriers only.  Each pass: digit histogram, its exclusive scan, then a stable
+// scatter in rounds of kRadixThreads keys (ranks within a warp from match_any,
+// earlier warps' counts of the digit from a per-round table).  Returns the
+// buffer holding the result.
+__device__ uint64_t* seg_radix_sort(uint64_t* a, uint64_t* b, int n, int ebits, RadixSmem& sm) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bool act = tid < kRadixThreads;
     const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int r = 0; r < kSortItems; r++) {
-        const int buf = r & 1;
-        const int64_t idx = base + (int64_t)r * kSortThreads + tid;
-        const bool valid = idx < M;
-        const uint32_t d = valid ? key_digit(key[r], shift, mask) : (uint32_t)kRadixMax;   // sentinel
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) s_cnt[buf][warp][d] = __popc(peers);
+    int shifts[12], np = 0;
+    for (int s = 0; s < ebits; s += kRadixBits) shifts[np++] = s;
+    for (int s = 32; s < 63; s += kRadixBits) shifts[np++] = s;
+    uint64_t* src = a;
+    uint64_t* dst = b;
+    for (int p = 0; p < np; p++) {
+        const int sh = shifts[p];
+        if (act) sm.hist[tid] = 0u;
         __syncthreads();
-        for (int dd = tid; dd < radix; dd += kSortThreads) {
-            uint32_t run = 0;
+        for (int i = tid; i < n; i += kSortThreads) atomicAdd(&sm.hist[(uint32_t)(src[i] >> sh) & (kRadix - 1)], 1u);
+        __syncthreads();
+        const uint32_t base = radix_exclusive_scan(act ? sm.hist[tid] : 0u, sm.warp);
+        if (act) sm.base[tid] = base;
+        for (int k = tid; k < 2 * kRadixWarps * kRadix; k += kSortThreads) (&sm.cnt[0][0][0])[k] = 0u;
+        __syncthreads();
+        for (int r0 = 0, round = 0; r0 < n; r0 += kRadixThreads, round++) {
+            const int buf = round & 1;
+            const int i = r0 + tid;
+            const bool valid = act && i < n;
+            const uint64_t key = valid ? src[i] : 0ull;
+            const uint32_t d = valid ? (uint32_t)(key >> sh) & (kRadix - 1) : (uint32_t)kRadix;   // sentinel
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & lt);
+            if (valid && rank == 0) sm.cnt[buf][warp][d] = __popc(peers);
+            __syncthreads();
+            if (act) {   // thread tid owns digit tid: earlier warps' counts, then the digit's running base
+                uint32_t run = 0;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; w++) {
-                const uint32_t c = s_cnt[buf][w][dd];
-                s_cnt[buf][w][dd] = run;
-                run += c;
-                s_cnt[buf ^ 1][w][dd] = 0u;
+                for (int w = 0; w < kRadixWarps; w++) {
+                    const uint32_t c = sm.cnt[buf][w][tid];
+                    sm.cnt[buf][w][tid] = run;
+                    run += c;
+                    sm.cnt[buf ^ 1][w][tid] = 0u;
+                }
+                sm.rbase[tid] = sm.base[tid];
+                sm.base[tid] += run;
             }
-            s_rbase[dd] = s_base[dd];
-            s_base[dd] += run;
+            __syncthreads();
+            if (valid) dst[sm.rbase[d] + sm.cnt[buf][warp][d] + rank] = key;
         }
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_rbase[d] + s_cnt[buf][warp][d] + rank;
-            kout[pos] = key[r];
-            vout[pos] = val[r];
-        }
+        uint64_t* t = src; src = dst; dst = t;
+    }
+    return src;
+}
+static_assert(kRadix == kRadixThreads, "one digit per working thread in the radix bookkeeping");
+
+// One compare-exchange stage (k, j) of a bitonic sort over s[0, P): pair q
+// is (a, a + j) with a = q with a zero bit inserted at j; the lower slot keeps
+// the smaller value where (a & k) == 0 (an ascending run), the larger elsewhere.
+__device__ __forceinline__ void bitonic_pair(uint64_t* s, int q, int j, int k) {
+    const int a = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+    const uint64_t x = s[a], y = s[a + j];
+    if ((x > y) == ((a & k) == 0)) {
+        s[a] = y;
+        s[a + j] = x;
     }
 }
 
-__global__ void k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
-                              int64_t capacity, uint2* __restrict__ ranges) {
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" :: "r"(g + 1), "r"(kGroup) : "memory");
+}
+
+// Bitonic sort of a tile of n <= kSmallCap composites by one group of kGroup
+// threads in its shared-memory slot (P = n rounded up to a power of two,
+// padded with the largest value; at most one pair per thread and stage, a
+// stage ends with the group's own named barrier).
+__device__ __forceinline__ void sort_group_tile(uint64_t* __restrict__ seg, uint32_t* __restrict__ vseg, int n,
+                                                uint64_t tile_hi, uint64_t* s, int g) {
+    const int gt = threadIdx.x & (kGroup - 1);
+    int P = 2;
+    while (P < n) P <<= 1;
+    for (int i = gt; i < P; i += kGroup) s[i] = i < n ? seg[i] : ~0ull;
+    group_sync(g);
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (gt < P / 2) bitonic_pair(s, gt, j, k);
+            group_sync(g);
+        }
+    for (int i = gt; i < n; i += kGroup) {
+        const uint64_t c = s[i];
+        seg[i] = tile_hi | (c >> 32);
+        vseg[i] = (uint32_t)c;
+    }
+    group_sync(g);
+}
+
+// The same by the whole CTA for n <= kSegCap (at most two pairs per thread).
+__device__ __forceinline__ void sort_cta_tile(uint64_t* __restrict__ seg, uint32_t* __restrict__ vseg, int n,
+                                              uint64_t tile_hi, uint64_t* s) {
+    const int tid = threadIdx.x;
+    int P = 2;
+    while (P < n) P <<= 1;
+    for (int i = tid; i < P; i += kSortThreads) s[i] = i < n ? seg[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (tid < P / 2) bitonic_pair(s, tid, j, k);
+            if (tid + kSortThreads < P / 2) bitonic_pair(s, tid + kSortThreads, j, k);
+            __syncthreads();
+        }
+    for (int i = tid; i < n; i += kSortThreads) {
+        const uint64_t c = s[i];
+        seg[i] = tile_hi | (c >> 32);
+        vseg[i] = (uint32_t)c;
+    }
+}
+
+// Two passes over the tiles (grid-stride): first each CTA sorts the tiles of
+// more than kSmallCap keys with all its threads (shared memory up to kSegCap
+// keys, the radix path above), then each of its groups sorts tiles of at most
+// kSmallCap keys on its own.  The long sorts start first; every stage of a sort
+// is one compare-exchange per thread (two for the largest shared-memory tiles).
+__global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                              uint64_t* __restrict__ alt,
+                                                              const uint2* __restrict__ ranges, int total_tiles,
+                                                              int ebits) {
+    __shared__ SortSmem sm;
     pdl_enter();
-    const int64_t M = sort_count(num_keys, capacity);
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    const uint32_t t = (uint32_t)(keys[s] >> 32);
-    if (s == 0 || (uint32_t)(keys[s - 1] >> 32) != t) ranges[t].x = (uint32_t)s;
-    if (s == M - 1 || (uint32_t)(keys[s + 1] >> 32) != t) ranges[t].y = (uint32_t)(s + 1);
+    const int tid = threadIdx.x, g = tid / kGroup;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const uint2 rg = ranges[t];
+        const int n = (int)(rg.y - rg.x);
+        if (n <= kSmallCap) continue;
+        uint64_t* seg = keys + rg.x;
+        uint32_t* vseg = vals + rg.x;
+        const uint64_t tile_hi = (uint64_t)t << 32;
+        if (n <= kSegCap) {
+            sort_cta_tile(seg, vseg, n, tile_hi, sm.keys);
+        } else {
+            const uint64_t* res = seg_radix_sort(seg, alt + rg.x, n, ebits, sm.rx);
+            for (int i = tid; i < n; i += kSortThreads) {
+                const uint64_t c = res[i];
+                seg[i] = tile_hi | (c >> 32);       // same index, same thread: in place is safe
+                vseg[i] = (uint32_t)c;
+            }
+        }
+        __syncthreads();                        // shared memory is reused by the next tile
+    }
+    const int ggroups = gridDim.x * kGroups;
+    for (int t = blockIdx.x * kGroups + g; t < total_tiles; t += ggroups) {
+        const uint2 rg = ranges[t];
+        const int n = (int)(rg.y - rg.x);
+        if (n > 0 && n <= kSmallCap) sort_group_tile(keys + rg.x, vals + rg.x, n, (uint64_t)t << 32, sm.group_keys[g], g);
+    }
 }
 
 }  // namespace
@@ -364,87 +425,66 @@ SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
 }
 
 // Workspace layout of launch_bin_sort (offsets in bytes, 256-byte aligned):
-//   block sums   : ceil(E / kScanBlock) u32
-//   counts       : kRadixMax * ceil(capacity / kSortBlock) u32
-//   digit totals : kRadixMax u32
-//   keys (alt)   : capacity u64
-//   vals (alt)   : capacity u32
-static size_t ws_block_sums(int64_t E) { return align_up(sizeof(uint32_t) * (size_t)(ceil_div(E, kScanBlock) + 1), 256); }
-static size_t ws_counts(int64_t cap) {
-    return align_up(sizeof(uint32_t) * (size_t)kRadixMax * (size_t)(ceil_div(cap, kSortBlock) + 1), 256);
+//   stripe counters / cursors : kStripes x total_tiles u32 (stripe-major)
+//   tile totals / starts      : total_tiles u32
+//   composites (alt)          : capacity u64 (the radix path's second buffer)
+static size_t ws_stripes(int32_t total_tiles) {
+    return align_up(sizeof(uint32_t) * (size_t)kStripes * (size_t)total_tiles, 256);
 }
+static size_t ws_totals(int32_t total_tiles) { return align_up(sizeof(uint32_t) * (size_t)(total_tiles + 1), 256); }
 
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles) {
-    (void)total_tiles;
-    return ws_block_sums(n_entries) + ws_counts(capacity) + align_up(sizeof(uint32_t) * kRadixMax, 256) +
-           align_up(sizeof(uint64_t) * (size_t)capacity, 256) + align_up(sizeof(uint32_t) * (size_t)capacity, 256);
+    (void)n_entries;
+    return ws_stripes(total_tiles) + ws_totals(total_tiles) +
+           align_up(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1), 256);
 }
 
 cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& views, const SortPlan& plan,
                             const gs_bins& bins, void* ws, cudaStream_t s) {
     const int64_t E = n * views.n;
     const int64_t cap = plan.capacity;
+    const int T = plan.total_tiles;
     char* p = static_cast<char*>(ws);
-    uint32_t* block_sums = reinterpret_cast<uint32_t*>(p);
-    p += ws_block_sums(E);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(p);
-    p += ws_counts(cap);
-    uint32_t* digit_total = reinterpret_cast<uint32_t*>(p);
-    p += align_up(sizeof(uint32_t) * kRadixMax, 256);
-    uint64_t* keys_alt = reinterpret_cast<uint64_t*>(p);
-    p += align_up(sizeof(uint64_t) * (size_t)cap, 256);
-    uint32_t* vals_alt = reinterpret_cast<uint32_t*>(p);
+    uint32_t* stripes = reinterpret_cast<uint32_t*>(p);
+    p += ws_stripes(T);
+    uint32_t* totals = reinterpret_cast<uint32_t*>(p);
+    p += ws_totals(T);
+    uint64_t* alt = reinterpret_cast<uint64_t*>(p);
 
     cudaError_t err = cudaSuccess;
-    if (E == 0) {
-        err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)views.total_tiles, s);
+    if (E == 0 || T == 0) {
+        err = cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, s);
         if (err != cudaSuccess) return err;
         return cudaMemsetAsync(bins.num_keys, 0, sizeof(uint32_t), s);
     }
-    // passes over the compacted key (tile << 31 | z bits), digits of at most 9 bits
-    int tile_bits = 0;
-    while ((1ll << tile_bits) < (int64_t)plan.total_tiles) tile_bits++;
-    const int bits = 31 + tile_bits;
-    const int n_passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
-    int width[8], shift[8];
-    for (int k = 0, sh = 0; k < n_passes; k++) {
-        width[k] = bits / n_passes + (k < bits % n_passes ? 1 : 0);
-        shift[k] = sh;
-        sh += width[k];
-    }
-    const int nb_scan = (int)ceil_div(E, kScanBlock);
-    err = launch_pdl(k_scan_reduce, nb_scan, kScanThreads, 0, s, pr.tiles_touched, E, block_sums, bins.ranges,
-                     2 * (int64_t)views.total_tiles);
+    int ebits = 0;
+    while ((1ll << ebits) < E) ebits++;
+    const int nb_tiles = (int)ceil_div(T, kBinThreads);
+    const int nb_entries = (int)ceil_div(E, kBinThreads);
+    const int4* rect = reinterpret_cast<const int4*>(pr.rect);
+    const float4* rgbd = reinterpret_cast<const float4*>(pr.rgbd);
+    const int64_t words = (int64_t)kStripes * T;
+    const int nb_zero = (int)(ceil_div(words, kBinThreads) < 4096 ? ceil_div(words, kBinThreads) : 4096);
+    err = launch_pdl(k_bin_zero, nb_zero, kBinThreads, 0, s, stripes, words);
     if (err == cudaSuccess)
-        err = launch_pdl(k_scan_blocks, 1, 1024, 0, s, block_sums, nb_scan, bins.num_keys, cap, bins.status);
-    if (err != cudaSuccess) return err;
-    // The duplicated list goes into the buffer that makes the last pass land in bins.keys.
-    uint64_t* k0 = (n_passes % 2 == 0) ? bins.keys : keys_alt;
-    uint32_t* v0 = (n_passes % 2 == 0) ? bins.vals : vals_alt;
-    uint64_t* k1 = (n_passes % 2 == 0) ? keys_alt : bins.keys;
-    uint32_t* v1 = (n_passes % 2 == 0) ? vals_alt : bins.vals;
-    err = launch_pdl(k_duplicate, nb_scan, kScanThreads, 0, s, pr.tiles_touched,
-                     reinterpret_cast<const int4*>(pr.rect), reinterpret_cast<const float4*>(pr.rgbd), E, n,
-                     block_sums, views, cap, k0, v0);
-    if (err != cudaSuccess) return err;
-    const int nb_sort = (int)ceil_div(cap, kSortBlock);
-    for (int pass = 0; pass < n_passes; pass++) {
-        err = launch_pdl(k_radix_hist, nb_sort, kSortThreads, 0, s, k0, bins.num_keys, cap, shift[pass], width[pass],
-                         counts);
-        const int radix = 1 << width[pass];
-        if (err == cudaSuccess)
-            err = launch_pdl(k_radix_scan, (unsigned)ceil_div(radix, kDigitScanWarps), kDigitScanThreads, 0, s, counts,
-                             digit_total, bins.num_keys, cap, radix);
-        if (err == cudaSuccess)
-            err = launch_pdl(k_radix_scatter, nb_sort, kSortThreads, 0, s, k0, v0, k1, v1, counts, digit_total,
-                             bins.num_keys, cap, shift[pass], width[pass]);
-        if (err != cudaSuccess) return err;
-        uint64_t* tk = k0; k0 = k1; k1 = tk;
-        uint32_t* tv = v0; v0 = v1; v1 = tv;
+        err = launch_pdl(k_bin_count, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, E, n, views, stripes);
+    if (err == cudaSuccess) err = launch_pdl(k_bin_stripes, nb_tiles, kBinThreads, 0, s, stripes, T, totals);
+    if (err == cudaSuccess)
+        err = launch_pdl(k_bin_offsets, 1, kScanThreads, 0, s, totals, T, reinterpret_cast<uint2*>(bins.ranges),
+                         bins.num_keys, cap, bins.status);
+    if (err == cudaSuccess)
+        err = launch_pdl(k_bin_scatter, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, rgbd, E, n, views,
+                         totals, stripes, cap, bins.keys);
+    if (err == cudaSuccess) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_sort, kSortThreads, 0);
+        const int64_t full = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        const int grid = (int)(T < full ? T : full);
+        err = launch_pdl(k_tile_sort, grid, kSortThreads, 0, s, bins.keys, bins.vals, alt,
+                         reinterpret_cast<const uint2*>(bins.ranges), T, ebits);
     }
-    const int nb_rng = (int)ceil_div(cap, 256);
-    err = launch_pdl(k_tile_ranges, nb_rng, 256, 0, s, bins.keys, bins.num_keys, cap,
-                     reinterpret_cast<uint2*>(bins.ranges));
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }

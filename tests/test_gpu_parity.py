@@ -112,6 +112,43 @@ def test_bin_sort_bit_exact_many_keys_ties_and_views():
     np.testing.assert_array_equal(ranges, ranges_o)
 
 
+@pytest.mark.parametrize("deep", [4096, 4097, 20000])
+def test_bin_sort_bit_exact_deep_tiles(deep):
+    # Tiles whose lists exceed what one CTA sorts in shared memory (4096 keys)
+    # take the CTA-wide radix path; `deep` entries cover one tile, half of them
+    # also its right neighbour (a list just below, at and far above the limit),
+    # scattered through the entry order among shallow random entries, with
+    # heavy depth ties (ties broken by entry index).
+    rng = np.random.default_rng(deep)
+    cam = synth.identity_camera(256, 128)                  # 16 x 8 tiles of 16 px
+    params = G.RenderParams(tile=16)
+    tx, ty = 16, 8
+    n = deep + 3000
+    x0 = rng.integers(0, tx, n); y0 = rng.integers(0, ty, n)
+    rect = np.stack([x0, y0, np.minimum(x0 + rng.integers(1, 4, n), tx),
+                     np.minimum(y0 + rng.integers(1, 3, n), ty)], 1)
+    pile = rng.permutation(n)[:deep]
+    rect[pile] = [5, 3, 6, 4]
+    rect[pile[::2], 2] = 7
+    culled = rng.random(n) < 0.1
+    culled[pile] = False
+    rect[culled] = 0
+    depth = rng.choice(np.linspace(0.3, 8.0, 300), n)
+    tiles = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
+    prs = [dict(xy=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)),
+                depth=f32(depth), rect=rect.astype(np.int32), radius=np.ones(n, np.int32), tiles=tiles)]
+    proj = projected_to_device(prs)
+    keys_o, vals_o, ranges_o = oracle_bins(prs, [cam], 16)
+    r = ranges_o.reshape(-1, 2)
+    assert r[3 * tx + 5, 1] - r[3 * tx + 5, 0] >= deep
+    bins, _ = run_bin_sort(proj, n, [cam], params, capacity=len(keys_o) + 5)
+    keys, vals, ranges = bins_to_numpy(bins)
+    assert int(bins.status[0].item()) == 0
+    np.testing.assert_array_equal(keys, keys_o)
+    np.testing.assert_array_equal(vals, vals_o)
+    np.testing.assert_array_equal(ranges, ranges_o)
+
+
 def test_capacity_overflow_is_reported_not_faulted():
     g, _, cam = _problem(0)
     params = G.RenderParams()
