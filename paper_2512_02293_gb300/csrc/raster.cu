@@ -6,10 +6,10 @@
 // persistent grid's warps take items from a device counter (views of uneven
 // size balance across SMs) and each works through its tile's depth-sorted
 // list on its own:
-// lane l gathers splat base + l of the list into registers (float2 / float4
-// rows), the warp parks those 32 splats in its private shared-memory slot and
-// composites them with broadcast reads while the next 32 (and the list entries
-// of the 32 after those) are already in flight.  A lane's per-splat tests are
+// lane l gathers splat base + l of the list into the warp's shared-memory ring
+// (cp.async), culls it, and the warp parks the kept splats in its compositing
+// slots and composites them with broadcast reads while the next two batches
+// of 32 (and the list entries of the batch after those) are already in flight.  A lane's per-splat tests are
 // predicates, not branches, so a warp never diverges inside a batch.  Before compositing, the warp drops the splats that cannot reach
 // alpha_min anywhere in its block.  There is no CTA-wide barrier, so a warp
 // stops as soon as its own 32 pixels are saturated and takes the next item; the
@@ -51,6 +51,24 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Gather of one splat's rows into shared memory without registers: 8 + 16 + 16
+// bytes as one commit group (committed even when the lane copies nothing, so
+// that every lane's group count advances by one per batch).
+__device__ __forceinline__ void cp_async_splat(float2* dxy, float4* dco, float4* dcd, const float2* xy,
+                                               const float4* conic_o, const float4* rgbd, uint32_t e, bool valid) {
+    if (valid) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"((uint32_t)__cvta_generic_to_shared(dxy)),
+                     "l"(xy + e) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"((uint32_t)__cvta_generic_to_shared(dco)),
+                     "l"(conic_o + e) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"((uint32_t)__cvta_generic_to_shared(dcd)),
+                     "l"(rgbd + e) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// all but this lane's newest commit group have landed
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -76,6 +94,7 @@ struct Splat {
     float4 q;     // -0.5 log2e A, -log2e B, -0.5 log2e C, opacity
     float4 cd;    // r, g, b, z
 };
+
 
 __device__ __forceinline__ Splat load_splat(const float2* __restrict__ xy, const float4* __restrict__ conic_o,
                                             const float4* __restrict__ rgbd, uint32_t e) {
@@ -160,19 +179,45 @@ __device__ void fused_loss_finish(const FusedLoss& fl, const Views& views, const
 }
 
 
-// Every warp takes items until it draws one >= n_items, so a launch makes
-// exactly n_items + (its warps) increments; the warp that draws the last value
-// returns the counter to zero for the next launch (no reset on the stream).
-__device__ __forceinline__ int next_item(int* queue, int lane, int n_items) {
-    int item = 0;
-    if (lane == 0) {
-        item = atomicAdd(queue, 1);
-        if (item == n_items + (int)(gridDim.x * kRasterWarps) - 1) *queue = 0;
+// The persistent launches' work queue over n items.  Plain: every warp draws
+// items from a device counter until it draws one >= n, so a launch makes n +
+// (its warps) increments.  Spread (a launch that walks a cost-ordered list,
+// deepest first): warp w of CTA c takes item w * gridDim.x + c first, without
+// the counter, so that the deepest items of the first round go to the first
+// warps of different CTAs instead of to the warps that happen to draw first
+// (which tend to share an SM); the later draws take items from gridDim.x *
+// warps on.  Either way the warp that draws the last value returns the counter
+// to zero for the next launch (no reset on the stream).
+struct WorkQueue {
+    int* counter;
+    int n, base, total;
+    bool spread;
+    __device__ WorkQueue(int* c, int n_items, bool spread_first) : counter(c), n(n_items), spread(spread_first) {
+        const int warps = (int)gridDim.x * kRasterWarps;
+        base = spread ? warps : 0;                                        // items handed out without the counter
+        total = spread ? max(n - warps, 0) + min(warps, n) : n + warps;   // increments of one launch
     }
-    return __shfl_sync(0xffffffffu, item, 0);
-}
+    __device__ __forceinline__ int first(int lane) {
+        if (spread) return (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x;
+        return next(lane);
+    }
+    __device__ __forceinline__ int next(int lane) {
+        int item = 0;
+        if (lane == 0) {
+            const int d = atomicAdd(counter, 1);
+            if (d == total - 1) *counter = 0;
+            item = base + d;
+        }
+        return __shfl_sync(0xffffffffu, item, 0);
+    }
+};
 
-template <int T, bool LOSS>
+// Prefetch: RING keeps two batches of splats in flight through a shared-memory
+// ring (a launch with few blocks per SM, where a lone warp's deep walk would
+// otherwise wait a gather latency per batch); without it one batch is in
+// flight in registers, and the smaller shared footprint leaves more L1 for the
+// splats that the warps of a tile share (a launch with many blocks per SM).
+template <int T, bool LOSS, bool RING>
 __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
@@ -185,6 +230,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
     __shared__ float s_loss[LOSS ? GS_MAX_VIEWS * 3 : 1];    // per-view sums of this CTA (fused loss)
     __shared__ float s_tgt[LOSS ? kRasterWarps : 1][4][32];   // each lane's targets, fetched at the item's start
     __shared__ float s_lacc[LOSS ? kRasterWarps : 1][3][32];  // each lane's running sums for the warp's view lv
+    // the next batches' splats, gathered by cp.async: two slots of 32 per warp (RING)
+    __shared__ float2 r_xy[RING ? kRasterWarps : 1][2][32];
+    __shared__ float4 r_co[RING ? kRasterWarps : 1][2][32];
+    __shared__ float4 r_cd[RING ? kRasterWarps : 1][2][32];
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lv = -1;                                               // view of the sums in s_lacc (warp-uniform)
@@ -209,7 +258,8 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
     if constexpr (LOSS)
         ordered = fl.order != nullptr && fl.order_tag[0] == (uint32_t)n_items &&
                   fl.order_tag[1] == ((uint32_t)n_items ^ kOrderTagMagic);
-    for (int raw = next_item(queue, lane, n_items); raw < n_items; raw = next_item(queue, lane, n_items)) {
+    WorkQueue wq(queue, n_items, ordered);
+    for (int raw = wq.first(lane); raw < n_items; raw = wq.next(lane)) {
         int item = raw;
         if (ordered) {                           // (an index out of range can only come from a foreign workspace)
             const uint32_t o = fl.order[raw];
@@ -248,13 +298,34 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
         uint32_t last = 0;
         bool done = !inside;
-        // the next batch's splats and the one after's list entries are in flight
-        // while a batch is composited, so a splat load never waits on its index
+        // RING: while batch b is composited, the splats of batches b + 1 and b + 2
+        // are in flight into the warp's two ring slots (cp.async, no registers
+        // held; batch b has left its slot for the compositing slots) and the list
+        // entries of batch b + 3 into a register.  Otherwise the splats of batch
+        // b + 1 and the list entries of b + 2 are in flight in registers.  Either
+        // way a splat load never waits on its index.
         Splat nxt;
         uint32_t nidx = 0;
-        if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
-        if (range.x + 32 + lane < range.y) nidx = vals[range.x + 32 + lane];
+        int slot_b = 0;                                  // ring slot of batch b
+        if constexpr (RING) {
+            const bool v0 = range.x + lane < range.y, v1 = range.x + 32 + lane < range.y;
+            const uint32_t i0 = v0 ? vals[range.x + lane] : 0u, i1 = v1 ? vals[range.x + 32 + lane] : 0u;
+            cp_async_splat(&r_xy[w][0][lane], &r_co[w][0][lane], &r_cd[w][0][lane], xy, conic_o, rgbd, i0, v0);
+            cp_async_splat(&r_xy[w][1][lane], &r_co[w][1][lane], &r_cd[w][1][lane], xy, conic_o, rgbd, i1, v1);
+            nidx = range.x + 64 + lane < range.y ? vals[range.x + 64 + lane] : 0u;
+        } else {
+            if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
+            if (range.x + 32 + lane < range.y) nidx = vals[range.x + 32 + lane];
+        }
         for (uint32_t base = range.x; base < range.y; base += 32) {
+            if constexpr (RING) {
+                cp_async_wait_all_but_one();             // this lane's splat of batch b has landed
+                nxt.xy = r_xy[w][slot_b][lane];
+                const float4 c = r_co[w][slot_b][lane];
+                scale_conic(c.x, c.y, c.z, &nxt.q.x, &nxt.q.y, &nxt.q.z);
+                nxt.q.w = c.w;
+                nxt.cd = r_cd[w][slot_b][lane];
+            }
             const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
             const uint32_t kept = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
@@ -266,8 +337,15 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 s_pos[w][slot] = base - range.x + lane;
             }
             __syncwarp();
-            if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
-            if (base + 64 + lane < range.y) nidx = vals[base + 64 + lane];
+            if constexpr (RING) {   // batch b + 2 into batch b's slot (this lane has read its entry)
+                cp_async_splat(&r_xy[w][slot_b][lane], &r_co[w][slot_b][lane], &r_cd[w][slot_b][lane], xy, conic_o,
+                               rgbd, nidx, base + 64 + lane < range.y);
+                nidx = base + 96 + lane < range.y ? vals[base + 96 + lane] : 0u;
+                slot_b ^= 1;
+            } else {
+                if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
+                if (base + 64 + lane < range.y) nidx = vals[base + 64 + lane];
+            }
             // warp-uniform loop; a lane's tests (power > 0, alpha < alpha_min, the
             // transmittance cutoff) become predicates, so the warp never diverges
             const int cnt = __popc(kept);
@@ -316,6 +394,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 }
             if (last_k >= 0) last = s_pos[w][last_k] + 1u;
             if (__all_sync(0xffffffffu, done)) break;
+        }
+        if constexpr (RING) {
+            cp_async_wait_all();                 // no gather into the ring outlives the item
+            __syncwarp();
         }
         float ec = 0.f, ed = 0.f, nv = 0.f;
         if (inside) {
@@ -602,7 +684,8 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
     __shared__ float4 s_c[kRasterWarps][32];      // raw conic A, B, C
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int raw = next_item(queue, lane, n_items); raw < n_items; raw = next_item(queue, lane, n_items)) {
+    WorkQueue wq(queue, n_items, LOSS && fl.order != nullptr);
+    for (int raw = wq.first(lane); raw < n_items; raw = wq.next(lane)) {
         const int item = (LOSS && fl.order != nullptr) ? (int)fl.order[raw] : raw;
         bwd_item<T, LOSS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
                           views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
@@ -664,6 +747,13 @@ __global__ void __launch_bounds__(kOrderThreads) k_item_order(const uint32_t* __
 }
 static_assert(kOrderBuckets == 2 * kOrderThreads, "two buckets per thread in the scan");
 
+// A launch with at most this many 8 x 4 pixel blocks per SM (a single 640x480
+// view: ~60) is "few": its time is bounded by its deepest blocks' walks, so both
+// passes take the blocks deepest first, the forward keeps two batches in flight
+// per warp and the backward runs 2 CTAs per SM (90 registers); a keyframe window
+// (~900 per SM) is bound by throughput instead.
+constexpr int kFewItemsPerSm = 256;
+
 // CTAs of a persistent raster launch: every SM filled to the kernel's occupancy
 // (host-side occupancy query; no stream operation, so it may run during capture).
 template <typename K>
@@ -703,29 +793,38 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
-    int* queue = bins.status + 1;      // zero between launches (see next_item)
+    int* queue = bins.status + 1;      // zero between launches (see WorkQueue)
     cudaError_t e = cudaSuccess;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     switch (rc.tile) {
+#define GS_FWD_LAUNCH(TT, L, R, F)                                                                     \
+    launch_pdl(k_render_fwd<TT, L, R>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, views, rc, img, \
+               queue, n_items, F)
 #define GS_FWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
+        const bool few = n_items <= kFewItemsPerSm * sms;                                             \
         if (fl) {                                                                                      \
-            const int grid = persistent_grid(k_render_fwd<TT, true>, n_items);                        \
+            const int grid = few ? persistent_grid(k_render_fwd<TT, true, true>, n_items)             \
+                                 : persistent_grid(k_render_fwd<TT, true, false>, n_items);           \
             if (grid > kFusedMaxCtas) return cudaErrorInvalidConfiguration;                           \
             FusedLoss f = *fl;                                                                         \
             if (n_items > kOrderMaxItems) f.item_cost = f.order = nullptr;                             \
-            e = launch_pdl(k_render_fwd<TT, true>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, \
-                           views, rc, img, queue, n_items, f);                                         \
-        } else                                                                                         \
-            e = launch_pdl(k_render_fwd<TT, false>, persistent_grid(k_render_fwd<TT, false>, n_items), \
-                           kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, views, rc, img, queue, n_items, \
-                           FusedLoss{});                                                               \
+            e = few ? GS_FWD_LAUNCH(TT, true, true, f) : GS_FWD_LAUNCH(TT, true, false, f);          \
+        } else {                                                                                       \
+            const int grid = few ? persistent_grid(k_render_fwd<TT, false, true>, n_items)            \
+                                 : persistent_grid(k_render_fwd<TT, false, false>, n_items);          \
+            e = few ? GS_FWD_LAUNCH(TT, false, true, FusedLoss{}) : GS_FWD_LAUNCH(TT, false, false, FusedLoss{}); \
+        }                                                                                              \
         break;                                                                                         \
     }
         GS_FWD(8)
         GS_FWD(16)
         GS_FWD(32)
 #undef GS_FWD
+#undef GS_FWD_LAUNCH
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -740,12 +839,12 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(bins.ranges);
-    int* queue = bins.status + 2;      // zero between launches (see next_item)
+    int* queue = bins.status + 2;      // zero between launches (see WorkQueue)
     cudaError_t e = cudaSuccess;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    constexpr int kBwdFewItemsPerSm = 256;
+
 #define GS_BWD_LAUNCH(TT, C, L, F)                                                                     \
     launch_pdl(k_render_bwd<TT, C, L>, persistent_grid(k_render_bwd<TT, C, L>, n_items), kRasterThreads, 0, s, \
                xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items, F)
@@ -753,7 +852,7 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
 #define GS_BWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        const bool few = n_items <= kBwdFewItemsPerSm * sms;                                          \
+        const bool few = n_items <= kFewItemsPerSm * sms;                                             \
         FusedLoss f = fl ? *fl : FusedLoss{};                                                          \
         /* few items per SM: deepest blocks first (costs from the fused forward) */                    \
         if (fl && few && n_items <= kOrderMaxItems)                                                    \

@@ -189,3 +189,45 @@ def test_mapping_iterations_reduce_the_loss(setup):
         if it == 0:
             assert not step.ensure_capacity()
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_ordered_forward_on_the_deepest_blocks_matches_oracle(setup):
+    """After one fused forward and backward, the next fused forward takes its
+    8 x 4 blocks deepest first (the backward's order), the first ones handed to
+    the first warps of different CTAs.  A 64x64 window around the deepest pixel
+    is compared with the oracle, n_contrib bit-exact, and the whole image with
+    the same step's first (natural-order) forward: bit for bit, since the order
+    changes only which warp takes which block."""
+    g, cam, params, _ = setup
+    P = cam.n_pixels
+    step = MappingStep(G.Gaussians.from_numpy(g), [cam], torch.zeros(3 * P, device="cuda"),
+                       torch.zeros(P, device="cuda"), params, MapParams(1.0, 1.0, 0.0))
+    step.render()
+    step.loss_and_backward()                 # the backward writes the deepest-first order
+    torch.cuda.synchronize()
+    col0 = step.img.color.clone(); nc0 = step.img.n_contrib.clone()
+    step.render()                            # ordered: deepest blocks first
+    torch.cuda.synchronize()
+    assert step.check() == 0
+    nc = step.img.n_contrib.cpu().numpy().view(np.uint32).reshape(cam.height, cam.width)
+    assert nc.max() > 768                    # a deep list (the long serial walk)
+    yd, xd = np.unravel_index(np.argmax(nc), nc.shape)
+    x0 = int(min(max(xd // 16 * 16 - 16, 0), cam.width - 64))
+    y0 = int(min(max(yd // 16 * 16 - 16, 0), cam.height - 64))
+    w = h = 64
+    crop = _crop(cam, x0, y0, w, h)
+    prm = prm_dict(params)
+    pr = oracle.project(g, crop, prm)
+    img = oracle.render_fwd(pr, crop, prm)
+    ex, _ = _excused(cam, (x0, y0, w, h), step.proj.rect.cpu().numpy(), pr, img)
+    ok = ~ex
+    assert ok.mean() > 0.9
+    col = step.color_image(0).cpu().numpy()[:, y0:y0 + h, x0:x0 + w]
+    dep = step.depth_image(0).cpu().numpy()[y0:y0 + h, x0:x0 + w]
+    Tf = step.img.T_final.cpu().numpy().reshape(cam.height, cam.width)[y0:y0 + h, x0:x0 + w]
+    np.testing.assert_allclose(col[:, ok], img["color"][:, ok], atol=COLOR_TOL)
+    np.testing.assert_allclose(dep[ok], img["depth"][ok], atol=COLOR_TOL)
+    np.testing.assert_allclose(Tf[ok], img["T_final"][ok], atol=1e-5)
+    np.testing.assert_array_equal(nc[y0:y0 + h, x0:x0 + w][ok], img["n_contrib"][ok])
+    # against the natural-order forward of the same map
+    assert torch.equal(step.img.color, col0) and torch.equal(step.img.n_contrib, nc0)
