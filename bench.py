@@ -37,14 +37,47 @@ sys.path.insert(0, ROOT)
 
 METRIC = "mapping iters/sec (fwd+bwd, 1 GB300) and Gpix-splats/s vs plain form at oracle tolerance"
 WORKLOAD = "plain single view, SLAM scale: 640x480, 200k Gaussians on a synthetic room (6 planes + 20 boxes)"
-FWD_OPS_PER_PAIR = 20    # FP32 ops per visited (pixel, splat) pair in the forward definition
-BWD_OPS_PER_PAIR = 45    # FP32 ops per blended pair in the backward definition (+ reductions)
+# The rasterisers' arithmetic per (pixel, splat) pair, two ways: FP32 operations
+# with a fused multiply-add counted as one (against the lane peak: 152 SMs x
+# 128 FP32 lanes x clock), and FP32 FLOPs of the method's arithmetic with a
+# multiply-add counted as two (against the FLOP peak, twice the lane peak).
+# Forward per visited pair: offset 2, exponent 9, opacity 1, cutoff test 2,
+# weight and colour / depth accumulation 9 -> 23 FLOPs (+ 1 exp2).  Backward per
+# pair: the forward's weight again 12, the transmittance before the splat 2,
+# dL/dalpha 13, the colour behind 12, dL/dpower 3, the ten gradients 20 -> 62
+# FLOPs (+ 1 exp2, 1 reciprocal).
+FWD_OPS_PER_PAIR = 20
+BWD_OPS_PER_PAIR = 45
+FWD_FLOP_PER_PAIR = 23
+BWD_FLOP_PER_PAIR = 62
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the rasterisers
-# on this workload, from an ncu capture of the current kernels
-# (profiles/k_render_{bwd,fwd}_640x480_200k.md); keyed by (stage, tile).
-PROFILED_TRAFFIC = {("gs_render_bwd_raster", 16): 22.28e6, ("gs_render_fwd", 16): 9.28e6,
-                    ("gs_render_bwd_raster_loss", 16): 27.23e6, ("gs_render_fwd_loss", 16): 14.25e6}
+# Algorithmic bytes of the memory-bound stages: projection 56 B read per
+# Gaussian (once for all views) + 64 B written per (view, Gaussian); binning 56 B per entry (rect and depth read by
+# the count and scatter passes), 28 B per key (composite written, read and the
+# key and value written by the per-tile sort) and 528 B per tile (32 stripe
+# counters zeroed, counted, scanned; the total and the range); projection
+# backward 56 B of parameters + 48 B of 2D gradients per view read and 56 B of
+# gradients written per Gaussian; Adam 28 B per parameter element (14 per
+# Gaussian).  For binning, the radix-sort reference count (12 B per key
+# duplicated + 2 x 12 B per key per 8-bit pass over 31 depth bits and the tile
+# bits) is reported beside it.
+PROJECT_BYTES_PER_GAUSSIAN, PROJECT_BYTES_PER_ENTRY = 56, 64
+BIN_BYTES_PER_ENTRY, BIN_BYTES_PER_KEY, BIN_BYTES_PER_TILE = 56, 28, 528
+PROJECT_BWD_BYTES_PER_GAUSSIAN, PROJECT_BWD_BYTES_PER_ENTRY = 56 + 56, 48
+ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
+# From one ncu capture of one iteration of this workload (640x480, 200k
+# Gaussians, tile 16; profiles/launch_list_640x480_200k.md): dram__bytes_read.sum
+# + dram__bytes_write.sum per launch of each stage's kernels (cold cache), and
+# the binding pipe of the rasterisers (profiles/k_render_{fwd,bwd}_640x480_200k.md).
+# None where the kernel changed after the capture.
+PROFILED_TRAFFIC = {("gs_project", 16): 11.30e6, ("gs_bin_sort", 16): 14.50e6, ("gs_render_fwd_loss", 16): 14.26e6,
+                    ("gs_render_bwd_raster_loss", 16): 27.30e6, ("gs_project_bwd", 16): 16.41e6,
+                    ("gs_adam_step", 16): 44.83e6}
+PROFILED_PIPE = {
+    ("gs_render_fwd_loss", 16): "instruction issue: 62.8 % of active cycles issue; pipes ALU 37.9 %, FMA 27.6 %, "
+                                "LSU 22.2 %, XU (ex2) 9.2 %; SMs active 82 % of the launch",
+    ("gs_render_bwd_raster_loss", 16): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, FMA 36.2 %, "
+                                       "LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the launch"}
 
 
 def _peaks():
@@ -266,6 +299,72 @@ def _oracle_iteration_fn(g, gt, cams, params, mp, sh_degree):
     return one
 
 
+def stage_rooflines(step, st, pairs, params, bwd_label=None):
+    """Roofline of every stage of one iteration from its CUDA-event time in the
+    instrumented graph replays: the rasterisers against the FP32 lane peak
+    (operations, a multiply-add as one) and the FP32 FLOP peak (a multiply-add as
+    two), the other stages against the measured HBM copy bandwidth."""
+    peaks, peak_kind = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    lane_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # T lane-ops/s
+    flop_peak = 2.0 * lane_peak                          # T FLOP/s FP32
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    if not st:
+        return out
+    fwd_st, bwd_st = raster_stages(step)
+    few = "few" if step.total_tiles * (params.tile // 8) * (params.tile // 4) <= 256 * 152 else "many"
+    fl = str(step.fused_loss).lower()
+    kern = {fwd_st: f"k_render_fwd<{params.tile}, {fl}, ring={few == 'few'}>",
+            bwd_st: f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> (+ its 2D-gradient "
+                    f"zero-fill{' and block ordering' if few == 'few' and step.fused_loss else ''})"}
+    for stage, ops, flop in ((fwd_st, FWD_OPS_PER_PAIR, FWD_FLOP_PER_PAIR), (bwd_st, BWD_OPS_PER_PAIR,
+                                                                            BWD_FLOP_PER_PAIR)):
+        sec = st[stage] * 1e-3
+        ach = pairs * ops / sec / 1e12
+        ach_f = pairs * flop / sec / 1e12
+        out[stage] = {"bound": "alu", "kernel": kern[stage], "achieved": ach, "peak": lane_peak,
+                      "unit": "T FP32 lane-ops/s", "frac": ach / lane_peak,
+                      "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops (a multiply-add as one)",
+                      "flop": {"achieved": ach_f, "peak": flop_peak, "unit": "TFLOP/s FP32", "frac": ach_f / flop_peak,
+                               "work": f"{pairs} pairs x {flop} FLOPs (a multiply-add as two)"},
+                      "binding_pipe": PROFILED_PIPE.get((stage, params.tile)),
+                      "traffic": PROFILED_TRAFFIC.get((stage, params.tile)),
+                      "ms": st[stage],
+                      "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
+    E = step.n * step.V
+    M = step.num_keys()
+    T = step.total_tiles
+    tile_bits = max(1, (T - 1).bit_length())
+    lsd_passes = -(-(31 + tile_bits) // 8)
+    hbm_stages = {
+        "gs_project": (step.n * PROJECT_BYTES_PER_GAUSSIAN + E * PROJECT_BYTES_PER_ENTRY,
+                       f"{step.n} Gaussians x {PROJECT_BYTES_PER_GAUSSIAN} B + {E} entries x {PROJECT_BYTES_PER_ENTRY} B"),
+        "gs_bin_sort": (E * BIN_BYTES_PER_ENTRY + M * BIN_BYTES_PER_KEY + T * BIN_BYTES_PER_TILE,
+                        f"{E} entries x {BIN_BYTES_PER_ENTRY} B + {M} keys x {BIN_BYTES_PER_KEY} B + {T} tiles x "
+                        f"{BIN_BYTES_PER_TILE} B"),
+        "gs_project_bwd": (step.n * (PROJECT_BWD_BYTES_PER_GAUSSIAN + step.V * PROJECT_BWD_BYTES_PER_ENTRY),
+                           f"{step.n} Gaussians x ({PROJECT_BWD_BYTES_PER_GAUSSIAN} + {step.V} views x "
+                           f"{PROJECT_BWD_BYTES_PER_ENTRY}) B"),
+        "gs_adam_step": (step.n * ADAM_ELEMENTS_PER_GAUSSIAN * ADAM_BYTES_PER_ELEMENT,
+                         f"{step.n * ADAM_ELEMENTS_PER_GAUSSIAN} elements x {ADAM_BYTES_PER_ELEMENT} B"),
+    }
+    for stage, (nbytes, work) in hbm_stages.items():
+        if stage not in st:
+            continue
+        gbs = nbytes / (st[stage] * 1e-3) / 1e9
+        out[stage] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                      "work": work, "ms": st[stage], "traffic": PROFILED_TRAFFIC.get((stage, params.tile)),
+                      "peak_basis": f"hbm_gbs ({peak_kind})"}
+    if "gs_bin_sort" in out:
+        lsd = M * (12 + 24 * lsd_passes)
+        out["gs_bin_sort"]["radix_reference"] = {
+            "bytes": lsd, "achieved": lsd / (st["gs_bin_sort"] * 1e-3) / 1e9,
+            "frac": lsd / (st["gs_bin_sort"] * 1e-3) / 1e9 / hbm,
+            "work": f"{M} keys x (12 + 24 x {lsd_passes} passes) B: an 8-bit LSD radix sort's traffic"}
+    return out
+
+
 def cpu_baseline(params, mp, reps=3):
     """The FP64 oracle, as it stands, on the host cores: the median of `reps`
     full mapping iterations (render, loss, gradients and the Adam update) on
@@ -350,20 +449,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
     views = len(cams)
-    peaks, peak_kind = _peaks()
-    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    roof = None
-    if st:
-        roof = {}
-        fwd_st, bwd_st = raster_stages(step)
-        fl = str(step.fused_loss).lower()
-        for stage, ops, kern in ((fwd_st, FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}, {fl}>"),
-                                 (bwd_st, BWD_OPS_PER_PAIR,
-                                  f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}>")):
-            ach = pairs * ops / (st[stage] * 1e-3) / 1e12
-            roof[stage] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
-                           "frac": ach / alu_peak, "work": f"{pairs} visited pairs x {ops} FP32 ops per launch",
-                           "peak_basis": f"152 SMs x 128 FP32 lanes x sm_max_mhz ({peak_kind})"}
+    roof = stage_rooflines(step, st, pairs, params) if st else None
     return {"workload": "batched window: 8 keyframes (4x 640x480, 2x 752x480, 2x 1280x1024), 500k Gaussians",
             "roofline": roof,
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
@@ -871,27 +957,12 @@ def main():
                    "eager_value with the two copies in, the C-ABI calls and the two copies out issued "
                    "each step"}
 
-    peaks, peak_kind = _peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # FP32 lane-ops/s (FMA = 1 op), in T ops/s
+    stages_roof = stage_rooflines(step, st, pairs, params)
     roofline = None
     if st:
         dominant = max(st, key=st.get)
-        fwd_st, bwd_st = raster_stages(step)
-        fl = str(step.fused_loss).lower()
-        if dominant == bwd_st:
-            ms, ops, kern = (st[bwd_st], BWD_OPS_PER_PAIR,
-                             f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> "
-                             f"(+ its grad2d zero-fill and block ordering)")
-        else:
-            ms, ops, kern = st[fwd_st], FWD_OPS_PER_PAIR, f"k_render_fwd<{params.tile}, {fl}>"
-        ach = pairs * ops / (ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tops/s FP32",
-                    "frac": ach / alu_peak, "traffic": PROFILED_TRAFFIC.get((dominant, params.tile)),
-                    "traffic_unit": "bytes per launch (DRAM read + write, ncu)", "dominant_stage": dominant,
-                    "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops per launch",
-                    "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
-                    "timing": "CUDA event-record nodes around the call in an instrumented copy of the step graph, median over as many replays as timed steps"}
+        roofline = dict(stages_roof[dominant])
+        roofline["dominant_stage"] = dominant
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -903,7 +974,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
             "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
-            "stages_ms": st, "roofline": roofline, "e2e": e2e,
+            "stages_ms": st, "roofline": roofline, "roofline_stages": stages_roof, "e2e": e2e,
             "gpu_launches": launches_per_step(step) * args.steps, "clocks": clocks}
     if not args.no_window:
         line["window"] = window_run(device, args, flush, value, dist, world)
