@@ -178,6 +178,17 @@ size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams,
 int32_t gs_project(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
                    const gs_render_params* params, gs_projected* out, void* stream);
 
+/* gs_project with each view's pose moved on the device first: xi is a device
+ * array [n_views][6] of pose tangents (rho, phi) and view v is rendered from
+ * Exp(xi_v) T_cw (rotation by Rodrigues' formula, translation to first order:
+ * T_cw <- (Exp(phi) R_cw, Exp(phi) t_cw + rho)), the left perturbation whose
+ * gradient gs_project_bwd reports (Sec. 3.3 poses; the pose tangent of the
+ * differentiable renderer).  It lets a caller render at a pose held in device
+ * memory without reading it back to the host.  xi = NULL is gs_project.
+ * Errors: as gs_project. */
+int32_t gs_project_perturbed(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                             const gs_render_params* params, const float* xi, gs_projected* out, void* stream);
+
 /* Tile binning and depth sort.  The paper does not describe this step: Sec. 3.3
  * renders with the 3D Gaussian splatting rasteriser it builds on, whose
  * compositing visits each tile's splats front to back.  Here: one key
@@ -278,6 +289,12 @@ int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, cons
 int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
                        const gs_render_params* params, const float* grad2d, float lambda_iso,
                        gs_grads* grads, float* iso_loss, void* stream);
+/* gs_project_bwd at the poses moved by the device tangents xi ([n_views][6], as
+ * gs_project_perturbed; the pose gradient is that of a further left
+ * perturbation of the moved pose).  xi = NULL is gs_project_bwd. */
+int32_t gs_project_bwd_perturbed(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                                 const gs_render_params* params, const float* xi, const float* grad2d,
+                                 float lambda_iso, gs_grads* grads, float* iso_loss, void* stream);
 
 /* The colour and depth terms of Eq. 6 fused into the rasterisers (the same
  * values as gs_render_fwd + gs_loss + gs_render_bwd_raster, without the two

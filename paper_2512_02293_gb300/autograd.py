@@ -1,19 +1,26 @@
 """torch.autograd binding of the differentiable renderer.
 
 ``render(gaussians..., pose_xi, rasterizer)`` renders colour and depth of every
-view through the C ABI (gs_project -> gs_bin_sort -> gs_render_fwd) and, in
-backward, calls gs_render_bwd: one hand-written backward kernel pass that
-starts from the per-pixel checkpoint (T_final, n_contrib) the forward wrote,
-and returns the gradients of every Gaussian parameter and of each view's
-6-DoF pose tangent xi = (rho, phi) (left perturbation T_cw <- Exp(xi) T_cw),
-the gradient a tracker needs.
+view through the C ABI (gs_project_perturbed -> gs_bin_sort -> gs_render_fwd)
+and, in backward, runs the hand-written backward kernels
+(gs_render_bwd_raster -> gs_project_bwd_perturbed), which start from the
+per-pixel checkpoint (T_final, n_contrib) the forward wrote and return the
+gradients of every Gaussian parameter and of each view's 6-DoF pose tangent
+xi = (rho, phi) (left perturbation T_cw <- Exp(xi) T_cw), the gradient a
+tracker needs.
 
-Pose convention: the cameras given to the Rasterizer are the base poses; a
-non-zero ``pose_xi`` is applied on the host as Exp(xi) T_cw before rendering
-(one small device-to-host read), and the returned pose gradient is the
-left-perturbation gradient at the rendered pose, i.e. d L / d xi exactly at
-xi = 0.  A tracker therefore keeps xi at zero, steps along -grad, and folds
-the step into the base pose.
+Pose convention: the cameras given to the Rasterizer are the base poses;
+``pose_xi`` (device [n_views, 6]) is applied on the device, view v rendered from
+Exp(xi_v) T_cw, and the returned pose gradient is the left-perturbation
+gradient at the rendered pose, i.e. d L / d xi exactly at xi = 0.  A tracker
+keeps xi at zero, steps along -grad, and folds the step into the base pose.
+
+No host synchronisation in forward or backward, so an iteration can be
+captured in a CUDA graph: the key buffers are sized once (the first forward
+measures the key count, or the caller passes a capacity), an overflow sets the
+device status word, and the caller checks it outside the graph with
+``Rasterizer.check()`` / ``ensure_capacity()`` (grow and redo), as
+mapping.MappingStep does.
 """
 from __future__ import annotations
 
@@ -50,7 +57,8 @@ def se3_left_update(cam, xi):
 class Rasterizer:
     """Device buffers for rendering n Gaussians into a fixed set of views."""
 
-    def __init__(self, cams, n: int, params: G.RenderParams | None = None, device="cuda", headroom=1.3):
+    def __init__(self, cams, n: int, params: G.RenderParams | None = None, device="cuda", headroom=1.3,
+                 key_capacity: int | None = None):
         self.cams = list(cams)
         self.params = params or G.RenderParams()
         self.n = int(n)
@@ -63,6 +71,8 @@ class Rasterizer:
         self.headroom = headroom
         self.bins = None
         self.ws = None
+        if key_capacity is not None:
+            self._alloc(key_capacity)
 
     def _alloc(self, capacity):
         capacity = max(int(capacity), 1024)
@@ -70,15 +80,28 @@ class Rasterizer:
         ws = G.gs_workspace_size(self.n, self.cams, self.params, capacity)
         self.ws = torch.empty((ws + 255) // 256 * 64, device=self.device, dtype=torch.float32)
 
-    def forward(self, g: G.Gaussians, cams):
-        G.gs_project(g, cams, self.params, self.proj)
-        if self.bins is None:
+    def check(self) -> int:
+        """Device status word of the last passes (0 = fine); synchronises."""
+        return 0 if self.bins is None else G.gs_read_device_status(self.bins.status)
+
+    def ensure_capacity(self) -> bool:
+        """Grow the key buffers if a pass overflowed them (outside any graph);
+        True if they were grown, in which case the iteration must be redone."""
+        st = self.check()
+        m = int(self.bins.num_keys.item()) & 0xFFFFFFFF if self.bins is not None else 0
+        if st == G.GS_ERR_CAPACITY or (self.bins is not None and m > self.bins.capacity):
+            self._alloc(int(m * self.headroom) + 1024)
+            return True
+        if st != 0:
+            raise G.GsError(st, "device status")
+        return False
+
+    def forward(self, g: G.Gaussians, xi):
+        G.gs_project(g, self.cams, self.params, self.proj, xi=xi)
+        if self.bins is None:       # first call without a given capacity: measure (a host read, before any capture)
             self._alloc(int(self.proj.tiles_touched.to(torch.int64).sum().item() * self.headroom) + 1024)
-        G.gs_bin_sort(self.proj, self.n, cams, self.params, self.bins, self.ws)
-        if G.gs_read_device_status(self.bins.status) == G.GS_ERR_CAPACITY:
-            self._alloc(int((int(self.bins.num_keys.item()) & 0xFFFFFFFF) * self.headroom) + 1024)
-            G.gs_bin_sort(self.proj, self.n, cams, self.params, self.bins, self.ws)
-        G.gs_render_fwd(self.proj, self.bins, cams, self.params, self.img)
+        G.gs_bin_sort(self.proj, self.n, self.cams, self.params, self.bins, self.ws)
+        G.gs_render_fwd(self.proj, self.bins, self.cams, self.params, self.img)
 
 
 class _Render(torch.autograd.Function):
@@ -86,12 +109,11 @@ class _Render(torch.autograd.Function):
     def forward(ctx, mean, quat, log_scale, opacity_logit, color, pose_xi, rast: Rasterizer):
         g = G.Gaussians(mean.detach().contiguous(), quat.detach().contiguous(), log_scale.detach().contiguous(),
                         opacity_logit.detach().contiguous(), color.detach().contiguous())
-        xi = pose_xi.detach().double().cpu().numpy().reshape(rast.V, 6)
-        cams = [se3_left_update(c, x) if np.any(x != 0) else c for c, x in zip(rast.cams, xi)]
-        rast.forward(g, cams)
+        xi = pose_xi.detach().reshape(rast.V, 6).contiguous().float()
+        rast.forward(g, xi)
         ctx.rast = rast
-        ctx.cams = cams
         ctx.g = g
+        ctx.xi = xi
         # the checkpoint lives in rast.img; the outputs are copies so that a later
         # render into the same buffers cannot change them
         return rast.img.color.clone(), rast.img.depth.clone()
@@ -104,8 +126,8 @@ class _Render(torch.autograd.Function):
         iso = torch.zeros(1, device=rast.device)
         dcolor = dcolor.contiguous().float() if dcolor is not None else torch.zeros_like(rast.img.color)
         ddepth = ddepth.contiguous().float() if ddepth is not None else torch.zeros_like(rast.img.depth)
-        G.gs_render_bwd(g, rast.proj, rast.bins, rast.img, dcolor, ddepth, ctx.cams, rast.params, 0.0, grads, iso,
-                        rast.ws)
+        G.gs_render_bwd_raster(rast.proj, rast.bins, rast.img, dcolor, ddepth, rast.cams, rast.params, g.n, rast.ws)
+        G.gs_project_bwd(g, rast.cams, rast.params, rast.ws, 0.0, grads, iso, xi=ctx.xi)
         return grads.mean, grads.quat, grads.log_scale, grads.opacity_logit, grads.color, grads.pose, None
 
 

@@ -158,11 +158,16 @@ size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, cons
 
 int32_t gs_project(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, const gs_render_params* params,
                    gs_projected* out, void* stream) {
+    return gs_project_perturbed(g, cams, n_views, params, nullptr, out, stream);
+}
+
+int32_t gs_project_perturbed(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                             const gs_render_params* params, const float* xi, gs_projected* out, void* stream) {
     if (!params_ok(params) || !gaussians_ok(g, n_views)) return GS_ERR_INVALID_ARG;
     Views views;
     if (!make_views(cams, n_views, params->tile, &views)) return GS_ERR_INVALID_ARG;
     if (g->n > 0 && !projected_ok(out)) return GS_ERR_INVALID_ARG;
-    return cuda_status(launch_project(*g, views, make_consts(params), *out, static_cast<cudaStream_t>(stream)));
+    return cuda_status(launch_project(*g, views, make_consts(params), *out, static_cast<cudaStream_t>(stream), xi));
 }
 
 int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, int32_t n_views,
@@ -290,6 +295,12 @@ int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, cons
 
 int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, const gs_render_params* params,
                        const float* grad2d, float lambda_iso, gs_grads* grads, float* iso_loss, void* stream) {
+    return gs_project_bwd_perturbed(g, cams, n_views, params, nullptr, grad2d, lambda_iso, grads, iso_loss, stream);
+}
+
+int32_t gs_project_bwd_perturbed(const gs_gaussians* g, const gs_camera* cams, int32_t n_views,
+                                 const gs_render_params* params, const float* xi, const float* grad2d,
+                                 float lambda_iso, gs_grads* grads, float* iso_loss, void* stream) {
     if (!params_ok(params) || !gaussians_ok(g, n_views) || grads == nullptr || !isfinite(lambda_iso))
         return GS_ERR_INVALID_ARG;
     if (g->n > 0 && (!grad2d || !aligned(grad2d, 16) || !grads->mean || !grads->quat || !grads->log_scale ||
@@ -301,7 +312,7 @@ int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_v
     cudaError_t e = cudaSuccess;
     e = launch_zero(grads->pose, 6 * (int64_t)n_views, iso_loss, 1, nullptr, 0, s);
     if (e == cudaSuccess && g->n > 0)
-        e = launch_project_bwd(*g, views, make_consts(params), grad2d, lambda_iso, *grads, iso_loss, s);
+        e = launch_project_bwd(*g, views, make_consts(params), grad2d, lambda_iso, *grads, iso_loss, s, xi);
     return cuda_status(e);
 }
 

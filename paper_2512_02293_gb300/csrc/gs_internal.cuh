@@ -80,7 +80,7 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
 
 // Launchers (one translation unit each).
 cudaError_t launch_project(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
-                           const gs_projected& out, cudaStream_t s);
+                           const gs_projected& out, cudaStream_t s, const float* xi = nullptr);
 cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n_entries, const Views& views,
                             const SortPlan& plan, const gs_bins& bins, void* ws, cudaStream_t s);
 // The Eq. 6 colour and depth L1 terms fused into the rasterisers: the forward
@@ -119,7 +119,7 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
                               float* g2d, cudaStream_t s, const FusedLoss* fl = nullptr);
 cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
-                               cudaStream_t s);
+                               cudaStream_t s, const float* xi = nullptr);
 cudaError_t noalloc_loss_scratch(float** out);
 // zero na, nb, nc floats at a, b, c (null or 0: skipped) with one kernel launch
 cudaError_t launch_zero(float* a, int64_t na, float* b, int64_t nb, float* c, int64_t nc, cudaStream_t s);

@@ -197,17 +197,66 @@ __device__ __forceinline__ void view_colour(const gs_gaussians& g, int i, const 
     rgb[0] = fmaxf(r0, 0.f); rgb[1] = fmaxf(r1, 0.f); rgb[2] = fmaxf(r2, 0.f);
 }
 
+// The views as this CTA uses them, in shared memory: the per-view constants,
+// each pose moved to Exp(xi_v) T_cw on the device when a tangent xi ([n_views][6],
+// (rho, phi)) is given: R <- Exp(phi) R (Rodrigues), t <- Exp(phi) t + rho (the
+// translation to first order), camera centre -R^T t.  The pose gradient of the
+// backward then refers to a further left perturbation of the moved pose.
+__device__ __forceinline__ void views_to_shared(const Views& views, const float* __restrict__ xi, ViewParams* s_vp) {
+    constexpr int kWords = sizeof(ViewParams) / sizeof(uint32_t);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(views.v);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_vp);
+    for (int k = threadIdx.x; k < views.n * kWords; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    if (xi != nullptr && (int)threadIdx.x < views.n) {
+        ViewParams& vp = s_vp[threadIdx.x];
+        const float* x = xi + 6 * threadIdx.x;
+        const float p0 = x[3], p1 = x[4], p2 = x[5];
+        const float th2 = p0 * p0 + p1 * p1 + p2 * p2, th = sqrtf(th2);
+        // Exp(phi) = I + a K + b K^2, K = [phi]x; a = sin th / th, b = (1 - cos th) / th^2
+        const float a = th < 1e-4f ? 1.f - th2 / 6.f : sinf(th) / th;
+        const float b = th < 1e-4f ? 0.5f - th2 / 24.f : (1.f - cosf(th)) / th2;
+        const float K[9] = {0.f, -p2, p1, p2, 0.f, -p0, -p1, p0, 0.f};
+        float E[9];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float kk = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+                E[3 * r + c] = (r == c ? 1.f : 0.f) + a * K[3 * r + c] + b * kk;
+            }
+        float R[9], t[3];
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                R[3 * r + c] = E[3 * r] * vp.Rcw[c] + E[3 * r + 1] * vp.Rcw[3 + c] + E[3 * r + 2] * vp.Rcw[6 + c];
+            t[r] = E[3 * r] * vp.tcw[0] + E[3 * r + 1] * vp.tcw[1] + E[3 * r + 2] * vp.tcw[2] + x[r];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; k++) vp.Rcw[k] = R[k];
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            vp.tcw[r] = t[r];
+            vp.centre[r] = -(R[r] * t[0] + R[3 + r] * t[1] + R[6 + r] * t[2]);
+        }
+    }
+    __syncthreads();
+}
+
 template <int SH>
 __global__ void __launch_bounds__(kProjThreads) k_project(gs_gaussians g, Views views, RenderConsts rc,
-                                                          gs_projected out) {
+                                                          gs_projected out, const float* __restrict__ xi) {
+    __shared__ ViewParams s_vp[GS_MAX_VIEWS];
     pdl_enter();
+    views_to_shared(views, xi, s_vp);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = (int)g.n;
     if (i >= n) return;
     Activated A;
     activate(g, i, A);
     for (int v = 0; v < views.n; v++) {
-        const ViewParams& vp = views.v[v];
+        const ViewParams& vp = s_vp[v];
         const size_t e = (size_t)v * n + i;
         ViewProj P;
         project_view(A, vp, rc, P);
@@ -247,8 +296,11 @@ template <int SH>
 __global__ void __launch_bounds__(kProjThreads, SH == 0 ? 3 : 1) k_project_bwd(gs_gaussians g, Views views,
                                                                                RenderConsts rc,
                                                               const float* __restrict__ g2d, float lambda_iso,
-                                                              float inv_n, gs_grads grads, float* iso_loss) {
+                                                              float inv_n, gs_grads grads, float* iso_loss,
+                                                              const float* __restrict__ xi) {
+    __shared__ ViewParams s_vp[GS_MAX_VIEWS];
     pdl_enter();
+    views_to_shared(views, xi, s_vp);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = (int)g.n;
     const bool active = i < n;
@@ -265,7 +317,7 @@ __global__ void __launch_bounds__(kProjThreads, SH == 0 ? 3 : 1) k_project_bwd(g
         for (int k = 0; k < 48; k++) G_sh[k] = 0.f;
     }
     for (int v = 0; v < views.n; v++) {
-        const ViewParams& vp = views.v[v];
+        const ViewParams& vp = s_vp[v];
         float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         ViewProj P;
         P.visible = false;
@@ -469,27 +521,27 @@ __global__ void __launch_bounds__(kProjThreads, SH == 0 ? 3 : 1) k_project_bwd(g
 }  // namespace
 
 cudaError_t launch_project(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
-                           const gs_projected& out, cudaStream_t s) {
+                           const gs_projected& out, cudaStream_t s, const float* xi) {
     if (g.n == 0) return cudaSuccess;
     const int blocks = (int)ceil_div(g.n, kProjThreads);
-    const cudaError_t e = rc.sh_degree == 0 ? launch_pdl(k_project<0>, blocks, kProjThreads, 0, s, g, views, rc, out)
-                                            : launch_pdl(k_project<3>, blocks, kProjThreads, 0, s, g, views, rc, out);
+    const cudaError_t e = rc.sh_degree == 0 ? launch_pdl(k_project<0>, blocks, kProjThreads, 0, s, g, views, rc, out, xi)
+                                            : launch_pdl(k_project<3>, blocks, kProjThreads, 0, s, g, views, rc, out, xi);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
-                               cudaStream_t s) {
+                               cudaStream_t s, const float* xi) {
     if (g.n == 0) return cudaSuccess;
     const int blocks = (int)ceil_div(g.n, kProjThreads);
     const float inv_n = 1.0f / (float)g.n;
     const cudaError_t e =
         rc.sh_degree == 0
             ? launch_pdl(k_project_bwd<0>, blocks, kProjThreads, 0, s, g, views, rc, g2d, lambda_iso, inv_n, grads,
-                         iso_loss)
+                         iso_loss, xi)
             : launch_pdl(k_project_bwd<3>, blocks, kProjThreads, 0, s, g, views, rc, g2d, lambda_iso, inv_n, grads,
-                         iso_loss);
+                         iso_loss, xi);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -125,7 +125,7 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
            "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
            "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss",
-           "gs_mapping_step", "gs_mlp_set_wait_polls"]
+           "gs_mapping_step", "gs_mlp_set_wait_polls", "gs_project_perturbed", "gs_project_bwd_perturbed"]
 
 
 def load_library(path: str | None = None):
@@ -197,6 +197,10 @@ def load_library(path: str | None = None):
     lib.gs_mapping_step.argtypes = [V, V]
     lib.gs_mlp_set_wait_polls.restype = ctypes.c_int64
     lib.gs_mlp_set_wait_polls.argtypes = [ctypes.c_int64]
+    lib.gs_project_perturbed.restype = ctypes.c_int32
+    lib.gs_project_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, V]
+    lib.gs_project_bwd_perturbed.restype = ctypes.c_int32
+    lib.gs_project_bwd_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, ctypes.c_float, V, V, V]
     if lib.gs_abi_version() != 4:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
@@ -397,10 +401,16 @@ def gs_workspace_size(n: int, cams, params: RenderParams, key_capacity: int) -> 
     return int(r)
 
 
-def gs_project(g: Gaussians, cams, params: RenderParams, out: Projected, stream=None):
+def gs_project(g: Gaussians, cams, params: RenderParams, out: Projected, stream=None, xi=None):
+    """xi: optional device float32 [n_views, 6] pose tangents applied on the device
+    (gs_project_perturbed)."""
     arr = camera_array(cams); p = params.struct(); gg = g.struct(); o = out.struct()
-    _check(load_library().gs_project(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), ctypes.byref(o),
-                                     _stream(stream)), "gs_project")
+    if xi is None:
+        _check(load_library().gs_project(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), ctypes.byref(o),
+                                         _stream(stream)), "gs_project")
+    else:
+        _check(load_library().gs_project_perturbed(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), _ptr(xi),
+                                                   ctypes.byref(o), _stream(stream)), "gs_project_perturbed")
 
 
 def gs_bin_sort(proj: Projected, n: int, cams, params: RenderParams, bins: Bins, ws, stream=None):
@@ -477,11 +487,17 @@ def gs_render_bwd_raster_loss(proj: Projected, bins: Bins, img: Image, target_co
 
 
 def gs_project_bwd(g: Gaussians, cams, params: RenderParams, grad2d, lambda_iso: float, grads: Grads, iso_loss,
-                   stream=None):
+                   stream=None, xi=None):
+    """xi: optional device float32 [n_views, 6] pose tangents (gs_project_bwd_perturbed)."""
     arr = camera_array(cams); p = params.struct(); gg = g.struct(); gr = grads.struct()
-    _check(load_library().gs_project_bwd(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), _ptr(grad2d),
-                                         float(lambda_iso), ctypes.byref(gr), _ptr(iso_loss), _stream(stream)),
-           "gs_project_bwd")
+    if xi is None:
+        _check(load_library().gs_project_bwd(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), _ptr(grad2d),
+                                             float(lambda_iso), ctypes.byref(gr), _ptr(iso_loss), _stream(stream)),
+               "gs_project_bwd")
+    else:
+        _check(load_library().gs_project_bwd_perturbed(ctypes.byref(gg), arr, len(cams), ctypes.byref(p), _ptr(xi),
+                                                       _ptr(grad2d), float(lambda_iso), ctypes.byref(gr),
+                                                       _ptr(iso_loss), _stream(stream)), "gs_project_bwd_perturbed")
 
 
 def gs_adam_step(groups, beta1: float, beta2: float, eps: float, d_step, stream=None):

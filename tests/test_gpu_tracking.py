@@ -1,6 +1,8 @@
 """Pose refinement through the re-rendering loss: a keyframe pose perturbed by a
 few centimetres and degrees is recovered from the pose-tangent gradient of the
-rendering loss alone, with the map fixed."""
+rendering loss alone, with the map fixed; the first steps match the same Adam
+driven by the FP64 oracle's gradient; a sequence of eight keyframes along a
+5 m path is tracked from the previous estimates."""
 import numpy as np
 import pytest
 import torch
@@ -42,3 +44,47 @@ def test_perturbed_pose_is_recovered(seed):
     dt, dr = pose_error(tr.cam, cam)
     assert losses[-1] < 0.05 * losses[0]
     assert dt < 1e-3 and dr < 5e-4, (dt0, dr0, dt, dr)     # 1 mm, 0.03 deg from 3 cm, ~1.1 deg
+
+
+@pytest.mark.gpu
+def test_three_steps_match_the_oracle_driven_steps():
+    """The GPU tracker's first three steps from a perturbed 64x48 pose against
+    the same Adam driven by the FP64 oracle's pose gradient
+    (tests/test_oracle_tracking.py): each pose within 1e-3 of the oracle-driven
+    displacement from the start."""
+    ensure_lib()
+    from test_oracle_tracking import LAMBDAS, XI0, oracle_track, tracking_problem
+    g, cam, target = tracking_problem()
+    start = se3_left_update(cam, XI0)
+    ref, _ = oracle_track(g, start, target)
+    tc = torch.from_numpy(np.asarray(target[0], np.float32).reshape(-1)).cuda()
+    td = torch.from_numpy(np.asarray(target[1], np.float32).reshape(-1)).cuda()
+    tr = PoseTracker(G.Gaussians.from_numpy(g), start, tc, td, G.RenderParams(tile=16), lambda_c=LAMBDAS[0],
+                     lambda_d=LAMBDAS[1])
+    for k in range(3):
+        tr.iterate()
+        dt, dr = pose_error(tr.cam, ref[k])
+        mt, mr = pose_error(ref[k], start)
+        assert dt < 1e-3 * mt and dr < 1e-3 * mr, (k, dt, mt, dr, mr)
+
+
+@pytest.mark.gpu
+def test_trajectory_of_eight_keyframes_is_recovered():
+    """The tracker over the 8 keyframes of the 5 m path through the 500k-Gaussian
+    room (4x 640x480, 2x 752x480, 2x 1280x1024): each keyframe starts from the
+    previous estimate's error carried along the path plus up to 3 cm / 1.1 deg
+    of fresh noise, the targets are the map's own renders at the true poses."""
+    ensure_lib()
+    from paper_2512_02293_gb300.tracking import TrajectoryTracker
+    g, _, cams = synth.cfg3_problem()
+    gd = G.Gaussians.from_numpy(g)
+    targets = []
+    for c in cams:
+        P = c.n_pixels
+        r = MappingStep(gd, [c], torch.zeros(3 * P, device="cuda"), torch.zeros(P, device="cuda"),
+                        G.RenderParams(tile=16), MapParams())
+        r.render()
+        targets.append((r.img.color.clone(), r.img.depth.clone()))
+    out = TrajectoryTracker(gd, cams, targets, G.RenderParams(tile=16), seed=5).run()
+    assert out["start_ate_rmse_m"] > 0.01
+    assert out["ate_rmse_m"] < 1e-3 and out["rot_rmse_rad"] < 5e-4, out
