@@ -70,14 +70,14 @@ ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # + dram__bytes_write.sum per launch of each stage's kernels (cold cache), and
 # the binding pipe of the rasterisers (profiles/k_render_{fwd,bwd}_640x480_200k.md).
 # None where the kernel changed after the capture.
-PROFILED_TRAFFIC = {("gs_project", 16): 11.30e6, ("gs_bin_sort", 16): 14.50e6, ("gs_render_fwd_loss", 16): 14.26e6,
-                    ("gs_render_bwd_raster_loss", 16): 27.30e6, ("gs_project_bwd", 16): 16.41e6,
-                    ("gs_adam_step", 16): 44.83e6}
+# Keyed by (stage, tile, ring) for the forward (its staging variant) and
+# (stage, tile, None) for the others.
+PROFILED_TRAFFIC = {("gs_project", 16, None): 11.30e6, ("gs_bin_sort", 16, None): 14.50e6,
+                    ("gs_render_bwd_raster_loss", 16, None): 27.30e6, ("gs_project_bwd", 16, None): 16.41e6,
+                    ("gs_adam_step", 16, None): 44.83e6}
 PROFILED_PIPE = {
-    ("gs_render_fwd_loss", 16): "instruction issue: 62.8 % of active cycles issue; pipes ALU 37.9 %, FMA 27.6 %, "
-                                "LSU 22.2 %, XU (ex2) 9.2 %; SMs active 82 % of the launch",
-    ("gs_render_bwd_raster_loss", 16): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, FMA 36.2 %, "
-                                       "LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the launch"}
+    ("gs_render_bwd_raster_loss", 16, None): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, "
+                                             "FMA 36.2 %, LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the launch"}
 
 
 def _peaks():
@@ -313,11 +313,13 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
     if not st:
         return out
     fwd_st, bwd_st = raster_stages(step)
-    few = "few" if step.total_tiles * (params.tile // 8) * (params.tile // 4) <= 256 * 152 else "many"
+    few = step.total_tiles * (params.tile // 8) * (params.tile // 4) <= 256 * 152
+    ring = params.splat_stages == 3 or (params.splat_stages == 0 and few)
     fl = str(step.fused_loss).lower()
-    kern = {fwd_st: f"k_render_fwd<{params.tile}, {fl}, ring={few == 'few'}>",
+    kern = {fwd_st: f"k_render_fwd<{params.tile}, {fl}, ring={ring}> ({3 if ring else 2} batches of 32 splats staged "
+                    f"per warp)",
             bwd_st: f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> (+ its 2D-gradient "
-                    f"zero-fill{' and block ordering' if few == 'few' and step.fused_loss else ''})"}
+                    f"zero-fill{' and block ordering' if few and step.fused_loss else ''})"}
     for stage, ops, flop in ((fwd_st, FWD_OPS_PER_PAIR, FWD_FLOP_PER_PAIR), (bwd_st, BWD_OPS_PER_PAIR,
                                                                             BWD_FLOP_PER_PAIR)):
         sec = st[stage] * 1e-3
@@ -328,8 +330,8 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
                       "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops (a multiply-add as one)",
                       "flop": {"achieved": ach_f, "peak": flop_peak, "unit": "TFLOP/s FP32", "frac": ach_f / flop_peak,
                                "work": f"{pairs} pairs x {flop} FLOPs (a multiply-add as two)"},
-                      "binding_pipe": PROFILED_PIPE.get((stage, params.tile)),
-                      "traffic": PROFILED_TRAFFIC.get((stage, params.tile)),
+                      "binding_pipe": PROFILED_PIPE.get((stage, params.tile, ring if stage == fwd_st else None)),
+                      "traffic": PROFILED_TRAFFIC.get((stage, params.tile, ring if stage == fwd_st else None)),
                       "ms": st[stage],
                       "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
     E = step.n * step.V
@@ -354,7 +356,7 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
             continue
         gbs = nbytes / (st[stage] * 1e-3) / 1e9
         out[stage] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                      "work": work, "ms": st[stage], "traffic": PROFILED_TRAFFIC.get((stage, params.tile)),
+                      "work": work, "ms": st[stage], "traffic": PROFILED_TRAFFIC.get((stage, params.tile, None)),
                       "peak_basis": f"hbm_gbs ({peak_kind})"}
     if "gs_bin_sort" in out:
         lsd = M * (12 + 24 * lsd_passes)
@@ -454,7 +456,8 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
             "roofline": roof,
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
             "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
-            "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
+            "tile": params.tile, "splat_stages": params.splat_stages,
+            "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
             "pixels_per_iter": step.total_pixels, "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
             "stages_ms": st, "graph": True, "persistent_raster": True}
@@ -1018,7 +1021,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480",
-                       "tile": params.tile, "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
+                       "tile": params.tile, "splat_stages": params.splat_stages,
+            "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
                        "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
                        "per_step_state": "map and Adam state restored before every timed step (identical work per step)",

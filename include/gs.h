@@ -82,7 +82,12 @@ typedef struct gs_render_params {
     float radius_sigma;       /* splat radius = ceil(radius_sigma sqrt(lambda_max)) (3) */
     float bg[3];              /* background colour (0, 0, 0) */
     int32_t sh_degree;        /* 0: direct RGB colour (Sec. 3.3); 3: degree-3 SH */
-    int32_t reserved;         /* must be 0 */
+    int32_t splat_stages;     /* batches of 32 splats a warp of the forward rasteriser
+                                 holds at once: 2 (the next batch in flight in
+                                 registers) or 3 (the next two in flight through a
+                                 shared-memory ring); 0: the library chooses (3 when a
+                                 launch has at most 256 pixel blocks per SM, else 2).
+                                 Results do not depend on it (0) */
 } gs_render_params;
 
 /* The Gaussian map G (Sec. 3.3 "Preliminary"), structure of arrays, device. */

@@ -60,6 +60,7 @@ RenderConsts make_consts(const gs_render_params* p) {
     c.radius_sigma = p->radius_sigma;
     c.bg[0] = p->bg[0]; c.bg[1] = p->bg[1]; c.bg[2] = p->bg[2];
     c.sh_degree = p->sh_degree;
+    c.splat_stages = p->splat_stages;
     return c;
 }
 
@@ -67,7 +68,7 @@ static bool params_ok(const gs_render_params* p) {
     if (p == nullptr) return false;
     if (p->tile != 8 && p->tile != 16 && p->tile != 32) return false;
     if (p->sh_degree != 0 && p->sh_degree != 3) return false;
-    if (p->reserved != 0) return false;
+    if (p->splat_stages != 0 && p->splat_stages != 2 && p->splat_stages != 3) return false;
     if (!(p->near_plane > 0.f) || !isfinite(p->near_plane)) return false;
     if (!(p->alpha_min >= 0.f) || !(p->alpha_max <= 1.f) || !(p->alpha_min <= p->alpha_max)) return false;
     if (!(p->T_cut >= 0.f) || !(p->T_cut < 1.f)) return false;

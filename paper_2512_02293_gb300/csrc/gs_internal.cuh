@@ -34,6 +34,7 @@ struct RenderConsts {
     float near_plane, alpha_min, alpha_max, T_cut, dilation, radius_sigma;
     float bg[3];
     int32_t sh_degree;
+    int32_t splat_stages;   // 0 (library's choice), 2 or 3: see gs_render_params
 };
 
 // Host helpers (api.cu).

@@ -805,7 +805,7 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 #define GS_FWD(TT)                                                                                     \
     case TT: {                                                                                         \
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        const bool few = n_items <= kFewItemsPerSm * sms;                                             \
+        const bool few = rc.splat_stages == 0 ? n_items <= kFewItemsPerSm * sms : rc.splat_stages == 3; \
         if (fl) {                                                                                      \
             const int grid = few ? persistent_grid(k_render_fwd<TT, true, true>, n_items)             \
                                  : persistent_grid(k_render_fwd<TT, true, false>, n_items);           \

@@ -47,7 +47,7 @@ class gs_render_params(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("near_plane", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_cut", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("radius_sigma", ctypes.c_float), ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("splat_stages", ctypes.c_int32)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -221,11 +221,12 @@ class RenderParams:
     radius_sigma: float = 3.0
     bg: tuple = (0.0, 0.0, 0.0)
     sh_degree: int = 0
+    splat_stages: int = 0      # 0: the library chooses; 2 or 3 batches of 32 splats per forward warp
 
     def struct(self) -> gs_render_params:
         return gs_render_params(int(self.tile), self.near_plane, self.alpha_min, self.alpha_max, self.T_cut,
                                 self.dilation, self.radius_sigma, (ctypes.c_float * 3)(*self.bg),
-                                int(self.sh_degree), 0)
+                                int(self.sh_degree), int(self.splat_stages))
 
 
 def camera_array(cams) -> ctypes.Array:

@@ -192,3 +192,13 @@ def test_mlp_wait_poll_limit_is_set_and_restored(lib):
         assert G.gs_mlp_set_wait_polls(-1) == G.MLP_WAIT_POLLS_DEFAULT
     finally:
         G.gs_mlp_set_wait_polls(-1)
+
+
+def test_splat_stages_parameter_is_checked(lib):
+    # 0 (the library's choice), 2 or 3 batches of 32 splats per forward warp; anything else is refused
+    cams = G.camera_array([synth.identity_camera()])
+    g0 = G.gs_gaussians(None, None, None, None, None, 0)
+    out = G.gs_projected()
+    for st, want in ((0, 0), (2, 0), (3, 0), (1, 1), (4, 1), (-1, 1)):
+        p = G.RenderParams(splat_stages=st).struct()
+        assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == want, st
