@@ -433,9 +433,12 @@ int32_t gs_mlp_pack(const gs_mlp_params* params, const gs_mlp_packed* packed, vo
  * dY = 2 loss_scale (Y - T) [n][8] and *loss += loss_scale sum (Y - T)^2 (the
  * caller zeroes *loss; loss_scale = 1 / (8 n) gives the mean squared error).
  * d_status: device int32 status word (GS_ERR_TIMEOUT if a bounded wait gave up).
- * One CTA per SM walks tiles of 128 samples (tcgen05 MMAs, accumulators in
- * tensor memory).  Errors: GS_ERR_INVALID_ARG on NULL / misaligned pointers,
- * n < 0, T without dY and loss. */
+ * One CTA per SM walks tiles of 128 samples, two in flight: X tiles copied by
+ * TMA into a two-stage ring, tcgen05 MMAs with accumulators and the hidden
+ * activations in tensor memory, issued by one control warp while 16 warps run
+ * the epilogues.  Errors: GS_ERR_INVALID_ARG on NULL / misaligned pointers,
+ * n < 0, T without dY and loss; GS_ERR_CUDA if the tensor maps of X cannot be
+ * made (the driver entry point is missing, or n > 2^31 - 129). */
 int32_t gs_mlp_fwd(const gs_mlp_packed* packed, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
                    uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int32_t* d_status,
                    void* stream);
@@ -444,6 +447,8 @@ int32_t gs_mlp_fwd(const gs_mlp_packed* packed, const uint16_t* X, int64_t n, fl
  * the inputs X, the forward's Z1, Z2 and dY (all [n][...] as above).
  * OVERWRITES `grads` (zeroed, then accumulated over the batch).  Rounding:
  * dZ2 = bf16((W3^T dY) * gelu'(Z2)), dZ1 = bf16((W2^T dZ2) * gelu'(Z1)).
+ * Every contraction runs on the tensor cores (dY enters as three BF16 parts
+ * whose sum is dY, so its products stay exact); X arrives by TMA.
  * Errors: as gs_mlp_fwd. */
 int32_t gs_mlp_bwd(const gs_mlp_packed* packed, const uint16_t* X, const uint16_t* Z1, const uint16_t* Z2,
                    const float* dY, int64_t n, const gs_mlp_grads* grads, int32_t* d_status, void* stream);

@@ -19,9 +19,13 @@
 //
 // One CTA of 512 threads per SM walks tiles of 128 samples; the four threads of
 // sample row r (tensor-memory lane r of every accumulator) split its columns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <atomic>
+#include <climits>
+#include <mutex>
 
 #include "gs_internal.cuh"
 #include "tc.cuh"
@@ -97,82 +101,6 @@ __device__ __forceinline__ void fill_kmajor(uint8_t* dst, const uint16_t* __rest
     }
 }
 
-// Chunk c (8 values, columns 8c .. 8c+7) of sample row `row` of the input X,
-// with the bias column set: columns >= 196 are 1 at 196 and 0 beyond, and rows
-// past n are zero.
-__device__ __forceinline__ uint4 x_chunk(const uint16_t* __restrict__ X, int64_t row, int64_t n, int c) {
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (row >= n) return v;
-    if (c < kIn / 8) return __ldg(reinterpret_cast<const uint4*>(X + row * kK1) + c);
-    if (c == kIn / 8) {   // columns 192..199: four inputs, the ones column, zeros
-        const uint2 lo = __ldg(reinterpret_cast<const uint2*>(X + row * kK1 + 8 * c));
-        v.x = lo.x; v.y = lo.y; v.z = 0x3F80u; v.w = 0u;   // bf16(1.0) at column 196
-    }
-    return v;
-}
-
-// ---------------------------------------------------------------- forward
-// Shared-memory plan of the forward kernel (bytes): the three weight operands
-// stay resident, X and H are the per-tile operands (H holds H1, then H2).
-constexpr uint32_t kFwdW1 = 0;                                  // 128 x 208
-constexpr uint32_t kFwdW2 = kFwdW1 + kHid * kK1 * 2;            // 128 x 144
-constexpr uint32_t kFwdW3 = kFwdW2 + kHid * kK2 * 2;            // 16 x 144
-constexpr uint32_t kFwdX = kFwdW3 + kN3 * kK2 * 2;              // 128 x 208
-constexpr uint32_t kFwdH = kFwdX + kTile * kK1 * 2;             // 128 x 144
-constexpr uint32_t kFwdBar = kFwdH + kTile * kK2 * 2;           // mbarrier (8 B) + tensor-memory base (4 B)
-constexpr uint32_t kFwdSmem = kFwdBar + 16;
-
-struct MlpFwdArgs {
-    gs_mlp_packed w;
-    const uint16_t* X;
-    int64_t n;
-    float* Y;            // [n][8] or null
-    uint16_t* Z1;        // [n][128] pre-activations (training) or null
-    uint16_t* Z2;
-    const float* T;      // [n][8] targets (training) or null
-    float* dY;           // [n][8] d loss / d Y, written when T is given
-    float* loss;         // += loss_scale * sum (Y - T)^2, when T is given
-    float loss_scale;
-    int* status;
-    uint32_t wait_polls; // mbarrier polls before a wait gives up
-};
-
-// Hidden-layer epilogue for this thread's sample row and columns [c_lo, c_hi):
-// accumulator -> Z = bf16, H = bf16(gelu(Z)) into the next layer's K-major
-// operand, Z to global memory.
-__device__ __forceinline__ void hidden_epilogue(uint32_t tacc, uint8_t* sH, int r, int64_t row, int64_t n,
-                                                uint16_t* __restrict__ Zout, int c_lo, int c_hi,
-                                                const uint16_t* __restrict__ gtab) {
-#pragma unroll 1
-    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tacc + (uint32_t)c0, v);
-        uint32_t zp[8], hp[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const uint16_t z0 = f2bf(v[2 * i]), z1 = f2bf(v[2 * i + 1]);
-            zp[i] = pack2(z0, z1);
-            hp[i] = pack2(__ldg(gtab + z0), __ldg(gtab + z1));
-        }
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, c0, kK2)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, c0 + 8, kK2)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
-        if (Zout != nullptr && row < n) {
-            uint4* zrow = reinterpret_cast<uint4*>(Zout + row * kHid + c0);
-            zrow[0] = make_uint4(zp[0], zp[1], zp[2], zp[3]);
-            zrow[1] = make_uint4(zp[4], zp[5], zp[6], zp[7]);
-        }
-    }
-}
-
-// Issue the K loop of one GEMM (one thread) and commit it to the barrier.
-__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t sa, uint32_t sb, int K, uint32_t idesc,
-                                           bool accumulate, uint32_t bar) {
-    tc::fence_after_sync();
-    for (int s = 0; s < K / 16; s++)
-        tc::mma_bf16(d_tmem, tc::kstep_desc(sa, K, s), tc::kstep_desc(sb, K, s), idesc, accumulate || s > 0);
-    tc::mma_commit(bar);
-}
-
 // Every thread waits (at most `polls` polls) for the barrier phase; the outcome
 // is made uniform.  If any thread gave up, the MMAs of that phase may still be
 // running: thread 0 then waits for them (bounded again) before the CTA goes on
@@ -192,145 +120,453 @@ __device__ __forceinline__ bool wait_all(uint32_t bar, uint32_t& phase, uint32_t
 
 // Sync point after this thread wrote shared-memory operands: visible to the
 // tensor core, prior tensor-memory reads ordered before the next MMA.
-// 16-byte asynchronous copy global -> shared (zero-filled when !valid; src must
-// then still be a readable address)
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 __device__ __forceinline__ void operands_ready() {
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_fwd(MlpFwdArgs a) {
+// ---------------------------------------------------------------- forward
+// The activation in shared memory: the packed tables' entries for the BF16
+// inputs with 2^-10 <= |z| < 2^4 (bit patterns 0x3A80 .. 0x417F of either sign,
+// 14 binades), where nearly every pre-activation falls.  Slot = magnitude
+// offset (11 bits, 0 .. 0x6FF) | sign << 11, so the index takes no branch; the
+// rare inputs outside are patched from the full tables in global memory.  A
+// random lookup in shared memory costs a few bank conflicts, one in a 128 KB
+// global table many L1 wavefronts.
+constexpr uint32_t kTabLo = 0x3A80u, kTabSpan = 0x0700u;
+constexpr int kTabEntries = 4096;
+
+__device__ __forceinline__ uint32_t tab_slot(uint32_t z, bool& miss) {
+    const uint32_t i = (z & 0x7FFFu) - kTabLo;       // wraps below the range
+    miss = i >= kTabSpan;
+    return (i & 0x7FFu) | ((z >> 4) & 0x800u);
+}
+// BF16 bit pattern of slot i, or 0xFFFFFFFF for the unused slots
+__device__ __forceinline__ uint32_t tab_bits(int i) {
+    return (uint32_t)(i & 0x7FF) < kTabSpan ? ((uint32_t)(i & 0x800) << 4) | (kTabLo + (uint32_t)(i & 0x7FF))
+                                            : 0xFFFFFFFFu;
+}
+// bf16(gelu) of both BF16 halves of w; `miss` if either lies outside the compact table
+__device__ __forceinline__ uint32_t gelu2(uint32_t w, const uint16_t* s_tab, bool& miss) {
+    bool m0, m1;
+    const uint32_t lo = s_tab[tab_slot(w & 0xFFFFu, m0)], hi = s_tab[tab_slot(w >> 16, m1)];
+    miss = m0 | m1;
+    return lo | (hi << 16);
+}
+__device__ __forceinline__ uint32_t gelu2_global(uint32_t w, const uint16_t* __restrict__ g_tab) {
+    return (uint32_t)__ldg(g_tab + (w & 0xFFFFu)) | ((uint32_t)__ldg(g_tab + (w >> 16)) << 16);
+}
+// BF16 pair (lower half = a) rounded to nearest
+__device__ __forceinline__ uint32_t bf16x2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+// Compact table from the full one (slots without an input get 0).
+template <typename T>
+__device__ __forceinline__ void fill_tab(T* s_tab, const T* __restrict__ g_tab) {
+    for (int i = threadIdx.x; i < kTabEntries; i += blockDim.x) {
+        const uint32_t z = tab_bits(i);
+        s_tab[i] = z != 0xFFFFFFFFu ? __ldg(g_tab + z) : T(0);
+    }
+}
+
+// One tile of X in shared memory, as TMA lands it: columns 0 .. 191 in three
+// boxes of 64 columns x 128 rows with the 128-byte swizzle (16 KB each, rows of
+// 128 bytes, the layout of tc::smem_desc_sw128), then columns 192 .. 207 as two
+// unswizzled chunks of 8 columns (element (r, k) at (k / 8 - 24) 2048 + r 16 +
+// (k % 8) 2).  Columns 196 .. 199 of the first chunk lie outside the tensor map
+// and arrive as zeros, as do rows past n; the second chunk stays zero.  A copy
+// of 128-byte rows costs one request per row where 8-column boxes cost 8.
+constexpr uint32_t kXChunk = kTile * 16;
+constexpr uint32_t kXBox = kTile * 128;                 // one 64-column box
+constexpr uint32_t kXTail = 3 * kXBox;                  // the two 8-column chunks
+constexpr uint32_t kXBytes = kXTail + 2 * kXChunk;
+constexpr uint32_t kXTx = 3 * kXBox + kXChunk;          // bytes per tile of X
+static_assert(kXBytes == (uint32_t)kTile * kK1 * 2, "X tile size");
+
+// descriptor of K step s (16 columns) of an X tile at sx (1024-byte aligned)
+__device__ __forceinline__ uint64_t x_desc(uint32_t sx, int s) {
+    return s < 12 ? tc::smem_desc_sw128(sx + (uint32_t)(s / 4) * kXBox + (uint32_t)(s % 4) * 32u)
+                  : tc::smem_desc(sx + kXTail, kXChunk, 128u);
+}
+
+// Shared-memory plan of the forward kernel (bytes): the three weight operands
+// stay resident; X is a two-stage ring of TMA destinations; then the activation
+// table, the layer-1 bias (added in the epilogue, since the tensor map zero-fills
+// the ones column) and the barriers.
+constexpr uint32_t kFwdX = 0;                                   // 2 x (128 x 208), 1024-byte aligned
+constexpr uint32_t kFwdW1 = kFwdX + 2 * kXBytes;                // 128 x 208
+constexpr uint32_t kFwdW2 = kFwdW1 + kHid * kK1 * 2;            // 128 x 144
+constexpr uint32_t kFwdW3 = kFwdW2 + kHid * kK2 * 2;            // 16 x 144
+constexpr uint32_t kFwdTab = kFwdW3 + kN3 * kK2 * 2;            // 4096 BF16
+constexpr uint32_t kFwdB1 = kFwdTab + kTabEntries * 2;          // 128 FP32
+constexpr uint32_t kFwdBar = kFwdB1 + kHid * 4;
+// barriers (8 bytes each): x_full[2], g1[2], g2[2], g3[2], h1[2], h2[2], drain; then
+// the tensor-memory base and the abort flag
+constexpr int kBarXFull = 0, kBarG1 = 2, kBarG2 = 4, kBarG3 = 6, kBarH1 = 8, kBarH2 = 10, kBarDrain = 12;
+constexpr uint32_t kFwdSmem = kFwdBar + 13 * 8 + 8;
+static_assert(kFwdX % 1024 == 0 && kXBytes % 1024 == 0, "swizzled TMA destinations are 1024-byte aligned");
+static_assert(kFwdSmem <= 227 * 1024, "shared memory of one CTA");
+
+// Tensor memory of the forward: two slots of 256 columns, one per tile in flight.
+// D: the 128 x 128 FP32 accumulator of layers 1 and 2; D3: layer 3 (N 16);
+// H: the next layer's A operand, 128 x 144 BF16 packed two per column (72
+// columns; columns 64 .. 71 hold the ones column and zeros, written once).
+constexpr uint32_t kSlotCols = 256, kColD = 0, kColD3 = 128, kColH = 160;
+
+// The epilogue warps are 0 .. 15, warp 16 issues the copies and the MMAs.
+constexpr int kEpiThreads = 512, kCtlWarp = kEpiThreads / 32, kFwdThreads2 = kEpiThreads + 32;
+
+struct MlpFwdArgs {
+    gs_mlp_packed w;
+    int64_t n;
+    float* Y;            // [n][8] or null
+    uint16_t* Z1;        // [n][128] pre-activations (training) or null
+    uint16_t* Z2;
+    const float* T;      // [n][8] targets (training) or null
+    float* dY;           // [n][8] d loss / d Y, written when T is given
+    float* loss;         // += loss_scale * sum (Y - T)^2, when T is given
+    float loss_scale;
+    int* status;
+    uint32_t wait_polls; // mbarrier polls before a wait gives up
+};
+
+// Poll the barrier phase at most `polls` times; give up early once another
+// thread of the CTA has raised the abort flag, and raise it on a timeout.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, uint32_t polls,
+                                              volatile int* abort_flag) {
+    for (uint32_t i = 0; i < polls; i++) {
+        if (tc::mbar_test(bar, parity)) return true;
+        if ((i & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+// The same for a whole warp, with a warp-uniform outcome (the tensor-memory
+// loads and stores that follow are warp-collective).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint32_t polls, volatile int* abort_flag) {
+    const bool ok = __all_sync(0xffffffffu, wait_or_abort(bar, parity, polls, abort_flag));
+    tc::fence_after_sync();
+    return ok;
+}
+
+// Hidden-layer epilogue of this thread's sample row, columns 32 cg .. 32 cg + 31,
+// in two halves of 16: accumulator (+ bias) -> Z = bf16 (to global memory when
+// Zrow is set) -> H = bf16(gelu(Z)) into tensor memory as the next layer's A
+// operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t tD, uint32_t tH, int cg, const float* bias,
+                                                uint16_t* Zrow, const uint16_t* s_tab,
+                                                const uint16_t* __restrict__ g_tab) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        const int c0 = 32 * cg + 16 * half;
+        float v[16];
+        tc::tmem_ld16(tD + (uint32_t)c0, v);
+        if (bias != nullptr) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+                const float4 b = *reinterpret_cast<const float4*>(bias + c0 + i);
+                v[i] += b.x; v[i + 1] += b.y; v[i + 2] += b.z; v[i + 3] += b.w;
+            }
+        }
+        uint32_t zp[8], hp[8], miss = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            zp[i] = bf16x2(v[2 * i], v[2 * i + 1]);
+            bool m;
+            hp[i] = gelu2(zp[i], s_tab, m);
+            miss |= (uint32_t)m << i;
+        }
+        if (miss != 0) {          // inputs outside the compact table (rare)
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                if (miss & (1u << i)) hp[i] = gelu2_global(zp[i], g_tab);
+        }
+        if (Zrow != nullptr) {
+            uint4* zr = reinterpret_cast<uint4*>(Zrow + c0);
+            zr[0] = make_uint4(zp[0], zp[1], zp[2], zp[3]);
+            zr[1] = make_uint4(zp[4], zp[5], zp[6], zp[7]);
+        }
+        tc::tmem_st8(tH + (uint32_t)(c0 / 2), hp);
+    }
+}
+
+// This warp is done with a stage: its tensor-memory accesses are ordered
+// before one arrival on the barrier (16 arrivals complete a phase).
+__device__ __forceinline__ void warp_arrive(uint32_t bar) {
+    tc::fence_before_sync();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(bar);
+}
+
+// Output layer of the tile's 128 samples (warps with cg == 0): Y, and in
+// training dY and the loss.
+__device__ __forceinline__ void output_epilogue(const MlpFwdArgs& a, uint32_t tD3, int64_t row, int lane) {
+    float y[16];
+    tc::tmem_ld16(tD3, y);
+    float part = 0.f;
+    if (row < a.n) {
+        if (a.Y != nullptr) {
+            float4* yr = reinterpret_cast<float4*>(a.Y + row * kOut);
+            yr[0] = make_float4(y[0], y[1], y[2], y[3]);
+            yr[1] = make_float4(y[4], y[5], y[6], y[7]);
+        }
+        if (a.T != nullptr) {
+            const float4* tr = reinterpret_cast<const float4*>(a.T + row * kOut);
+            const float4 t0 = tr[0], t1 = tr[1];
+            const float d[8] = {y[0] - t0.x, y[1] - t0.y, y[2] - t0.z, y[3] - t0.w,
+                                y[4] - t1.x, y[5] - t1.y, y[6] - t1.z, y[7] - t1.w};
+            float gr[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) { part += d[i] * d[i]; gr[i] = 2.f * a.loss_scale * d[i]; }
+            float4* dr = reinterpret_cast<float4*>(a.dY + row * kOut);
+            dr[0] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+            dr[1] = make_float4(gr[4], gr[5], gr[6], gr[7]);
+        }
+    }
+    if (a.T != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) atomicAdd(a.loss, a.loss_scale * part);
+    }
+}
+
+// The CTA walks its tiles t = blockIdx.x + k gridDim.x in pairs (slots 0 and 1),
+// so that the tensor core runs one tile's GEMM while the epilogue warps work on
+// the other's.  Per pair, the MMA order is
+//   G2(a) G2(b) G3(a) G1(a') G3(b) G1(b')       (G1 of the first pair up front)
+// and the epilogue order E1(a) E1(b) E2(a) E2(b) Out(a) Out(b); X(a') is copied
+// by TMA as soon as G1(a) has consumed X(a).  Each barrier completes once per
+// pair, so every wait uses the pair's parity.
+__global__ void __launch_bounds__(kFwdThreads2, 1) k_mlp_fwd(const __grid_constant__ CUtensorMap xmap_sw,
+                                                              const __grid_constant__ CUtensorMap xmap,
+                                                              MlpFwdArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, cg = warp >> 2;            // tensor-memory lane quarter, column group
-    const int r = quarter * 32 + lane;                       // this thread's sample row in the tile
-    uint8_t* sX = sm + kFwdX;
-    uint8_t* sH = sm + kFwdH;
-    const uint32_t bar = tc::smem_addr(sm + kFwdBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kFwdBar + 8);
+    uint16_t* s_tab = reinterpret_cast<uint16_t*>(sm + kFwdTab);
+    float* s_b1 = reinterpret_cast<float*>(sm + kFwdB1);
+    const uint32_t bars = tc::smem_addr(sm + kFwdBar);
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kFwdBar + 13 * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kFwdBar + 13 * 8 + 4);
 
     fill_kmajor(sm + kFwdW1, a.w.W1a, kHid, kK1);
     fill_kmajor(sm + kFwdW2, a.w.W2a, kHid, kK2);
     fill_kmajor(sm + kFwdW3, a.w.W3a, kN3, kK2);
-    if (cg == 0) {   // constant augmentation of H: column 128 = 1, columns 129..143 = 0
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, kHid, kK2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_offset(r, kHid + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < 2 * kTile; i += blockDim.x)      // chunk 25 (columns 200 .. 207) of both stages
+        *reinterpret_cast<uint4*>(sm + kFwdX + (i / kTile) * kXBytes + kXTail + kXChunk + (i % kTile) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    fill_tab(s_tab, a.w.gelu_tab);
+    for (int j = tid; j < kHid; j += blockDim.x) s_b1[j] = bf2f(a.w.W1a[j * kK1 + kIn]);
+    if (tid == 0) {
+        for (int i = 0; i < 13; i++)
+            tc::mbar_init(bar(i), (i == kBarH1 || i == kBarH1 + 1 || i == kBarH2 || i == kBarH2 + 1) ? 16u : 1u);
+        *abort_flag = 0;
     }
-    if (tid == 0) tc::mbar_init(bar, 1);
-    if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
+    if (warp == kCtlWarp) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
     operands_ready();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const uint32_t tD1 = tbase, tD2 = tbase + 128, tD3 = tbase + 256;
-    const uint32_t sa_x = tc::smem_addr(sX), sa_h = tc::smem_addr(sH);
-    const uint32_t sa_w1 = tc::smem_addr(sm + kFwdW1), sa_w2 = tc::smem_addr(sm + kFwdW2);
-    const uint32_t sa_w3 = tc::smem_addr(sm + kFwdW3);
-    const int c_lo = cg * (kHid / kColGroups), c_hi = c_lo + kHid / kColGroups;
-    uint32_t phase = 0;
-    bool ok = true;
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
-    // the four threads of a sample row take every fourth 8-value chunk of its X row;
-    // the next tile's chunks are loaded into registers while this tile computes
-    constexpr int kXc = (kK1 / 8 + kColGroups - 1) / kColGroups;
-    uint4 xn[kXc];
-    auto load_x = [&](int64_t tile) {
-#pragma unroll
-        for (int q = 0; q < kXc; q++) {
-            const int c = cg + q * kColGroups;
-            xn[q] = c < kK1 / 8 ? x_chunk(a.X, tile * kTile + r, a.n, c) : make_uint4(0u, 0u, 0u, 0u);
+    const int cnt = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // tiles of this CTA (>= 1)
+    const uint32_t polls = a.wait_polls;
+
+    if (warp < kCtlWarp) {
+        // ------------------------------------------------ epilogue warps
+        const int q = warp & 3, cg = warp >> 2;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int r = q * 32 + lane;
+        if (cg == 0) {   // H columns 64 .. 71 of both slots: the ones column (K index 128) and zeros
+            uint32_t ones[16] = {0x3F80u};
+            for (int s = 0; s < 2; s++) tc::tmem_st16(tbase + lane_off + s * kSlotCols + kColH + 64, ones);
         }
-    };
-    if ((int64_t)blockIdx.x < n_tiles) load_x(blockIdx.x);
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int64_t row0 = t * kTile, row = row0 + r;
-#pragma unroll
-        for (int q = 0; q < kXc; q++) {
-            const int c = cg + q * kColGroups;
-            if (c < kK1 / 8) *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(r, 8 * c, kK1)) = xn[q];
-        }
-        operands_ready();
-        if (tid == 0) issue_gemm(tD1, sa_x, sa_w1, kK1, tc::idesc_bf16(128, kHid), false, bar);
-        if (t + gridDim.x < n_tiles) load_x(t + gridDim.x);     // in flight during the epilogues
-        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
-        hidden_epilogue(tD1 + lane_off, sH, r, row, a.n, a.Z1, c_lo, c_hi, a.w.gelu_tab);
-        operands_ready();
-        if (tid == 0) issue_gemm(tD2, sa_h, sa_w2, kK2, tc::idesc_bf16(128, kHid), false, bar);
-        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
-        hidden_epilogue(tD2 + lane_off, sH, r, row, a.n, a.Z2, c_lo, c_hi, a.w.gelu_tab);
-        operands_ready();
-        if (tid == 0) issue_gemm(tD3, sa_h, sa_w3, kK2, tc::idesc_bf16(128, kN3), false, bar);
-        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
-        if (cg == 0) {                       // the 8 outputs: one column group (warp-uniform)
-            float y[16];
-            tc::tmem_ld16(tD3 + lane_off, y);
-            float part = 0.f;
-            if (row < a.n) {
-                if (a.Y != nullptr) {
-                    float4* yr = reinterpret_cast<float4*>(a.Y + row * kOut);
-                    yr[0] = make_float4(y[0], y[1], y[2], y[3]);
-                    yr[1] = make_float4(y[4], y[5], y[6], y[7]);
-                }
-                if (a.T != nullptr) {
-                    const float4* tr = reinterpret_cast<const float4*>(a.T + row * kOut);
-                    const float4 t0 = tr[0], t1 = tr[1];
-                    const float d[8] = {y[0] - t0.x, y[1] - t0.y, y[2] - t0.z, y[3] - t0.w,
-                                        y[4] - t1.x, y[5] - t1.y, y[6] - t1.z, y[7] - t1.w};
-                    float gr[8];
-#pragma unroll
-                    for (int i = 0; i < 8; i++) { part += d[i] * d[i]; gr[i] = 2.f * a.loss_scale * d[i]; }
-                    float4* dr = reinterpret_cast<float4*>(a.dY + row * kOut);
-                    dr[0] = make_float4(gr[0], gr[1], gr[2], gr[3]);
-                    dr[1] = make_float4(gr[4], gr[5], gr[6], gr[7]);
+        bool ok = true;
+        for (int k = 0; k < cnt && ok; k += 2) {
+            const uint32_t par = (uint32_t)(k >> 1) & 1u;
+            const int nslot = k + 1 < cnt ? 2 : 1;
+            for (int s = 0; s < nslot && ok; s++) {          // E1
+                if (!(ok = warp_wait(bar(kBarG1 + s), par, polls, abort_flag))) break;
+                const int64_t row = (blockIdx.x + (int64_t)(k + s) * gridDim.x) * kTile + r;
+                const uint32_t ts = tbase + lane_off + s * kSlotCols;
+                hidden_epilogue(ts + kColD, ts + kColH, cg, s_b1,
+                                a.Z1 != nullptr && row < a.n ? a.Z1 + row * kHid : nullptr, s_tab, a.w.gelu_tab);
+                warp_arrive(bar(kBarH1 + s));
+            }
+            for (int s = 0; s < nslot && ok; s++) {          // E2
+                if (!(ok = warp_wait(bar(kBarG2 + s), par, polls, abort_flag))) break;
+                const int64_t row = (blockIdx.x + (int64_t)(k + s) * gridDim.x) * kTile + r;
+                const uint32_t ts = tbase + lane_off + s * kSlotCols;
+                hidden_epilogue(ts + kColD, ts + kColH, cg, nullptr,
+                                a.Z2 != nullptr && row < a.n ? a.Z2 + row * kHid : nullptr, s_tab, a.w.gelu_tab);
+                warp_arrive(bar(kBarH2 + s));
+            }
+            if (cg == 0) {
+                for (int s = 0; s < nslot && ok; s++) {      // outputs
+                    if (!(ok = warp_wait(bar(kBarG3 + s), par, polls, abort_flag))) break;
+                    const int64_t row = (blockIdx.x + (int64_t)(k + s) * gridDim.x) * kTile + r;
+                    output_epilogue(a, tbase + lane_off + s * kSlotCols + kColD3, row, lane);
                 }
             }
-            if (a.T != nullptr) {
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------ copies and MMAs (one thread)
+        const uint32_t sw1 = tc::smem_addr(sm + kFwdW1), sw2 = tc::smem_addr(sm + kFwdW2);
+        const uint32_t sw3 = tc::smem_addr(sm + kFwdW3);
+        uint32_t xpar = 0u, pending = 0u;      // bit s: parity of slot s's next copy; a copy in flight
+        auto load_x = [&](int k) {
+            if (k >= cnt) return;
+            const int s = k & 1;
+            const int y = (int)((blockIdx.x + (int64_t)k * gridDim.x) * kTile);
+            const uint32_t sxs = tc::smem_addr(sm + kFwdX) + (uint32_t)s * kXBytes;
+            tc::mbar_arrive_expect_tx(bar(kBarXFull + s), kXTx);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                if (lane == 0) atomicAdd(a.loss, a.loss_scale * part);
+            for (int c = 0; c < 3; c++) tc::tma_load_2d(sxs + (uint32_t)c * kXBox, &xmap_sw, 64 * c, y, bar(kBarXFull + s));
+            tc::tma_load_2d(sxs + kXTail, &xmap, 192, y, bar(kBarXFull + s));
+            pending |= 1u << s;
+        };
+        auto wait_x = [&](int s) {
+            if (!wait_or_abort(bar(kBarXFull + s), (xpar >> s) & 1u, polls, abort_flag)) return false;
+            xpar ^= 1u << s;
+            pending &= ~(1u << s);
+            return true;
+        };
+        // descriptors of K step 0; step st adds st times the step's byte offset >> 4
+        // to the start-address field (no carry: shared addresses stay below 2^18)
+        const uint32_t sx0 = tc::smem_addr(sm + kFwdX), sx1 = sx0 + kXBytes;
+        const uint64_t dx0 = x_desc(sx0, 0), dx1 = x_desc(sx1, 0), dt0 = x_desc(sx0, 12), dt1 = x_desc(sx1, 12);
+        const uint64_t dw1 = tc::kstep_desc(sw1, kK1, 0), dw2 = tc::kstep_desc(sw2, kK2, 0);
+        const uint64_t dw3 = tc::kstep_desc(sw3, kK2, 0);
+        auto gemm1 = [&](int s) {
+            const uint32_t d = tbase + s * kSlotCols + kColD;
+            const uint64_t dx = s ? dx1 : dx0, dt = s ? dt1 : dt0;
+#pragma unroll
+            for (int st = 0; st < kK1 / 16; st++)
+                tc::mma_bf16(d, st < 12 ? dx + (uint64_t)(((st / 4) * kXBox + (st % 4) * 32) >> 4) : dt,
+                             dw1 + (uint64_t)(st * 16), tc::idesc_bf16(128, kHid), st > 0);
+            tc::mma_commit(bar(kBarG1 + s));
+        };
+        auto gemm_h = [&](int s, uint32_t col, uint64_t dw, uint32_t idesc, int g) {
+            const uint32_t h = tbase + s * kSlotCols + kColH;
+#pragma unroll
+            for (int st = 0; st < kK2 / 16; st++)
+                tc::mma_bf16_ts(tbase + s * kSlotCols + col, h + 8u * (uint32_t)st, dw + (uint64_t)(st * 16), idesc,
+                                st > 0);
+            tc::mma_commit(bar(g + s));
+        };
+        bool ok = true;
+        load_x(0);
+        load_x(1);
+        if ((ok = wait_x(0))) gemm1(0);
+        if (ok && cnt > 1 && (ok = wait_x(1))) gemm1(1);
+        for (int k = 0; k < cnt && ok; k += 2) {
+            const uint32_t par = (uint32_t)(k >> 1) & 1u;
+            const bool has_b = k + 1 < cnt;
+            if (!(ok = wait_or_abort(bar(kBarG1), par, polls, abort_flag))) break;
+            load_x(k + 2);                                           // X(a) consumed
+            if (!(ok = wait_or_abort(bar(kBarH1), par, polls, abort_flag))) break;
+            tc::fence_after_sync();
+            gemm_h(0, kColD, dw2, tc::idesc_bf16(128, kHid), kBarG2);
+            if (has_b) {
+                if (!(ok = wait_or_abort(bar(kBarG1 + 1), par, polls, abort_flag))) break;
+                load_x(k + 3);
+                if (!(ok = wait_or_abort(bar(kBarH1 + 1), par, polls, abort_flag))) break;
+                tc::fence_after_sync();
+                gemm_h(1, kColD, dw2, tc::idesc_bf16(128, kHid), kBarG2);
+            }
+            if (!(ok = wait_or_abort(bar(kBarH2), par, polls, abort_flag))) break;
+            tc::fence_after_sync();
+            gemm_h(0, kColD3, dw3, tc::idesc_bf16(128, kN3), kBarG3);
+            if (k + 2 < cnt) {                                       // D(a) read by E2(a): next tile's layer 1
+                if (!(ok = wait_x(0))) break;
+                gemm1(0);
+            }
+            if (has_b) {
+                if (!(ok = wait_or_abort(bar(kBarH2 + 1), par, polls, abort_flag))) break;
+                tc::fence_after_sync();
+                gemm_h(1, kColD3, dw3, tc::idesc_bf16(128, kN3), kBarG3);
+                if (k + 3 < cnt) {
+                    if (!(ok = wait_x(1))) break;
+                    gemm1(1);
+                }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();      // tensor memory and shared operands are reused by the next tile
+        // drain: every MMA issued and every copy in flight completes before the
+        // CTA frees its tensor memory and exits (bounded again)
+        tc::mma_commit(bar(kBarDrain));
+        tc::mbar_wait(bar(kBarDrain), 0, kDrainPolls);
+        for (int s = 0; s < 2; s++)
+            if (pending & (1u << s)) tc::mbar_wait(bar(kBarXFull + s), (xpar >> s) & 1u, kDrainPolls);
     }
-    if (!ok && tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kCtlWarp) {
         tc::fence_after_sync();
+        if (lane == 0 && *abort_flag) set_status(a.status, GS_ERR_TIMEOUT);
         tc::tmem_dealloc(tbase, kTmemCols);
     }
 }
 
 // ---------------------------------------------------------------- backward
-// Shared-memory plan (bytes).  "x^T" operands are contracted over the tile's 128
-// samples (K = sample) by the weight-gradient GEMMs; they are stored MN-major
-// (tc.cuh), so the thread that owns a sample writes 8 consecutive rows of one as
-// one 16-byte store.
-constexpr uint32_t kBwdW2t = 0;                                 // W2^T [128 i][128 j]         B of dH1
-constexpr uint32_t kBwdW3f = kBwdW2t + kHid * kHid * 2;         // W3 as float [8][128]
-constexpr uint32_t kBwdA2 = kBwdW3f + kOut * kHid * 4;          // dZ2 [128 b][128 j]           A of dH1
-                                                                //   later dZ1^T [128 i][128 b] A of dW1
-constexpr uint32_t kBwdA2t = kBwdA2 + kTile * kHid * 2;         // dZ2^T [128 j][128 b]         A of dW2
-                                                                //   first H2 [128 b][128 j] row-major
-constexpr uint32_t kBwdB2 = kBwdA2t + kHid * kTile * 2;         // H1_aug^T [144 i][128 b]      B of dW2
-constexpr uint32_t kBwdB1 = kBwdB2 + kK2 * kTile * 2;           // X_aug^T [208 k][128 b]       B of dW1
-constexpr uint32_t kBwdDY = kBwdB1 + kK1 * kTile * 2;           // dY [128 b][8] float
-constexpr uint32_t kBwdBar = kBwdDY + kTile * kOut * 4;
-constexpr uint32_t kBwdSmem = kBwdBar + 16;
-// tensor-memory columns of the three accumulators
-constexpr uint32_t kTdH1 = 0, kTdW2 = 128, kTdW1 = 288;
+// Every contraction runs on the tensor cores.  Per tile of 128 samples b:
+//   (1) dH2 = dY W3           A = dY split [b][32], B = W3 split [j][32]   (K 32)
+//   (2) Z2 pass: H2 = bf16(gelu(Z2)), dZ2 = bf16(dH2 * gelu'(Z2))
+//   (3) dH1 = dZ2 W2          A = dZ2 [b][j], B = W2^T [i][j]             (K 128)
+//       dW3_split += H2^T dY  A = H2^T [j][b], B = dY split^T [n][b]      (K 128 = b)
+//   (4) Z1 pass: H1 = bf16(gelu(Z1)) -> H1_aug^T; then dZ1 = bf16(dH1 * gelu'(Z1))
+//   (5) dW2_aug += dZ2^T H1_aug   A = dZ2 (read transposed), B = H1_aug^T [i][b]
+//       dW1_aug += dZ1^T X_aug    A = dZ1^T [i][b], B = X_aug^T [k][b]   (TMA)
+// dY is FP32; it enters the tensor core as three BF16 parts h + m + l (h =
+// bf16(dY), m = bf16(dY - h), l = bf16(dY - h - m)), which hold its 24-bit
+// significand, so with BF16 W3 / H2 every product is exact and only the FP32
+// accumulation rounds, as on the CUDA cores.  dW3 is the sum of its three part
+// columns; db3 is summed on the CUDA cores.
+//
+// The per-tile operands share one layout: element (sample b, column c) at
+// (c / 8) 2048 + b 16 + (c % 8) 2 (chunks of 8 columns x 128 samples, as TMA
+// lands X).  Read with leading byte offset 2048 / stride byte offset 128 it is
+// the K-major operand [b][c]; with 128 / 2048 the MN-major operand [c][b].  So
+// one copy of dZ2 serves as A of dH1 (K-major) and, transposed, as A of dW2.
+//
+// The activation: one 8-byte entry {gelu'(z) FP32, bf16(gelu(z))} per BF16
+// input with 2^-9 <= |z| < 2^4 (13 binades, slot = offset + sign * span),
+// others from the full tables in global memory.
+constexpr uint32_t kBTabLo = 0x3B00u, kBTabSpan = 0x0680u;
+constexpr int kBTabEntries = 2 * kBTabSpan;
+
+__device__ __forceinline__ uint32_t btab_slot(uint32_t z, bool& miss) {
+    const uint32_t i = (z & 0x7FFFu) - kBTabLo;
+    miss = i >= kBTabSpan;
+    return min(i, kBTabSpan - 1u) + (z >> 15) * kBTabSpan;
+}
+
+// Shared-memory plan (bytes)
+constexpr uint32_t kBwdW2t = 0;                                   // W2^T [128 i][128 j], K-major
+constexpr uint32_t kBwdW3s = kBwdW2t + kHid * kHid * 2;           // W3 split [128 j][32], K-major
+constexpr uint32_t kBwdDYs = kBwdW3s + kHid * 32 * 2;             // dY split, chunk layout (4 chunks)
+constexpr uint32_t kBwdP1 = kBwdDYs + 4 * kXChunk;                // H2^T, then dZ1^T (16 chunks)
+constexpr uint32_t kBwdDZ2 = kBwdP1 + 16 * kXChunk;               // dZ2 (16 chunks)
+constexpr uint32_t kBwdH1 = kBwdDZ2 + 16 * kXChunk;               // H1_aug^T (18 chunks)
+constexpr uint32_t kBwdX = kBwdH1 + 18 * kXChunk;                 // X_aug^T (26 chunks, TMA)
+constexpr uint32_t kBwdTab = kBwdX + 26 * kXChunk;                // 3328 x 8 bytes
+constexpr uint32_t kBwdBar = kBwdTab + kBTabEntries * 8;          // MMA, X and drain barriers, tmem base
+constexpr uint32_t kBwdB3 = kBwdBar + 32;                         // db3 of this CTA (8 FP32)
+constexpr uint32_t kBwdSmem = kBwdB3 + 32;
+static_assert(kBwdX % 128 == 0, "TMA destination is 128-byte aligned");
+// X_aug^T: chunks 0 .. 24 copied per tile (8 columns each, unswizzled), chunk 25 stays zero
+constexpr int kBwdXLoads = kIn / 8 + 1;
+constexpr uint32_t kBwdXTx = kBwdXLoads * kXChunk;
+static_assert(kBwdSmem <= 227 * 1024, "shared memory of one CTA");
+// tensor-memory columns: dH (dH2, then dH1), the dW3 parts, dW1_aug, dW2_aug
+constexpr uint32_t kTdH = 0, kTdW3 = 128, kTdW1 = 160, kTdW2 = 368;
+static_assert(kTdW2 + kK2 <= kTmemCols, "tensor-memory columns");
+
+__device__ __forceinline__ uint64_t chunk_kmajor(uint32_t base, int s) { return tc::smem_desc(base + 4096u * s, 2048u, 128u); }
+__device__ __forceinline__ uint64_t chunk_mnmajor(uint32_t base, int s) { return tc::smem_desc(base + 256u * s, 128u, 2048u); }
 
 struct MlpBwdArgs {
     gs_mlp_packed w;
-    const uint16_t *X, *Z1, *Z2;
+    const uint16_t *Z1, *Z2;
     const float* dY;
     int64_t n;
     gs_mlp_grads g;      // zeroed before the launch; accumulated with atomics
@@ -338,183 +574,242 @@ struct MlpBwdArgs {
     uint32_t wait_polls; // mbarrier polls before a wait gives up
 };
 
-__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
+__global__ void __launch_bounds__(kEpiThreads, 1) k_mlp_bwd(const __grid_constant__ CUtensorMap xmap, MlpBwdArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, cg = warp >> 2;            // tensor-memory lane quarter, column group
     const int r = quarter * 32 + lane;                       // this thread's sample (or weight) row
-    float* sW3f = reinterpret_cast<float*>(sm + kBwdW3f);
-    uint8_t* sA2 = sm + kBwdA2;
-    uint8_t* sA2t = sm + kBwdA2t;
-    uint8_t* sB2 = sm + kBwdB2;
-    uint8_t* sB1 = sm + kBwdB1;
-    float* sDY = reinterpret_cast<float*>(sm + kBwdDY);
-    const uint32_t bar = tc::smem_addr(sm + kBwdBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBwdBar + 8);
+    const uint2* s_tab = reinterpret_cast<const uint2*>(sm + kBwdTab);
+    const uint32_t bar = tc::smem_addr(sm + kBwdBar), xbar = bar + 8, dbar = bar + 16;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBwdBar + 24);
+    float* s_b3 = reinterpret_cast<float*>(sm + kBwdB3);
 
     fill_kmajor(sm + kBwdW2t, a.w.W2t, kHid, kHid);
-    for (int i = tid; i < kOut * kHid; i += kFwdThreads)
-        sW3f[i] = bf2f(a.w.W3a[(i / kHid) * kK2 + (i % kHid)]);
-    // constant rows of H1_aug^T: row 128 = 1 (the ones column of H1), rows 129..143 = 0
-    for (int k = tid; k < 2 * kTile; k += kFwdThreads) {
-        const int b = k % kTile, q = k / kTile;
-        *reinterpret_cast<uint4*>(sB2 + tc::mnmajor_offset(kHid + 8 * q, b, kTile)) =
-            make_uint4(q == 0 ? 0x3F80u : 0u, 0u, 0u, 0u);
+    for (int i = tid; i < kHid * 4; i += kEpiThreads) {       // W3 split: columns 8p + o = W3[o][j], p < 3
+        const int j = i % kHid, c = i / kHid;
+        uint32_t v[4] = {0u, 0u, 0u, 0u};
+        if (c < 3)
+            for (int o = 0; o < kOut; o += 2)
+                v[o / 2] = pack2(a.w.W3a[o * kK2 + j], a.w.W3a[(o + 1) * kK2 + j]);
+        *reinterpret_cast<uint4*>(sm + kBwdW3s + tc::kmajor_offset(j, 8 * c, 32)) = make_uint4(v[0], v[1], v[2], v[3]);
     }
-    for (int b = tid; b < kTile; b += kFwdThreads)       // X_aug^T rows 200..207: zeros
-        *reinterpret_cast<uint4*>(sB1 + tc::mnmajor_offset(kK1 - 8, b, kTile)) = make_uint4(0u, 0u, 0u, 0u);
-    if (tid == 0) tc::mbar_init(bar, 1);
+    for (int i = tid; i < kBTabEntries; i += kEpiThreads) {
+        const uint32_t z = (i < (int)kBTabSpan ? 0u : 0x8000u) | (kBTabLo + (uint32_t)i % kBTabSpan);
+        reinterpret_cast<uint2*>(sm + kBwdTab)[i] =
+            make_uint2(__float_as_uint(__ldg(a.w.dgelu_tab + z)), (uint32_t)__ldg(a.w.gelu_tab + z));
+    }
+    if (tid < kTile) {
+        // H1_aug^T rows 128 .. 143: the ones row and zeros; X_aug^T rows 200 .. 207: zeros
+        *reinterpret_cast<uint4*>(sm + kBwdH1 + 16 * kXChunk + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + kBwdH1 + 17 * kXChunk + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + kBwdX + 25 * kXChunk + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid < kOut) s_b3[tid] = 0.f;
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init(xbar, 1);
+        tc::mbar_init(dbar, 1);
+    }
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), kTmemCols);
     operands_ready();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const uint32_t sa_a2 = tc::smem_addr(sA2), sa_a2t = tc::smem_addr(sA2t), sa_b2 = tc::smem_addr(sB2);
-    const uint32_t sa_b1 = tc::smem_addr(sB1), sa_w2t = tc::smem_addr(sm + kBwdW2t);
-    const int jw = tid & (kHid - 1), part = tid >> 7;        // dW3: hidden unit, quarter of the samples
-    float acc3[kOut];
-#pragma unroll
-    for (int o = 0; o < kOut; o++) acc3[o] = 0.f;
-    float accb3 = 0.f;
-    uint32_t phase = 0;
-    bool ok = true, first = true;
+    const uint32_t s_w2t = tc::smem_addr(sm + kBwdW2t), s_w3s = tc::smem_addr(sm + kBwdW3s);
+    const uint32_t s_dys = tc::smem_addr(sm + kBwdDYs), s_p1 = tc::smem_addr(sm + kBwdP1);
+    const uint32_t s_dz2 = tc::smem_addr(sm + kBwdDZ2), s_h1 = tc::smem_addr(sm + kBwdH1);
+    const uint32_t s_x = tc::smem_addr(sm + kBwdX);
     const int64_t n_tiles = (a.n + kTile - 1) / kTile;
-    // this thread's hidden columns: chunks 4 cg .. 4 cg + 3 (32 values) of Z2 and Z1,
-    // and its sample's dY, loaded for tile t + gridDim.x while tile t's last GEMM
-    // runs, and used by steps (1), (3) and (5) of the next tile
+
+    auto load_x = [&](int64_t tile) {     // thread 0
+        tc::mbar_arrive_expect_tx(xbar, kBwdXTx);
+        for (int c = 0; c < kBwdXLoads; c++)
+            tc::tma_load_2d(s_x + (uint32_t)c * kXChunk, &xmap, 8 * c, (int)(tile * kTile), xbar);
+    };
+    // this thread's sample row of Z1 and Z2 (columns 32 cg .. 32 cg + 31) and dY
+    // (column group 0), for a tile; each is loaded for the next tile as soon as
+    // this tile has used it, so the loads have most of a tile to arrive
     constexpr int kZc = kHid / 8 / kColGroups;
     uint4 z2c[kZc], z1c[kZc];
-    float4 dy0, dy1;
-    auto load_rows = [&](int64_t tile) {
+    float4 dy0 = make_float4(0.f, 0.f, 0.f, 0.f), dy1 = dy0;
+    auto load_z2dy = [&](int64_t tile) {
         const int64_t rw = tile * kTile + r;
         const bool v = tile < n_tiles && rw < a.n;
 #pragma unroll
-        for (int q = 0; q < kZc; q++) {
-            const int c = kZc * cg + q;
-            z2c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z2 + rw * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
-            z1c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z1 + rw * kHid) + c) : make_uint4(0u, 0u, 0u, 0u);
-        }
-        dy0 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        dy1 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-    };
-    load_rows(blockIdx.x);
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int64_t row = t * kTile + r;
-        const bool valid = row < a.n;
-        // (1) X_aug^T, dY and H2 (row-major, for the CUDA-core dW3) of this sample
-#pragma unroll 1
-        for (int c = cg; c < kIn / 8 + 1; c += kColGroups) {
-            // the inputs are needed only by the dW1 GEMM at the end of the tile: copied
-            // asynchronously, waited for just before it; the partial chunk 24 (4 inputs,
-            // the ones column) by a plain store; chunk 25 holds zeros from the start
-            uint8_t* dst = sB1 + tc::mnmajor_offset(8 * c, r, kTile);
-            if (c < kIn / 8) cp_async16(tc::smem_addr(dst), a.X + (valid ? row : 0) * kK1 + 8 * c, valid);
-            else *reinterpret_cast<uint4*>(dst) = x_chunk(a.X, row, a.n, c);
-        }
-        const float dy[kOut] = {dy0.x, dy0.y, dy0.z, dy0.w, dy1.x, dy1.y, dy1.z, dy1.w};
+        for (int q = 0; q < kZc; q++)
+            z2c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z2 + rw * kHid) + kZc * cg + q)
+                       : make_uint4(0u, 0u, 0u, 0u);
         if (cg == 0) {
-            reinterpret_cast<float4*>(sDY + r * kOut)[0] = dy0;
-            reinterpret_cast<float4*>(sDY + r * kOut)[1] = dy1;
+            dy0 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            dy1 = v ? __ldg(reinterpret_cast<const float4*>(a.dY + rw * kOut) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        uint16_t* sH2 = reinterpret_cast<uint16_t*>(sA2t);   // [b][j], aliases dZ2^T until step (3)
+    };
+    auto load_z1 = [&](int64_t tile) {
+        const int64_t rw = tile * kTile + r;
+        const bool v = tile < n_tiles && rw < a.n;
 #pragma unroll
-        for (int q = 0; q < kZc; q++) {
-            const int c = kZc * cg + q;
-            const uint32_t w[4] = {z2c[q].x, z2c[q].y, z2c[q].z, z2c[q].w};
-            uint32_t h[4];
+        for (int q = 0; q < kZc; q++)
+            z1c[q] = v ? __ldg(reinterpret_cast<const uint4*>(a.Z1 + rw * kHid) + kZc * cg + q)
+                       : make_uint4(0u, 0u, 0u, 0u);
+    };
+
+    uint32_t phase = 0, xphase = 0;
+    bool ok = true, first = true, x_inflight = false;
+    if (tid == 0 && (int64_t)blockIdx.x < n_tiles) { load_x(blockIdx.x); x_inflight = true; }
+    load_z2dy(blockIdx.x);
+    load_z1(blockIdx.x);
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        // (1) the dY split of this sample -> chunks 0 .. 3; dH2 = dY W3
+        if (cg == 0) {
+            const float dy[kOut] = {dy0.x, dy0.y, dy0.z, dy0.w, dy1.x, dy1.y, dy1.z, dy1.w};
+            uint32_t hp[4], mp[4], lp[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                h[i] = pack2(__ldg(a.w.gelu_tab + (w[i] & 0xFFFFu)), __ldg(a.w.gelu_tab + (w[i] >> 16)));
-            *reinterpret_cast<uint4*>(sH2 + r * kHid + 8 * c) = make_uint4(h[0], h[1], h[2], h[3]);
-        }
-        __syncthreads();
-        // (2) dW3[o][j] += sum_b dY[b][o] H2[b][j] (thread j, a quarter of the samples); db3
-#pragma unroll 4
-        for (int b = part * 32; b < part * 32 + 32; b++) {
-            const float h = bf2f(sH2[b * kHid + jw]);
-            const float4 d0 = reinterpret_cast<const float4*>(sDY + b * kOut)[0];
-            const float4 d1 = reinterpret_cast<const float4*>(sDY + b * kOut)[1];
-            acc3[0] += d0.x * h; acc3[1] += d0.y * h; acc3[2] += d0.z * h; acc3[3] += d0.w * h;
-            acc3[4] += d1.x * h; acc3[5] += d1.y * h; acc3[6] += d1.z * h; acc3[7] += d1.w * h;
-        }
-        if (tid < kOut)
-            for (int b = 0; b < kTile; b++) accb3 += sDY[b * kOut + tid];
-        __syncthreads();
-        // (3) dZ2 = bf16((dY W3) * gelu'(Z2)) as dZ2 rows and dZ2^T; H1 = bf16(gelu(Z1)) as H1_aug^T
-#pragma unroll
-        for (int q = 0; q < kZc; q++) {
-            const int c = kZc * cg + q;
-            const uint32_t w[4] = {z2c[q].x, z2c[q].y, z2c[q].z, z2c[q].w};
-            uint16_t g[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int j = 8 * c + i;
-                float dh = 0.f;
-#pragma unroll
-                for (int o = 0; o < kOut; o++) dh += dy[o] * sW3f[o * kHid + j];
-                const uint32_t zb = (i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu);
-                g[i] = f2bf(dh * __ldg(a.w.dgelu_tab + zb));
+            for (int o = 0; o < kOut; o += 2) {
+                const uint32_t h = bf16x2(dy[o], dy[o + 1]);
+                const float r0 = dy[o] - bf2f(h & 0xFFFFu), r1 = dy[o + 1] - bf2f(h >> 16);
+                const uint32_t m = bf16x2(r0, r1);
+                const uint32_t l = bf16x2(r0 - bf2f(m & 0xFFFFu), r1 - bf2f(m >> 16));
+                hp[o / 2] = h; mp[o / 2] = m; lp[o / 2] = l;
             }
-            const uint4 gp = make_uint4(pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
-            *reinterpret_cast<uint4*>(sA2t + tc::mnmajor_offset(8 * c, r, kTile)) = gp;
-            *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(r, 8 * c, kHid)) = gp;
-            const uint32_t w1[4] = {z1c[q].x, z1c[q].y, z1c[q].z, z1c[q].w};
-            uint32_t hp[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                hp[i] = pack2(__ldg(a.w.gelu_tab + (w1[i] & 0xFFFFu)), __ldg(a.w.gelu_tab + (w1[i] >> 16)));
-            *reinterpret_cast<uint4*>(sB2 + tc::mnmajor_offset(8 * c, r, kTile)) =
-                make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            for (int o = 0; o < kOut; o++) {      // db3: this warp's 32 samples
+                float sum = dy[o];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+                if (lane == 0) atomicAdd(s_b3 + o, sum);
+            }
+            uint8_t* d = sm + kBwdDYs + r * 16;
+            *reinterpret_cast<uint4*>(d) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            *reinterpret_cast<uint4*>(d + kXChunk) = make_uint4(mp[0], mp[1], mp[2], mp[3]);
+            *reinterpret_cast<uint4*>(d + 2 * kXChunk) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+            *reinterpret_cast<uint4*>(d + 3 * kXChunk) = make_uint4(0u, 0u, 0u, 0u);
         }
         operands_ready();
-        // (4) dH1 = dZ2 W2 and dW2_aug += dZ2^T H1_aug
         if (tid == 0) {
             tc::fence_after_sync();
-            for (int st = 0; st < kHid / 16; st++)
-                tc::mma_bf16(tbase + kTdH1, tc::kstep_desc(sa_a2, kHid, st), tc::kstep_desc(sa_w2t, kHid, st),
-                             tc::idesc_bf16(128, kHid), st > 0);
-            for (int st = 0; st < kTile / 16; st++)
-                tc::mma_bf16(tbase + kTdW2, tc::kstep_desc(sa_a2t, kTile, st), tc::kstep_desc(sa_b2, kTile, st),
-                             tc::idesc_bf16_mn(128, kK2, true, true), !first || st > 0);
+            for (int s = 0; s < 2; s++)
+                tc::mma_bf16(tbase + kTdH, chunk_kmajor(s_dys, s), tc::kstep_desc(s_w3s, 32, s),
+                             tc::idesc_bf16(128, kHid), s > 0);
             tc::mma_commit(bar);
         }
         if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
-        // (5) dZ1 = bf16(dH1 * gelu'(Z1)) as dZ1^T (over the dZ2 buffer, whose GEMM is done)
-        uint8_t* sA1t = sA2;
+        // (2) Z2 pass -> H2^T (P1) and dZ2, in two halves of 16 columns
 #pragma unroll
-        for (int h2 = 0; h2 < kZc / 2; h2++) {
-            const int c0 = 8 * kZc * cg + 16 * h2;
-            float v[16];
-            tc::tmem_ld16(tbase + kTdH1 + lane_off + (uint32_t)c0, v);
-            const uint32_t w[8] = {z1c[2 * h2].x, z1c[2 * h2].y, z1c[2 * h2].z, z1c[2 * h2].w,
-                                   z1c[2 * h2 + 1].x, z1c[2 * h2 + 1].y, z1c[2 * h2 + 1].z, z1c[2 * h2 + 1].w};
-            uint32_t gp[8];
+        for (int half = 0; half < 2; half++) {
+            float dh[16];
+            tc::tmem_ld16(tbase + kTdH + lane_off + 32u * cg + 16u * half, dh);
 #pragma unroll
-            for (int i = 0; i < 8; i++)
-                gp[i] = pack2(f2bf(v[2 * i] * __ldg(a.w.dgelu_tab + (w[i] & 0xFFFFu))),
-                              f2bf(v[2 * i + 1] * __ldg(a.w.dgelu_tab + (w[i] >> 16))));
-            *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0, r, kTile)) = make_uint4(gp[0], gp[1], gp[2], gp[3]);
-            *reinterpret_cast<uint4*>(sA1t + tc::mnmajor_offset(c0 + 8, r, kTile)) =
-                make_uint4(gp[4], gp[5], gp[6], gp[7]);
+            for (int c = 2 * half; c < 2 * half + 2; c++) {
+                const uint32_t ws[4] = {z2c[c].x, z2c[c].y, z2c[c].z, z2c[c].w};
+                uint32_t hp[4], dz[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int l = 8 * (c - 2 * half) + 2 * u;
+                    const uint32_t w = ws[u];
+                    bool m0, m1;
+                    uint2 e0 = s_tab[btab_slot(w & 0xFFFFu, m0)], e1 = s_tab[btab_slot(w >> 16, m1)];
+                    if (m0 | m1) {        // inputs outside the compact table (rare)
+                        e0 = make_uint2(__float_as_uint(__ldg(a.w.dgelu_tab + (w & 0xFFFFu))), __ldg(a.w.gelu_tab + (w & 0xFFFFu)));
+                        e1 = make_uint2(__float_as_uint(__ldg(a.w.dgelu_tab + (w >> 16))), __ldg(a.w.gelu_tab + (w >> 16)));
+                    }
+                    hp[u] = (e0.y & 0xFFFFu) | (e1.y << 16);
+                    dz[u] = bf16x2(dh[l] * __uint_as_float(e0.x), dh[l + 1] * __uint_as_float(e1.x));
+                }
+                const uint32_t off = (uint32_t)(4 * cg + c) * kXChunk + r * 16;
+                *reinterpret_cast<uint4*>(sm + kBwdP1 + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                *reinterpret_cast<uint4*>(sm + kBwdDZ2 + off) = make_uint4(dz[0], dz[1], dz[2], dz[3]);
+            }
         }
-        load_rows(t + gridDim.x);          // the next tile's rows, in flight during the dW1 GEMM
-        cp_async_wait_all();
         operands_ready();
-        // (6) dW1_aug += dZ1^T X_aug
+        // (3) dH1 = dZ2 W2; dW3 parts += H2^T dY split
         if (tid == 0) {
             tc::fence_after_sync();
-            for (int st = 0; st < kTile / 16; st++)
-                tc::mma_bf16(tbase + kTdW1, tc::kstep_desc(sa_a2, kTile, st), tc::kstep_desc(sa_b1, kTile, st),
-                             tc::idesc_bf16_mn(128, kK1, true, true), !first || st > 0);
+            for (int s = 0; s < kHid / 16; s++)
+                tc::mma_bf16(tbase + kTdH, chunk_kmajor(s_dz2, s), tc::kstep_desc(s_w2t, kHid, s),
+                             tc::idesc_bf16(128, kHid), s > 0);
+            for (int s = 0; s < kTile / 16; s++)
+                tc::mma_bf16(tbase + kTdW3, chunk_mnmajor(s_p1, s), chunk_mnmajor(s_dys, s),
+                             tc::idesc_bf16_mn(128, 32, true, true), !first || s > 0);
             tc::mma_commit(bar);
         }
+        // (4) Z1 pass, first half (under the MMAs): H1 -> H1_aug^T, gelu'(Z1) kept
+        float g1[32];
+        {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const uint32_t ws[4] = {z1c[c].x, z1c[c].y, z1c[c].z, z1c[c].w};
+                uint32_t hp[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int i = 4 * c + u;
+                    const uint32_t w = ws[u];
+                    bool m0, m1;
+                    uint2 e0 = s_tab[btab_slot(w & 0xFFFFu, m0)], e1 = s_tab[btab_slot(w >> 16, m1)];
+                    if (m0 | m1) {
+                        e0 = make_uint2(__float_as_uint(__ldg(a.w.dgelu_tab + (w & 0xFFFFu))), __ldg(a.w.gelu_tab + (w & 0xFFFFu)));
+                        e1 = make_uint2(__float_as_uint(__ldg(a.w.dgelu_tab + (w >> 16))), __ldg(a.w.gelu_tab + (w >> 16)));
+                    }
+                    hp[u] = (e0.y & 0xFFFFu) | (e1.y << 16);
+                    g1[2 * i] = __uint_as_float(e0.x);
+                    g1[2 * i + 1] = __uint_as_float(e1.x);
+                }
+                *reinterpret_cast<uint4*>(sm + kBwdH1 + (uint32_t)(4 * cg + c) * kXChunk + r * 16) =
+                    make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            }
+        }
+        if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
+        // (4) second half: dZ1 = bf16(dH1 * gelu'(Z1)) -> dZ1^T (over H2^T, whose GEMM is done)
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            float dh[16];
+            tc::tmem_ld16(tbase + kTdH + lane_off + 32u * cg + 16u * half, dh);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int i = 8 * half + 4 * c + u, l = 8 * c + 2 * u;
+                    v[u] = bf16x2(dh[l] * g1[2 * i], dh[l + 1] * g1[2 * i + 1]);
+                }
+                *reinterpret_cast<uint4*>(sm + kBwdP1 + (uint32_t)(4 * cg + 2 * half + c) * kXChunk + r * 16) =
+                    make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        // X of this tile (TMA): the ones column 196 of X_aug (zero-filled by the copy)
+        const bool x_ok = wait_all(xbar, xphase, a.wait_polls);
+        if (tid == 0) x_inflight = false;     // on a timeout wait_all has waited for the copy (bounded)
+        if (!(ok = x_ok)) break;
+        if (cg == 0) *reinterpret_cast<uint16_t*>(sm + kBwdX + (kIn / 8) * kXChunk + r * 16 + (kIn % 8) * 2) = 0x3F80u;
+        operands_ready();
+        // (5) dW2_aug += dZ2^T H1_aug; dW1_aug += dZ1^T X_aug
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int s = 0; s < kTile / 16; s++)
+                tc::mma_bf16(tbase + kTdW2, chunk_mnmajor(s_dz2, s), chunk_mnmajor(s_h1, s),
+                             tc::idesc_bf16_mn(128, kK2, true, true), !first || s > 0);
+            for (int s = 0; s < kTile / 16; s++)
+                tc::mma_bf16(tbase + kTdW1, chunk_mnmajor(s_p1, s), chunk_mnmajor(s_x, s),
+                             tc::idesc_bf16_mn(128, kK1, true, true), !first || s > 0);
+            tc::mma_commit(bar);
+        }
+        load_z2dy(t + gridDim.x);
+        load_z1(t + gridDim.x);
         if (!(ok = wait_all(bar, phase, a.wait_polls))) break;
         first = false;
+        if (tid == 0 && t + gridDim.x < n_tiles) { load_x(t + gridDim.x); x_inflight = true; }
     }
-    if (!ok && tid == 0) set_status(a.status, GS_ERR_TIMEOUT);
-    cp_async_wait_all();     // after a timeout this thread's input copies may still be in flight
+    if (tid == 0) {
+        if (!ok) set_status(a.status, GS_ERR_TIMEOUT);
+        // nothing in flight when the CTA frees its tensor memory (bounded waits)
+        tc::mma_commit(dbar);
+        tc::mbar_wait(dbar, 0, kDrainPolls);
+        if (x_inflight) tc::mbar_wait(xbar, xphase, kDrainPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
     if (ok && !first) {
-        // accumulated weight gradients of this CTA -> global (row r of dW1_aug, dW2_aug; every fourth chunk)
+        // accumulated weight gradients of this CTA -> global (row r of dW1_aug, dW2_aug, dW3 parts)
 #pragma unroll 1
         for (int c0 = 16 * cg; c0 < kK1; c0 += 16 * kColGroups) {
             float v[16];
@@ -537,9 +832,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_bwd(MlpBwdArgs a) {
                 else if (k == kHid) atomicAdd(a.g.b2 + r, v[i]);
             }
         }
+        if (cg == 0) {
+            float v[32];
+            tc::tmem_ld32(tbase + kTdW3 + lane_off, v);
 #pragma unroll
-        for (int o = 0; o < kOut; o++) atomicAdd(a.g.W3 + o * kHid + jw, acc3[o]);
-        if (tid < kOut) atomicAdd(a.g.b3 + tid, accb3);
+            for (int o = 0; o < kOut; o++) atomicAdd(a.g.W3 + o * kHid + r, (v[o] + v[8 + o]) + v[16 + o]);
+            if (tid < kOut) atomicAdd(a.g.b3 + tid, s_b3[tid]);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -565,16 +864,55 @@ cudaError_t launch_mlp_pack(const gs_mlp_params& p, const gs_mlp_packed& q, cuda
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query
+// (no link-time dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// X as a 2-D tensor of 196 BF16 columns (the inputs; the row stride is 208
+// values) and n rows, copied in boxes of 8 columns x 128 rows (unswizzled) or
+// 64 columns x 128 rows (128-byte swizzle); columns past 195 and rows past n
+// arrive as zeros.
+static cudaError_t x_tensor_map(CUtensorMap* m, const uint16_t* X, int64_t n, bool swizzled = false) {
+    if (n > (int64_t)INT_MAX - kTile) return cudaErrorInvalidValue;    // TMA row coordinates are 32-bit
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (encode == nullptr) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)kIn, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)kK1 * 2};
+    const cuuint32_t box[2] = {swizzled ? 64u : 8u, (cuuint32_t)kTile};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzled ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 cudaError_t launch_mlp_fwd(const gs_mlp_packed& w, const uint16_t* X, int64_t n, float* Y, uint16_t* Z1,
                            uint16_t* Z2, const float* T, float* dY, float* loss, float loss_scale, int* status,
                            cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    CUtensorMap xmap_sw, xmap;
+    cudaError_t e = x_tensor_map(&xmap_sw, X, n, true);
+    if (e == cudaSuccess) e = x_tensor_map(&xmap, X, n);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-    MlpFwdArgs a{w, X, n, Y, Z1, Z2, T, dY, loss, loss_scale, status, g_wait_polls.load()};
-    k_mlp_fwd<<<grid, kFwdThreads, kFwdSmem, s>>>(a);
+    MlpFwdArgs a{w, n, Y, Z1, Z2, T, dY, loss, loss_scale, status, g_wait_polls.load()};
+    k_mlp_fwd<<<grid, kFwdThreads2, kFwdSmem, s>>>(xmap_sw, xmap, a);
     return cudaGetLastError();
 }
 
@@ -588,12 +926,15 @@ cudaError_t launch_mlp_bwd(const gs_mlp_packed& w, const uint16_t* X, const uint
         if (e != cudaSuccess) return e;
     }
     if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    CUtensorMap xmap;
+    cudaError_t e = x_tensor_map(&xmap, X, n);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + kTile - 1) / kTile;
     const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
-    MlpBwdArgs a{w, X, Z1, Z2, dY, n, g, status, g_wait_polls.load()};
-    k_mlp_bwd<<<grid, kFwdThreads, kBwdSmem, s>>>(a);
+    MlpBwdArgs a{w, Z1, Z2, dY, n, g, status, g_wait_polls.load()};
+    k_mlp_bwd<<<grid, kEpiThreads, kBwdSmem, s>>>(xmap, a);
     return cudaGetLastError();
 }
 

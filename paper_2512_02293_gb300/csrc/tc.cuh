@@ -1,9 +1,10 @@
 // tc.cuh -- fifth-generation tensor-core (tcgen05) building blocks for sm_103a:
 // tensor-memory allocation, shared-memory matrix descriptors, the BF16 MMA with
-// an FP32 accumulator in tensor memory, its commit to an mbarrier, bounded
-// mbarrier waits and tensor-memory loads.  Inline PTX only.
+// an FP32 accumulator in tensor memory (A from shared or tensor memory), its
+// commit to an mbarrier, mbarrier arrivals and bounded waits, TMA tensor copies,
+// tensor-memory loads and stores.  Inline PTX only.
 //
-// Operand layout used throughout (K-major, no swizzle): a tile of R rows and K
+// Basic operand layout (K-major, no swizzle): a tile of R rows and K
 // columns of 16-bit values is stored as 8 x 8 "core matrices" (8 rows of 16
 // bytes, 128 contiguous bytes).  Element (r, k) lives at byte
 //     (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,   SBO = 16 K,
@@ -18,7 +19,9 @@
 // matrix is transposed, its 16-byte lines holding 8 consecutive rows at one K:
 //     (r / 8) * SBO + (k / 8) * 128 + (k % 8) * 16 + (r % 8) * 2.
 // So a thread that owns one K index (a sample) and 8 consecutive rows writes
-// them as one 16-byte store.
+// them as one 16-byte store.  Other leading / stride byte offsets describe other
+// arrangements of the same core matrices (e.g. 8-column chunks of 128 rows, as
+// a TMA box of 8 x 128 lands), and smem_desc_sw128 the 128-byte swizzle.
 #pragma once
 #include <cstdint>
 
@@ -51,6 +54,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;    // base offset 0, relative LBO mode, layout type 0 (no swizzle)
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout that TMA
+// writes with CU_TENSOR_MAP_SWIZZLE_128B: rows of 64 BF16 (128 bytes), 8-row
+// atoms of 1024 bytes (stride byte offset), the 16-byte units of each row
+// permuted by the row index within the atom; layout type 2 in bits 61-63.  The
+// atom must be 1024-byte aligned; K step s within a row of 64 starts 32 s bytes
+// on (the hardware applies the same permutation to the offset addresses).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                     // leading byte offset: unused for this layout
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // descriptor of K step s of a K-major tile with K columns starting at saddr
 __device__ __forceinline__ uint64_t kstep_desc(uint32_t saddr, int K, int s) {
     return smem_desc(saddr + 256u * (uint32_t)s, 128u, (uint32_t)(K * 16));
@@ -77,6 +96,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate) : "memory");
 }
 
+// The same with A read from tensor memory: an M x K BF16 operand occupies the
+// M lanes from a_tmem on, two consecutive K values per 32-bit column (the lower
+// K index in the low half), so K step s of a K loop starts 8 s columns on.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate) : "memory");
+}
+
 // The mbarrier at mbar receives one arrival when every MMA issued so far by
 // this thread has completed.
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -98,6 +129,33 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+// One arrival that also announces `bytes` of asynchronous copies to come.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+// One poll: has the phase with the given parity completed?
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Tensor-memory-access (TMA) copy of one box of a 2-D tensor map into shared
+// memory at dst, completing `box bytes` of transactions on mbar.  Coordinates
+// (x innermost, in elements); out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(mbar) : "memory");
 }
 
 // Wait for the phase with the given parity to complete; gives up after
@@ -141,6 +199,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         : "r"(taddr) : "memory");
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Store 16 consecutive 32-bit columns of this thread's tensor-memory lane and
+// wait until the stores have completed.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+           "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+// The same for 8 columns.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's lane (as tmem_ld16).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace tc
