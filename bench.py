@@ -143,9 +143,10 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_step(device, g, gt, cams, candidates=(8, 16, 32)):
+def build_step(device, g, gt, cams, candidates=(8, 16, 32), stages=(2, 3)):
     """Target images of the perturbed map (input preparation, not timed), then a
-    mapping step on the map with the tile size autotuned over `candidates`."""
+    mapping step on the map with the tile size and the forward's splat staging
+    autotuned over `candidates` x `stages`."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep, autotune_tile
@@ -159,7 +160,7 @@ def build_step(device, g, gt, cams, candidates=(8, 16, 32)):
     tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
     del tstep
     gd = G.Gaussians.from_numpy(g, device)
-    params, tune = autotune_tile(gd, cams, tc, td, params, mp, candidates=candidates)
+    params, tune = autotune_tile(gd, cams, tc, td, params, mp, candidates=candidates, stages=stages)
     step = MappingStep(gd, cams, tc, td, params, mp)
     step.tune = tune
     return params, mp, step, tc, td
@@ -446,7 +447,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     iteration one CUDA graph, tile size autotuned."""
     from paper_2512_02293_gb300 import synth
     g, gt, cams = synth.cfg3_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, cams, args.tiles)
+    params, mp, step, tc, td = build_step(device, g, gt, cams, args.tiles, args.stages)
     steps = max(10, args.steps // 4)
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
@@ -911,12 +912,15 @@ def main():
     ap.add_argument("--li-eval-rooms", type=int, default=5)
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
                     help="fix the tile size instead of autotuning over {8, 16, 32}")
+    ap.add_argument("--splat-stages", type=int, choices=[2, 3], default=None,
+                    help="fix the forward rasteriser's splat staging instead of autotuning over {2, 3}")
     ap.add_argument("--only", choices=["loop_closure", "pose_refinement", "bundle_adjustment", "keyframe_insertion",
                                        "mlp_kernels", "final_colour_refinement"],
                     default=None, help="run one extra section alone and print its line (for profiling runs)")
     ap.add_argument("--mlp-samples", type=int, default=2_457_600, help="batch of the mlp_kernels section")
     args = ap.parse_args()
     args.tiles = (args.tile,) if args.tile else (8, 16, 32)
+    args.stages = (args.splat_stages,) if args.splat_stages else (2, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -946,7 +950,7 @@ def main():
 
     from paper_2512_02293_gb300 import synth
     g, gt, cam = synth.cfg2_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, [cam], args.tiles)
+    params, mp, step, tc, td = build_step(device, g, gt, [cam], args.tiles, args.stages)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
     flush = lambda: flush_buf.fill_(1.0)
     times, st, pairs, clocks = timed_run(step, args.steps, args.warmup, flush, dist, local)

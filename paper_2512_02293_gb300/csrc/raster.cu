@@ -223,8 +223,12 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
         gs_image img, int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;     // pixel blocks per tile
-    __shared__ float2 s_xy[kRasterWarps][32];
-    __shared__ float4 s_q[kRasterWarps][32];
+    // the batch's kept splats in pairs (slots 2i, 2i + 1), so that the weights of
+    // two splats are formed by packed FP32x2 operations: {-mx, -mx', -my, -my'},
+    // {qa, qa', qb, qb'}, {qc, qc', o, o'}
+    __shared__ float4 s_pm[kRasterWarps][16];
+    __shared__ float4 s_pab[kRasterWarps][16];
+    __shared__ float4 s_pco[kRasterWarps][16];
     __shared__ float4 s_cd[kRasterWarps][32];
     __shared__ uint32_t s_pos[kRasterWarps][32];
     __shared__ float s_loss[LOSS ? GS_MAX_VIEWS * 3 : 1];    // per-view sums of this CTA (fused loss)
@@ -289,6 +293,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             }
         }
         const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+        const float2 sx2 = make_float2(sx, sx), sy2 = make_float2(sy, sy);
         // sample rectangle of this 8 x 4 block
         const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f;
         const float by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
@@ -330,9 +335,13 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             const uint32_t kept = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
             if (keep) {
-                const int slot = __popc(kept & lt_mask);
-                s_xy[w][slot] = nxt.xy;
-                s_q[w][slot] = nxt.q;
+                const int slot = __popc(kept & lt_mask), pi = slot >> 1, h = slot & 1;
+                float* pm = reinterpret_cast<float*>(&s_pm[w][pi]);
+                float* pab = reinterpret_cast<float*>(&s_pab[w][pi]);
+                float* pco = reinterpret_cast<float*>(&s_pco[w][pi]);
+                pm[h] = -nxt.xy.x; pm[2 + h] = -nxt.xy.y;
+                pab[h] = nxt.q.x; pab[2 + h] = nxt.q.y;
+                pco[h] = nxt.q.z; pco[2 + h] = nxt.q.w;
                 s_cd[w][slot] = nxt.cd;
                 s_pos[w][slot] = base - range.x + lane;
             }
@@ -366,12 +375,26 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 Tr = b ? test : Tr;
                 last_k = b ? k : last_k;
             };
+            // splat k alone (the same operations as splat_power2 / splat_weight)
             auto alpha = [&](int k, float* p2, float* a) {
-                const float2 m = s_xy[w][k];
-                const float4 q = s_q[w][k];
-                const float dx = __fsub_rn(sx, m.x), dy = __fsub_rn(sy, m.y);
-                *p2 = splat_power2(q.x, q.y, q.z, dx, dy);
-                *a = fminf(amax, __fmul_rn(q.w, splat_weight(p2[0])));
+                const int h = k & 1;
+                const float4 m = s_pm[w][k >> 1], ab = s_pab[w][k >> 1], co = s_pco[w][k >> 1];
+                const float dx = __fadd_rn(sx, h ? m.y : m.x), dy = __fadd_rn(sy, h ? m.w : m.z);
+                *p2 = splat_power2(h ? ab.y : ab.x, h ? ab.w : ab.z, h ? co.y : co.x, dx, dy);
+                *a = fminf(amax, __fmul_rn(h ? co.w : co.z, splat_weight(p2[0])));
+            };
+            // splats 2i and 2i + 1 by packed FP32x2 operations: each element is
+            // rounded as the scalar intrinsics round it, so the results are identical
+            auto alpha_pair = [&](int i, float* p2, float* a) {
+                const float4 m = s_pm[w][i], ab = s_pab[w][i], co = s_pco[w][i];
+                const float2 dx = __fadd2_rn(sx2, make_float2(m.x, m.y));
+                const float2 dy = __fadd2_rn(sy2, make_float2(m.z, m.w));
+                const float2 u = __ffma2_rn(make_float2(ab.z, ab.w), dy, __fmul2_rn(make_float2(ab.x, ab.y), dx));
+                const float2 q = __fmul2_rn(make_float2(co.x, co.y), dy);
+                const float2 pw = __ffma2_rn(dx, u, __fmul2_rn(q, dy));
+                const float2 ao = __fmul2_rn(make_float2(co.z, co.w), make_float2(splat_weight(pw.x), splat_weight(pw.y)));
+                p2[0] = pw.x; p2[1] = pw.y;
+                a[0] = fminf(amax, ao.x); a[1] = fminf(amax, ao.y);
             };
             // groups of four: the four weights do not depend on the transmittance, so
             // they are formed before the four serial steps; the warp checks for
@@ -380,8 +403,8 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             bool all_done = false;
             for (; k + 4 <= cnt; k += 4) {
                 float p2[4], a[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) alpha(k + u, &p2[u], &a[u]);
+                alpha_pair(k >> 1, &p2[0], &a[0]);
+                alpha_pair((k >> 1) + 1, &p2[2], &a[2]);
 #pragma unroll
                 for (int u = 0; u < 4; u++) step(k + u, p2[u], a[u]);
                 if ((all_done = __all_sync(0xffffffffu, done))) break;
