@@ -73,9 +73,16 @@ ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # Keyed by (stage, tile, ring) for the forward (its staging variant) and
 # (stage, tile, None) for the others.
 PROFILED_TRAFFIC = {("gs_project", 16, None): 11.30e6, ("gs_bin_sort", 16, None): 14.50e6,
+                    ("gs_render_fwd_loss", 16, False): 14.25e6,
                     ("gs_render_bwd_raster_loss", 16, None): 27.30e6, ("gs_project_bwd", 16, None): 16.41e6,
                     ("gs_adam_step", 16, None): 44.83e6}
+# L2 bytes (lts__t_bytes.sum) per launch of the binning stage's six kernels, from
+# the same kind of capture (profiles/launch_list_640x480_200k.md).
+PROFILED_L2 = {("gs_bin_sort", 16): 92.1e6}
 PROFILED_PIPE = {
+    ("gs_render_fwd_loss", 16, False): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
+                                       "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
+                                       "XU (ex2) 9.4 %",
     ("gs_render_bwd_raster_loss", 16, None): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, "
                                              "FMA 36.2 %, LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the launch"}
 
@@ -300,6 +307,41 @@ def _oracle_iteration_fn(g, gt, cams, params, mp, sh_degree):
     return one
 
 
+L2_PEAK = {}     # measured once per run by measure_l2_peak
+
+
+def measure_l2_peak(device, total_gib=1.0):
+    """Read bandwidth of a buffer that stays in L2 (129 MB): one reduction over
+    the buffer repeated (a stride-0 view of k copies, about `total_gib` GiB of
+    reads in one launch, so the launch costs nothing), bytes read over the
+    launch's device time, for buffers of 4, 8, 16 and 32 MiB; the best of the
+    sizes.  This is the denominator of the binning stage's L2 roofline (its
+    keys, counters and ranges live in L2 between the stage's six launches)."""
+    import torch
+    best, per = 0.0, {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for mib in (4, 8, 16, 32):
+        n = mib * (1 << 20) // 4
+        k = max(1, int(total_gib * (1 << 30)) // (n * 4))
+        src = torch.ones(n, device=device)
+        view = src.expand(k, n)
+        for _ in range(2):
+            view.sum()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(5):
+            ev[0].record(); view.sum(); ev[1].record(); torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        gbs = k * n * 4 / (min(times) * 1e-3) / 1e9
+        per[f"{mib}MiB"] = round(gbs, 1)
+        best = max(best, gbs)
+        del src, view
+    L2_PEAK.update({"gbs": best, "per_size": per,
+                    "method": f"one reduction reading an L2-resident buffer over and over (a stride-0 view, about "
+                              f"{total_gib:g} GiB of reads per launch), best of 4 / 8 / 16 / 32 MiB buffers"})
+    return L2_PEAK
+
+
 def stage_rooflines(step, st, pairs, params, bwd_label=None):
     """Roofline of every stage of one iteration from its CUDA-event time in the
     instrumented graph replays: the rasterisers against the FP32 lane peak
@@ -365,6 +407,19 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
             "bytes": lsd, "achieved": lsd / (st["gs_bin_sort"] * 1e-3) / 1e9,
             "frac": lsd / (st["gs_bin_sort"] * 1e-3) / 1e9 / hbm,
             "work": f"{M} keys x (12 + 24 x {lsd_passes} passes) B: an 8-bit LSD radix sort's traffic"}
+        if L2_PEAK.get("gbs"):
+            b = out["gs_bin_sort"]
+            alg = b["achieved"] * b["ms"] * 1e-3 * 1e9             # algorithmic bytes
+            l2 = {"achieved": b["achieved"], "peak": L2_PEAK["gbs"], "unit": "GB/s",
+                  "frac": b["achieved"] / L2_PEAK["gbs"], "work": b["work"],
+                  "peak_basis": "L2-resident copy, measured in this run (" + L2_PEAK["method"] + ")",
+                  "peak_per_size": L2_PEAK["per_size"]}
+            t = PROFILED_L2.get(("gs_bin_sort", params.tile))
+            if t is not None:
+                l2["traffic"] = t
+                l2["traffic_frac"] = t / (b["ms"] * 1e-3) / 1e9 / L2_PEAK["gbs"]
+            l2["algorithmic_bytes"] = alg
+            b["l2"] = l2
     return out
 
 
@@ -1015,6 +1070,7 @@ def main():
                    "eager_value with the two copies in, the C-ABI calls and the two copies out issued "
                    "each step"}
 
+    measure_l2_peak(device)               # after the timed region: the L2 roofline's denominator
     stages_roof = stage_rooflines(step, st, pairs, params)
     roofline = None
     if st:

@@ -197,11 +197,14 @@ int32_t gs_project_perturbed(const gs_gaussians* g, const gs_camera* cams, int32
 /* Tile binning and depth sort.  The paper does not describe this step: Sec. 3.3
  * renders with the 3D Gaussian splatting rasteriser it builds on, whose
  * compositing visits each tile's splats front to back.  Here: one key
- * (global tile << 32) | bits(float z) per
- * (entry, covered tile), keys sorted ascending by a stable LSD radix sort of
- * the entry-ordered list (ties in z keep entry order), and [start, end) of each
- * tile in the sorted list.  Global tile of view v = tile_base(v) + ty * tiles_x(v)
- * + tx with tile_base(v) = tiles of views 0..v-1.  Writes M to *bins->num_keys;
+ * (global tile << 32) | bits(float z) with value e per (entry e, covered tile),
+ * in the order of a stable ascending sort of the entry-ordered list by key
+ * (so within a tile by depth, ties in z by entry index), and [start, end) of
+ * each tile in it.  Built without a global sort: per-tile counts, a prefix
+ * over the tiles, a scatter of (bits(z), e) into each tile's segment, and a
+ * sort of every segment (six launches).  Global tile of view v = tile_base(v) +
+ * ty * tiles_x(v) + tx with tile_base(v) = tiles of views 0..v-1.  Writes M to
+ * *bins->num_keys;
  * if M > key_capacity it sets *bins->status = GS_ERR_CAPACITY and the outputs
  * are undefined (grow the capacity to M and call again).
  * `ws` must hold gs_workspace_size(...) bytes.

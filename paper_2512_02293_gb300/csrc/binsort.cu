@@ -13,7 +13,7 @@
 //                      whole warp.  Each tile has kStripes counters (the lane
 //                      picks one), so that the thousands of keys of a deep tile
 //                      do not queue on one address
-//   3. k_bin_stripes : per tile, the exclusive scan of its stripe counters (each
+//   3. k_bin_stripes : per tile (one warp), the exclusive scan of its stripe counters (each
 //                      becomes its stripe's offset inside the tile) and the total
 //   4. k_bin_offsets : one CTA: exclusive scan of the tile totals in coalesced
 //                      rounds -> ranges [start, end) of every tile (clamped to
@@ -152,22 +152,24 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint32_t* __res
     for_each_key(tt, rect, nullptr, E, n, views, [&](uint32_t g, uint32_t, uint32_t) { atomicAdd(mine + g, 1u); });
 }
 
-// Per tile: each stripe counter becomes the exclusive prefix of the stripes
-// before it (its offset inside the tile); total[t] = the tile's key count.
+// Per tile (one warp, lane = stripe): each stripe counter becomes the exclusive
+// prefix of the stripes before it (its offset inside the tile); total[t] = the
+// tile's key count.
 __global__ void __launch_bounds__(kBinThreads) k_bin_stripes(uint32_t* __restrict__ cnt, int total_tiles,
                                                             uint32_t* __restrict__ total) {
     pdl_enter();
-    const int t = blockIdx.x * kBinThreads + threadIdx.x;
-    if (t >= total_tiles) return;
-    uint32_t run = 0;
-#pragma unroll 8
-    for (int s = 0; s < kStripes; s++) {
-        uint32_t* c = cnt + (size_t)s * total_tiles + t;
-        const uint32_t v = *c;
-        *c = run;
-        run += v;
+    const int t = (int)(((int64_t)blockIdx.x * kBinThreads + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (t >= total_tiles) return;                    // warp-uniform
+    uint32_t* c = cnt + (size_t)lane * total_tiles + t;
+    const uint32_t v = *c;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
-    total[t] = run;
+    *c = inc - v;
+    if (lane == 31) total[t] = inc;
 }
 
 // One CTA: ranges[t] = [start, start + count) of every tile with keys (both
@@ -459,7 +461,6 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     }
     int ebits = 0;
     while ((1ll << ebits) < E) ebits++;
-    const int nb_tiles = (int)ceil_div(T, kBinThreads);
     const int nb_entries = (int)ceil_div(E, kBinThreads);
     const int4* rect = reinterpret_cast<const int4*>(pr.rect);
     const float4* rgbd = reinterpret_cast<const float4*>(pr.rgbd);
@@ -468,7 +469,9 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     err = launch_pdl(k_bin_zero, nb_zero, kBinThreads, 0, s, stripes, words);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_count, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, E, n, views, stripes);
-    if (err == cudaSuccess) err = launch_pdl(k_bin_stripes, nb_tiles, kBinThreads, 0, s, stripes, T, totals);
+    if (err == cudaSuccess)
+        err = launch_pdl(k_bin_stripes, (int)ceil_div((int64_t)T * 32, kBinThreads), kBinThreads, 0, s, stripes, T,
+                         totals);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_offsets, 1, kScanThreads, 0, s, totals, T, reinterpret_cast<uint2*>(bins.ranges),
                          bins.num_keys, cap, bins.status);
