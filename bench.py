@@ -310,35 +310,36 @@ def _oracle_iteration_fn(g, gt, cams, params, mp, sh_degree):
 L2_PEAK = {}     # measured once per run by measure_l2_peak
 
 
-def measure_l2_peak(device, total_gib=1.0):
-    """Read bandwidth of a buffer that stays in L2 (129 MB): one reduction over
-    the buffer repeated (a stride-0 view of k copies, about `total_gib` GiB of
-    reads in one launch, so the launch costs nothing), bytes read over the
-    launch's device time, for buffers of 4, 8, 16 and 32 MiB; the best of the
-    sizes.  This is the denominator of the binning stage's L2 roofline (its
+def measure_l2_peak(device, total_gib=2.0):
+    """Read bandwidth of a buffer that stays in L2 (129 MB), by the library's
+    gs_l2_read_probe: one launch reads the buffer over and over (about
+    `total_gib` GiB in all) with 16-byte loads cached in L2 only; bytes read over
+    the launch's device time, for buffers of 8, 16, 32 and 48 MiB, the best of
+    the sizes.  This is the denominator of the binning stage's L2 roofline (its
     keys, counters and ranges live in L2 between the stage's six launches)."""
     import torch
+    from paper_2512_02293_gb300 import gs as G
     best, per = 0.0, {}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for mib in (4, 8, 16, 32):
+    out = torch.zeros(1, device=device)
+    for mib in (8, 16, 32, 48):
         n = mib * (1 << 20) // 4
-        k = max(1, int(total_gib * (1 << 30)) // (n * 4))
-        src = torch.ones(n, device=device)
-        view = src.expand(k, n)
+        reps = max(1, int(total_gib * (1 << 30)) // (n * 4))
+        buf = torch.ones(n, device=device)
         for _ in range(2):
-            view.sum()
+            G.gs_l2_read_probe(buf, reps, out)
         torch.cuda.synchronize()
         times = []
         for _ in range(5):
-            ev[0].record(); view.sum(); ev[1].record(); torch.cuda.synchronize()
+            ev[0].record(); G.gs_l2_read_probe(buf, reps, out); ev[1].record(); torch.cuda.synchronize()
             times.append(ev[0].elapsed_time(ev[1]))
-        gbs = k * n * 4 / (min(times) * 1e-3) / 1e9
+        gbs = reps * n * 4 / (min(times) * 1e-3) / 1e9
         per[f"{mib}MiB"] = round(gbs, 1)
         best = max(best, gbs)
-        del src, view
+        del buf
     L2_PEAK.update({"gbs": best, "per_size": per,
-                    "method": f"one reduction reading an L2-resident buffer over and over (a stride-0 view, about "
-                              f"{total_gib:g} GiB of reads per launch), best of 4 / 8 / 16 / 32 MiB buffers"})
+                    "method": f"gs_l2_read_probe: one launch reading an L2-resident buffer over and over (about "
+                              f"{total_gib:g} GiB), best of 8 / 16 / 32 / 48 MiB buffers"})
     return L2_PEAK
 
 
@@ -412,7 +413,7 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
             alg = b["achieved"] * b["ms"] * 1e-3 * 1e9             # algorithmic bytes
             l2 = {"achieved": b["achieved"], "peak": L2_PEAK["gbs"], "unit": "GB/s",
                   "frac": b["achieved"] / L2_PEAK["gbs"], "work": b["work"],
-                  "peak_basis": "L2-resident copy, measured in this run (" + L2_PEAK["method"] + ")",
+                  "peak_basis": "L2 read bandwidth measured in this run (" + L2_PEAK["method"] + ")",
                   "peak_per_size": L2_PEAK["per_size"]}
             t = PROFILED_L2.get(("gs_bin_sort", params.tile))
             if t is not None:

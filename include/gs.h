@@ -594,6 +594,16 @@ size_t gs_ba_workspace_size(int32_t n_keyframes, int32_t n_edges, int32_t height
 int32_t gs_ba_step(const gs_ba_problem* problem, float lambda, float eps, float* cost, void* ws, size_t ws_bytes,
                    void* stream);
 
+/* Measurement helper, no part of the method: reads buf[n] (device FP32,
+ * 16-byte aligned, n a multiple of 4) `reps` times over in one launch with
+ * 16-byte loads cached in L2 only, and adds the sum of everything read to
+ * *out (device FP32), so the loads cannot be dropped.  With buf smaller than
+ * the L2 cache, n * 4 * reps bytes over the launch's time is the L2 read
+ * bandwidth: the denominator of the binning stage's L2 roofline.
+ * Errors: GS_ERR_INVALID_ARG on NULL pointers, n <= 0, n % 4 != 0, reps < 1,
+ * misalignment. */
+int32_t gs_l2_read_probe(const float* buf, int64_t n, int32_t reps, float* out, void* stream);
+
 /* Synchronises `stream`, copies the device status word to *host_status and
  * returns GS_OK (or GS_ERR_CUDA if the copy failed).  Not capturable. */
 int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* host_status);

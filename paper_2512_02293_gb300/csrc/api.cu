@@ -377,6 +377,12 @@ int32_t gs_read_device_status(const int32_t* d_status, void* stream, int32_t* ho
     return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+int32_t gs_l2_read_probe(const float* buf, int64_t n, int32_t reps, float* out, void* stream) {
+    if (buf == nullptr || out == nullptr || n <= 0 || n % 4 != 0 || reps < 1 || !aligned(buf, 16))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_l2_read(buf, n, reps, out, static_cast<cudaStream_t>(stream)));
+}
+
 int32_t gs_mlp_pack(const gs_mlp_params* p, const gs_mlp_packed* q, void* stream) {
     if (p == nullptr || q == nullptr) return GS_ERR_INVALID_ARG;
     if (!p->W1 || !p->b1 || !p->W2 || !p->b2 || !p->W3 || !p->b3) return GS_ERR_INVALID_ARG;

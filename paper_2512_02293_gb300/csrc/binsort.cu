@@ -492,4 +492,53 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     return cudaGetLastError();
 }
 
+// L2 read probe (a measurement helper, not part of the method): every CTA
+// streams its grid-stride share of buf `reps` times with 16-byte loads cached in
+// L2 only; four independent sums keep four loads in flight per thread; one
+// atomic per CTA into *out keeps the loads from being dropped.
+__global__ void __launch_bounds__(kBinThreads) k_l2_read(const float4* __restrict__ buf, int64_t n4, int reps,
+                                                        float* __restrict__ out) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * kBinThreads;
+    for (int r = 0; r < reps; r++) {
+        int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+        for (; i + 3 * stride < n4; i += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
+                             : "=f"(v[u].x), "=f"(v[u].y), "=f"(v[u].z), "=f"(v[u].w) : "l"(buf + i + u * stride));
+            a0 += (v[0].x + v[0].y) + (v[0].z + v[0].w);
+            a1 += (v[1].x + v[1].y) + (v[1].z + v[1].w);
+            a2 += (v[2].x + v[2].y) + (v[2].z + v[2].w);
+            a3 += (v[3].x + v[3].y) + (v[3].z + v[3].w);
+        }
+        for (; i < n4; i += stride) {
+            float4 v;
+            asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(buf + i));
+            a0 += (v.x + v.y) + (v.z + v.w);
+        }
+    }
+    float sum = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ float s_w[kBinThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kBinThreads / 32; w++) t += s_w[w];
+        atomicAdd(out, t);
+    }
+}
+
+cudaError_t launch_l2_read(const float* buf, int64_t n, int reps, float* out, cudaStream_t s) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_l2_read<<<8 * sms, kBinThreads, 0, s>>>(reinterpret_cast<const float4*>(buf), n / 4, reps, out);
+    return cudaGetLastError();
+}
+
 }  // namespace gs

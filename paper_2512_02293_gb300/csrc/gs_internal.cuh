@@ -82,6 +82,8 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
 // Launchers (one translation unit each).
 cudaError_t launch_project(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                            const gs_projected& out, cudaStream_t s, const float* xi = nullptr);
+// L2 read-bandwidth probe (binsort.cu): reps grid-stride passes over buf[n], n % 4 == 0
+cudaError_t launch_l2_read(const float* buf, int64_t n, int reps, float* out, cudaStream_t s);
 cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n_entries, const Views& views,
                             const SortPlan& plan, const gs_bins& bins, void* ws, cudaStream_t s);
 // The Eq. 6 colour and depth L1 terms fused into the rasterisers: the forward

@@ -125,7 +125,8 @@ EXPORTS = ["gs_abi_version", "gs_status_string", "gs_total_tiles", "gs_total_pix
            "gs_project_bwd", "gs_adam_step", "gs_read_device_status", "gs_mlp_pack", "gs_mlp_fwd", "gs_mlp_bwd",
            "gs_extract_patches", "gs_insert_gaussians", "gs_loop_closure_update", "gs_ba_workspace_size",
            "gs_ba_step", "gs_fused_loss_workspace_size", "gs_render_fwd_loss", "gs_render_bwd_raster_loss",
-           "gs_mapping_step", "gs_mlp_set_wait_polls", "gs_project_perturbed", "gs_project_bwd_perturbed"]
+           "gs_mapping_step", "gs_mlp_set_wait_polls", "gs_project_perturbed", "gs_project_bwd_perturbed",
+           "gs_l2_read_probe"]
 
 
 def load_library(path: str | None = None):
@@ -167,6 +168,8 @@ def load_library(path: str | None = None):
     lib.gs_project_bwd.argtypes = [V, V, ctypes.c_int32, V, V, ctypes.c_float, V, V, V]
     lib.gs_adam_step.restype = ctypes.c_int32
     lib.gs_adam_step.argtypes = [V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float, V, V]
+    lib.gs_l2_read_probe.restype = ctypes.c_int32
+    lib.gs_l2_read_probe.argtypes = [V, ctypes.c_int64, ctypes.c_int32, V, V]
     lib.gs_read_device_status.restype = ctypes.c_int32
     lib.gs_read_device_status.argtypes = [V, V, V]
     lib.gs_mlp_pack.restype = ctypes.c_int32
@@ -583,6 +586,13 @@ def bind_mapping_step(g: Gaussians, proj: Projected, bins: Bins, img: Image, cam
         BoundCall("gs_adam_step", (groups, len(adam_groups), float(beta1), float(beta2), float(eps), _ptr(d_step)),
                   keep),
     ]
+
+
+def gs_l2_read_probe(buf, reps: int, out, stream=None):
+    """Read buf (FP32, length a multiple of 4) reps times over in one launch,
+    adding the sum to out[0] (see gs.h: the L2 bandwidth probe)."""
+    _check(load_library().gs_l2_read_probe(_ptr(buf), buf.numel(), int(reps), _ptr(out), _stream(stream)),
+           "gs_l2_read_probe")
 
 
 def gs_read_device_status(d_status, stream=None) -> int:

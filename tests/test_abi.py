@@ -202,3 +202,15 @@ def test_splat_stages_parameter_is_checked(lib):
     for st, want in ((0, 0), (2, 0), (3, 0), (1, 1), (4, 1), (-1, 1)):
         p = G.RenderParams(splat_stages=st).struct()
         assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == want, st
+
+
+def test_l2_read_probe_rejects_bad_arguments(lib):
+    """The L2 bandwidth probe checks its arguments on the host (no launch)."""
+    buf = ctypes.c_void_p(16)
+    out = ctypes.c_void_p(32)
+    assert lib.gs_l2_read_probe(None, 4, 1, out, None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_l2_read_probe(buf, 4, 1, None, None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_l2_read_probe(buf, 6, 1, out, None) == G.GS_ERR_INVALID_ARG      # not a multiple of 4
+    assert lib.gs_l2_read_probe(buf, 0, 1, out, None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_l2_read_probe(buf, 4, 0, out, None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_l2_read_probe(ctypes.c_void_p(20), 4, 1, out, None) == G.GS_ERR_INVALID_ARG   # misaligned

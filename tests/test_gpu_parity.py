@@ -611,3 +611,17 @@ def test_adam_matches_oracle():
             np.testing.assert_allclose(d[0].cpu().numpy(), r[0], rtol=1e-6, atol=1e-7)
             np.testing.assert_allclose(d[2].cpu().numpy(), r[1], rtol=1e-5, atol=1e-6 * np.abs(r[1]).max())
             np.testing.assert_allclose(d[3].cpu().numpy(), r[2], rtol=1e-5, atol=1e-6 * np.abs(r[2]).max())
+
+
+def test_l2_read_probe_reads_every_element_reps_times():
+    """gs_l2_read_probe (the L2 roofline's denominator) reads the whole buffer
+    `reps` times: the sum it adds is exactly reps * sum(buf) (0 / 1 values, every
+    partial sum an integer below 2^24), for a length that runs the four-load
+    loop and leaves a ragged tail in every CTA's share."""
+    n = 152 * 8 * 256 * 4 * 4 + 44
+    vals = (np.arange(n) % 2).astype(np.float32)
+    buf = torch.from_numpy(vals).cuda()
+    out = torch.zeros(1, device="cuda")
+    G.gs_l2_read_probe(buf, 3, out)
+    torch.cuda.synchronize()
+    assert out.item() == 3.0 * float(vals.sum())
