@@ -314,7 +314,7 @@ def measure_l2_peak(device, total_gib=2.0):
     """Read bandwidth of a buffer that stays in L2 (129 MB), by the library's
     gs_l2_read_probe: one launch reads the buffer over and over (about
     `total_gib` GiB in all) with 16-byte loads cached in L2 only; bytes read over
-    the launch's device time, for buffers of 8, 16, 32 and 48 MiB, the best of
+    the launch's device time, for buffers of 8 to 96 MiB, the best of
     the sizes.  This is the denominator of the binning stage's L2 roofline (its
     keys, counters and ranges live in L2 between the stage's six launches)."""
     import torch
@@ -322,7 +322,7 @@ def measure_l2_peak(device, total_gib=2.0):
     best, per = 0.0, {}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     out = torch.zeros(1, device=device)
-    for mib in (8, 16, 32, 48):
+    for mib in (8, 16, 32, 48, 64, 96):
         n = mib * (1 << 20) // 4
         reps = max(1, int(total_gib * (1 << 30)) // (n * 4))
         buf = torch.ones(n, device=device)
@@ -339,16 +339,18 @@ def measure_l2_peak(device, total_gib=2.0):
         del buf
     L2_PEAK.update({"gbs": best, "per_size": per,
                     "method": f"gs_l2_read_probe: one launch reading an L2-resident buffer over and over (about "
-                              f"{total_gib:g} GiB), best of 8 / 16 / 32 / 48 MiB buffers"})
+                              f"{total_gib:g} GiB), best of 8 / 16 / 32 / 48 / 64 / 96 MiB buffers"})
     return L2_PEAK
 
 
-def stage_rooflines(step, st, pairs, params, bwd_label=None):
+def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
     """Roofline of every stage of one iteration from its CUDA-event time in the
     instrumented graph replays: the rasterisers against the FP32 lane peak
     (operations, a multiply-add as one) and the FP32 FLOP peak (a multiply-add as
     two), the other stages against the measured HBM copy bandwidth."""
     peaks, peak_kind = _peaks()
+    # the ncu figures belong to the 640x480 / 200k workload they were captured on
+    prof = (lambda table, key: table.get(key)) if profiled else (lambda table, key: None)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     lane_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # T lane-ops/s
     flop_peak = 2.0 * lane_peak                          # T FLOP/s FP32
@@ -374,8 +376,8 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
                       "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops (a multiply-add as one)",
                       "flop": {"achieved": ach_f, "peak": flop_peak, "unit": "TFLOP/s FP32", "frac": ach_f / flop_peak,
                                "work": f"{pairs} pairs x {flop} FLOPs (a multiply-add as two)"},
-                      "binding_pipe": PROFILED_PIPE.get((stage, params.tile, ring if stage == fwd_st else None)),
-                      "traffic": PROFILED_TRAFFIC.get((stage, params.tile, ring if stage == fwd_st else None)),
+                      "binding_pipe": prof(PROFILED_PIPE, (stage, params.tile, ring if stage == fwd_st else None)),
+                      "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, ring if stage == fwd_st else None)),
                       "ms": st[stage],
                       "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
     E = step.n * step.V
@@ -400,7 +402,7 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
             continue
         gbs = nbytes / (st[stage] * 1e-3) / 1e9
         out[stage] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                      "work": work, "ms": st[stage], "traffic": PROFILED_TRAFFIC.get((stage, params.tile, None)),
+                      "work": work, "ms": st[stage], "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, None)),
                       "peak_basis": f"hbm_gbs ({peak_kind})"}
     if "gs_bin_sort" in out:
         lsd = M * (12 + 24 * lsd_passes)
@@ -415,7 +417,7 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None):
                   "frac": b["achieved"] / L2_PEAK["gbs"], "work": b["work"],
                   "peak_basis": "L2 read bandwidth measured in this run (" + L2_PEAK["method"] + ")",
                   "peak_per_size": L2_PEAK["per_size"]}
-            t = PROFILED_L2.get(("gs_bin_sort", params.tile))
+            t = prof(PROFILED_L2, ("gs_bin_sort", params.tile))
             if t is not None:
                 l2["traffic"] = t
                 l2["traffic_frac"] = t / (b["ms"] * 1e-3) / 1e9 / L2_PEAK["gbs"]
@@ -508,7 +510,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
     views = len(cams)
-    roof = stage_rooflines(step, st, pairs, params) if st else None
+    roof = stage_rooflines(step, st, pairs, params, profiled=False) if st else None
     return {"workload": "batched window: 8 keyframes (4x 640x480, 2x 752x480, 2x 1280x1024), 500k Gaussians",
             "roofline": roof,
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
