@@ -91,8 +91,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
     return r;
 }
 
-__global__ void __launch_bounds__(kBinThreads) k_bin_zero(uint32_t* __restrict__ cnt, int64_t words) {
+__global__ void __launch_bounds__(kBinThreads) k_bin_zero(uint32_t* __restrict__ cnt, int64_t words,
+                                                         uint32_t* __restrict__ sort_ctrs) {
     pdl_enter();
+    if (blockIdx.x == 0 && threadIdx.x < 4) sort_ctrs[threadIdx.x] = 0u;
     for (int64_t t = (int64_t)blockIdx.x * kBinThreads + threadIdx.x; t < words; t += (int64_t)gridDim.x * kBinThreads)
         cnt[t] = 0u;
 }
@@ -175,13 +177,22 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_stripes(uint32_t* __restric
 // One CTA: ranges[t] = [start, start + count) of every tile with keys (both
 // clamped to the capacity, so that no reader of the ranges leaves the key
 // buffers after an overflow) and (0, 0) for an empty tile, cnt[t] = start (the
-// tile's first slot for the scatter), M, the overflow flag.
+// tile's first slot for the scatter), M, the overflow flag; and the work lists
+// of the per-tile sort: the tiles of more than kSmallCap keys (sorted by a whole
+// CTA) and the others with keys (sorted by a group), in no particular order,
+// with their lengths in sort_ctrs[0], sort_ctrs[1].
 __global__ void __launch_bounds__(kScanThreads) k_bin_offsets(uint32_t* __restrict__ cnt, int total_tiles,
                                                              uint2* __restrict__ ranges,
                                                              uint32_t* __restrict__ num_keys, int64_t capacity,
-                                                             int32_t* __restrict__ status) {
+                                                             int32_t* __restrict__ status,
+                                                             uint32_t* __restrict__ big_list,
+                                                             uint32_t* __restrict__ small_list,
+                                                             uint32_t* __restrict__ sort_ctrs) {
     __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_nbig, s_nsmall;
     pdl_enter();
+    if (threadIdx.x == 0) s_nbig = s_nsmall = 0u;
+    const int lane = threadIdx.x & 31;
     const uint32_t cap = (uint32_t)capacity;     // < 2^32 (host check)
     uint32_t carry = 0;
     for (int base = 0; base < total_tiles; base += kScanThreads) {
@@ -189,11 +200,31 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_offsets(uint32_t* __restri
         const uint32_t c = t < total_tiles ? cnt[t] : 0u;
         uint32_t total;
         const uint32_t st = carry + block_exclusive_scan<kScanThreads>(c, &total, s_warp);
+        uint32_t len = 0;                                   // the tile's length as the sort sees it
         if (t < total_tiles) {
-            ranges[t] = c > 0 ? make_uint2(min(st, cap), min(st + c, cap)) : make_uint2(0u, 0u);   // (0, 0): empty
+            const uint2 rg = c > 0 ? make_uint2(min(st, cap), min(st + c, cap)) : make_uint2(0u, 0u);   // (0, 0): empty
+            ranges[t] = rg;
             cnt[t] = st;
+            len = rg.y - rg.x;
         }
         carry += total;
+        const bool big = len > (uint32_t)kSmallCap, small = len > 0 && !big;
+        const uint32_t bb = __ballot_sync(0xffffffffu, big), sb = __ballot_sync(0xffffffffu, small);
+        uint32_t ob = 0, os = 0;
+        if (lane == 0) {
+            if (bb) ob = atomicAdd(&s_nbig, (uint32_t)__popc(bb));
+            if (sb) os = atomicAdd(&s_nsmall, (uint32_t)__popc(sb));
+        }
+        ob = __shfl_sync(0xffffffffu, ob, 0);
+        os = __shfl_sync(0xffffffffu, os, 0);
+        const uint32_t below = lanemask_lt();
+        if (big) big_list[ob + __popc(bb & below)] = (uint32_t)t;
+        if (small) small_list[os + __popc(sb & below)] = (uint32_t)t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sort_ctrs[0] = s_nbig;
+        sort_ctrs[1] = s_nsmall;
     }
     if (threadIdx.x == 0) {
         *num_keys = carry;
@@ -378,22 +409,34 @@ __device__ __forceinline__ void sort_cta_tile(uint64_t* __restrict__ seg, uint32
     }
 }
 
-// Two passes over the tiles (grid-stride): first each CTA sorts the tiles of
-// more than kSmallCap keys with all its threads (shared memory up to kSegCap
-// keys, the radix path above), then each of its groups sorts tiles of at most
-// kSmallCap keys on its own.  The long sorts start first; every stage of a sort
-// is one compare-exchange per thread (two for the largest shared-memory tiles).
+// Two passes over the work lists of k_bin_offsets, each claimed dynamically
+// with an atomic counter (sort_ctrs[2], [3], zeroed by k_bin_zero), so that the
+// large tiles, which cluster in the image, spread over all CTAs: first each CTA
+// claims tiles of more than kSmallCap keys and sorts them with all its threads
+// (shared memory up to kSegCap keys, the radix path above), then each of its
+// groups claims tiles of at most kSmallCap keys and sorts them on its own.  Every
+// stage of a sort is one compare-exchange per thread (two for the largest
+// shared-memory tiles).
 __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                               uint64_t* __restrict__ alt,
-                                                              const uint2* __restrict__ ranges, int total_tiles,
-                                                              int ebits) {
+                                                              const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ big_list,
+                                                              const uint32_t* __restrict__ small_list,
+                                                              uint32_t* __restrict__ sort_ctrs, int ebits) {
     __shared__ SortSmem sm;
+    __shared__ uint32_t s_claim[1 + kGroups];
     pdl_enter();
     const int tid = threadIdx.x, g = tid / kGroup;
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const uint32_t n_big = sort_ctrs[0], n_small = sort_ctrs[1];
+    for (;;) {
+        if (tid == 0) s_claim[0] = atomicAdd(&sort_ctrs[2], 1u);
+        __syncthreads();
+        const uint32_t r = s_claim[0];
+        __syncthreads();                        // read by every thread before the next claim
+        if (r >= n_big) break;
+        const uint32_t t = big_list[r];
         const uint2 rg = ranges[t];
         const int n = (int)(rg.y - rg.x);
-        if (n <= kSmallCap) continue;
         uint64_t* seg = keys + rg.x;
         uint32_t* vseg = vals + rg.x;
         const uint64_t tile_hi = (uint64_t)t << 32;
@@ -409,11 +452,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restr
         }
         __syncthreads();                        // shared memory is reused by the next tile
     }
-    const int ggroups = gridDim.x * kGroups;
-    for (int t = blockIdx.x * kGroups + g; t < total_tiles; t += ggroups) {
+    for (;;) {
+        if ((tid & (kGroup - 1)) == 0) s_claim[1 + g] = atomicAdd(&sort_ctrs[3], 1u);
+        group_sync(g);
+        const uint32_t r = s_claim[1 + g];
+        group_sync(g);
+        if (r >= n_small) break;
+        const uint32_t t = small_list[r];
         const uint2 rg = ranges[t];
-        const int n = (int)(rg.y - rg.x);
-        if (n > 0 && n <= kSmallCap) sort_group_tile(keys + rg.x, vals + rg.x, n, (uint64_t)t << 32, sm.group_keys[g], g);
+        sort_group_tile(keys + rg.x, vals + rg.x, (int)(rg.y - rg.x), (uint64_t)t << 32, sm.group_keys[g], g);
     }
 }
 
@@ -429,15 +476,17 @@ SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
 // Workspace layout of launch_bin_sort (offsets in bytes, 256-byte aligned):
 //   stripe counters / cursors : kStripes x total_tiles u32 (stripe-major)
 //   tile totals / starts      : total_tiles u32
+//   sort work lists           : 2 x total_tiles u32 (large tiles, small tiles) + 4 u32 counters
 //   composites (alt)          : capacity u64 (the radix path's second buffer)
 static size_t ws_stripes(int32_t total_tiles) {
     return align_up(sizeof(uint32_t) * (size_t)kStripes * (size_t)total_tiles, 256);
 }
 static size_t ws_totals(int32_t total_tiles) { return align_up(sizeof(uint32_t) * (size_t)(total_tiles + 1), 256); }
+static size_t ws_lists(int32_t total_tiles) { return align_up(sizeof(uint32_t) * (2 * (size_t)total_tiles + 4), 256); }
 
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles) {
     (void)n_entries;
-    return ws_stripes(total_tiles) + ws_totals(total_tiles) +
+    return ws_stripes(total_tiles) + ws_totals(total_tiles) + ws_lists(total_tiles) +
            align_up(sizeof(uint64_t) * (size_t)(capacity > 0 ? capacity : 1), 256);
 }
 
@@ -451,6 +500,10 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     p += ws_stripes(T);
     uint32_t* totals = reinterpret_cast<uint32_t*>(p);
     p += ws_totals(T);
+    uint32_t* big_list = reinterpret_cast<uint32_t*>(p);
+    uint32_t* small_list = big_list + T;
+    uint32_t* sort_ctrs = small_list + T;
+    p += ws_lists(T);
     uint64_t* alt = reinterpret_cast<uint64_t*>(p);
 
     cudaError_t err = cudaSuccess;
@@ -466,7 +519,7 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     const float4* rgbd = reinterpret_cast<const float4*>(pr.rgbd);
     const int64_t words = (int64_t)kStripes * T;
     const int nb_zero = (int)(ceil_div(words, kBinThreads) < 4096 ? ceil_div(words, kBinThreads) : 4096);
-    err = launch_pdl(k_bin_zero, nb_zero, kBinThreads, 0, s, stripes, words);
+    err = launch_pdl(k_bin_zero, nb_zero, kBinThreads, 0, s, stripes, words, sort_ctrs);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_count, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, E, n, views, stripes);
     if (err == cudaSuccess)
@@ -474,7 +527,7 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
                          totals);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_offsets, 1, kScanThreads, 0, s, totals, T, reinterpret_cast<uint2*>(bins.ranges),
-                         bins.num_keys, cap, bins.status);
+                         bins.num_keys, cap, bins.status, big_list, small_list, sort_ctrs);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_scatter, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, rgbd, E, n, views,
                          totals, stripes, cap, bins.keys);
@@ -486,7 +539,8 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
         const int64_t full = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         const int grid = (int)(T < full ? T : full);
         err = launch_pdl(k_tile_sort, grid, kSortThreads, 0, s, bins.keys, bins.vals, alt,
-                         reinterpret_cast<const uint2*>(bins.ranges), T, ebits);
+                         reinterpret_cast<const uint2*>(bins.ranges), (const uint32_t*)big_list,
+                         (const uint32_t*)small_list, sort_ctrs, ebits);
     }
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
