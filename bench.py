@@ -78,7 +78,7 @@ PROFILED_TRAFFIC = {("gs_project", 16, None): 11.30e6, ("gs_bin_sort", 16, None)
                     ("gs_adam_step", 16, None): 44.83e6}
 # L2 bytes (lts__t_bytes.sum) per launch of the binning stage's six kernels, from
 # the same kind of capture (profiles/launch_list_640x480_200k.md).
-PROFILED_L2 = {("gs_bin_sort", 16): 92.1e6}
+PROFILED_L2 = {("gs_bin_sort", 16): 90.2e6}
 PROFILED_PIPE = {
     ("gs_render_fwd_loss", 16, False): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
                                        "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
