@@ -70,21 +70,22 @@ ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # + dram__bytes_write.sum per launch of each stage's kernels (cold cache), and
 # the binding pipe of the rasterisers (profiles/k_render_{fwd,bwd}_640x480_200k.md).
 # None where the kernel changed after the capture.
-# Keyed by (stage, tile, ring) for the forward (its staging variant) and
-# (stage, tile, None) for the others.
-PROFILED_TRAFFIC = {("gs_project", 16, None): 11.30e6, ("gs_bin_sort", 16, None): 14.50e6,
-                    ("gs_render_fwd_loss", 16, False): 14.25e6,
-                    ("gs_render_bwd_raster_loss", 16, None): 27.30e6, ("gs_project_bwd", 16, None): 16.41e6,
-                    ("gs_adam_step", 16, None): 44.83e6}
-# L2 bytes (lts__t_bytes.sum) per launch of the binning stage's six kernels, from
+# Keyed by (stage, tile, ring, block_masks) for the forward (its staging variant)
+# and (stage, tile, None, block_masks) for the others.
+PROFILED_TRAFFIC = {("gs_project", 16, None, 0): 11.30e6, ("gs_bin_sort", 16, None, 0): 14.50e6,
+                    ("gs_render_fwd_loss", 16, False, 0): 14.25e6,
+                    ("gs_render_bwd_raster_loss", 16, None, 0): 27.30e6, ("gs_project_bwd", 16, None, 0): 16.41e6,
+                    ("gs_adam_step", 16, None, 0): 44.83e6}
+# L2 bytes (lts__t_bytes.sum) per launch of the binning stage's kernels, from
 # the same kind of capture (profiles/launch_list_640x480_200k.md).
-PROFILED_L2 = {("gs_bin_sort", 16): 90.2e6}
+PROFILED_L2 = {("gs_bin_sort", 16, 0): 90.2e6}
 PROFILED_PIPE = {
-    ("gs_render_fwd_loss", 16, False): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
-                                       "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
-                                       "XU (ex2) 9.4 %",
-    ("gs_render_bwd_raster_loss", 16, None): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, "
-                                             "FMA 36.2 %, LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the launch"}
+    ("gs_render_fwd_loss", 16, False, 0): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
+                                          "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
+                                          "XU (ex2) 9.4 %",
+    ("gs_render_bwd_raster_loss", 16, None, 0): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, "
+                                                "FMA 36.2 %, LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the "
+                                                "launch"}
 
 
 def _peaks():
@@ -107,14 +108,18 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
+        self.start_at = 0
+        self.after = False
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=5.0)          # nvidia-smi is up before the timed region starts
         except Exception:
             self.proc = None
         return self
@@ -122,9 +127,21 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
+
+    def mark(self):
+        """Start of the timed region: samples before it are dropped."""
+        self.start_at = len(self.lines)
 
     def __exit__(self, *a):
         if self.proc is not None:
+            if len(self.lines) <= self.start_at:
+                # a timed region shorter than the sampling period: keep the first
+                # sample taken right after it (noted in the summary)
+                t0 = time.time()
+                while len(self.lines) <= self.start_at and time.time() - t0 < 0.5:
+                    time.sleep(0.005)
+                self.after = True
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -134,7 +151,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.start_at:]:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -147,13 +164,16 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        if self.after:
+            out["note"] = "timed region shorter than the 20 ms sampling period: sample taken just after it"
+        return out
 
 
-def build_step(device, g, gt, cams, candidates=(8, 16, 32), stages=(2, 3)):
+def build_step(device, g, gt, cams, candidates=(8, 16, 32), stages=(2, 3), masks=(1, 0)):
     """Target images of the perturbed map (input preparation, not timed), then a
-    mapping step on the map with the tile size and the forward's splat staging
-    autotuned over `candidates` x `stages`."""
+    mapping step on the map with the tile size, the forward's splat staging and
+    the block masks autotuned over `candidates` x `stages` x `masks`."""
     import torch
     from paper_2512_02293_gb300 import gs as G
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep, autotune_tile
@@ -167,7 +187,7 @@ def build_step(device, g, gt, cams, candidates=(8, 16, 32), stages=(2, 3)):
     tc = tstep.img.color.clone(); td = tstep.img.depth.clone()
     del tstep
     gd = G.Gaussians.from_numpy(g, device)
-    params, tune = autotune_tile(gd, cams, tc, td, params, mp, candidates=candidates, stages=stages)
+    params, tune = autotune_tile(gd, cams, tc, td, params, mp, candidates=candidates, stages=stages, masks=masks)
     step = MappingStep(gd, cams, tc, td, params, mp)
     step.tune = tune
     return params, mp, step, tc, td
@@ -214,6 +234,8 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
         clk.__enter__()
     try:
         torch.cuda.synchronize()
+        if clk:
+            clk.mark()
         for _ in range(steps):
             restore()
             flush()
@@ -248,14 +270,15 @@ def bwd_ctas_per_sm(step, tile) -> int:
 
 def launches_per_step(step) -> int:
     """Kernels of ours per iteration: project 1; bin/sort 6 (count zeroing, striped
-    tile counts, stripe prefixes, tile offsets, scatter, per-tile sort); render 1 (with the fused
+    tile counts, stripe prefixes, tile offsets and work lists, scatter, per-tile
+    sort) + 1 for the block masks; render 1 (with the fused
     loss); loss (unfused only): accumulator zeroing 1 + 2; backward: gradient
     zeroing 1 + block order 1 (fused, few blocks per SM) + raster 1, pose/iso
     zeroing 1 + projection backward 1; Adam 1."""
     tile = step.params.tile
     items = step.total_tiles * (tile // 8) * (tile // 4)
     order = 1 if step.fused_loss and items <= 256 * 152 and items <= 65536 else 0   # k_item_order
-    return 1 + 6 + 1 + (0 if step.fused_loss else 3) + 4 + order + 1
+    return 1 + 6 + int(step.params.block_masks) + 1 + (0 if step.fused_loss else 3) + 4 + order + 1
 
 
 def raster_stages(step):
@@ -376,8 +399,10 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
                       "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops (a multiply-add as one)",
                       "flop": {"achieved": ach_f, "peak": flop_peak, "unit": "TFLOP/s FP32", "frac": ach_f / flop_peak,
                                "work": f"{pairs} pairs x {flop} FLOPs (a multiply-add as two)"},
-                      "binding_pipe": prof(PROFILED_PIPE, (stage, params.tile, ring if stage == fwd_st else None)),
-                      "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, ring if stage == fwd_st else None)),
+                      "binding_pipe": prof(PROFILED_PIPE, (stage, params.tile, ring if stage == fwd_st else None,
+                                                           params.block_masks)),
+                      "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, ring if stage == fwd_st else None,
+                                                         params.block_masks)),
                       "ms": st[stage],
                       "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)"}
     E = step.n * step.V
@@ -402,7 +427,8 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
             continue
         gbs = nbytes / (st[stage] * 1e-3) / 1e9
         out[stage] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                      "work": work, "ms": st[stage], "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, None)),
+                      "work": work, "ms": st[stage],
+                      "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, None, params.block_masks)),
                       "peak_basis": f"hbm_gbs ({peak_kind})"}
     if "gs_bin_sort" in out:
         lsd = M * (12 + 24 * lsd_passes)
@@ -417,7 +443,7 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
                   "frac": b["achieved"] / L2_PEAK["gbs"], "work": b["work"],
                   "peak_basis": "L2 read bandwidth measured in this run (" + L2_PEAK["method"] + ")",
                   "peak_per_size": L2_PEAK["per_size"]}
-            t = prof(PROFILED_L2, ("gs_bin_sort", params.tile))
+            t = prof(PROFILED_L2, ("gs_bin_sort", params.tile, params.block_masks))
             if t is not None:
                 l2["traffic"] = t
                 l2["traffic_frac"] = t / (b["ms"] * 1e-3) / 1e9 / L2_PEAK["gbs"]
@@ -505,7 +531,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
     iteration one CUDA graph, tile size autotuned."""
     from paper_2512_02293_gb300 import synth
     g, gt, cams = synth.cfg3_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, cams, args.tiles, args.stages)
+    params, mp, step, tc, td = build_step(device, g, gt, cams, args.tiles, args.stages, args.masks)
     steps = max(10, args.steps // 4)
     times, st, pairs, _ = timed_run(step, steps, args.warmup, flush, dist)
     rate, total_ms = whole_job_rate(sum(times), steps, world, dist, device)
@@ -515,7 +541,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
             "roofline": roof,
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
             "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
-            "tile": params.tile, "splat_stages": params.splat_stages,
+            "tile": params.tile, "splat_stages": params.splat_stages, "block_masks": params.block_masks,
             "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
             "pixels_per_iter": step.total_pixels, "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
@@ -972,6 +998,9 @@ def main():
                     help="fix the tile size instead of autotuning over {8, 16, 32}")
     ap.add_argument("--splat-stages", type=int, choices=[2, 3], default=None,
                     help="fix the forward rasteriser's splat staging instead of autotuning over {2, 3}")
+    ap.add_argument("--block-masks", type=int, choices=[0, 1], default=None,
+                    help="fix the binning's pixel-block masks (1) or the rasterisers' own test (0) instead of "
+                         "autotuning")
     ap.add_argument("--only", choices=["loop_closure", "pose_refinement", "bundle_adjustment", "keyframe_insertion",
                                        "mlp_kernels", "final_colour_refinement"],
                     default=None, help="run one extra section alone and print its line (for profiling runs)")
@@ -979,6 +1008,7 @@ def main():
     args = ap.parse_args()
     args.tiles = (args.tile,) if args.tile else (8, 16, 32)
     args.stages = (args.splat_stages,) if args.splat_stages else (2, 3)
+    args.masks = (args.block_masks,) if args.block_masks is not None else (1, 0)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -1008,7 +1038,7 @@ def main():
 
     from paper_2512_02293_gb300 import synth
     g, gt, cam = synth.cfg2_problem()
-    params, mp, step, tc, td = build_step(device, g, gt, [cam], args.tiles, args.stages)
+    params, mp, step, tc, td = build_step(device, g, gt, [cam], args.tiles, args.stages, args.masks)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, device=device, dtype=torch.float32)
     flush = lambda: flush_buf.fill_(1.0)
     times, st, pairs, clocks = timed_run(step, args.steps, args.warmup, flush, dist, local)
@@ -1085,7 +1115,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480",
                        "tile": params.tile, "splat_stages": params.splat_stages,
-            "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
+                       "block_masks": params.block_masks,
+                       "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
                        "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",
                        "per_step_state": "map and Adam state restored before every timed step (identical work per step)",

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 4
+#define GS_ABI_VERSION 5
 #define GS_MAX_VIEWS 32
 
 typedef enum gs_status {
@@ -88,6 +88,12 @@ typedef struct gs_render_params {
                                  shared-memory ring); 0: the library chooses (3 when a
                                  launch has at most 256 pixel blocks per SM, else 2).
                                  Results do not depend on it (0) */
+    int32_t block_masks;      /* 1: gs_bin_sort writes gs_bins.masks and the
+                                 rasterisers read them instead of testing every list
+                                 entry against their pixel block; 0: no masks, the
+                                 rasterisers test.  The render calls must be given
+                                 the value the gs_bin_sort call that made `bins` was
+                                 given.  Results do not depend on it (1) */
 } gs_render_params;
 
 /* The Gaussian map G (Sec. 3.3 "Preliminary"), structure of arrays, device. */
@@ -121,6 +127,15 @@ typedef struct gs_bins {
                                  work counters of the persistent rasterisers: zero
                                  before the first render call, and every render
                                  launch leaves them zero */
+    uint32_t* masks;          /* [key_capacity] per key, bit b: the splat can reach
+                                 pixel block b of its tile (8 x 4 pixel blocks,
+                                 row-major within the tile; tile / 8 x tile / 4
+                                 bits): its weight reaches 0.99 alpha_min somewhere
+                                 in the block's box of pixel centres (the
+                                 rasterisers' own culling test, as a conservative
+                                 superset); written by gs_bin_sort and read by the
+                                 rasterisers when gs_render_params.block_masks is
+                                 set */
 } gs_bins;
 
 /* Rendered images and the per-pixel checkpoint the backward pass uses. */

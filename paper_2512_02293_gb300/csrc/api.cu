@@ -61,6 +61,7 @@ RenderConsts make_consts(const gs_render_params* p) {
     c.bg[0] = p->bg[0]; c.bg[1] = p->bg[1]; c.bg[2] = p->bg[2];
     c.sh_degree = p->sh_degree;
     c.splat_stages = p->splat_stages;
+    c.block_masks = p->block_masks;
     return c;
 }
 
@@ -69,6 +70,7 @@ static bool params_ok(const gs_render_params* p) {
     if (p->tile != 8 && p->tile != 16 && p->tile != 32) return false;
     if (p->sh_degree != 0 && p->sh_degree != 3) return false;
     if (p->splat_stages != 0 && p->splat_stages != 2 && p->splat_stages != 3) return false;
+    if (p->block_masks != 0 && p->block_masks != 1) return false;
     if (!(p->near_plane > 0.f) || !isfinite(p->near_plane)) return false;
     if (!(p->alpha_min >= 0.f) || !(p->alpha_max <= 1.f) || !(p->alpha_min <= p->alpha_max)) return false;
     if (!(p->T_cut >= 0.f) || !(p->T_cut < 1.f)) return false;
@@ -102,7 +104,8 @@ static bool image_ok(const gs_image* im) {
 }
 
 static bool bins_ok(const gs_bins* b) {
-    return b != nullptr && b->keys && b->vals && b->ranges && b->num_keys && b->status && b->key_capacity >= 0 &&
+    return b != nullptr && b->keys && b->vals && b->masks && b->ranges && b->num_keys && b->status &&
+           b->key_capacity >= 0 &&
            b->key_capacity < (1ll << 32) && aligned(b->ranges, 8);
 }
 
@@ -180,7 +183,8 @@ int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, 
     if (n > 0 && !projected_ok(proj)) return GS_ERR_INVALID_ARG;
     const size_t need = bin_sort_workspace(n * n_views, bins->key_capacity, views.total_tiles);
     if (ws == nullptr || ws_bytes < need || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
-    SortPlan plan = make_sort_plan(bins->key_capacity, views.total_tiles);
+    SortPlan plan =
+        make_sort_plan(bins->key_capacity, views.total_tiles, params->tile, params->alpha_min, params->block_masks);
     return cuda_status(launch_bin_sort(*proj, n, views, plan, *bins, ws, static_cast<cudaStream_t>(stream)));
 }
 

@@ -464,12 +464,42 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restr
     }
 }
 
+// One thread per key of the sorted lists: the key's block mask (gs_bins.masks),
+// from the splat of its entry with the rasterisers' operands (mean, scaled
+// conic and opacity) and their culling test.  Keys past M (the device count,
+// clamped to the capacity) are left alone.
+template <int T>
+__global__ void __launch_bounds__(kBinThreads) k_bin_masks(const uint64_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const uint32_t* __restrict__ num_keys, int64_t capacity,
+                                                          const float2* __restrict__ xy,
+                                                          const float4* __restrict__ conic_o, Views views,
+                                                          float amin, uint32_t* __restrict__ masks) {
+    pdl_enter();
+    const int64_t k = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const int64_t M = min((int64_t)*num_keys, capacity);
+    if (k >= M) return;
+    const int t = (int)(keys[k] >> 32);
+    const uint32_t e = vals[k];
+    const int v = view_of_tile(views, t);
+    const int lt = t - views.v[v].tile_base;
+    const float4 c = conic_o[e];
+    float4 q;
+    scale_conic(c.x, c.y, c.z, &q.x, &q.y, &q.z);
+    q.w = c.w;
+    masks[k] = splat_block_mask<T>(xy[e], q, lt % views.v[v].tiles_x, lt / views.v[v].tiles_x, amin);
+}
+
 }  // namespace
 
-SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles) {
+SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles, int32_t tile, float alpha_min,
+                        int32_t block_masks) {
     SortPlan p;
     p.capacity = key_capacity;
     p.total_tiles = total_tiles;
+    p.tile = tile;
+    p.alpha_min = alpha_min;
+    p.block_masks = block_masks;
     return p;
 }
 
@@ -514,6 +544,7 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     }
     int ebits = 0;
     while ((1ll << ebits) < E) ebits++;
+
     const int nb_entries = (int)ceil_div(E, kBinThreads);
     const int4* rect = reinterpret_cast<const int4*>(pr.rect);
     const float4* rgbd = reinterpret_cast<const float4*>(pr.rgbd);
@@ -541,6 +572,13 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
         err = launch_pdl(k_tile_sort, grid, kSortThreads, 0, s, bins.keys, bins.vals, alt,
                          reinterpret_cast<const uint2*>(bins.ranges), (const uint32_t*)big_list,
                          (const uint32_t*)small_list, sort_ctrs, ebits);
+    }
+    if (err == cudaSuccess && plan.block_masks) {
+        const int grid = (int)ceil_div(cap > 0 ? cap : 1, kBinThreads);
+        auto kernel = plan.tile == 8 ? k_bin_masks<8> : plan.tile == 16 ? k_bin_masks<16> : k_bin_masks<32>;
+        err = launch_pdl(kernel, grid, kBinThreads, 0, s, (const uint64_t*)bins.keys, (const uint32_t*)bins.vals,
+                         (const uint32_t*)bins.num_keys, cap, reinterpret_cast<const float2*>(pr.xy),
+                         reinterpret_cast<const float4*>(pr.conic_o), views, plan.alpha_min, bins.masks);
     }
     if (err != cudaSuccess) return err;
     return cudaGetLastError();

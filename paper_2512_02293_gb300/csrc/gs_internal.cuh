@@ -35,6 +35,7 @@ struct RenderConsts {
     float bg[3];
     int32_t sh_degree;
     int32_t splat_stages;   // 0 (library's choice), 2 or 3: see gs_render_params
+    int32_t block_masks;    // 1: the rasterisers read gs_bins.masks; 0: they test
 };
 
 // Host helpers (api.cu).
@@ -45,8 +46,12 @@ RenderConsts make_consts(const gs_render_params* p);
 struct SortPlan {
     int64_t capacity;
     int32_t total_tiles;
+    int32_t tile;          // tile size (the block masks)
+    float alpha_min;       // the rasterisers' culling threshold (the block masks)
+    int32_t block_masks;   // write gs_bins.masks
 };
-SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles);
+SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles, int32_t tile, float alpha_min,
+                        int32_t block_masks);
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles);
 
 constexpr int kGradStride = 12;                  // floats per entry of the 2D-gradient scratch
@@ -189,6 +194,88 @@ __device__ __forceinline__ float splat_power2(float qa, float qb, float qc, floa
 }
 
 __device__ __forceinline__ float splat_weight(float p2) { return ex2_approx(p2); }
+
+// View of global tile g (tile bases ascend with the view index).
+__device__ __forceinline__ int view_of_tile(const Views& views, int g) {
+    int v = 0;
+    for (int k = 1; k < views.n; k++)
+        if (g >= views.v[k].tile_base) v = k;
+    return v;
+}
+
+// Warp-level culling.  A splat is dropped from a warp's batch only if its
+// weight o exp(power) stays below alpha_min (with a 1 % margin for rounding) at
+// every pixel sample of the warp's 8 x 4 block, so dropping it changes no
+// pixel.  The maximum of the concave power over the block's sample rectangle
+// [x0, x1] x [y0, y1] lies at the mean if the mean is inside, else on an edge,
+// where it is the clamped optimum of a 1-D quadratic; p2 is power * log2(e).
+__device__ __forceinline__ float edge_max_p2(float qa, float qb, float qc, float fixed_d, float lo, float hi,
+                                             bool fixed_is_x) {
+    // fixed_is_x: dx = fixed_d, maximise over dy in [lo, hi]; else dy fixed, dx free
+    const float qf = fixed_is_x ? qa : qc, qv = fixed_is_x ? qc : qa;
+    float t = qv < 0.f ? -qb * fixed_d / (2.f * qv) : lo;   // stationary point of qv t^2 + qb f t
+    t = fminf(fmaxf(t, lo), hi);
+    return qf * fixed_d * fixed_d + qb * fixed_d * t + qv * t * t;
+}
+
+__device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4 q, float x0, float x1, float y0,
+                                                    float y1, float amin) {
+    if (m.x >= x0 && m.x <= x1 && m.y >= y0 && m.y <= y1) return true;
+    const float dx0 = x0 - m.x, dx1 = x1 - m.x, dy0 = y0 - m.y, dy1 = y1 - m.y;
+    float p = edge_max_p2(q.x, q.y, q.z, dx0, dy0, dy1, true);
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dx1, dy0, dy1, true));
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy0, dx0, dx1, false));
+    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy1, dx0, dx1, false));
+    return q.w * splat_weight(p) >= 0.99f * amin;
+}
+
+// Bit b is set when the splat (projected mean m, scaled conic and opacity q)
+// can reach pixel block b of the T x T tile (tx, ty) of its view: the blocks are
+// 8 x 4 pixels, row-major within the tile, as the rasterisers walk them.  Written
+// once per key by the binning, read by both rasterisers instead of testing.
+//
+// For a negative-definite power p2 (every conic the projection writes) p2 is
+// concave with its maximum 0 at the mean, so over a block's box of pixel centres
+// its maximum lies on the box edges that face the mean (or is 0 when the mean is
+// inside): the vertical edge at dx = clamp(0, dx0, dx1) and the horizontal edge at
+// dy = clamp(0, dy0, dy1), each maximised at its clamped stationary point (where
+// the mean is level with the box, the "edge" is a line through the box, a lower
+// bound that the other edge dominates).  The bit is set when that maximum reaches
+// log2(0.99 alpha_min / o), lowered by 0.004 against rounding, so the mask is a
+// superset of the blocks where any pixel's weight reaches 0.99 alpha_min and
+// drops nothing that blends.  Any other conic takes the rasterisers' own test.
+template <int T>
+__device__ __forceinline__ uint32_t splat_block_mask(const float2 m, const float4 q, int tx, int ty, float amin) {
+    constexpr int bw = T / 8, nb = (T / 8) * (T / 4);
+    const float thr = 0.99f * amin;
+    if (q.w < thr) return 0u;                           // o 2^p2 <= o < 0.99 alpha_min everywhere
+    const float qa = q.x, qb = q.y, qc = q.z;
+    uint32_t mask = 0;
+    if (!(qa < 0.f && qc < 0.f && 4.f * qa * qc - qb * qb > 0.f)) {
+#pragma unroll
+        for (int b = 0; b < nb; b++) {
+            const float bx0 = (float)(tx * T + (b % bw) * 8) + 0.5f;
+            const float by0 = (float)(ty * T + (b / bw) * 4) + 0.5f;
+            if (splat_reaches_block(m, q, bx0, bx0 + 7.f, by0, by0 + 3.f, amin)) mask |= 1u << b;
+        }
+        return mask;
+    }
+    const float L = __log2f(__fdividef(thr, q.w)) - 0.004f;
+    const float rx = __fdividef(-qb, 2.f * qc);         // stationary dy / dx on a vertical line
+    const float ry = __fdividef(-qb, 2.f * qa);         // stationary dx / dy on a horizontal line
+    const float ox = (float)(tx * T) + 0.5f - m.x, oy = (float)(ty * T) + 0.5f - m.y;
+#pragma unroll
+    for (int b = 0; b < nb; b++) {
+        const float dx0 = ox + (float)((b % bw) * 8), dx1 = dx0 + 7.f;
+        const float dy0 = oy + (float)((b / bw) * 4), dy1 = dy0 + 3.f;
+        const float vx = fminf(fmaxf(0.f, dx0), dx1), vy = fminf(fmaxf(0.f, dy0), dy1);
+        const float ty_ = fminf(fmaxf(rx * vx, dy0), dy1), tx_ = fminf(fmaxf(ry * vy, dx0), dx1);
+        const float pv = vx * fmaf(qa, vx, qb * ty_) + qc * ty_ * ty_;
+        const float ph = vy * fmaf(qc, vy, qb * tx_) + qa * tx_ * tx_;
+        if (fmaxf(pv, ph) >= L) mask |= 1u << b;
+    }
+    return mask;
+}
 #endif
 
 // Quaternion (w, x, y, z) of a rotation matrix (row-major), by the larger-of-

@@ -35,13 +35,6 @@
 namespace gs {
 namespace {
 
-__device__ __forceinline__ int view_of_tile(const Views& views, int g) {
-    int v = 0;
-    for (int k = 1; k < views.n; k++)
-        if (g >= views.v[k].tile_base) v = k;
-    return v;
-}
-
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
 // 4-byte asynchronous copy global -> shared (no register held while in flight)
@@ -105,32 +98,6 @@ __device__ __forceinline__ Splat load_splat(const float2* __restrict__ xy, const
     s.xy = xy[e];
     s.cd = rgbd[e];
     return s;
-}
-
-// Warp-level culling.  A splat is dropped from a warp's batch only if its
-// weight o exp(power) stays below alpha_min (with a 1 % margin for rounding) at
-// every pixel sample of the warp's 8 x 4 block, so dropping it changes no
-// pixel.  The maximum of the concave power over the block's sample rectangle
-// [x0, x1] x [y0, y1] lies at the mean if the mean is inside, else on an edge,
-// where it is the clamped optimum of a 1-D quadratic; p2 is power * log2(e).
-__device__ __forceinline__ float edge_max_p2(float qa, float qb, float qc, float fixed_d, float lo, float hi,
-                                             bool fixed_is_x) {
-    // fixed_is_x: dx = fixed_d, maximise over dy in [lo, hi]; else dy fixed, dx free
-    const float qf = fixed_is_x ? qa : qc, qv = fixed_is_x ? qc : qa;
-    float t = qv < 0.f ? -qb * fixed_d / (2.f * qv) : lo;   // stationary point of qv t^2 + qb f t
-    t = fminf(fmaxf(t, lo), hi);
-    return qf * fixed_d * fixed_d + qb * fixed_d * t + qv * t * t;
-}
-
-__device__ __forceinline__ bool splat_reaches_block(const float2 m, const float4 q, float x0, float x1, float y0,
-                                                    float y1, float amin) {
-    if (m.x >= x0 && m.x <= x1 && m.y >= y0 && m.y <= y1) return true;
-    const float dx0 = x0 - m.x, dx1 = x1 - m.x, dy0 = y0 - m.y, dy1 = y1 - m.y;
-    float p = edge_max_p2(q.x, q.y, q.z, dx0, dy0, dy1, true);
-    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dx1, dy0, dy1, true));
-    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy0, dx0, dx1, false));
-    p = fmaxf(p, edge_max_p2(q.x, q.y, q.z, dy1, dx0, dx1, false));
-    return q.w * splat_weight(p) >= 0.99f * amin;
 }
 
 // Persistent launch: kRasterThreads-thread CTAs, as many as fit on the GPU;
@@ -217,11 +184,11 @@ struct WorkQueue {
 // otherwise wait a gather latency per batch); without it one batch is in
 // flight in registers, and the smaller shared footprint leaves more L1 for the
 // splats that the warps of a tile share (a launch with many blocks per SM).
-template <int T, bool LOSS, bool RING>
+template <int T, bool LOSS, bool RING, bool MASKS>
 __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
-        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
-        gs_image img, int* __restrict__ queue, int n_items, FusedLoss fl) {
+        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ masks, const uint2* __restrict__ ranges,
+        Views views, RenderConsts rc, gs_image img, int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;     // pixel blocks per tile
     // the batch's kept splats in pairs (slots 2i, 2i + 1), so that the weights of
     // two splats are formed by packed FP32x2 operations: {-mx, -mx', -my, -my'},
@@ -294,10 +261,11 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         }
         const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
         const float2 sx2 = make_float2(sx, sx), sy2 = make_float2(sy, sy);
-        // sample rectangle of this 8 x 4 block
+        // sample rectangle of this 8 x 4 block (the culling test without block masks)
         const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f;
         const float by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
         const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
+        constexpr bool use_masks = MASKS;
         const uint2 range = ranges[g];
 
         float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
@@ -309,18 +277,32 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
         // entries of batch b + 3 into a register.  Otherwise the splats of batch
         // b + 1 and the list entries of b + 2 are in flight in registers.  Either
         // way a splat load never waits on its index.
+        // With block masks, the mask of each list position (gs_bins.masks) is in flight with its
+        // list entry; m0 is the mask of batch b, m1 (and m2 with the ring) those of the batches after.
         Splat nxt;
-        uint32_t nidx = 0;
+        uint32_t nidx = 0, m0 = 0, m1 = 0, m2 = 0;
+        const uint32_t bbit = 1u << blk;
         int slot_b = 0;                                  // ring slot of batch b
         if constexpr (RING) {
             const bool v0 = range.x + lane < range.y, v1 = range.x + 32 + lane < range.y;
             const uint32_t i0 = v0 ? vals[range.x + lane] : 0u, i1 = v1 ? vals[range.x + 32 + lane] : 0u;
+            m0 = v0 && use_masks ? masks[range.x + lane] : 0u;
+            m1 = v1 && use_masks ? masks[range.x + 32 + lane] : 0u;
             cp_async_splat(&r_xy[w][0][lane], &r_co[w][0][lane], &r_cd[w][0][lane], xy, conic_o, rgbd, i0, v0);
             cp_async_splat(&r_xy[w][1][lane], &r_co[w][1][lane], &r_cd[w][1][lane], xy, conic_o, rgbd, i1, v1);
-            nidx = range.x + 64 + lane < range.y ? vals[range.x + 64 + lane] : 0u;
+            if (range.x + 64 + lane < range.y) {
+                nidx = vals[range.x + 64 + lane];
+                if (use_masks) m2 = masks[range.x + 64 + lane];
+            }
         } else {
-            if (range.x + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
-            if (range.x + 32 + lane < range.y) nidx = vals[range.x + 32 + lane];
+            if (range.x + lane < range.y) {
+                nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
+                if (use_masks) m0 = masks[range.x + lane];
+            }
+            if (range.x + 32 + lane < range.y) {
+                nidx = vals[range.x + 32 + lane];
+                if (use_masks) m1 = masks[range.x + 32 + lane];
+            }
         }
         for (uint32_t base = range.x; base < range.y; base += 32) {
             if constexpr (RING) {
@@ -331,7 +313,9 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 nxt.q.w = c.w;
                 nxt.cd = r_cd[w][slot_b][lane];
             }
-            const bool keep = base + lane < range.y && splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin);
+            const bool keep = base + lane < range.y &&
+                              (use_masks ? (m0 & bbit) != 0u
+                                         : splat_reaches_block(nxt.xy, nxt.q, bx0, bx1, by0, by1, amin));
             const uint32_t kept = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
             if (keep) {
@@ -349,11 +333,22 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             if constexpr (RING) {   // batch b + 2 into batch b's slot (this lane has read its entry)
                 cp_async_splat(&r_xy[w][slot_b][lane], &r_co[w][slot_b][lane], &r_cd[w][slot_b][lane], xy, conic_o,
                                rgbd, nidx, base + 64 + lane < range.y);
-                nidx = base + 96 + lane < range.y ? vals[base + 96 + lane] : 0u;
+                m0 = m1;
+                m1 = m2;
+                nidx = 0u;
+                m2 = 0u;
+                if (base + 96 + lane < range.y) {
+                    nidx = vals[base + 96 + lane];
+                    if (use_masks) m2 = masks[base + 96 + lane];
+                }
                 slot_b ^= 1;
             } else {
                 if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
-                if (base + 64 + lane < range.y) nidx = vals[base + 64 + lane];
+                m0 = m1;
+                if (base + 64 + lane < range.y) {
+                    nidx = vals[base + 64 + lane];
+                    if (use_masks) m1 = masks[base + 64 + lane];
+                }
             }
             // warp-uniform loop; a lane's tests (power > 0, alpha < alpha_min, the
             // transmittance cutoff) become predicates, so the warp never diverges
@@ -569,12 +564,13 @@ __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const f
 
 // Backward of one work item (pixel block blk of tile g) by one warp, using the
 // warp's shared-memory slot (s_m .. s_c: 32 entries each).
-template <int T, bool LOSS>
+template <int T, bool LOSS, bool MASKS>
 __device__ __forceinline__ void bwd_item(
         int g, int blk, float4* s_m, float4* s_q, float4* s_cd, float4* s_c,
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
-        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, const Views& views,
-        const RenderConsts& rc, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ masks, const uint2* __restrict__ ranges,
+        const Views& views, const RenderConsts& rc, const float* __restrict__ T_final,
+        const uint32_t* __restrict__ n_contrib,
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
         const FusedLoss& fl) {
     const int lane = threadIdx.x & 31;
@@ -589,6 +585,7 @@ __device__ __forceinline__ void bwd_item(
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
     const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
     const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
+    constexpr bool use_masks = MASKS;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint2 range = ranges[g];
     const float amin = rc.alpha_min, amax = rc.alpha_max;
@@ -632,19 +629,25 @@ __device__ __forceinline__ void bwd_item(
     uint32_t lo = below(top);
     float2 n_xy = make_float2(0.f, 0.f);
     float4 n_q = make_float4(0.f, 0.f, 0.f, 0.f), n_cd = n_q, n_c = n_q;
-    uint32_t n_e = 0, nn_e = 0;
-    auto fetch = [&](uint32_t e) {
+    uint32_t n_e = 0, nn_e = 0, n_m = 0, nn_m = 0;    // list entries and their block masks
+    const uint32_t bbit = 1u << blk;
+    auto fetch = [&](uint32_t e, uint32_t m) {
         n_e = e;
+        n_m = m;
         n_c = conic_o[e];
         scale_conic(n_c.x, n_c.y, n_c.z, &n_q.x, &n_q.y, &n_q.z);
         n_q.w = n_c.w;
         n_xy = xy[e];
         n_cd = rgbd[e];
     };
-    if (lo + lane < top) fetch(vals[lo + lane]);
-    if (lo > range.x && below(lo) + lane < lo) nn_e = vals[below(lo) + lane];
+    if (lo + lane < top) fetch(vals[lo + lane], use_masks ? masks[lo + lane] : 0u);
+    if (lo > range.x && below(lo) + lane < lo) {
+        nn_e = vals[below(lo) + lane];
+        if (use_masks) nn_m = masks[below(lo) + lane];
+    }
     for (uint32_t hi = top; hi > range.x; hi = lo, lo = below(lo)) {
-        const bool keep = lo + lane < hi && splat_reaches_block(n_xy, n_q, bx0, bx1, by0, by1, amin);
+        const bool keep = lo + lane < hi && (use_masks ? (n_m & bbit) != 0u
+                                                       : splat_reaches_block(n_xy, n_q, bx0, bx1, by0, by1, amin));
         const uint32_t kept = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
         if (keep) {
@@ -656,8 +659,11 @@ __device__ __forceinline__ void bwd_item(
         }
         __syncwarp();
         const uint32_t nlo = below(lo);
-        if (lo > range.x && nlo + lane < lo) fetch(nn_e);
-        if (nlo > range.x && below(nlo) + lane < nlo) nn_e = vals[below(nlo) + lane];
+        if (lo > range.x && nlo + lane < lo) fetch(nn_e, nn_m);
+        if (nlo > range.x && below(nlo) + lane < nlo) {
+            nn_e = vals[below(nlo) + lane];
+            if (use_masks) nn_m = masks[below(nlo) + lane];
+        }
         const int cnt = __popc(kept);
         int k = cnt - 1;
         for (; k >= 1; k -= 2) {
@@ -693,11 +699,11 @@ __device__ __forceinline__ void bwd_item(
 // Two occupancies (kCtas CTAs per SM): few work items per SM (a single 640x480
 // view: ~60) run best with 2 CTAs and 90 registers, where the deepest blocks'
 // chains are shorter; many (a keyframe window: ~900) with 3 CTAs and 80.
-template <int T, int kCtas, bool LOSS>
+template <int T, int kCtas, bool LOSS, bool MASKS>
 __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
-        const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, Views views, RenderConsts rc,
-        const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ masks, const uint2* __restrict__ ranges,
+        Views views, RenderConsts rc, const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
         int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;
@@ -710,8 +716,8 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
     WorkQueue wq(queue, n_items, LOSS && fl.order != nullptr);
     for (int raw = wq.first(lane); raw < n_items; raw = wq.next(lane)) {
         const int item = (LOSS && fl.order != nullptr) ? (int)fl.order[raw] : raw;
-        bwd_item<T, LOSS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, ranges,
-                          views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
+        bwd_item<T, LOSS, MASKS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, masks,
+                          ranges, views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
         __syncwarp();
     }
 }
@@ -809,6 +815,33 @@ void fused_loss_layout(void* ws, int32_t n_views, FusedLoss* fl) {
     fl->order = fl->item_cost + kOrderMaxItems;
 }
 
+// One tile size and mask mode of the forward launch: the fused-loss or plain
+// kernel, with one or two batches of splats in flight per warp.
+template <int TT, bool M>
+static cudaError_t fwd_tile(const float2* xy, const float4* co, const float4* cd, const gs_bins& bins,
+                            const uint2* rg, const Views& views, const RenderConsts& rc, const gs_image& img,
+                            int* queue, int sms, cudaStream_t s, const FusedLoss* fl) {
+    const int n_items = views.total_tiles * TileShape<TT>::kWarps;
+    const bool few = rc.splat_stages == 0 ? n_items <= kFewItemsPerSm * sms : rc.splat_stages == 3;
+    if (fl) {
+        const int grid = few ? persistent_grid(k_render_fwd<TT, true, true, M>, n_items)
+                             : persistent_grid(k_render_fwd<TT, true, false, M>, n_items);
+        if (grid > kFusedMaxCtas) return cudaErrorInvalidConfiguration;
+        FusedLoss f = *fl;
+        if (n_items > kOrderMaxItems) f.item_cost = f.order = nullptr;
+        return few ? launch_pdl(k_render_fwd<TT, true, true, M>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals,
+                                bins.masks, rg, views, rc, img, queue, n_items, f)
+                   : launch_pdl(k_render_fwd<TT, true, false, M>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals,
+                                bins.masks, rg, views, rc, img, queue, n_items, f);
+    }
+    const int grid = few ? persistent_grid(k_render_fwd<TT, false, true, M>, n_items)
+                         : persistent_grid(k_render_fwd<TT, false, false, M>, n_items);
+    return few ? launch_pdl(k_render_fwd<TT, false, true, M>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals,
+                            bins.masks, rg, views, rc, img, queue, n_items, FusedLoss{})
+               : launch_pdl(k_render_fwd<TT, false, false, M>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals,
+                            bins.masks, rg, views, rc, img, queue, n_items, FusedLoss{});
+}
+
 cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const Views& views,
                               const RenderConsts& rc, const gs_image& img, cudaStream_t s, const FusedLoss* fl) {
     if (views.total_tiles == 0) return cudaSuccess;
@@ -821,35 +854,15 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int pick = rc.block_masks ? 1 : 0;
+#define ARGS_FWD xy, co, cd, bins, rg, views, rc, img, queue, sms, s, fl
     switch (rc.tile) {
-#define GS_FWD_LAUNCH(TT, L, R, F)                                                                     \
-    launch_pdl(k_render_fwd<TT, L, R>, grid, kRasterThreads, 0, s, xy, co, cd, bins.vals, rg, views, rc, img, \
-               queue, n_items, F)
-#define GS_FWD(TT)                                                                                     \
-    case TT: {                                                                                         \
-        const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
-        const bool few = rc.splat_stages == 0 ? n_items <= kFewItemsPerSm * sms : rc.splat_stages == 3; \
-        if (fl) {                                                                                      \
-            const int grid = few ? persistent_grid(k_render_fwd<TT, true, true>, n_items)             \
-                                 : persistent_grid(k_render_fwd<TT, true, false>, n_items);           \
-            if (grid > kFusedMaxCtas) return cudaErrorInvalidConfiguration;                           \
-            FusedLoss f = *fl;                                                                         \
-            if (n_items > kOrderMaxItems) f.item_cost = f.order = nullptr;                             \
-            e = few ? GS_FWD_LAUNCH(TT, true, true, f) : GS_FWD_LAUNCH(TT, true, false, f);          \
-        } else {                                                                                       \
-            const int grid = few ? persistent_grid(k_render_fwd<TT, false, true>, n_items)            \
-                                 : persistent_grid(k_render_fwd<TT, false, false>, n_items);          \
-            e = few ? GS_FWD_LAUNCH(TT, false, true, FusedLoss{}) : GS_FWD_LAUNCH(TT, false, false, FusedLoss{}); \
-        }                                                                                              \
-        break;                                                                                         \
-    }
-        GS_FWD(8)
-        GS_FWD(16)
-        GS_FWD(32)
-#undef GS_FWD
-#undef GS_FWD_LAUNCH
+        case 8: e = pick ? fwd_tile<8, true>(ARGS_FWD) : fwd_tile<8, false>(ARGS_FWD); break;
+        case 16: e = pick ? fwd_tile<16, true>(ARGS_FWD) : fwd_tile<16, false>(ARGS_FWD); break;
+        case 32: e = pick ? fwd_tile<32, true>(ARGS_FWD) : fwd_tile<32, false>(ARGS_FWD); break;
         default: return cudaErrorInvalidValue;
     }
+#undef ARGS_FWD
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -868,9 +881,12 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-#define GS_BWD_LAUNCH(TT, C, L, F)                                                                     \
-    launch_pdl(k_render_bwd<TT, C, L>, persistent_grid(k_render_bwd<TT, C, L>, n_items), kRasterThreads, 0, s, \
-               xy, co, cd, bins.vals, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, n_items, F)
+#define GS_BWD_LAUNCH_M(TT, C, L, M, F)                                                                \
+    launch_pdl(k_render_bwd<TT, C, L, M>, persistent_grid(k_render_bwd<TT, C, L, M>, n_items), kRasterThreads, 0, \
+               s, xy, co, cd, bins.vals, bins.masks, rg, views, rc, img.T_final, img.n_contrib, dc, dd, g2d, queue, \
+               n_items, F)
+#define GS_BWD_LAUNCH(TT, C, L, F) \
+    (rc.block_masks ? GS_BWD_LAUNCH_M(TT, C, L, true, F) : GS_BWD_LAUNCH_M(TT, C, L, false, F))
     switch (rc.tile) {
 #define GS_BWD(TT)                                                                                     \
     case TT: {                                                                                         \
@@ -899,6 +915,7 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
         GS_BWD(32)
 #undef GS_BWD
 #undef GS_BWD_LAUNCH
+#undef GS_BWD_LAUNCH_M
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

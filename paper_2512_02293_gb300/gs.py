@@ -47,7 +47,7 @@ class gs_render_params(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("near_plane", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_cut", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("radius_sigma", ctypes.c_float), ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
-                ("splat_stages", ctypes.c_int32)]
+                ("splat_stages", ctypes.c_int32), ("block_masks", ctypes.c_int32)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -62,7 +62,8 @@ class gs_projected(ctypes.Structure):
 
 class gs_bins(ctypes.Structure):
     _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("key_capacity", ctypes.c_int64),
-                ("ranges", ctypes.c_void_p), ("num_keys", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+                ("ranges", ctypes.c_void_p), ("num_keys", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("masks", ctypes.c_void_p)]
 
 
 class gs_image(ctypes.Structure):
@@ -204,7 +205,7 @@ def load_library(path: str | None = None):
     lib.gs_project_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, V]
     lib.gs_project_bwd_perturbed.restype = ctypes.c_int32
     lib.gs_project_bwd_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, ctypes.c_float, V, V, V]
-    if lib.gs_abi_version() != 4:
+    if lib.gs_abi_version() != 5:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
         _lib = lib
@@ -225,11 +226,12 @@ class RenderParams:
     bg: tuple = (0.0, 0.0, 0.0)
     sh_degree: int = 0
     splat_stages: int = 0      # 0: the library chooses; 2 or 3 batches of 32 splats per forward warp
+    block_masks: int = 1       # 1: binning writes per-key pixel-block masks the rasterisers read
 
     def struct(self) -> gs_render_params:
         return gs_render_params(int(self.tile), self.near_plane, self.alpha_min, self.alpha_max, self.T_cut,
                                 self.dilation, self.radius_sigma, (ctypes.c_float * 3)(*self.bg),
-                                int(self.sh_degree), int(self.splat_stages))
+                                int(self.sh_degree), int(self.splat_stages), int(self.block_masks))
 
 
 def camera_array(cams) -> ctypes.Array:
@@ -321,13 +323,15 @@ class Bins:
     ranges: "torch.Tensor"     # int32 [total_tiles, 2]
     num_keys: "torch.Tensor"   # int32 [1]
     status: "torch.Tensor"     # int32 [4]: status word + raster work counters
+    masks: "torch.Tensor"      # int32 storage of uint32 per-key pixel-block masks
 
     @staticmethod
     def empty(capacity, total_tiles, device="cuda"):
         import torch
         i = dict(device=device, dtype=torch.int32)
         return Bins(torch.empty(max(capacity, 1), device=device, dtype=torch.int64), torch.empty(max(capacity, 1), **i),
-                    torch.zeros(total_tiles, 2, **i), torch.zeros(1, **i), torch.zeros(4, **i))
+                    torch.zeros(total_tiles, 2, **i), torch.zeros(1, **i), torch.zeros(4, **i),
+                    torch.empty(max(capacity, 1), **i))
 
     @property
     def capacity(self):
@@ -335,7 +339,7 @@ class Bins:
 
     def struct(self) -> gs_bins:
         return gs_bins(_ptr(self.keys), _ptr(self.vals), self.capacity, _ptr(self.ranges), _ptr(self.num_keys),
-                       _ptr(self.status))
+                       _ptr(self.status), _ptr(self.masks))
 
 
 @dataclass

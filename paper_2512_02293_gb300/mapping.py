@@ -280,18 +280,20 @@ class MappingStep:
 
 
 def autotune_tile(gaussians: G.Gaussians, cams, target_color, target_depth, params: G.RenderParams | None = None,
-                  mparams: MapParams | None = None, candidates=(8, 16, 32), iters: int = 10, stages=(2, 3)):
-    """Pick the tile size and the forward rasteriser's splat staging (batches of
-    32 splats a warp holds at once: 2 or 3) with the fastest graph-replayed
-    mapping iteration for this map and these views.  Every trial starts from
-    the same map and the map is restored afterwards.  Returns (best
-    RenderParams, {"tile/stages": ms})."""
+                  mparams: MapParams | None = None, candidates=(8, 16, 32), iters: int = 10, stages=(2, 3),
+                  masks=(1, 0)):
+    """Pick the tile size, the forward rasteriser's splat staging (batches of
+    32 splats a warp holds at once: 2 or 3) and whether the binning writes the
+    pixel-block masks the rasterisers read (1) or they test every list entry
+    (0), by the fastest graph-replayed mapping iteration for this map and these
+    views.  Every trial starts from the same map and the map is restored
+    afterwards.  Returns (best RenderParams, {"tile/stages/masks": ms})."""
     import dataclasses
     base = params or G.RenderParams()
     saved = [t.clone() for t in gaussians.tensors()]
     times = {}
-    for tile, st in [(t, s) for t in candidates for s in stages]:
-        p = dataclasses.replace(base, tile=tile, splat_stages=st)
+    for tile, st, bm in [(t, s, m) for t in candidates for s in stages for m in masks]:
+        p = dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm)
         step = MappingStep(gaussians, cams, target_color, target_depth, p, mparams)
         step.step()
         step.ensure_capacity()
@@ -307,10 +309,10 @@ def autotune_tile(gaussians: G.Gaussians, cams, target_color, target_depth, para
             torch.cuda.synchronize()
             ms.append(ev[0].elapsed_time(ev[1]))
         ms.sort()
-        times[f"{tile}/{st}"] = ms[len(ms) // 2]
+        times[f"{tile}/{st}/{bm}"] = ms[len(ms) // 2]
         del step
     for t, s0 in zip(gaussians.tensors(), saved):
         t.copy_(s0)
     best = min(times, key=times.get)
-    tile, st = (int(x) for x in best.split("/"))
-    return dataclasses.replace(base, tile=tile, splat_stages=st), times
+    tile, st, bm = (int(x) for x in best.split("/"))
+    return dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm), times

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gs_abi_version() == 4
+    assert lib.gs_abi_version() == 5
     assert lib.gs_status_string(0) == b"GS_OK"
     assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
     assert lib.gs_status_string(99) == b"GS_ERR_UNKNOWN"
@@ -44,9 +44,9 @@ def test_abi_version_and_status_strings(lib):
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(G.gs_camera) == 4 * 4 + 2 * 4 + 9 * 4 + 3 * 4
-    assert ctypes.sizeof(G.gs_render_params) == 4 * 12
+    assert ctypes.sizeof(G.gs_render_params) == 4 * 13
     assert ctypes.sizeof(G.gs_gaussians) == 6 * 8
-    assert ctypes.sizeof(G.gs_bins) == 6 * 8
+    assert ctypes.sizeof(G.gs_bins) == 7 * 8
     assert ctypes.sizeof(G.gs_adam_group) == 4 * 8 + 8 + 8
     # 11 pointers, (ws, bytes), (loss_ws, bytes), 2 pointers, 2 int32, 6 floats
     assert ctypes.sizeof(G.gs_mapping_step_args) == 11 * 8 + 2 * 16 + 2 * 8 + 2 * 4 + 6 * 4
@@ -158,7 +158,7 @@ def test_mapping_step_rejects_a_workspace_smaller_than_gs_workspace_size(lib):
     sort_only = lib.gs_workspace_size(0, 1, cams, ctypes.byref(p), cap)
     assert need >= 12 * 4 * n > sort_only
     g = G.gs_gaussians(V(256), V(256), V(256), V(256), V(256), n)
-    bins = G.gs_bins(V(256), V(256), cap, V(256), V(256), V(256))
+    bins = G.gs_bins(V(256), V(256), cap, V(256), V(256), V(256), V(256))
     a = G.gs_mapping_step_args()
     a.gaussians = ctypes.addressof(g)
     a.cams = ctypes.addressof(cams)
@@ -214,3 +214,13 @@ def test_l2_read_probe_rejects_bad_arguments(lib):
     assert lib.gs_l2_read_probe(buf, 0, 1, out, None) == G.GS_ERR_INVALID_ARG
     assert lib.gs_l2_read_probe(buf, 4, 0, out, None) == G.GS_ERR_INVALID_ARG
     assert lib.gs_l2_read_probe(ctypes.c_void_p(20), 4, 1, out, None) == G.GS_ERR_INVALID_ARG   # misaligned
+
+
+def test_block_masks_parameter_is_checked(lib):
+    # 1 (binning writes the pixel-block masks the rasterisers read) or 0 (they test); anything else is refused
+    cams = G.camera_array([synth.identity_camera()])
+    g0 = G.gs_gaussians(None, None, None, None, None, 0)
+    out = G.gs_projected()
+    for bm, want in ((0, 0), (1, 0), (2, 1), (-1, 1)):
+        p = G.RenderParams(block_masks=bm).struct()
+        assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == want, bm

@@ -84,6 +84,46 @@ def test_bin_sort_bit_exact(tile):
     np.testing.assert_array_equal(ranges, ranges_o)
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_sort_block_masks_are_conservative(tile):
+    """gs_bins.masks, bit b of a key: the splat can reach pixel block b of its tile
+    (8 x 4 blocks, row-major).  At every pixel centre of a block where the
+    splat's weight o exp(power), in FP64 from the same projected values, reaches
+    alpha_min, the block's bit must be set, so the rasterisers' culling drops
+    nothing that blends; and the masks do cull (some bits are clear)."""
+    g, _, cam = _problem(0)
+    params = G.RenderParams(tile=tile)
+    prs = _stage_inputs(g, [cam], params)
+    proj = projected_to_device(prs)
+    keys_o, vals_o, ranges_o = oracle_bins(prs, [cam], tile)
+    bins, _ = run_bin_sort(proj, g.n, [cam], params, capacity=len(keys_o) + 17)
+    keys, vals, _ = bins_to_numpy(bins)
+    M = len(keys_o)
+    masks = bins.masks[:M].cpu().numpy().view(np.uint32).astype(np.int64)
+    pr = prs[0]
+    t = (keys.astype(np.uint64) >> np.uint64(32)).astype(np.int64)
+    e = vals.astype(np.int64)
+    tiles_x = (cam.width + tile - 1) // tile
+    tx, ty = t % tiles_x, t // tiles_x
+    mx, my = pr["xy"][e, 0].astype(np.float64), pr["xy"][e, 1].astype(np.float64)
+    A, B, C = (pr["conic"][e, k].astype(np.float64) for k in range(3))
+    o = pr["opacity"][e].astype(np.float64)
+    bw, nb = tile // 8, (tile // 8) * (tile // 4)
+    cleared = 0
+    for b in range(nb):
+        px = (tx * tile + (b % bw) * 8)[:, None] + np.arange(8)[None, :] + 0.5      # [M, 8]
+        py = (ty * tile + (b // bw) * 4)[:, None] + np.arange(4)[None, :] + 0.5     # [M, 4]
+        dx = px[:, None, :] - mx[:, None, None]
+        dy = py[:, :, None] - my[:, None, None]
+        power = -0.5 * (A[:, None, None] * dx * dx + 2 * B[:, None, None] * dx * dy + C[:, None, None] * dy * dy)
+        reach = (o[:, None, None] * np.exp(power) >= params.alpha_min).any(axis=(1, 2))
+        bit = (masks >> b) & 1
+        assert np.all(bit[reach] == 1), (b, int((bit[reach] == 0).sum()))
+        cleared += int((bit == 0).sum())
+    assert (masks >> nb).max() == 0            # no bits past the tile's blocks
+    assert cleared > 0
+
+
 def test_bin_sort_bit_exact_many_keys_ties_and_views():
     # Synthetic projected entries over three views of uneven size: ~300k keys,
     # many equal depths (ties broken by entry index), several sort blocks.
@@ -184,10 +224,12 @@ def _compare_images(gpu, ref, what=""):
     return n_exc
 
 
+@pytest.mark.parametrize("masks", [1, 0])
 @pytest.mark.parametrize("tile,bg", [(16, (0.0, 0.0, 0.0)), (8, (0.2, 0.3, 0.4)), (32, (0.0, 0.0, 0.0))])
-def test_render_fwd_matches_oracle(tile, bg):
+def test_render_fwd_matches_oracle(tile, bg, masks):
+    """masks: the binning's pixel-block masks (1) or the rasteriser's own test (0)."""
     g, _, cam = _problem(1)
-    params = G.RenderParams(tile=tile, bg=bg)
+    params = G.RenderParams(tile=tile, bg=bg, block_masks=masks)
     prs = _stage_inputs(g, [cam], params)
     proj = projected_to_device(prs)
     m = int(sum(p["tiles"].sum() for p in prs))
@@ -374,8 +416,9 @@ def test_render_bwd_stagewise_matches_oracle(sh):
     assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
 
 
+@pytest.mark.parametrize("masks", [1, 0])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_render_bwd_deep_lists(tile):
+def test_render_bwd_deep_lists(tile, masks):
     # Thousands of faint, wide splats over the 64x48 case: front-to-back lists
     # of more than 2048 blending splats per pixel (the transmittance reaches its
     # cutoff only after thousands of splats; many batches of the backward's walk
@@ -387,7 +430,7 @@ def test_render_bwd_deep_lists(tile):
     faint = synth.GaussianMap(faint.mean, faint.quat, faint.log_scale,
                               np.full(faint.n, -6.0, np.float32), faint.color)
     both = synth.GaussianMap(*(np.concatenate([b, a]) for a, b in zip(g.arrays(), faint.arrays())))
-    params = G.RenderParams(tile=tile)
+    params = G.RenderParams(tile=tile, block_masks=masks)
     prm = prm_dict(params)
     prs = _stage_inputs(both, [cam], params)
     proj = projected_to_device(prs)
@@ -418,12 +461,13 @@ def test_render_bwd_deep_lists(tile):
     assert rel_l2(got["pose"][0], ref["pose"]) < GRAD_RTOL
 
 
+@pytest.mark.parametrize("masks", [1, 0])
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("lambdas", [(1.0, 1.0, 0.0), (0.9, 0.1, 10.0)])
-def test_full_iteration_end_to_end_matches_oracle(lambdas, fused):
+def test_full_iteration_end_to_end_matches_oracle(lambdas, fused, masks):
     from paper_2512_02293_gb300.mapping import MapParams, MappingStep
     g, gt, cam = _problem(0)
-    params = G.RenderParams()
+    params = G.RenderParams(block_masks=masks)
     cams = [cam]
     targets = _oracle_targets(gt, cams, params)
     tc, td = pack_images([t[0] for t in targets], [t[1] for t in targets])
