@@ -288,16 +288,19 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             const uint32_t i0 = v0 ? vals[range.x + lane] : 0u, i1 = v1 ? vals[range.x + 32 + lane] : 0u;
             m0 = v0 && use_masks ? masks[range.x + lane] : 0u;
             m1 = v1 && use_masks ? masks[range.x + 32 + lane] : 0u;
-            cp_async_splat(&r_xy[w][0][lane], &r_co[w][0][lane], &r_cd[w][0][lane], xy, conic_o, rgbd, i0, v0);
-            cp_async_splat(&r_xy[w][1][lane], &r_co[w][1][lane], &r_cd[w][1][lane], xy, conic_o, rgbd, i1, v1);
+            // with masks, only the splats that reach this block are gathered
+            cp_async_splat(&r_xy[w][0][lane], &r_co[w][0][lane], &r_cd[w][0][lane], xy, conic_o, rgbd, i0,
+                           v0 && (!use_masks || (m0 & bbit) != 0u));
+            cp_async_splat(&r_xy[w][1][lane], &r_co[w][1][lane], &r_cd[w][1][lane], xy, conic_o, rgbd, i1,
+                           v1 && (!use_masks || (m1 & bbit) != 0u));
             if (range.x + 64 + lane < range.y) {
                 nidx = vals[range.x + 64 + lane];
                 if (use_masks) m2 = masks[range.x + 64 + lane];
             }
         } else {
             if (range.x + lane < range.y) {
-                nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
                 if (use_masks) m0 = masks[range.x + lane];
+                if (!use_masks || (m0 & bbit) != 0u) nxt = load_splat(xy, conic_o, rgbd, vals[range.x + lane]);
             }
             if (range.x + 32 + lane < range.y) {
                 nidx = vals[range.x + 32 + lane];
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
             __syncwarp();
             if constexpr (RING) {   // batch b + 2 into batch b's slot (this lane has read its entry)
                 cp_async_splat(&r_xy[w][slot_b][lane], &r_co[w][slot_b][lane], &r_cd[w][slot_b][lane], xy, conic_o,
-                               rgbd, nidx, base + 64 + lane < range.y);
+                               rgbd, nidx, base + 64 + lane < range.y && (!use_masks || (m2 & bbit) != 0u));
                 m0 = m1;
                 m1 = m2;
                 nidx = 0u;
@@ -343,7 +346,8 @@ __global__ void __launch_bounds__(kRasterThreads, 4) k_render_fwd(
                 }
                 slot_b ^= 1;
             } else {
-                if (base + 32 + lane < range.y) nxt = load_splat(xy, conic_o, rgbd, nidx);
+                if (base + 32 + lane < range.y && (!use_masks || (m1 & bbit) != 0u))
+                    nxt = load_splat(xy, conic_o, rgbd, nidx);
                 m0 = m1;
                 if (base + 64 + lane < range.y) {
                     nidx = vals[base + 64 + lane];
@@ -634,6 +638,7 @@ __device__ __forceinline__ void bwd_item(
     auto fetch = [&](uint32_t e, uint32_t m) {
         n_e = e;
         n_m = m;
+        if (use_masks && (m & bbit) == 0u) return;     // culled by its mask: nothing to gather
         n_c = conic_o[e];
         scale_conic(n_c.x, n_c.y, n_c.z, &n_q.x, &n_q.y, &n_q.z);
         n_q.w = n_c.w;
