@@ -566,11 +566,91 @@ __device__ __forceinline__ bool bwd_pixel(BwdPix& P, float sx, float sy, const f
     return blend;
 }
 
+// A warp's kept splats of one batch in pairs (slots 2i, 2i + 1 as elements 0
+// and 1 of pair i), so that the two splats' pixel-independent operands load as
+// packed FP32x2 pairs.
+struct BwdPairs {
+    float4 nm[16];     // -mean x 0, -mean x 1, -mean y 0, -mean y 1
+    float4 qab[16];    // scaled conic qa 0, qa 1, qb 0, qb 1
+    float4 qco[16];    // qc 0, qc 1, opacity 0, opacity 1
+    float4 rg[16];     // r 0, r 1, g 0, g 1
+    float4 bz[16];     // b 0, b 1, z 0, z 1
+    float4 ab[16];     // raw conic A 0, A 1, B 0, B 1
+    float2 c[16];      // raw conic C 0, C 1
+    uint4 pe[16];      // list position 0, 1, entry 0, 1
+};
+
+// Splat 1 of pair i (the farther) and then splat 0 for one pixel: bwd_pixel
+// twice, with every operation that does not depend on the pixel's running state
+// (transmittance, colour behind) done for both splats at once by packed FP32x2
+// intrinsics, each element rounded as the scalar operation rounds it.  ga / gb
+// receive splat 1's / splat 0's gradients; returns whether each blended.
+__device__ __forceinline__ void bwd_pair(BwdPix& P, const float2 sx2, const float2 sy2, const BwdPairs& S, int i,
+                                         float amin, float amax, float (&ga)[10], float (&gb)[10], bool* b1,
+                                         bool* b0) {
+    const float4 nm = S.nm[i], qab = S.qab[i], qco = S.qco[i], rg = S.rg[i], bz = S.bz[i], ab = S.ab[i];
+    const float2 C = S.c[i];
+    const uint4 pe = S.pe[i];
+    const float2 dx = __fadd2_rn(sx2, make_float2(nm.x, nm.y)), dy = __fadd2_rn(sy2, make_float2(nm.z, nm.w));
+    const float2 u = __ffma2_rn(make_float2(qab.z, qab.w), dy, __fmul2_rn(make_float2(qab.x, qab.y), dx));
+    const float2 wq = __fmul2_rn(make_float2(qco.x, qco.y), dy);
+    const float2 p2 = __ffma2_rn(dx, u, __fmul2_rn(wq, dy));
+    const float2 G = make_float2(splat_weight(p2.x), splat_weight(p2.y));
+    const float2 araw = __fmul2_rn(make_float2(qco.z, qco.w), G);
+    const float a0 = fminf(amax, araw.x), a1 = fminf(amax, araw.y);
+    const bool bl1 = pe.y < P.np && !(p2.y > 0.f) && !(a1 < amin);
+    const bool bl0 = pe.x < P.np && !(p2.x > 0.f) && !(a0 < amin);
+    const float ac1 = bl1 ? a1 : 0.f, ac0 = bl0 ? a0 : 0.f;
+    const float2 om = __ffma2_rn(make_float2(-1.f, -1.f), make_float2(a0, a1), make_float2(1.f, 1.f));   // 1 - a
+    // the running state, splat 1 then splat 0
+    const float Tb1 = __fdividef(P.T, om.y);
+    const float T1 = bl1 ? Tb1 : P.T;
+    const float Tb0 = __fdividef(T1, om.x);
+    P.T = bl0 ? Tb0 : T1;
+    const float dr1 = rg.y - P.Sr, dg1 = rg.w - P.Sg, db1 = bz.y - P.Sb, dz1 = bz.w - P.Sd;
+    P.Sr = fmaf(ac1, dr1, P.Sr);
+    P.Sg = fmaf(ac1, dg1, P.Sg);
+    P.Sb = fmaf(ac1, db1, P.Sb);
+    P.Sd = fmaf(ac1, dz1, P.Sd);
+    const float dr0 = rg.x - P.Sr, dg0 = rg.z - P.Sg, db0 = bz.x - P.Sb, dz0 = bz.z - P.Sd;
+    P.Sr = fmaf(ac0, dr0, P.Sr);
+    P.Sg = fmaf(ac0, dg0, P.Sg);
+    P.Sb = fmaf(ac0, db0, P.Sb);
+    P.Sd = fmaf(ac0, dz0, P.Sd);
+    // gradients of both splats
+    const float2 Tb = make_float2(Tb0, Tb1);
+    const float2 w = __fmul2_rn(make_float2(ac0, ac1), Tb);
+    float2 sum = __fmul2_rn(make_float2(dr0, dr1), make_float2(P.gr, P.gr));
+    sum = __ffma2_rn(make_float2(dg0, dg1), make_float2(P.gg, P.gg), sum);
+    sum = __ffma2_rn(make_float2(db0, db1), make_float2(P.gb, P.gb), sum);
+    sum = __ffma2_rn(make_float2(dz0, dz1), make_float2(P.gd, P.gd), sum);
+    const float2 dLda = __fmul2_rn(Tb, sum);
+    const bool fr1 = bl1 && araw.y < amax, fr0 = bl0 && araw.x < amax;     // alpha not clamped
+    const float2 dpa = __fmul2_rn(dLda, make_float2(a0, a1));               // d alpha / d power = alpha
+    const float2 dpow = make_float2(fr0 ? dpa.x : 0.f, fr1 ? dpa.y : 0.f);
+    const float2 e = __fmul2_rn(dpow, dx), f = __fmul2_rn(dpow, dy);
+    const float2 A2 = make_float2(ab.x, ab.y), B2 = make_float2(ab.z, ab.w);
+    const float2 g0 = __ffma2_rn(A2, e, __fmul2_rn(B2, f));                                 // d mean x
+    const float2 g1 = __ffma2_rn(B2, e, __fmul2_rn(C, f));                                  // d mean y
+    const float2 g2 = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), e), dx);             // d A
+    const float2 g3 = __fmul2_rn(__fmul2_rn(make_float2(-1.f, -1.f), e), dy);               // d B
+    const float2 g4 = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), f), dy);             // d C
+    const float2 gG = __fmul2_rn(dLda, G);                                                   // d alpha / d o = G
+    const float2 g6 = __fmul2_rn(make_float2(P.gd, P.gd), w), g7 = __fmul2_rn(make_float2(P.gr, P.gr), w);
+    const float2 g8 = __fmul2_rn(make_float2(P.gg, P.gg), w), g9 = __fmul2_rn(make_float2(P.gb, P.gb), w);
+    ga[0] = g0.y; ga[1] = g1.y; ga[2] = g2.y; ga[3] = g3.y; ga[4] = g4.y;
+    ga[5] = fr1 ? gG.y : 0.f; ga[6] = g6.y; ga[7] = g7.y; ga[8] = g8.y; ga[9] = g9.y;
+    gb[0] = g0.x; gb[1] = g1.x; gb[2] = g2.x; gb[3] = g3.x; gb[4] = g4.x;
+    gb[5] = fr0 ? gG.x : 0.f; gb[6] = g6.x; gb[7] = g7.x; gb[8] = g8.x; gb[9] = g9.x;
+    *b1 = bl1;
+    *b0 = bl0;
+}
+
 // Backward of one work item (pixel block blk of tile g) by one warp, using the
-// warp's shared-memory slot (s_m .. s_c: 32 entries each).
+// warp's shared-memory slot S (its kept splats, in pairs).
 template <int T, bool LOSS, bool MASKS>
 __device__ __forceinline__ void bwd_item(
-        int g, int blk, float4* s_m, float4* s_q, float4* s_cd, float4* s_c,
+        int g, int blk, BwdPairs& S,
         const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
         const uint32_t* __restrict__ vals, const uint32_t* __restrict__ masks, const uint2* __restrict__ ranges,
         const Views& views, const RenderConsts& rc, const float* __restrict__ T_final,
@@ -587,6 +667,7 @@ __device__ __forceinline__ void bwd_item(
     const int px = tx * T + ox, py = ty * T + oy;
     const bool inside = px < vp.W && py < vp.H;
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    const float2 sx2 = make_float2(sx, sx), sy2 = make_float2(sy, sy);
     const float bx0 = (float)(tx * T + (blk % (T / 8)) * 8) + 0.5f, by0 = (float)(ty * T + (blk / (T / 8)) * 4) + 0.5f;
     const float bx1 = bx0 + 7.f, by1 = by0 + 3.f;
     constexpr bool use_masks = MASKS;
@@ -656,11 +737,22 @@ __device__ __forceinline__ void bwd_item(
         const uint32_t kept = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
         if (keep) {
-            const int sl = __popc(kept & lt_mask);
-            s_m[sl] = make_float4(n_xy.x, n_xy.y, __uint_as_float(lo + lane - range.x), __uint_as_float(n_e));
-            s_q[sl] = n_q;
-            s_cd[sl] = n_cd;
-            s_c[sl] = n_c;
+            const int sl = __popc(kept & lt_mask), pi = sl >> 1, h = sl & 1;
+            float* nm = reinterpret_cast<float*>(&S.nm[pi]);
+            float* qab = reinterpret_cast<float*>(&S.qab[pi]);
+            float* qco = reinterpret_cast<float*>(&S.qco[pi]);
+            float* rg = reinterpret_cast<float*>(&S.rg[pi]);
+            float* bz = reinterpret_cast<float*>(&S.bz[pi]);
+            float* ab = reinterpret_cast<float*>(&S.ab[pi]);
+            uint32_t* pe = reinterpret_cast<uint32_t*>(&S.pe[pi]);
+            nm[h] = -n_xy.x; nm[2 + h] = -n_xy.y;
+            qab[h] = n_q.x; qab[2 + h] = n_q.y;
+            qco[h] = n_q.z; qco[2 + h] = n_q.w;
+            rg[h] = n_cd.x; rg[2 + h] = n_cd.y;
+            bz[h] = n_cd.z; bz[2 + h] = n_cd.w;
+            ab[h] = n_c.x; ab[2 + h] = n_c.y;
+            reinterpret_cast<float*>(&S.c[pi])[h] = n_c.z;
+            pe[h] = lo + lane - range.x; pe[2 + h] = n_e;
         }
         __syncwarp();
         const uint32_t nlo = below(lo);
@@ -670,32 +762,36 @@ __device__ __forceinline__ void bwd_item(
             if (use_masks) nn_m = masks[below(nlo) + lane];
         }
         const int cnt = __popc(kept);
-        int k = cnt - 1;
-        for (; k >= 1; k -= 2) {
+        if (cnt & 1) {                       // the farthest kept splat alone: element 0 of the last pair
+            const int pi = cnt >> 1;
+            const float4 nm = S.nm[pi], qab = S.qab[pi], qco = S.qco[pi], rg = S.rg[pi], bz = S.bz[pi], ab = S.ab[pi];
+            const uint4 pe = S.pe[pi];
+            const float4 m = make_float4(-nm.x, -nm.z, __uint_as_float(pe.x), __uint_as_float(pe.z));
             float ga[10], gb[10];
-            const float4 ma = s_m[k], mb = s_m[k - 1];
-            const bool ca = bwd_pixel(P, sx, sy, ma, s_q[k], s_cd[k], s_c[k], amin, amax, ga);
-            const bool cb = bwd_pixel(P, sx, sy, mb, s_q[k - 1], s_cd[k - 1], s_c[k - 1], amin, amax, gb);
-            const bool anya = __any_sync(0xffffffffu, ca), anyb = __any_sync(0xffffffffu, cb);
-            if (anya || anyb) {
-                float ua, ub;
-                warp_reduce10x2(ga, gb, lane, &ua, &ub);
-                if (slot >= 0) {
-                    if (anya) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(ma.w) + col, ua);
-                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(mb.w) + col, ub);
-                }
-            }
-        }
-        if (k == 0) {
-            float ga[10], gb[10];
-            const float4 ma = s_m[0];
-            const bool ca = bwd_pixel(P, sx, sy, ma, s_q[0], s_cd[0], s_c[0], amin, amax, ga);
+            const bool ca = bwd_pixel(P, sx, sy, m, make_float4(qab.x, qab.z, qco.x, qco.z),
+                                      make_float4(rg.x, rg.z, bz.x, bz.z), make_float4(ab.x, ab.z, S.c[pi].x, 0.f),
+                                      amin, amax, ga);
 #pragma unroll
             for (int r = 0; r < 10; r++) gb[r] = 0.f;
             if (__any_sync(0xffffffffu, ca)) {
                 float ua, ub;
                 warp_reduce10x2(ga, gb, lane, &ua, &ub);
-                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * __float_as_uint(ma.w) + col, ua);
+                if (slot >= 0) atomicAdd(g2d + (size_t)kGradStride * pe.z + col, ua);
+            }
+        }
+        for (int pi = (cnt >> 1) - 1; pi >= 0; pi--) {
+            float ga[10], gb[10];
+            bool ca, cb;
+            bwd_pair(P, sx2, sy2, S, pi, amin, amax, ga, gb, &ca, &cb);
+            const bool anya = __any_sync(0xffffffffu, ca), anyb = __any_sync(0xffffffffu, cb);
+            if (anya || anyb) {
+                float ua, ub;
+                warp_reduce10x2(ga, gb, lane, &ua, &ub);
+                if (slot >= 0) {
+                    const uint4 pe = S.pe[pi];
+                    if (anya) atomicAdd(g2d + (size_t)kGradStride * pe.w + col, ua);
+                    if (anyb) atomicAdd(g2d + (size_t)kGradStride * pe.z + col, ub);
+                }
             }
         }
     }
@@ -712,16 +808,13 @@ __global__ void __launch_bounds__(kRasterThreads, kCtas) k_render_bwd(
         const float* __restrict__ dL_dcolor, const float* __restrict__ dL_ddepth, float* __restrict__ g2d,
         int* __restrict__ queue, int n_items, FusedLoss fl) {
     constexpr int W = TileShape<T>::kWarps;
-    __shared__ float4 s_m[kRasterWarps][32];      // mean x, y, list position, entry (bit patterns)
-    __shared__ float4 s_q[kRasterWarps][32];      // scaled conic + opacity
-    __shared__ float4 s_cd[kRasterWarps][32];     // r, g, b, z
-    __shared__ float4 s_c[kRasterWarps][32];      // raw conic A, B, C
+    __shared__ BwdPairs s_pairs[kRasterWarps];
     pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WorkQueue wq(queue, n_items, LOSS && fl.order != nullptr);
     for (int raw = wq.first(lane); raw < n_items; raw = wq.next(lane)) {
         const int item = (LOSS && fl.order != nullptr) ? (int)fl.order[raw] : raw;
-        bwd_item<T, LOSS, MASKS>(item / W, item % W, s_m[w], s_q[w], s_cd[w], s_c[w], xy, conic_o, rgbd, vals, masks,
+        bwd_item<T, LOSS, MASKS>(item / W, item % W, s_pairs[w], xy, conic_o, rgbd, vals, masks,
                           ranges, views, rc, T_final, n_contrib, dL_dcolor, dL_ddepth, g2d, fl);
         __syncwarp();
     }
