@@ -66,25 +66,31 @@ BIN_BYTES_PER_ENTRY, BIN_BYTES_PER_KEY, BIN_BYTES_PER_TILE = 56, 28, 528
 PROJECT_BWD_BYTES_PER_GAUSSIAN, PROJECT_BWD_BYTES_PER_ENTRY = 56 + 56, 48
 ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # From one ncu capture of one iteration of this workload (640x480, 200k
-# Gaussians, tile 16; profiles/launch_list_640x480_200k.md): dram__bytes_read.sum
-# + dram__bytes_write.sum per launch of each stage's kernels (cold cache), and
-# the binding pipe of the rasterisers (profiles/k_render_{fwd,bwd}_640x480_200k.md).
-# None where the kernel changed after the capture.
+# Gaussians, tile 16): dram__bytes_read.sum + dram__bytes_write.sum per launch
+# of each stage's kernels (cold cache), and the binding pipe of the rasterisers
+# (their full-section captures).  None where the kernel changed after the
+# capture.
 # Keyed by (stage, tile, ring, block_masks) for the forward (its staging variant)
 # and (stage, tile, None, block_masks) for the others.
 PROFILED_TRAFFIC = {("gs_project", 16, None, 0): 11.30e6, ("gs_bin_sort", 16, None, 0): 14.50e6,
                     ("gs_render_fwd_loss", 16, False, 0): 14.25e6,
-                    ("gs_render_bwd_raster_loss", 16, None, 0): 27.30e6, ("gs_project_bwd", 16, None, 0): 16.41e6,
-                    ("gs_adam_step", 16, None, 0): 44.83e6}
+                    ("gs_project_bwd", 16, None, 0): 16.41e6, ("gs_adam_step", 16, None, 0): 44.83e6,
+                    ("gs_project", 16, None, 1): 11.28e6, ("gs_bin_sort", 16, None, 1): 23.69e6,
+                    ("gs_render_fwd_loss", 16, False, 1): 15.58e6,
+                    ("gs_render_bwd_raster_loss", 16, None, 1): 28.52e6, ("gs_project_bwd", 16, None, 1): 16.41e6,
+                    ("gs_adam_step", 16, None, 1): 44.82e6}
 # L2 bytes (lts__t_bytes.sum) per launch of the binning stage's kernels, from
-# the same kind of capture (profiles/launch_list_640x480_200k.md).
-PROFILED_L2 = {("gs_bin_sort", 16, 0): 90.2e6}
+# the same kind of capture.
+PROFILED_L2 = {("gs_bin_sort", 16, 0): 90.2e6, ("gs_bin_sort", 16, 1): 131.1e6}
 PROFILED_PIPE = {
     ("gs_render_fwd_loss", 16, False, 0): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
                                           "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
                                           "XU (ex2) 9.4 %",
-    ("gs_render_bwd_raster_loss", 16, None, 0): "instruction issue: 74.6 % of active cycles issue; pipes ALU 43.5 %, "
-                                                "FMA 36.2 %, LSU 36.2 %, XU (ex2, rcp) 7.0 %; SMs active 94 % of the "
+    ("gs_render_fwd_loss", 16, False, 1): "the deepest blocks' serial walks, then instruction issue: SMs active 65.3 % "
+                                          "of the launch, 63.3 % of active cycles issue; pipes ALU 44.9 %, LSU 27.5 %, "
+                                          "FMA 21.1 %, XU (ex2) 6.2 %",
+    ("gs_render_bwd_raster_loss", 16, None, 1): "instruction issue: 69.8 % of active cycles issue; pipes LSU 45.1 %, "
+                                                "ALU 44.3 %, FMA 29.2 %, XU (ex2, rcp) 5.5 %; SMs active 94 % of the "
                                                 "launch"}
 
 
@@ -366,6 +372,73 @@ def measure_l2_peak(device, total_gib=2.0):
     return L2_PEAK
 
 
+def evaluated_pairs(step, alpha_min=None) -> int:
+    """(pixel, splat) pairs the rasterisers evaluate, counted independently of
+    their kernels: for every 8 x 4 pixel block of every tile, the splats of the
+    tile's list before the block's deepest n_contrib whose weight can reach
+    0.99 alpha_min somewhere in the block's box of pixel centres (the culling test,
+    here in FP64 from the projected splats: the maximum of the concave power over
+    the box edges that face the mean), times the block's 32 lanes.  A lower bound
+    of the kernels' per-lane work: a walk also passes the positions it culls, and
+    a batch of 32 positions may run past the deepest n_contrib."""
+    import torch
+    T = step.params.tile
+    bw, bh = T // 8, T // 4
+    nb = bw * bh
+    amin = step.params.alpha_min if alpha_min is None else alpha_min
+    dev = step.device
+    M = min(step.num_keys(), step.bins.capacity)
+    if M == 0:
+        return 0
+    tile = step.bins.keys[:M] >> 32
+    ent = step.bins.vals[:M].to(torch.int64)
+    ranges = step.bins.ranges.to(torch.int64)
+    pos = torch.arange(M, device=dev) - ranges[tile, 0]
+    # per view: tiles across, first global tile, first pixel
+    tx_v = [(int(c.width) + T - 1) // T for c in step.cams]
+    ty_v = [(int(c.height) + T - 1) // T for c in step.cams]
+    tbase = [0]
+    pbase = [0]
+    for c, a, b in zip(step.cams, tx_v, ty_v):
+        tbase.append(tbase[-1] + a * b)
+        pbase.append(pbase[-1] + int(c.width) * int(c.height))
+    # deepest n_contrib of every block: [total_tiles, nb]
+    nc = step.img.n_contrib.to(torch.int64)
+    maxnc = torch.zeros(tbase[-1], nb, device=dev, dtype=torch.int64)
+    for v, c in enumerate(step.cams):
+        W, H = int(c.width), int(c.height)
+        img = torch.zeros(ty_v[v] * T, tx_v[v] * T, device=dev, dtype=torch.int64)
+        img[:H, :W] = nc[pbase[v]:pbase[v] + W * H].view(H, W)
+        blk = img.view(ty_v[v], bh, 4, tx_v[v], bw, 8).amax(dim=(2, 5))          # [ty, bh, tx, bw]
+        maxnc[tbase[v]:tbase[v + 1]] = blk.permute(0, 2, 1, 3).reshape(-1, nb)
+    tb = torch.tensor(tbase[:-1], device=dev)
+    txs = torch.tensor(tx_v, device=dev)
+    v = torch.searchsorted(tb, tile, right=True) - 1
+    lt = tile - tb[v]
+    gx, gy = (lt % txs[v]).double() * T, (lt // txs[v]).double() * T
+    xy = step.proj.xy[ent].double()
+    co = step.proj.conic_o[ent].double()
+    A, B, C, o = co[:, 0], co[:, 1], co[:, 2], co[:, 3]
+    qa, qb, qc = -0.5 * A, -B, -0.5 * C                   # power = qa dx^2 + qb dx dy + qc dy^2
+    L = torch.log(torch.clamp(0.99 * amin / o, min=1e-300))
+    ox, oy = gx + 0.5 - xy[:, 0], gy + 0.5 - xy[:, 1]
+    count = 0
+    for b in range(nb):
+        dx0 = ox + (b % bw) * 8
+        dx1 = dx0 + 7.0
+        dy0 = oy + (b // bw) * 4
+        dy1 = dy0 + 3.0
+        vx = torch.minimum(torch.clamp(dx0, min=0.0), dx1)
+        vy = torch.minimum(torch.clamp(dy0, min=0.0), dy1)
+        ty = torch.minimum(torch.maximum(-qb * vx / (2 * qc), dy0), dy1)
+        tx = torch.minimum(torch.maximum(-qb * vy / (2 * qa), dx0), dx1)
+        pv = qa * vx * vx + qb * vx * ty + qc * ty * ty
+        ph = qa * tx * tx + qb * tx * vy + qc * vy * vy
+        reach = (torch.maximum(pv, ph) >= L) & (o >= 0.99 * amin)
+        count += int((reach & (pos < maxnc[tile, b])).sum().item())
+    return 32 * count
+
+
 def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
     """Roofline of every stage of one iteration from its CUDA-event time in the
     instrumented graph replays: the rasterisers against the FP32 lane peak
@@ -389,16 +462,25 @@ def stage_rooflines(step, st, pairs, params, bwd_label=None, profiled=True):
                     f"per warp)",
             bwd_st: f"k_render_bwd<{params.tile}, {bwd_ctas_per_sm(step, params.tile)}, {fl}> (+ its 2D-gradient "
                     f"zero-fill{' and block ordering' if few and step.fused_loss else ''})"}
+    evald = evaluated_pairs(step)
     for stage, ops, flop in ((fwd_st, FWD_OPS_PER_PAIR, FWD_FLOP_PER_PAIR), (bwd_st, BWD_OPS_PER_PAIR,
                                                                             BWD_FLOP_PER_PAIR)):
         sec = st[stage] * 1e-3
         ach = pairs * ops / sec / 1e12
         ach_f = pairs * flop / sec / 1e12
+        ach_e = evald * ops / sec / 1e12
         out[stage] = {"bound": "alu", "kernel": kern[stage], "achieved": ach, "peak": lane_peak,
                       "unit": "T FP32 lane-ops/s", "frac": ach / lane_peak,
                       "work": f"{pairs} visited (pixel, splat) pairs x {ops} FP32 ops (a multiply-add as one)",
                       "flop": {"achieved": ach_f, "peak": flop_peak, "unit": "TFLOP/s FP32", "frac": ach_f / flop_peak,
                                "work": f"{pairs} pairs x {flop} FLOPs (a multiply-add as two)"},
+                      "evaluated_pairs": {
+                          "pairs": evald, "achieved": ach_e, "frac": ach_e / lane_peak,
+                          "work": f"{evald} evaluated (pixel, splat) pairs x {ops} FP32 ops",
+                          "note": "the pairs the culling keeps: each 8x4 block's list positions before its deepest "
+                                  "n_contrib whose splat can reach 0.99 alpha_min in the block, x 32 lanes, counted "
+                                  "in FP64 from the projected splats; the visited count above (sum of n_contrib) "
+                                  "includes the pairs the culling proves weightless and skips"},
                       "binding_pipe": prof(PROFILED_PIPE, (stage, params.tile, ring if stage == fwd_st else None,
                                                            params.block_masks)),
                       "traffic": prof(PROFILED_TRAFFIC, (stage, params.tile, ring if stage == fwd_st else None,
