@@ -1192,6 +1192,9 @@ def main():
         dominant = max(st, key=st.get)
         roofline = dict(stages_roof[dominant])
         roofline["dominant_stage"] = dominant
+        fwd_st, bwd_st = raster_stages(step)
+        for tag, stg in (("fwd", fwd_st), ("bwd", bwd_st)):     # both rasterisers, each with its own work and time
+            roofline[tag] = dict(stages_roof[stg], stage=stg)
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -48,7 +48,7 @@ constexpr int kSortThreads = 1024;                       // a tile-sort CTA
 constexpr int kGroup = 256;                              // threads of a small-tile group
 constexpr int kGroups = kSortThreads / kGroup;
 constexpr int kSmallCap = 2 * kGroup;                    // keys a group sorts (one pair per thread)
-constexpr int kSegCap = 4 * kSortThreads;                // keys a CTA sorts (two pairs per thread)
+constexpr int kSegCap = 4 * kSortThreads;                // keys a CTA sorts in shared memory
 constexpr int kRadixThreads = 256;                       // threads that work in the radix path
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixBits = 8;
@@ -256,8 +256,8 @@ struct RadixSmem {
     uint32_t warp[kRadixThreads / 32 + 1];
 };
 union SortSmem {
-    uint64_t group_keys[kGroups][kSmallCap];    // the groups' own sorts
-    uint64_t keys[kSegCap];                     // a CTA's sort of one larger tile
+    uint64_t group_keys[kGroups][2][kSmallCap];   // the groups' own sorts (two buffers each)
+    uint64_t keys[2][kSegCap];                    // a CTA's sort of one larger tile (two buffers)
     RadixSmem rx;
 };
 
@@ -348,62 +348,97 @@ __device__ uint64_t* seg_radix_sort(uint64_t* a, uint64_t* b, int n, int ebits, 
 }
 static_assert(kRadix == kRadixThreads, "one digit per working thread in the radix bookkeeping");
 
-// One compare-exchange stage (k, j) of a bitonic sort over s[0, P): pair q
-// is (a, a + j) with a = q with a zero bit inserted at j; the lower slot keeps
-// the smaller value where (a & k) == 0 (an ascending run), the larger elsewhere.
-__device__ __forceinline__ void bitonic_pair(uint64_t* s, int q, int j, int k) {
-    const int a = ((q & ~(j - 1)) << 1) | (q & (j - 1));
-    const uint64_t x = s[a], y = s[a + j];
-    if ((x > y) == ((a & k) == 0)) {
-        s[a] = y;
-        s[a + j] = x;
-    }
-}
-
 __device__ __forceinline__ void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" :: "r"(g + 1), "r"(kGroup) : "memory");
 }
 
-// Bitonic sort of a tile of n <= kSmallCap composites by one group of kGroup
-// threads in its shared-memory slot (P = n rounded up to a power of two,
-// padded with the largest value; at most one pair per thread and stage, a
-// stage ends with the group's own named barrier).
+// Sorts the composites s[0, P) in shared memory (P a power of two >= 32; t a
+// second buffer of P) by NT threads (tid in [0, NT)) that meet at sync():
+// each warp sorts runs of 32 in registers (a bitonic network over its lanes,
+// no barrier), then log2(P / 32) merge levels double the runs.  At each level
+// thread tid writes outputs [tid k, tid k + k) (k = P / NT, at least 1) of
+// its pair of runs: a binary search on the merge path finds how many of the
+// first outputs come from the first run, then k sequential merge steps.  The
+// composites are unique (z bits, entry), so the order is the sorted one however
+// the work is split.  Returns the buffer that holds the result.
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+template <int NT, typename Sync>
+__device__ __forceinline__ uint64_t* merge_sort_smem(uint64_t* s, uint64_t* t, int P, int tid, Sync sync) {
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int c = wid; c < P / 32; c += NT / 32) {
+        uint64_t x = s[c * 32 + lane];
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                const bool up = (lane & k) == 0, lower = (lane & j) == 0;   // k = 32: ascending
+                x = (lower == up) ? umin64(x, y) : umax64(x, y);
+            }
+        s[c * 32 + lane] = x;
+    }
+    sync();
+    uint64_t* src = s;
+    uint64_t* dst = t;
+    const int k = P >= NT ? P / NT : 1;
+    for (int r = 32; r < P; r <<= 1) {
+        const int o = tid * k;
+        if (o < P) {
+            const int pair = o / (2 * r), d = o - pair * 2 * r;
+            const uint64_t* A = src + pair * 2 * r;
+            const uint64_t* B = A + r;
+            int lo = d > r ? d - r : 0, hi = d < r ? d : r;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] < B[d - mid - 1]) lo = mid + 1;
+                else hi = mid;
+            }
+            int i = lo, j = d - lo;
+            for (int q = 0; q < k; q++) {
+                const bool take_a = i < r && (j >= r || A[i] < B[j]);
+                dst[o + q] = take_a ? A[i++] : B[j++];
+            }
+        }
+        sync();
+        uint64_t* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    return src;
+}
+
+// Merge sort of a tile of n <= kSmallCap composites by one group of kGroup
+// threads in its two shared-memory buffers (P = n rounded up to a power of two,
+// at least 32, padded with the largest value; the group's own named barrier).
 __device__ __forceinline__ void sort_group_tile(uint64_t* __restrict__ seg, uint32_t* __restrict__ vseg, int n,
-                                                uint64_t tile_hi, uint64_t* s, int g) {
+                                                uint64_t tile_hi, uint64_t* s, uint64_t* t, int g) {
     const int gt = threadIdx.x & (kGroup - 1);
-    int P = 2;
+    int P = 32;
     while (P < n) P <<= 1;
     for (int i = gt; i < P; i += kGroup) s[i] = i < n ? seg[i] : ~0ull;
     group_sync(g);
-    for (int k = 2; k <= P; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (gt < P / 2) bitonic_pair(s, gt, j, k);
-            group_sync(g);
-        }
+    const uint64_t* res = merge_sort_smem<kGroup>(s, t, P, gt, [&]() { group_sync(g); });
     for (int i = gt; i < n; i += kGroup) {
-        const uint64_t c = s[i];
+        const uint64_t c = res[i];
         seg[i] = tile_hi | (c >> 32);
         vseg[i] = (uint32_t)c;
     }
     group_sync(g);
 }
 
-// The same by the whole CTA for n <= kSegCap (at most two pairs per thread).
+// The same by the whole CTA for n <= kSegCap.
 __device__ __forceinline__ void sort_cta_tile(uint64_t* __restrict__ seg, uint32_t* __restrict__ vseg, int n,
-                                              uint64_t tile_hi, uint64_t* s) {
+                                              uint64_t tile_hi, uint64_t* s, uint64_t* t) {
     const int tid = threadIdx.x;
-    int P = 2;
+    int P = 32;
     while (P < n) P <<= 1;
     for (int i = tid; i < P; i += kSortThreads) s[i] = i < n ? seg[i] : ~0ull;
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (tid < P / 2) bitonic_pair(s, tid, j, k);
-            if (tid + kSortThreads < P / 2) bitonic_pair(s, tid + kSortThreads, j, k);
-            __syncthreads();
-        }
+    const uint64_t* res = merge_sort_smem<kSortThreads>(s, t, P, tid, []() { __syncthreads(); });
     for (int i = tid; i < n; i += kSortThreads) {
-        const uint64_t c = s[i];
+        const uint64_t c = res[i];
         seg[i] = tile_hi | (c >> 32);
         vseg[i] = (uint32_t)c;
     }
@@ -423,7 +458,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restr
                                                               const uint32_t* __restrict__ big_list,
                                                               const uint32_t* __restrict__ small_list,
                                                               uint32_t* __restrict__ sort_ctrs, int ebits) {
-    __shared__ SortSmem sm;
+    extern __shared__ __align__(16) unsigned char s_sort_raw[];   // SortSmem, dynamic (above 48 KB)
+    SortSmem& sm = *reinterpret_cast<SortSmem*>(s_sort_raw);
     __shared__ uint32_t s_claim[1 + kGroups];
     pdl_enter();
     const int tid = threadIdx.x, g = tid / kGroup;
@@ -441,7 +477,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restr
         uint32_t* vseg = vals + rg.x;
         const uint64_t tile_hi = (uint64_t)t << 32;
         if (n <= kSegCap) {
-            sort_cta_tile(seg, vseg, n, tile_hi, sm.keys);
+            sort_cta_tile(seg, vseg, n, tile_hi, sm.keys[0], sm.keys[1]);
         } else {
             const uint64_t* res = seg_radix_sort(seg, alt + rg.x, n, ebits, sm.rx);
             for (int i = tid; i < n; i += kSortThreads) {
@@ -460,7 +496,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort(uint64_t* __restr
         if (r >= n_small) break;
         const uint32_t t = small_list[r];
         const uint2 rg = ranges[t];
-        sort_group_tile(keys + rg.x, vals + rg.x, (int)(rg.y - rg.x), (uint64_t)t << 32, sm.group_keys[g], g);
+        sort_group_tile(keys + rg.x, vals + rg.x, (int)(rg.y - rg.x), (uint64_t)t << 32, sm.group_keys[g][0],
+                        sm.group_keys[g][1], g);
     }
 }
 
@@ -566,10 +603,14 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_sort, kSortThreads, 0);
+        // the sort's shared memory is above the 48 KB static limit: opt in (per
+        // device; not a stream operation, so it may run during capture)
+        err = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+        if (err != cudaSuccess) return err;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_sort, kSortThreads, sizeof(SortSmem));
         const int64_t full = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         const int grid = (int)(T < full ? T : full);
-        err = launch_pdl(k_tile_sort, grid, kSortThreads, 0, s, bins.keys, bins.vals, alt,
+        err = launch_pdl(k_tile_sort, grid, kSortThreads, sizeof(SortSmem), s, bins.keys, bins.vals, alt,
                          reinterpret_cast<const uint2*>(bins.ranges), (const uint32_t*)big_list,
                          (const uint32_t*)small_list, sort_ctrs, ebits);
     }
