@@ -110,7 +110,7 @@ __device__ __forceinline__ uint32_t covered_tile(int4 r, int tb, int tx, int k) 
 // thread's entry e; entries with more than kBigEntry tiles are enumerated by
 // the whole warp (32 tiles at a time), so one large splat near the camera does
 // not leave a single thread looping over hundreds of tiles.
-template <typename F>
+template <bool kClaim = false, typename F>
 __device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
                                              const float4* __restrict__ rgbd, int64_t E, int64_t n,
                                              const Views& views, F f) {
@@ -127,8 +127,19 @@ __device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, co
         tx = views.v[v].tiles_x;
         if (rgbd != nullptr) zbits = __float_as_uint(rgbd[e].w);
     }
-    if (cnt > 0 && cnt <= (uint32_t)kBigEntry)
+    if constexpr (kClaim) {
+        // two phases for the scatter: all of this entry's slot claims (atomics) in
+        // flight together, then the writes
+        uint32_t pos[kBigEntry];
+#pragma unroll
+        for (int k = 0; k < kBigEntry; k++)
+            if (cnt <= (uint32_t)kBigEntry && k < (int)cnt) pos[k] = f.claim(covered_tile(r, tb, tx, k));
+#pragma unroll
+        for (int k = 0; k < kBigEntry; k++)
+            if (cnt <= (uint32_t)kBigEntry && k < (int)cnt) f.write(pos[k], (uint32_t)e, zbits);
+    } else if (cnt > 0 && cnt <= (uint32_t)kBigEntry) {
         for (int k = 0; k < (int)cnt; k++) f(covered_tile(r, tb, tx, k), (uint32_t)e, zbits);
+    }
     uint32_t big = __ballot_sync(0xffffffffu, cnt > (uint32_t)kBigEntry);
     while (big) {
         const int src = __ffs(big) - 1;
@@ -142,7 +153,10 @@ __device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, co
         const int btb = __shfl_sync(0xffffffffu, tb, src), btx = __shfl_sync(0xffffffffu, tx, src);
         const uint32_t bz = __shfl_sync(0xffffffffu, zbits, src);
         const uint32_t be = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)e, src);
-        for (int k = lane; k < bcnt; k += 32) f(covered_tile(br, btb, btx, k), be, bz);
+        for (int k = lane; k < bcnt; k += 32) {
+            if constexpr (kClaim) f.write(f.claim(covered_tile(br, btb, btx, k)), be, bz);
+            else f(covered_tile(br, btb, btx, k), be, bz);
+        }
     }
 }
 
@@ -239,11 +253,18 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const uint32_t* __r
                                                             uint32_t* __restrict__ stripes, int64_t capacity,
                                                             uint64_t* __restrict__ comp) {
     pdl_enter();
-    uint32_t* mine = stripes + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles;   // this lane's stripe
-    for_each_key(tt, rect, rgbd, E, n, views, [&](uint32_t g, uint32_t e, uint32_t zbits) {
-        const uint32_t pos = start[g] + atomicAdd(mine + g, 1u);
-        if ((int64_t)pos < capacity) comp[pos] = ((uint64_t)zbits << 32) | e;
-    });
+    struct Claim {
+        const uint32_t* start;
+        uint32_t* mine;          // this lane's stripe
+        int64_t capacity;
+        uint64_t* comp;
+        __device__ uint32_t claim(uint32_t g) const { return start[g] + atomicAdd(mine + g, 1u); }
+        __device__ void write(uint32_t pos, uint32_t e, uint32_t zbits) const {
+            if ((int64_t)pos < capacity) comp[pos] = ((uint64_t)zbits << 32) | e;
+        }
+    };
+    const Claim c{start, stripes + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles, capacity, comp};
+    for_each_key<true>(tt, rect, rgbd, E, n, views, c);
 }
 
 // Shared memory of k_tile_sort: the groups' keys, one large tile's keys, or the
@@ -361,9 +382,6 @@ __device__ __forceinline__ void group_sync(int g) {
 // first outputs come from the first run, then k sequential merge steps.  The
 // composites are unique (z bits, entry), so the order is the sorted one however
 // the work is split.  Returns the buffer that holds the result.
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
-
 template <int NT, typename Sync>
 __device__ __forceinline__ uint64_t* merge_sort_smem(uint64_t* s, uint64_t* t, int P, int tid, Sync sync) {
     const int lane = tid & 31, wid = tid >> 5;
@@ -375,7 +393,8 @@ __device__ __forceinline__ uint64_t* merge_sort_smem(uint64_t* s, uint64_t* t, i
             for (int j = k >> 1; j > 0; j >>= 1) {
                 const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
                 const bool up = (lane & k) == 0, lower = (lane & j) == 0;   // k = 32: ascending
-                x = (lower == up) ? umin64(x, y) : umax64(x, y);
+                // the lower lane of an ascending pair keeps the smaller key, and so on
+                x = ((x < y) == (lower == up)) ? x : y;
             }
         s[c * 32 + lane] = x;
     }
