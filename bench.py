@@ -277,14 +277,11 @@ def bwd_ctas_per_sm(step, tile) -> int:
 def launches_per_step(step) -> int:
     """Kernels of ours per iteration: project 1; bin/sort 6 (count zeroing, striped
     tile counts, stripe prefixes, tile offsets and work lists, scatter, per-tile
-    sort) + 1 for the block masks; render 1 (with the fused
-    loss); loss (unfused only): accumulator zeroing 1 + 2; backward: gradient
-    zeroing 1 + block order 1 (fused, few blocks per SM) + raster 1, pose/iso
-    zeroing 1 + projection backward 1; Adam 1."""
-    tile = step.params.tile
-    items = step.total_tiles * (tile // 8) * (tile // 4)
-    order = 1 if step.fused_loss and items <= 256 * 152 and items <= 65536 else 0   # k_item_order
-    return 1 + 6 + int(step.params.block_masks) + 1 + (0 if step.fused_loss else 3) + 4 + order + 1
+    sort) + 1 for the block masks; render 1 (with the fused loss); loss (unfused
+    only): accumulator zeroing 1 + 2; backward: gradient zeroing 1 (the block
+    order's launch when the fused backward orders its blocks, few blocks per SM)
+    + raster 1, pose/iso zeroing 1 + projection backward 1; Adam 1."""
+    return 1 + 6 + int(step.params.block_masks) + 1 + (0 if step.fused_loss else 3) + 4 + 1
 
 
 def raster_stages(step):

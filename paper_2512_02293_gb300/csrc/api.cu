@@ -242,10 +242,8 @@ int32_t gs_render_bwd_raster_loss(const gs_projected* proj, const gs_bins* bins,
     fl.color = img->color; fl.depth = img->depth;
     fl.lc = lambda_c; fl.ld = lambda_d;
     fused_loss_layout(const_cast<void*>(loss_ws), n_views, &fl);
-    cudaError_t e = launch_zero(grad2d, kGradStride * E, nullptr, 0, nullptr, 0, s);
-    if (e == cudaSuccess)
-        e = launch_render_bwd(*proj, *bins, *img, nullptr, nullptr, views, make_consts(params), grad2d, s, &fl);
-    return cuda_status(e);
+    return cuda_status(launch_render_bwd(*proj, *bins, *img, nullptr, nullptr, views, make_consts(params), grad2d,
+                                         kGradStride * E, s, &fl));
 }
 
 int32_t gs_loss(const gs_image* img, const float* target_color, const float* target_depth, const gs_camera* cams,
@@ -292,10 +290,8 @@ int32_t gs_render_bwd_raster(const gs_projected* proj, const gs_bins* bins, cons
     if (E >= (1ll << 31)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (E == 0) return GS_OK;
-    cudaError_t e = launch_zero(grad2d, kGradStride * E, nullptr, 0, nullptr, 0, s);
-    if (e == cudaSuccess)
-        e = launch_render_bwd(*proj, *bins, *img, dL_dcolor, dL_ddepth, views, make_consts(params), grad2d, s);
-    return cuda_status(e);
+    return cuda_status(launch_render_bwd(*proj, *bins, *img, dL_dcolor, dL_ddepth, views, make_consts(params),
+                                         grad2d, kGradStride * E, s));
 }
 
 int32_t gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, const gs_render_params* params,

@@ -122,9 +122,10 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
                               const FusedLoss* fl = nullptr);
 cudaError_t launch_loss(const gs_image& img, const float* tc, const float* td, const Views& views,
                         float lc, float ld, float* dc, float* dd, float* terms, void* ws, cudaStream_t s);
+// g2d_zero floats of g2d are zeroed first (the accumulators the backward adds into).
 cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img,
                               const float* dc, const float* dd, const Views& views, const RenderConsts& rc,
-                              float* g2d, cudaStream_t s, const FusedLoss* fl = nullptr);
+                              float* g2d, int64_t g2d_zero, cudaStream_t s, const FusedLoss* fl = nullptr);
 cudaError_t launch_project_bwd(const gs_gaussians& g, const Views& views, const RenderConsts& rc,
                                const float* g2d, float lambda_iso, const gs_grads& grads, float* iso_loss,
                                cudaStream_t s, const float* xi = nullptr);

@@ -830,10 +830,19 @@ constexpr int kOrderThreads = 1024;
 constexpr int kOrderBuckets = 2048;
 
 __global__ void __launch_bounds__(kOrderThreads) k_item_order(const uint32_t* __restrict__ cost,
-                                                              uint32_t* __restrict__ order, uint32_t* tag, int n) {
+                                                              uint32_t* __restrict__ order, uint32_t* tag, int n,
+                                                              float* __restrict__ zero, int64_t zero_n) {
     __shared__ uint32_t h[kOrderBuckets];
     __shared__ uint32_t s_warp[kOrderThreads / 32];
     pdl_enter();
+    if (blockIdx.x > 0) {            // the other CTAs zero the backward's 2D-gradient accumulators meanwhile
+        const int64_t stride = (int64_t)(gridDim.x - 1) * kOrderThreads;
+        const int64_t t0 = (int64_t)(blockIdx.x - 1) * kOrderThreads + threadIdx.x;
+        for (int64_t k = t0; k < zero_n / 4; k += stride)
+            reinterpret_cast<float4*>(zero)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t k = zero_n / 4 * 4 + t0; k < zero_n; k += stride) zero[k] = 0.f;
+        return;
+    }
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     auto bucket = [](uint32_t c) { return (uint32_t)(kOrderBuckets - 1) - min(c, (uint32_t)(kOrderBuckets - 1)); };
     for (int k = t; k < kOrderBuckets; k += kOrderThreads) h[k] = 0u;
@@ -966,9 +975,9 @@ cudaError_t launch_render_fwd(const gs_projected& pr, const gs_bins& bins, const
 }
 
 cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const gs_image& img, const float* dc,
-                              const float* dd, const Views& views, const RenderConsts& rc, float* g2d, cudaStream_t s,
-                              const FusedLoss* fl) {
-    if (views.total_tiles == 0) return cudaSuccess;
+                              const float* dd, const Views& views, const RenderConsts& rc, float* g2d,
+                              int64_t g2d_zero, cudaStream_t s, const FusedLoss* fl) {
+    if (views.total_tiles == 0) return launch_zero(g2d, g2d_zero, nullptr, 0, nullptr, 0, s);
     const float2* xy = reinterpret_cast<const float2*>(pr.xy);
     const float4* co = reinterpret_cast<const float4*>(pr.conic_o);
     const float4* cd = reinterpret_cast<const float4*>(pr.rgbd);
@@ -991,12 +1000,16 @@ cudaError_t launch_render_bwd(const gs_projected& pr, const gs_bins& bins, const
         const int n_items = views.total_tiles * TileShape<TT>::kWarps;                                \
         const bool few = n_items <= kFewItemsPerSm * sms;                                             \
         FusedLoss f = fl ? *fl : FusedLoss{};                                                          \
-        /* few items per SM: deepest blocks first (costs from the fused forward) */                    \
-        if (fl && few && n_items <= kOrderMaxItems)                                                    \
-            e = launch_pdl(k_item_order, 1, kOrderThreads, 0, s, (const uint32_t*)f.item_cost, f.order, \
-                           f.order_tag, n_items);                                                      \
-        else                                                                                           \
+        /* few items per SM: deepest blocks first (costs from the fused forward); the order's launch  \
+           zeroes the 2D gradients with its other CTAs, else a zero-fill launch does */                \
+        if (fl && few && n_items <= kOrderMaxItems) {                                                  \
+            const int64_t zb = ceil_div(g2d_zero / 4 + 1, (int64_t)kOrderThreads);                     \
+            e = launch_pdl(k_item_order, (unsigned)(1 + (zb < 2 * sms ? zb : 2 * sms)), kOrderThreads, 0, s, \
+                           (const uint32_t*)f.item_cost, f.order, f.order_tag, n_items, g2d, g2d_zero); \
+        } else {                                                                                       \
             f.order = nullptr;                                                                         \
+            e = launch_zero(g2d, g2d_zero, nullptr, 0, nullptr, 0, s);                                 \
+        }                                                                                              \
         if (e != cudaSuccess) return e;                                                                \
         if (few && fl)                                                                                 \
             e = GS_BWD_LAUNCH(TT, 2, true, f);                                                         \
