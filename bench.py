@@ -621,6 +621,7 @@ def window_run(device, args, flush, plain_rate, dist=None, world=1):
             "value": rate, "unit": "iters/s", "steps": steps, "ms_per_step": total_ms / steps,
             "views_per_s": rate * views, "views_per_s_vs_plain_iters_per_s": rate * views / plain_rate,
             "tile": params.tile, "splat_stages": params.splat_stages, "block_masks": params.block_masks,
+            "cull_tiles": params.cull_tiles,
             "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
             "pixels_per_iter": step.total_pixels, "pairs_per_iter": pairs, "keys_per_iter": step.num_keys(),
             "gpix_splats_per_s": pairs / (st[raster_stages(step)[0]] * 1e-3) / 1e9 if st else None,
@@ -1197,7 +1198,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": 1, "gaussians": g.n, "resolution": "640x480",
                        "tile": params.tile, "splat_stages": params.splat_stages,
-                       "block_masks": params.block_masks,
+                       "block_masks": params.block_masks, "cull_tiles": params.cull_tiles,
                        "autotune_ms": {str(k): round(v, 4) for k, v in step.tune.items()},
                        "lambdas": [mp.lambda_c, mp.lambda_d, mp.lambda_iso], "graph": True,
                        "l2": "flushed between timed iterations (256 MiB write, outside the step events)",

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define GS_ABI_VERSION 5
+#define GS_ABI_VERSION 6
 #define GS_MAX_VIEWS 32
 
 typedef enum gs_status {
@@ -94,6 +94,14 @@ typedef struct gs_render_params {
                                  rasterisers test.  The render calls must be given
                                  the value the gs_bin_sort call that made `bins` was
                                  given.  Results do not depend on it (1) */
+    int32_t cull_tiles;       /* 1: gs_bin_sort keeps only the (entry, tile) pairs
+                                 whose splat can reach 0.99 alpha_min somewhere in
+                                 the tile's box of pixel centres (the rasterisers'
+                                 culling test at tile granularity); 0: every tile of
+                                 the entry's rectangle.  Images, depth and T_final
+                                 do not depend on it; n_contrib counts list
+                                 positions, so it counts those of the shorter list
+                                 with 1 (the same last blended splat) */
 } gs_render_params;
 
 /* The Gaussian map G (Sec. 3.3 "Preliminary"), structure of arrays, device. */
@@ -215,9 +223,11 @@ int32_t gs_project_perturbed(const gs_gaussians* g, const gs_camera* cams, int32
  * (global tile << 32) | bits(float z) with value e per (entry e, covered tile),
  * in the order of a stable ascending sort of the entry-ordered list by key
  * (so within a tile by depth, ties in z by entry index), and [start, end) of
- * each tile in it.  Built without a global sort: per-tile counts, a prefix
- * over the tiles, a scatter of (bits(z), e) into each tile's segment, and a
- * sort of every segment (six launches).  Global tile of view v = tile_base(v) +
+ * each tile in it.  With params->cull_tiles the covered tiles are those of the
+ * rectangle that the splat can reach at 0.99 alpha_min (see gs_render_params).
+ * Built without a global sort: per-tile counts, a prefix over the tiles, a
+ * scatter of (bits(z), e) into each tile's segment, and a sort of every segment
+ * (six launches; a seventh writes the block masks).  Global tile of view v = tile_base(v) +
  * ty * tiles_x(v) + tx with tile_base(v) = tiles of views 0..v-1.  Writes M to
  * *bins->num_keys;
  * if M > key_capacity it sets *bins->status = GS_ERR_CAPACITY and the outputs

@@ -71,6 +71,7 @@ static bool params_ok(const gs_render_params* p) {
     if (p->sh_degree != 0 && p->sh_degree != 3) return false;
     if (p->splat_stages != 0 && p->splat_stages != 2 && p->splat_stages != 3) return false;
     if (p->block_masks != 0 && p->block_masks != 1) return false;
+    if (p->cull_tiles != 0 && p->cull_tiles != 1) return false;
     if (!(p->near_plane > 0.f) || !isfinite(p->near_plane)) return false;
     if (!(p->alpha_min >= 0.f) || !(p->alpha_max <= 1.f) || !(p->alpha_min <= p->alpha_max)) return false;
     if (!(p->T_cut >= 0.f) || !(p->T_cut < 1.f)) return false;
@@ -184,7 +185,8 @@ int32_t gs_bin_sort(const gs_projected* proj, int64_t n, const gs_camera* cams, 
     const size_t need = bin_sort_workspace(n * n_views, bins->key_capacity, views.total_tiles);
     if (ws == nullptr || ws_bytes < need || !aligned(ws, 256)) return GS_ERR_INVALID_ARG;
     SortPlan plan =
-        make_sort_plan(bins->key_capacity, views.total_tiles, params->tile, params->alpha_min, params->block_masks);
+        make_sort_plan(bins->key_capacity, views.total_tiles, params->tile, params->alpha_min, params->block_masks,
+                       params->cull_tiles);
     return cuda_status(launch_bin_sort(*proj, n, views, plan, *bins, ws, static_cast<cudaStream_t>(stream)));
 }
 

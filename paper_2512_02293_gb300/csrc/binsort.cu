@@ -106,39 +106,113 @@ __device__ __forceinline__ uint32_t covered_tile(int4 r, int tb, int tx, int k) 
     return (uint32_t)(tb + (r.y + k / w) * tx + r.x + k % w);
 }
 
+// The culling test of the rasterisers (0.99 alpha_min) at tile granularity, for
+// one entry: whether its splat can reach 0.99 alpha_min anywhere in a tile's box
+// of pixel centres.  For a negative-definite power the maximum over the box lies
+// on the two edges that face the mean (0 with the mean inside), each maximised at
+// its clamped stationary point, as for the block masks; it is compared with
+// log2(0.99 alpha_min / o) - 0.004 against rounding.  An opacity below 0.99
+// alpha_min reaches no tile; any other conic keeps every tile.
+struct TileCull {
+    float mx, my, qa, qb, qc, rx, ry, L;
+    int mode;                                  // 0: test, 1: every tile, 2: no tile
+};
+
+__device__ __forceinline__ TileCull tile_cull_of(const float2 m, const float4 c, float amin) {
+    TileCull t;
+    float4 q;
+    scale_conic(c.x, c.y, c.z, &q.x, &q.y, &q.z);
+    q.w = c.w;
+    const float thr = 0.99f * amin;
+    t.mx = m.x; t.my = m.y; t.qa = q.x; t.qb = q.y; t.qc = q.z;
+    t.rx = t.ry = t.L = 0.f;
+    if (q.w < thr) {
+        t.mode = 2;
+    } else if (!(q.x < 0.f && q.z < 0.f && 4.f * q.x * q.z - q.y * q.y > 0.f)) {
+        t.mode = 1;
+    } else {
+        t.mode = 0;
+        t.L = __log2f(__fdividef(thr, q.w)) - 0.004f;
+        t.rx = __fdividef(-q.y, 2.f * q.z);
+        t.ry = __fdividef(-q.y, 2.f * q.x);
+    }
+    return t;
+}
+
+// Tile (tx, ty) of T x T pixels of the entry's view.
+__device__ __forceinline__ bool tile_reached(const TileCull& t, int tx, int ty, int T) {
+    if (t.mode != 0) return t.mode == 1;
+    const float dx0 = (float)(tx * T) + 0.5f - t.mx, dx1 = dx0 + (float)(T - 1);
+    const float dy0 = (float)(ty * T) + 0.5f - t.my, dy1 = dy0 + (float)(T - 1);
+    const float vx = fminf(fmaxf(0.f, dx0), dx1), vy = fminf(fmaxf(0.f, dy0), dy1);
+    const float sy = fminf(fmaxf(t.rx * vx, dy0), dy1), sx = fminf(fmaxf(t.ry * vy, dx0), dx1);
+    const float pv = vx * fmaf(t.qa, vx, t.qb * sy) + t.qc * sy * sy;
+    const float ph = vy * fmaf(t.qc, vy, t.qb * sx) + t.qa * sx * sx;
+    return fmaxf(pv, ph) >= t.L;
+}
+
+// Operands of the tile culling (kCull): projected means and conics, tile size.
+struct CullArgs {
+    const float2* xy;
+    const float4* conic_o;
+    int T;
+    float amin;
+};
+
 // Calls f(tile, entry, z bits) once for every (entry, covered tile) pair of this
-// thread's entry e; entries with more than kBigEntry tiles are enumerated by
-// the whole warp (32 tiles at a time), so one large splat near the camera does
-// not leave a single thread looping over hundreds of tiles.
-template <bool kClaim = false, typename F>
+// thread's entry e (with kCull, only for the tiles the entry's splat can reach);
+// entries with more than kBigEntry tiles are enumerated by the whole warp (32
+// tiles at a time), so one large splat near the camera does not leave a single
+// thread looping over hundreds of tiles.  With kClaim, f has claim(tile) -> slot
+// and write(slot, entry, z bits), and a small entry's claims are all in flight
+// before its writes.  The count and the scatter take the same decisions: the
+// same function of the same operands.
+template <bool kClaim = false, bool kCull = false, typename F>
 __device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
                                              const float4* __restrict__ rgbd, int64_t E, int64_t n,
-                                             const Views& views, F f) {
+                                             const Views& views, const CullArgs& ca, F f) {
     const int lane = threadIdx.x & 31;
     const int64_t e = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
     const uint32_t cnt = e < E ? tt[e] : 0u;
     int4 r = make_int4(0, 0, 1, 1);
     int tb = 0, tx = 1;
     uint32_t zbits = 0;
+    TileCull tc{};
     if (cnt > 0) {
         const int v = (int)(e / n);
         r = rect[e];
         tb = views.v[v].tile_base;
         tx = views.v[v].tiles_x;
         if (rgbd != nullptr) zbits = __float_as_uint(rgbd[e].w);
+        if constexpr (kCull)
+            if (cnt <= (uint32_t)kBigEntry) tc = tile_cull_of(ca.xy[e], ca.conic_o[e], ca.amin);
     }
+    auto keep = [&](const TileCull& t, const int4& rr, int k) -> bool {
+        if constexpr (kCull) {
+            const int w = rr.z - rr.x;
+            return tile_reached(t, rr.x + k % w, rr.y + k / w, ca.T);
+        } else {
+            return true;
+        }
+    };
+    const bool small = cnt > 0 && cnt <= (uint32_t)kBigEntry;
     if constexpr (kClaim) {
         // two phases for the scatter: all of this entry's slot claims (atomics) in
         // flight together, then the writes
         uint32_t pos[kBigEntry];
+        uint32_t claimed = 0;
 #pragma unroll
         for (int k = 0; k < kBigEntry; k++)
-            if (cnt <= (uint32_t)kBigEntry && k < (int)cnt) pos[k] = f.claim(covered_tile(r, tb, tx, k));
+            if (small && k < (int)cnt && keep(tc, r, k)) {
+                pos[k] = f.claim(covered_tile(r, tb, tx, k));
+                claimed |= 1u << k;
+            }
 #pragma unroll
         for (int k = 0; k < kBigEntry; k++)
-            if (cnt <= (uint32_t)kBigEntry && k < (int)cnt) f.write(pos[k], (uint32_t)e, zbits);
-    } else if (cnt > 0 && cnt <= (uint32_t)kBigEntry) {
-        for (int k = 0; k < (int)cnt; k++) f(covered_tile(r, tb, tx, k), (uint32_t)e, zbits);
+            if ((claimed >> k) & 1u) f.write(pos[k], (uint32_t)e, zbits);
+    } else if (small) {
+        for (int k = 0; k < (int)cnt; k++)
+            if (keep(tc, r, k)) f(covered_tile(r, tb, tx, k), (uint32_t)e, zbits);
     }
     uint32_t big = __ballot_sync(0xffffffffu, cnt > (uint32_t)kBigEntry);
     while (big) {
@@ -153,19 +227,24 @@ __device__ __forceinline__ void for_each_key(const uint32_t* __restrict__ tt, co
         const int btb = __shfl_sync(0xffffffffu, tb, src), btx = __shfl_sync(0xffffffffu, tx, src);
         const uint32_t bz = __shfl_sync(0xffffffffu, zbits, src);
         const uint32_t be = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)e, src);
+        TileCull btc{};
+        if constexpr (kCull) btc = tile_cull_of(ca.xy[be], ca.conic_o[be], ca.amin);   // the same on every lane
         for (int k = lane; k < bcnt; k += 32) {
+            if (!keep(btc, br, k)) continue;
             if constexpr (kClaim) f.write(f.claim(covered_tile(br, btb, btx, k)), be, bz);
             else f(covered_tile(br, btb, btx, k), be, bz);
         }
     }
 }
 
+template <bool kCull>
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint32_t* __restrict__ tt, const int4* __restrict__ rect,
                                                           int64_t E, int64_t n, Views views,
-                                                          uint32_t* __restrict__ cnt) {
+                                                          uint32_t* __restrict__ cnt, CullArgs ca) {
     pdl_enter();
     uint32_t* mine = cnt + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles;     // this lane's stripe
-    for_each_key(tt, rect, nullptr, E, n, views, [&](uint32_t g, uint32_t, uint32_t) { atomicAdd(mine + g, 1u); });
+    for_each_key<false, kCull>(tt, rect, nullptr, E, n, views, ca,
+                               [&](uint32_t g, uint32_t, uint32_t) { atomicAdd(mine + g, 1u); });
 }
 
 // Per tile (one warp, lane = stripe): each stripe counter becomes the exclusive
@@ -246,12 +325,13 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_offsets(uint32_t* __restri
     }
 }
 
+template <bool kCull>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const uint32_t* __restrict__ tt,
                                                             const int4* __restrict__ rect,
                                                             const float4* __restrict__ rgbd, int64_t E, int64_t n,
                                                             Views views, const uint32_t* __restrict__ start,
                                                             uint32_t* __restrict__ stripes, int64_t capacity,
-                                                            uint64_t* __restrict__ comp) {
+                                                            uint64_t* __restrict__ comp, CullArgs ca) {
     pdl_enter();
     struct Claim {
         const uint32_t* start;
@@ -264,7 +344,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const uint32_t* __r
         }
     };
     const Claim c{start, stripes + (size_t)(threadIdx.x & 31) * (size_t)views.total_tiles, capacity, comp};
-    for_each_key<true>(tt, rect, rgbd, E, n, views, c);
+    for_each_key<true, kCull>(tt, rect, rgbd, E, n, views, ca, c);
 }
 
 // Shared memory of k_tile_sort: the groups' keys, one large tile's keys, or the
@@ -549,13 +629,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_masks(const uint64_t* __res
 }  // namespace
 
 SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles, int32_t tile, float alpha_min,
-                        int32_t block_masks) {
+                        int32_t block_masks, int32_t cull_tiles) {
     SortPlan p;
     p.capacity = key_capacity;
     p.total_tiles = total_tiles;
     p.tile = tile;
     p.alpha_min = alpha_min;
     p.block_masks = block_masks;
+    p.cull_tiles = cull_tiles;
     return p;
 }
 
@@ -607,8 +688,11 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
     const int64_t words = (int64_t)kStripes * T;
     const int nb_zero = (int)(ceil_div(words, kBinThreads) < 4096 ? ceil_div(words, kBinThreads) : 4096);
     err = launch_pdl(k_bin_zero, nb_zero, kBinThreads, 0, s, stripes, words, sort_ctrs);
+    const CullArgs ca{reinterpret_cast<const float2*>(pr.xy), reinterpret_cast<const float4*>(pr.conic_o), plan.tile,
+                      plan.alpha_min};
     if (err == cudaSuccess)
-        err = launch_pdl(k_bin_count, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, E, n, views, stripes);
+        err = launch_pdl(plan.cull_tiles ? k_bin_count<true> : k_bin_count<false>, nb_entries, kBinThreads, 0, s,
+                         pr.tiles_touched, rect, E, n, views, stripes, ca);
     if (err == cudaSuccess)
         err = launch_pdl(k_bin_stripes, (int)ceil_div((int64_t)T * 32, kBinThreads), kBinThreads, 0, s, stripes, T,
                          totals);
@@ -616,8 +700,8 @@ cudaError_t launch_bin_sort(const gs_projected& pr, int64_t n, const Views& view
         err = launch_pdl(k_bin_offsets, 1, kScanThreads, 0, s, totals, T, reinterpret_cast<uint2*>(bins.ranges),
                          bins.num_keys, cap, bins.status, big_list, small_list, sort_ctrs);
     if (err == cudaSuccess)
-        err = launch_pdl(k_bin_scatter, nb_entries, kBinThreads, 0, s, pr.tiles_touched, rect, rgbd, E, n, views,
-                         totals, stripes, cap, bins.keys);
+        err = launch_pdl(plan.cull_tiles ? k_bin_scatter<true> : k_bin_scatter<false>, nb_entries, kBinThreads, 0,
+                         s, pr.tiles_touched, rect, rgbd, E, n, views, totals, stripes, cap, bins.keys, ca);
     if (err == cudaSuccess) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);

@@ -49,9 +49,10 @@ struct SortPlan {
     int32_t tile;          // tile size (the block masks)
     float alpha_min;       // the rasterisers' culling threshold (the block masks)
     int32_t block_masks;   // write gs_bins.masks
+    int32_t cull_tiles;    // keep only the (entry, tile) pairs whose splat can reach 0.99 alpha_min in the tile
 };
 SortPlan make_sort_plan(int64_t key_capacity, int32_t total_tiles, int32_t tile, float alpha_min,
-                        int32_t block_masks);
+                        int32_t block_masks, int32_t cull_tiles);
 size_t bin_sort_workspace(int64_t n_entries, int64_t capacity, int32_t total_tiles);
 
 constexpr int kGradStride = 12;                  // floats per entry of the 2D-gradient scratch

@@ -47,7 +47,7 @@ class gs_render_params(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("near_plane", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_cut", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("radius_sigma", ctypes.c_float), ("bg", ctypes.c_float * 3), ("sh_degree", ctypes.c_int32),
-                ("splat_stages", ctypes.c_int32), ("block_masks", ctypes.c_int32)]
+                ("splat_stages", ctypes.c_int32), ("block_masks", ctypes.c_int32), ("cull_tiles", ctypes.c_int32)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -205,7 +205,7 @@ def load_library(path: str | None = None):
     lib.gs_project_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, V]
     lib.gs_project_bwd_perturbed.restype = ctypes.c_int32
     lib.gs_project_bwd_perturbed.argtypes = [V, V, ctypes.c_int32, V, V, V, ctypes.c_float, V, V, V]
-    if lib.gs_abi_version() != 5:
+    if lib.gs_abi_version() != 6:
         raise RuntimeError("libgs ABI version mismatch")
     if path is None:
         _lib = lib
@@ -227,11 +227,13 @@ class RenderParams:
     sh_degree: int = 0
     splat_stages: int = 0      # 0: the library chooses; 2 or 3 batches of 32 splats per forward warp
     block_masks: int = 1       # 1: binning writes per-key pixel-block masks the rasterisers read
+    cull_tiles: int = 0        # 1: binning drops the tiles a splat cannot reach at 0.99 alpha_min
 
     def struct(self) -> gs_render_params:
         return gs_render_params(int(self.tile), self.near_plane, self.alpha_min, self.alpha_max, self.T_cut,
                                 self.dilation, self.radius_sigma, (ctypes.c_float * 3)(*self.bg),
-                                int(self.sh_degree), int(self.splat_stages), int(self.block_masks))
+                                int(self.sh_degree), int(self.splat_stages), int(self.block_masks),
+                                int(self.cull_tiles))
 
 
 def camera_array(cams) -> ctypes.Array:

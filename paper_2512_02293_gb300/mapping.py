@@ -284,16 +284,17 @@ def autotune_tile(gaussians: G.Gaussians, cams, target_color, target_depth, para
                   masks=(1, 0)):
     """Pick the tile size, the forward rasteriser's splat staging (batches of
     32 splats a warp holds at once: 2 or 3) and whether the binning writes the
-    pixel-block masks the rasterisers read (1) or they test every list entry
-    (0), by the fastest graph-replayed mapping iteration for this map and these
-    views.  Every trial starts from the same map and the map is restored
+    pixel-block masks the rasterisers read and drops the tiles a splat cannot
+    reach (1) or keeps every tile of the rectangle and the rasterisers test
+    every list entry (0), by the fastest graph-replayed mapping iteration for
+    this map and these views.  Every trial starts from the same map and the map is restored
     afterwards.  Returns (best RenderParams, {"tile/stages/masks": ms})."""
     import dataclasses
     base = params or G.RenderParams()
     saved = [t.clone() for t in gaussians.tensors()]
     times = {}
     for tile, st, bm in [(t, s, m) for t in candidates for s in stages for m in masks]:
-        p = dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm)
+        p = dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm, cull_tiles=bm)
         step = MappingStep(gaussians, cams, target_color, target_depth, p, mparams)
         step.step()
         step.ensure_capacity()
@@ -315,4 +316,4 @@ def autotune_tile(gaussians: G.Gaussians, cams, target_color, target_depth, para
         t.copy_(s0)
     best = min(times, key=times.get)
     tile, st, bm = (int(x) for x in best.split("/"))
-    return dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm), times
+    return dataclasses.replace(base, tile=tile, splat_stages=st, block_masks=bm, cull_tiles=bm), times

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.gs_abi_version() == 5
+    assert lib.gs_abi_version() == 6
     assert lib.gs_status_string(0) == b"GS_OK"
     assert lib.gs_status_string(2) == b"GS_ERR_CAPACITY"
     assert lib.gs_status_string(99) == b"GS_ERR_UNKNOWN"
@@ -44,7 +44,7 @@ def test_abi_version_and_status_strings(lib):
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(G.gs_camera) == 4 * 4 + 2 * 4 + 9 * 4 + 3 * 4
-    assert ctypes.sizeof(G.gs_render_params) == 4 * 13
+    assert ctypes.sizeof(G.gs_render_params) == 4 * 14
     assert ctypes.sizeof(G.gs_gaussians) == 6 * 8
     assert ctypes.sizeof(G.gs_bins) == 7 * 8
     assert ctypes.sizeof(G.gs_adam_group) == 4 * 8 + 8 + 8
@@ -224,3 +224,13 @@ def test_block_masks_parameter_is_checked(lib):
     for bm, want in ((0, 0), (1, 0), (2, 1), (-1, 1)):
         p = G.RenderParams(block_masks=bm).struct()
         assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == want, bm
+
+
+def test_cull_tiles_parameter_is_checked(lib):
+    # 1 (binning drops the tiles a splat cannot reach at 0.99 alpha_min) or 0 (every tile of the rectangle)
+    cams = G.camera_array([synth.identity_camera()])
+    g0 = G.gs_gaussians(None, None, None, None, None, 0)
+    out = G.gs_projected()
+    for ct, want in ((0, 0), (1, 0), (2, 1), (-1, 1)):
+        p = G.RenderParams(cull_tiles=ct).struct()
+        assert lib.gs_project(ctypes.byref(g0), cams, 1, ctypes.byref(p), ctypes.byref(out), None) == want, ct
