@@ -71,26 +71,26 @@ ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # (their full-section captures).  None where the kernel changed after the
 # capture.
 # Keyed by (stage, tile, ring, block_masks) for the forward (its staging variant)
-# and (stage, tile, None, block_masks) for the others.
-PROFILED_TRAFFIC = {("gs_project", 16, None, 0): 11.30e6, ("gs_bin_sort", 16, None, 0): 14.50e6,
-                    ("gs_render_fwd_loss", 16, False, 0): 14.25e6,
+# and (stage, tile, None, block_masks) for the others; block_masks 1 is the
+# build with the masks and the tile culling the autotuner pairs with them.
+PROFILED_TRAFFIC = {("gs_project", 16, None, 0): 11.30e6, ("gs_render_fwd_loss", 16, False, 0): 14.25e6,
                     ("gs_project_bwd", 16, None, 0): 16.41e6, ("gs_adam_step", 16, None, 0): 44.83e6,
-                    ("gs_project", 16, None, 1): 11.28e6, ("gs_bin_sort", 16, None, 1): 23.69e6,
-                    ("gs_render_fwd_loss", 16, False, 1): 15.58e6,
-                    ("gs_render_bwd_raster_loss", 16, None, 1): 28.52e6, ("gs_project_bwd", 16, None, 1): 16.41e6,
+                    ("gs_project", 16, None, 1): 11.29e6, ("gs_bin_sort", 16, None, 1): 30.52e6,
+                    ("gs_render_fwd_loss", 16, False, 1): 14.56e6,
+                    ("gs_render_bwd_raster_loss", 16, None, 1): 27.58e6, ("gs_project_bwd", 16, None, 1): 16.42e6,
                     ("gs_adam_step", 16, None, 1): 44.82e6}
 # L2 bytes (lts__t_bytes.sum) per launch of the binning stage's kernels, from
 # the same kind of capture.
-PROFILED_L2 = {("gs_bin_sort", 16, 0): 90.2e6, ("gs_bin_sort", 16, 1): 131.1e6}
+PROFILED_L2 = {("gs_bin_sort", 16, 1): 114.6e6}
 PROFILED_PIPE = {
     ("gs_render_fwd_loss", 16, False, 0): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
                                           "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
                                           "XU (ex2) 9.4 %",
-    ("gs_render_fwd_loss", 16, False, 1): "the deepest blocks' serial walks, then instruction issue: SMs active 65.3 % "
-                                          "of the launch, 63.3 % of active cycles issue; pipes ALU 44.9 %, LSU 27.5 %, "
-                                          "FMA 21.1 %, XU (ex2) 6.2 %",
-    ("gs_render_bwd_raster_loss", 16, None, 1): "instruction issue: 69.8 % of active cycles issue; pipes LSU 45.1 %, "
-                                                "ALU 44.3 %, FMA 29.2 %, XU (ex2, rcp) 5.5 %; SMs active 94 % of the "
+    ("gs_render_fwd_loss", 16, False, 1): "the deepest blocks' serial walks, then instruction issue: SMs active 67.8 % "
+                                          "of the launch, 65.0 % of active cycles issue; pipes ALU 46.0 %, LSU 28.0 %, "
+                                          "FMA 22.4 %, XU (ex2) 6.8 %",
+    ("gs_render_bwd_raster_loss", 16, None, 1): "instruction issue: 70.6 % of active cycles issue; pipes LSU 45.2 %, "
+                                                "ALU 44.9 %, FMA 29.8 %, XU (ex2, rcp) 5.5 %; SMs active 93 % of the "
                                                 "launch"}
 
 
