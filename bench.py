@@ -213,7 +213,7 @@ def timed_run(step, steps, warmup, flush, dist=None, clock_index=None):
     if step.ensure_capacity():
         step.step()
         assert not step.ensure_capacity()
-    pairs = int(step.img.n_contrib.to(torch.int64).sum().item())
+    pairs = plain_visited_pairs(step)
     evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(step.stages) + 1)]
     staged_graph = step.capture(warmup=1, events=evs)
     step.capture(warmup=0)                          # the plain graph, replayed by step()
@@ -367,6 +367,27 @@ def measure_l2_peak(device, total_gib=2.0):
                     "method": f"gs_l2_read_probe: one launch reading an L2-resident buffer over and over (about "
                               f"{total_gib:g} GiB), best of 8 / 16 / 32 / 48 / 64 / 96 MiB buffers"})
     return L2_PEAK
+
+
+def plain_visited_pairs(step) -> int:
+    """Sum of n_contrib over the step's views on the plain lists (every tile of
+    each rectangle): the method's count of visited (pixel, splat) pairs.  With
+    tile culling the step's own n_contrib counts positions in the shorter lists,
+    so one uncaptured render without it gives the count (the image is the same)."""
+    import dataclasses
+    import torch
+    from paper_2512_02293_gb300.mapping import MappingStep
+    if not step.params.cull_tiles:
+        return int(step.img.n_contrib.to(torch.int64).sum().item())
+    plain = MappingStep(step.g, step.cams, step.target_color, step.target_depth,
+                        dataclasses.replace(step.params, cull_tiles=0), step.mp, fused_loss=step.fused_loss)
+    plain.render()
+    if plain.ensure_capacity():
+        plain.render()
+    n = int(plain.img.n_contrib.to(torch.int64).sum().item())
+    del plain
+    torch.cuda.empty_cache()
+    return n
 
 
 def evaluated_pairs(step, alpha_min=None) -> int:
