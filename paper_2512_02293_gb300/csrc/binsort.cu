@@ -112,7 +112,9 @@ __device__ __forceinline__ uint32_t covered_tile(int4 r, int tb, int tx, int k) 
 // on the two edges that face the mean (0 with the mean inside), each maximised at
 // its clamped stationary point, as for the block masks; it is compared with
 // log2(0.99 alpha_min / o) - 0.004 against rounding.  An opacity below 0.99
-// alpha_min reaches no tile; any other conic keeps every tile.
+// alpha_min reaches no tile; any other conic keeps every tile.  Every rounding
+// step is an explicit intrinsic, so that the count and the scatter, which both
+// evaluate the test, take the same decisions whatever the compiler contracts.
 struct TileCull {
     float mx, my, qa, qb, qc, rx, ry, L;
     int mode;                                  // 0: test, 1: every tile, 2: no tile
@@ -123,18 +125,18 @@ __device__ __forceinline__ TileCull tile_cull_of(const float2 m, const float4 c,
     float4 q;
     scale_conic(c.x, c.y, c.z, &q.x, &q.y, &q.z);
     q.w = c.w;
-    const float thr = 0.99f * amin;
+    const float thr = __fmul_rn(0.99f, amin);
     t.mx = m.x; t.my = m.y; t.qa = q.x; t.qb = q.y; t.qc = q.z;
     t.rx = t.ry = t.L = 0.f;
     if (q.w < thr) {
         t.mode = 2;
-    } else if (!(q.x < 0.f && q.z < 0.f && 4.f * q.x * q.z - q.y * q.y > 0.f)) {
+    } else if (!(q.x < 0.f && q.z < 0.f && __fsub_rn(__fmul_rn(__fmul_rn(4.f, q.x), q.z), __fmul_rn(q.y, q.y)) > 0.f)) {
         t.mode = 1;
     } else {
         t.mode = 0;
-        t.L = __log2f(__fdividef(thr, q.w)) - 0.004f;
-        t.rx = __fdividef(-q.y, 2.f * q.z);
-        t.ry = __fdividef(-q.y, 2.f * q.x);
+        t.L = __fsub_rn(__log2f(__fdividef(thr, q.w)), 0.004f);
+        t.rx = __fdividef(-q.y, __fmul_rn(2.f, q.z));
+        t.ry = __fdividef(-q.y, __fmul_rn(2.f, q.x));
     }
     return t;
 }
@@ -142,12 +144,12 @@ __device__ __forceinline__ TileCull tile_cull_of(const float2 m, const float4 c,
 // Tile (tx, ty) of T x T pixels of the entry's view.
 __device__ __forceinline__ bool tile_reached(const TileCull& t, int tx, int ty, int T) {
     if (t.mode != 0) return t.mode == 1;
-    const float dx0 = (float)(tx * T) + 0.5f - t.mx, dx1 = dx0 + (float)(T - 1);
-    const float dy0 = (float)(ty * T) + 0.5f - t.my, dy1 = dy0 + (float)(T - 1);
+    const float dx0 = __fsub_rn(__fadd_rn((float)(tx * T), 0.5f), t.mx), dx1 = __fadd_rn(dx0, (float)(T - 1));
+    const float dy0 = __fsub_rn(__fadd_rn((float)(ty * T), 0.5f), t.my), dy1 = __fadd_rn(dy0, (float)(T - 1));
     const float vx = fminf(fmaxf(0.f, dx0), dx1), vy = fminf(fmaxf(0.f, dy0), dy1);
-    const float sy = fminf(fmaxf(t.rx * vx, dy0), dy1), sx = fminf(fmaxf(t.ry * vy, dx0), dx1);
-    const float pv = vx * fmaf(t.qa, vx, t.qb * sy) + t.qc * sy * sy;
-    const float ph = vy * fmaf(t.qc, vy, t.qb * sx) + t.qa * sx * sx;
+    const float sy = fminf(fmaxf(__fmul_rn(t.rx, vx), dy0), dy1), sx = fminf(fmaxf(__fmul_rn(t.ry, vy), dx0), dx1);
+    const float pv = __fmaf_rn(vx, __fmaf_rn(t.qa, vx, __fmul_rn(t.qb, sy)), __fmul_rn(__fmul_rn(t.qc, sy), sy));
+    const float ph = __fmaf_rn(vy, __fmaf_rn(t.qc, vy, __fmul_rn(t.qb, sx)), __fmul_rn(__fmul_rn(t.qa, sx), sx));
     return fmaxf(pv, ph) >= t.L;
 }
 
