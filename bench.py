@@ -75,13 +75,13 @@ ADAM_BYTES_PER_ELEMENT, ADAM_ELEMENTS_PER_GAUSSIAN = 28, 14
 # build with the masks and the tile culling the autotuner pairs with them.
 PROFILED_TRAFFIC = {("gs_project", 16, None, 0): 11.30e6, ("gs_render_fwd_loss", 16, False, 0): 14.25e6,
                     ("gs_project_bwd", 16, None, 0): 16.41e6, ("gs_adam_step", 16, None, 0): 44.83e6,
-                    ("gs_project", 16, None, 1): 11.29e6, ("gs_bin_sort", 16, None, 1): 30.52e6,
-                    ("gs_render_fwd_loss", 16, False, 1): 14.56e6,
-                    ("gs_render_bwd_raster_loss", 16, None, 1): 27.58e6, ("gs_project_bwd", 16, None, 1): 16.42e6,
+                    ("gs_project", 16, None, 1): 11.28e6, ("gs_bin_sort", 16, None, 1): 30.65e6,
+                    ("gs_render_fwd_loss", 16, False, 1): 14.61e6,
+                    ("gs_render_bwd_raster_loss", 16, None, 1): 27.59e6, ("gs_project_bwd", 16, None, 1): 16.42e6,
                     ("gs_adam_step", 16, None, 1): 44.82e6}
 # L2 bytes (lts__t_bytes.sum) per launch of the binning stage's kernels, from
 # the same kind of capture.
-PROFILED_L2 = {("gs_bin_sort", 16, 1): 114.6e6}
+PROFILED_L2 = {("gs_bin_sort", 16, 1): 115.1e6}
 PROFILED_PIPE = {
     ("gs_render_fwd_loss", 16, False, 0): "the deepest blocks' serial walks, then instruction issue: SMs active 64.5 % "
                                           "of the launch, 62.7 % of active cycles issue; pipes ALU 38.3 %, FMA 28.1 %, "
